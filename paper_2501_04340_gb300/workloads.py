@@ -1,0 +1,367 @@
+"""Seeded synthetic multipatch problems (input generation only).
+
+This module builds the *inputs* of the method: patch layouts, glued control nets,
+per-patch reluctivities, subdomain partitions of the patch dual graph and source
+parameters. It holds none of the method's arithmetic (no basis functions, no
+quadrature, no gauge, no solver) and is the only module shared by the CUDA path
+and by the oracle.
+
+Problem shape (Sec. 2, patches / patch-facets / subdomains):
+  * a structured block grid of P0 x P1 x P2 patches, each the image of (0,1)^3
+    under a B-spline/NURBS map of degree p with an open uniform knot vector;
+    patch slab ``a`` in direction d has ``nspan[d][a]`` knot spans, so
+    neighbouring patches share full facets (conforming patch interfaces);
+  * consecutive patches share the control points of their common facet, so the
+    whole domain has one glued control net with N_d = sum_a (n_a + p - 1) + 1
+    points in direction d (N_0 = sum_a (n_a + p - 1) when direction 0 is periodic);
+  * the control net is stored as ``ctrl[k, j, i, :] = (x, y, z, w)``;
+  * patch (a, b, c) has flat index a + P0 * (b + P1 * c);
+  * ``sub_of_patch`` groups patches into connected subdomains (Sec. 2).
+
+Source kinds (right-hand side j of Eq. (3), one column per load case):
+  * SOURCE_SINE: J = s * 2 pi^2 (sin(pi y) sin(pi z), sin(pi x) sin(pi z),
+    sin(pi x) sin(pi y)), params = the amplitudes s, one per load case. With
+    nu = 1 this is curl curl A for A = J / (2 pi^2), which has n x A = 0 on the
+    unit cube's boundary.
+  * SOURCE_FOURIER: J = sum_m Re(c_m exp(2 pi i k_m . x)); params per load case:
+    nmodes, then for each mode k (3 values) and Re c (3), Im c (3).
+  * SOURCE_PATCHWISE: J constant on each patch; params = nrhs x npatch x 3.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Sequence, Tuple
+
+import numpy as np
+
+SOURCE_SINE = 0
+SOURCE_FOURIER = 1
+SOURCE_PATCHWISE = 2
+
+
+@dataclasses.dataclass
+class Problem:
+    name: str
+    p: int
+    npatch: Tuple[int, int, int]
+    nspan: List[List[int]]
+    periodic0: bool
+    ctrl: np.ndarray            # (N2, N1, N0, 4) float64
+    nu: np.ndarray              # (npatch_total,) float64
+    sub_of_patch: np.ndarray    # (npatch_total,) int32
+    source_kind: int
+    source_params: np.ndarray   # float64, layout per kind (module docstring)
+    nrhs: int
+
+    @property
+    def npatch_total(self) -> int:
+        return int(self.npatch[0] * self.npatch[1] * self.npatch[2])
+
+    @property
+    def nsub(self) -> int:
+        return int(self.sub_of_patch.max()) + 1
+
+    def grid_shape(self) -> Tuple[int, int, int]:
+        """Control points per direction of the glued net (N0, N1, N2)."""
+        out = []
+        for d in range(3):
+            n = sum(s + self.p - 1 for s in self.nspan[d])
+            if not (d == 0 and self.periodic0):
+                n += 1
+            out.append(n)
+        return tuple(out)
+
+    def with_params(self, nu=None, source_params=None, nrhs=None) -> "Problem":
+        return dataclasses.replace(
+            self,
+            nu=self.nu if nu is None else np.asarray(nu, np.float64),
+            source_params=self.source_params if source_params is None
+            else np.asarray(source_params, np.float64),
+            nrhs=self.nrhs if nrhs is None else int(nrhs))
+
+
+# ----------------------------------------------------------------------------
+# geometry helpers (control nets)
+# ----------------------------------------------------------------------------
+
+def _greville_1d(p: int, nspan: int) -> np.ndarray:
+    """Greville abscissae of the open uniform knot vector of degree p with
+    ``nspan`` spans on [0, 1]; control points placed there give the identity map."""
+    inner = [i / nspan for i in range(1, nspan)]
+    t = [0.0] * (p + 1) + inner + [1.0] * (p + 1)
+    n = nspan + p
+    return np.array([sum(t[i + 1:i + p + 1]) / p for i in range(n)])
+
+
+def _glued_coords_1d(p: int, spans: Sequence[int], breaks: Sequence[float]) -> np.ndarray:
+    pts = []
+    for a, s in enumerate(spans):
+        g = breaks[a] + (breaks[a + 1] - breaks[a]) * _greville_1d(p, s)
+        pts.extend(g if a == 0 else g[1:])
+    return np.array(pts)
+
+
+def box_control_net(p: int, nspan: List[List[int]], breaks: List[Sequence[float]]) -> np.ndarray:
+    """Affine box patches: tensor product of 1D Greville coordinates, weights 1."""
+    xs = [_glued_coords_1d(p, nspan[d], breaks[d]) for d in range(3)]
+    z, y, x = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
+    return np.stack([x, y, z, np.ones_like(x)], axis=-1)
+
+
+# ----------------------------------------------------------------------------
+# partitions of the patch dual graph
+# ----------------------------------------------------------------------------
+
+def block_partition(npatch: Tuple[int, int, int], block: Tuple[int, int, int]) -> np.ndarray:
+    """Subdomains = aligned blocks of patches (recursive coordinate bisection of a
+    power-of-two patch grid gives exactly these blocks)."""
+    P0, P1, P2 = npatch
+    B0, B1, B2 = block
+    n0, n1 = P0 // B0, P1 // B1
+    sub = np.empty(P0 * P1 * P2, np.int32)
+    for c in range(P2):
+        for b in range(P1):
+            for a in range(P0):
+                sub[a + P0 * (b + P1 * c)] = (a // B0) + n0 * ((b // B1) + n1 * (c // B2))
+    return sub
+
+
+def _patch_neighbours(npatch, q):
+    P0, P1, P2 = npatch
+    a, r = q % P0, q // P0
+    b, c = r % P1, r // P1
+    out = []
+    for d, (x, lim) in enumerate(((a, P0), (b, P1), (c, P2))):
+        for s in (-1, 1):
+            y = x + s
+            if 0 <= y < lim:
+                abc = [a, b, c]
+                abc[d] = y
+                out.append(abc[0] + P0 * (abc[1] + P1 * abc[2]))
+    return out
+
+
+def _euler_char_of_patch_union(npatch, members) -> int:
+    """Euler characteristic V - E + F - C of the union of closed unit cubes
+    (patches) in the patch block grid; 1 for a contractible union."""
+    P0, P1, P2 = npatch
+    cubes = set()
+    for q in members:
+        a, r = q % P0, q // P0
+        cubes.add((a, r % P1, r // P1))
+    verts, edges, faces = set(), set(), set()
+    for (a, b, c) in cubes:
+        for dx in (0, 1):
+            for dy in (0, 1):
+                for dz in (0, 1):
+                    verts.add((a + dx, b + dy, c + dz))
+        for d in range(3):
+            for o1 in (0, 1):
+                for o2 in (0, 1):
+                    base = [a, b, c]
+                    others = [e for e in range(3) if e != d]
+                    base[others[0]] += o1
+                    base[others[1]] += o2
+                    edges.add((d, tuple(base)))
+            for o in (0, 1):
+                base = [a, b, c]
+                base[d] += o
+                faces.add((d, tuple(base)))
+    return len(verts) - len(edges) + len(faces) - len(cubes)
+
+
+def _complement_connected(npatch, members) -> bool:
+    """True if the patches NOT in ``members`` plus the outside form a connected
+    set (no enclosed cavity)."""
+    P0, P1, P2 = npatch
+    mem = set(members)
+    # pad the grid by one layer representing the outside
+    seen = set()
+    start = (-1, -1, -1)
+    stack = [start]
+    seen.add(start)
+    while stack:
+        a, b, c = stack.pop()
+        for d in range(3):
+            for s in (-1, 1):
+                n = [a, b, c]
+                n[d] += s
+                if not (-1 <= n[0] <= P0 and -1 <= n[1] <= P1 and -1 <= n[2] <= P2):
+                    continue
+                t = tuple(n)
+                if t in seen:
+                    continue
+                inside = 0 <= t[0] < P0 and 0 <= t[1] < P1 and 0 <= t[2] < P2
+                if inside and (t[0] + P0 * (t[1] + P1 * t[2])) in mem:
+                    continue
+                seen.add(t)
+                stack.append(t)
+    n_out = sum(1 for t in seen if 0 <= t[0] < P0 and 0 <= t[1] < P1 and 0 <= t[2] < P2)
+    return n_out == P0 * P1 * P2 - len(mem)
+
+
+def is_simply_connected_union(npatch, members) -> bool:
+    """Connected, Euler characteristic 1 and connected complement (no cavity):
+    for unions of grid cubes this characterises a contractible set."""
+    members = list(members)
+    if not members:
+        return False
+    mem = set(members)
+    seen = {members[0]}
+    stack = [members[0]]
+    while stack:
+        q = stack.pop()
+        for n in _patch_neighbours(npatch, q):
+            if n in mem and n not in seen:
+                seen.add(n)
+                stack.append(n)
+    if len(seen) != len(mem):
+        return False
+    return _euler_char_of_patch_union(npatch, members) == 1 and _complement_connected(npatch, members)
+
+
+def greedy_partition(npatch, sizes_lo: int, sizes_hi: int, nsub: int, seed: int,
+                     max_tries: int = 200) -> np.ndarray:
+    """Uneven partition of the patch grid into ``nsub`` simply connected subdomains
+    with sizes in [sizes_lo, sizes_hi] (seeded BFS region growing; a draw whose
+    parts are not all simply connected is rejected and redrawn)."""
+    total = int(np.prod(npatch))
+    rng = np.random.default_rng(seed)
+    for _ in range(max_tries):
+        # seeded sizes summing to total
+        sizes = rng.integers(sizes_lo, sizes_hi + 1, size=nsub)
+        while sizes.sum() != total:
+            i = int(rng.integers(nsub))
+            if sizes.sum() > total and sizes[i] > sizes_lo:
+                sizes[i] -= 1
+            elif sizes.sum() < total and sizes[i] < sizes_hi:
+                sizes[i] += 1
+        sub = -np.ones(total, np.int32)
+        ok = True
+        for s in range(nsub):
+            free = np.flatnonzero(sub < 0)
+            # start at the free patch with the smallest index (sweeps the grid)
+            start = int(free[0])
+            region = [start]
+            sub[start] = s
+            frontier = [n for n in _patch_neighbours(npatch, start) if sub[n] < 0]
+            while len(region) < sizes[s]:
+                frontier = [n for n in dict.fromkeys(frontier) if sub[n] < 0]
+                if not frontier:
+                    ok = False
+                    break
+                # prefer the most compact growth: frontier patch with most region neighbours
+                scores = [sum(1 for m in _patch_neighbours(npatch, n) if sub[m] == s) for n in frontier]
+                best = max(scores)
+                cands = [n for n, sc in zip(frontier, scores) if sc == best]
+                n = int(cands[int(rng.integers(len(cands)))])
+                sub[n] = s
+                region.append(n)
+                frontier.extend(m for m in _patch_neighbours(npatch, n) if sub[m] < 0)
+            if not ok:
+                break
+        if not ok or (sub < 0).any():
+            continue
+        if all(is_simply_connected_union(npatch, np.flatnonzero(sub == s)) for s in range(nsub)):
+            return sub
+    raise RuntimeError("no simply connected partition found")
+
+
+# ----------------------------------------------------------------------------
+# sources
+# ----------------------------------------------------------------------------
+
+def fourier_source_params(nrhs: int, kmax: int, seed: int, nmodes: int | None = None) -> np.ndarray:
+    """Random divergence-free Fourier sources: modes 0 < |k|_inf <= kmax (half of
+    the +-k pairs, since the real part is taken), complex N(0,1) coefficients with
+    the Leray projection c <- c - (k.c) k / |k|^2 applied."""
+    rng = np.random.default_rng(seed)
+    ks = []
+    for kz in range(-kmax, kmax + 1):
+        for ky in range(-kmax, kmax + 1):
+            for kx in range(-kmax, kmax + 1):
+                k = (kx, ky, kz)
+                if k == (0, 0, 0):
+                    continue
+                # keep one of each +-k pair
+                if k > tuple(-v for v in k):
+                    ks.append(k)
+    ks = np.array(ks, np.float64)
+    out = []
+    for _ in range(nrhs):
+        sel = ks if nmodes is None else ks[rng.choice(len(ks), nmodes, replace=False)]
+        col = [float(len(sel))]
+        for k in sel:
+            c = rng.standard_normal(3) + 1j * rng.standard_normal(3)
+            c = c - (k @ c) * k / (k @ k)
+            col.extend(list(k) + list(c.real) + list(c.imag))
+        out.append(np.array(col))
+    return np.concatenate(out)
+
+
+# ----------------------------------------------------------------------------
+# named workloads
+# ----------------------------------------------------------------------------
+
+def unit_cube(p: int, patches: Tuple[int, int, int], spans, sub_of_patch=None, nu=None,
+              name="cube", source_kind=SOURCE_SINE, source_params=None, nrhs=1) -> Problem:
+    """Unit cube split into a block grid of affine patches."""
+    if isinstance(spans, int):
+        spans = [[spans] * patches[d] for d in range(3)]
+    breaks = [np.linspace(0.0, 1.0, patches[d] + 1) for d in range(3)]
+    ctrl = box_control_net(p, spans, breaks)
+    npt = int(np.prod(patches))
+    if sub_of_patch is None:
+        sub_of_patch = np.arange(npt, dtype=np.int32)
+    if nu is None:
+        nu = np.ones(npt)
+    if source_params is None:
+        source_params = np.arange(1, nrhs + 1, dtype=np.float64)
+    return Problem(name=name, p=p, npatch=tuple(patches), nspan=[list(s) for s in spans],
+                   periodic0=False, ctrl=ctrl, nu=np.asarray(nu, np.float64),
+                   sub_of_patch=np.asarray(sub_of_patch, np.int32), source_kind=source_kind,
+                   source_params=np.asarray(source_params, np.float64), nrhs=nrhs)
+
+
+def cube8_p2n4(spans: int = 4, p: int = 2) -> Problem:
+    """Unit cube, 2x2x2 patches, one patch per subdomain, p=2, 4 spans per
+    direction per patch, nu=1, manufactured sine source."""
+    return unit_cube(p, (2, 2, 2), spans, name=f"cube8_p{p}n{spans}")
+
+
+def cube64_p3n8_sub16(seed: int = 2, spans: int = 8, p: int = 3, nrhs: int = 1) -> Problem:
+    """Unit cube, 4x4x4 patches in 16 subdomains of 2x2x1 patches, p=3, 8 spans,
+    per-patch nu log-uniform in [1, 1e3] (seeded), sine source."""
+    rng = np.random.default_rng(seed)
+    nu = 10.0 ** rng.uniform(0.0, 3.0, size=64)
+    sub = block_partition((4, 4, 4), (2, 2, 1))
+    return unit_cube(p, (4, 4, 4), spans, sub_of_patch=sub, nu=nu,
+                     name=f"cube64_p{p}n{spans}_sub16", nrhs=nrhs,
+                     source_params=np.arange(1, nrhs + 1, dtype=np.float64))
+
+
+def cube512_p3_uneven64(seed: int = 3, nrhs: int = 32, span_lo: int = 4, span_hi: int = 12) -> Problem:
+    """Unit cube, 8x8x8 patches, spans per patch slab drawn from {4..12}, p=3,
+    64 uneven simply connected subdomains of 4-12 patches, divergence-free random
+    Fourier sources (|k|_inf <= 4), nu = 1."""
+    rng = np.random.default_rng(seed)
+    spans = [list(rng.integers(span_lo, span_hi + 1, size=8)) for _ in range(3)]
+    sub = greedy_partition((8, 8, 8), 4, 12, 64, seed)
+    sp = fourier_source_params(nrhs, 4, seed)
+    return unit_cube(3, (8, 8, 8), spans, sub_of_patch=sub, nu=np.ones(512),
+                     name="cube512_p3_uneven64", source_kind=SOURCE_FOURIER,
+                     source_params=sp, nrhs=nrhs)
+
+
+def small_cases():
+    """Tiny problems for the parity tests (several tiles, ragged sizes)."""
+    out = []
+    out.append(cube8_p2n4(spans=2))
+    out.append(unit_cube(1, (2, 2, 2), 2, name="cube8_p1n2"))
+    out.append(unit_cube(3, (2, 2, 1), 2, name="cube4_p3n2"))
+    rng = np.random.default_rng(7)
+    out.append(unit_cube(2, (3, 2, 2), [[2, 3, 2], [2, 2], [3, 2]],
+                         sub_of_patch=np.array([0, 0, 1, 2, 2, 1, 3, 3, 4, 5, 5, 4], np.int32),
+                         nu=10.0 ** rng.uniform(0, 3, 12), name="cube12_p2_mixed"))
+    return out
