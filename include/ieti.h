@@ -1,0 +1,224 @@
+/*
+ * ieti.h -- C ABI of the GB300 library for the dual-primal isogeometric tearing
+ * and interconnecting (IETI-DP / FETI-DP) method for 3D curl-curl magnetostatics
+ * on multipatch spline discretisations (arXiv 2501.04340).
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns an ieti_status; IETI_OK = 0, errors are negative.
+ *     After an error, ieti_last_error(ctx) returns a message owned by ctx.
+ *   - Pointers named *_host are host memory owned by the caller; the library
+ *     copies what it keeps before returning. Pointers named *_dev are device
+ *     memory of the current CUDA device, owned by the caller.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Entry points
+ *     that take a stream enqueue their work on it and may return before the
+ *     work completes, unless stated otherwise.
+ *   - Multi-column vectors are column-major with `nrhs` columns.
+ *   - The context owns all device memory it allocates until ieti_destroy.
+ *   - Global numbering (the data format of every index argument):
+ *       node (i,j,k) of the glued control net -> i + N0 (j + N1 k);
+ *       an edge of direction d joins node (i,j,k) to (i,j,k)+e_d (wrapping in a
+ *       periodic direction 0) and is oriented along increasing parameter;
+ *       edge ids: all direction-0 edges, then direction 1, then direction 2,
+ *       each block lexicographic with i fastest.
+ *     Multipliers (dual DOFs) are numbered by increasing edge id, as are the
+ *     primal (coarse) DOFs.
+ */
+#ifndef IETI_H
+#define IETI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IETI_OK = 0,
+  IETI_ERR_INVALID_ARG = -1,
+  IETI_ERR_NOT_SIMPLY_CONNECTED = -2,
+  IETI_ERR_TREE_INCONSISTENT = -3,
+  IETI_ERR_SINGULAR_LOCAL = -4,
+  IETI_ERR_NO_CONVERGENCE = -5,
+  IETI_ERR_TIMEOUT = -6,
+  IETI_ERR_CUDA = -7,
+  IETI_ERR_OOM = -8,
+  IETI_ERR_STATE = -9
+} ieti_status;
+
+/* Precision of the local factorisations (Sec. 2.1: K_rr^(k) is factored per
+ * subdomain).
+ *   IETI_FP64:    FP64 Cholesky of every K_rr^(k); every operator in FP64.
+ *   IETI_FP32_IR: FP32 Cholesky and FP32 local interface operators, used as an
+ *                 approximate FETI-DP solver inside FP64 iterative refinement on
+ *                 the assembled system (FP64 residuals, FP64 coarse matrix,
+ *                 FP64 PCG vectors and inner products). */
+typedef enum { IETI_FP64 = 0, IETI_FP32_IR = 1 } ieti_precision;
+
+/* Source kinds of the right-hand side j of Eq. (3). */
+typedef enum {
+  IETI_SOURCE_SINE = 0,      /* J = s 2 pi^2 (sin pi y sin pi z, sin pi x sin pi z, sin pi x sin pi y);
+                                params: one amplitude s per load case */
+  IETI_SOURCE_FOURIER = 1,   /* J = sum_m Re(c_m exp(2 pi i k_m.x)); params per load case:
+                                nmodes, then per mode k(3), Re c(3), Im c(3) */
+  IETI_SOURCE_PATCHWISE = 2  /* J constant per patch; params: nrhs x npatch x 3 */
+} ieti_source_kind;
+
+/* Multipatch problem (Sec. 2): a structured P0 x P1 x P2 block grid of patches,
+ * each the image of (0,1)^3 under a trivariate B-spline/NURBS map of degree p
+ * with an open uniform knot vector; patch slab a of direction d has
+ * nspan[d][a] knot spans. Neighbouring patches share full patch-facets and the
+ * control points on them, so the geometry is one glued control net of
+ * N0 x N1 x N2 points, N_d = sum_a (nspan[d][a] + p - 1) + 1 (no "+1" when
+ * direction 0 is periodic). Patch (a,b,c) has index a + P0 (b + P1 c).
+ * Subdomains (Sec. 2) are the groups of sub_of_patch; each must be connected
+ * and simply connected. The edge space has degree p-1 along an edge and p
+ * across it; homogeneous tangential Dirichlet data n x A = 0 on the boundary. */
+typedef struct {
+  int degree;                  /* p >= 1 */
+  int npatch[3];               /* P0, P1, P2 */
+  const int* nspan_host[3];    /* nspan_host[d][a], a < npatch[d], each >= 1 */
+  int periodic0;               /* 1: direction 0 is periodic (closed ring) */
+  const double* ctrl_host;     /* N2 x N1 x N0 x 4: x, y, z, weight (i fastest) */
+  const double* nu_host;       /* reluctivity per patch, > 0 */
+  const int* sub_of_patch_host;/* subdomain id per patch, 0 .. nsub-1, all used */
+  int source_kind;             /* ieti_source_kind */
+  const double* source_params_host;
+  int n_source_params;
+  int nrhs;                    /* load cases, 1 .. 64 */
+  int affine;                  /* 1 if every patch map is an axis-aligned affine
+                                  map (enables the Kronecker assembly path) */
+} ieti_problem_desc;
+
+typedef struct ieti_ctx ieti_ctx;
+
+typedef struct {
+  int64_t nedge, nnode;        /* control mesh */
+  int64_t n_dirichlet, n_tree; /* removed DOFs (Sec. 2, Sec. 2.2) */
+  int64_t n_gauged;            /* unknowns of the gauged global system */
+  int64_t m_r;                 /* multipliers lambda_r (Eq. (5)) */
+  int64_t n_gp;                /* coarse primal DOFs */
+  int64_t nsub, nrhs;
+  int64_t max_nr, max_nI;      /* largest local r block / interface block */
+  int64_t sum_nr2, sum_nI2;    /* sum_k n_r^2, sum_k n_I^2 (dense sizes) */
+  int64_t bytes_device;        /* device memory held by the context */
+  int tree_rerun;              /* 1 if Kruskal was rerun with boundary edges first */
+} ieti_sizes;
+
+typedef struct {
+  int iterations;              /* PCG iterations (summed over refinement steps) */
+  int refinement_steps;        /* FP64 refinement steps (IETI_FP32_IR), else 1 */
+  double relres;               /* last ||b - F lambda|| / ||b|| (max over load cases) */
+  double global_relres;        /* FP64 ||j - K a|| / ||j|| of the returned field */
+  double kappa;                /* Lanczos estimate of kappa(M^-1 F) (first load case) */
+  int converged;               /* 1 if every load case met the tolerance */
+  double ms_total;             /* device time of the call */
+} ieti_solve_info;
+
+/* Builds the mesh, the 1D basis tables at the Gauss points (p+1 per span), the
+ * facets, wire basket, edge weights (Fig. "weights"), the Kruskal spanning tree
+ * (Sec. 2.2), primal (cotree weight-2) and dual DOFs, the signed jump operator
+ * B_r (Eq. (4)/(5)) and C_p, and allocates every device buffer. Host-side and
+ * one-off. Errors: INVALID_ARG (bad sizes), NOT_SIMPLY_CONNECTED (a subdomain
+ * is not a contractible union of patches), TREE_INCONSISTENT (the spanning
+ * tree is not a tree on the Dirichlet boundary even after the rerun, or a
+ * multiplier would couple more than two subdomains), OOM, CUDA. */
+ieti_status ieti_create(const ieti_problem_desc* desc, ieti_ctx** out);
+
+/* Host-only variant of ieti_create: builds the mesh, tables, gauge and DOF maps
+ * without touching the GPU, for inspection through ieti_query and
+ * ieti_get_dofmap. Every other entry point returns IETI_ERR_STATE on such a
+ * context. Same errors as ieti_create except CUDA and OOM. */
+ieti_status ieti_create_host(const ieti_problem_desc* desc, ieti_ctx** out);
+
+/* Replaces the per-patch reluctivities (npatch values) and/or the source
+ * parameters (same layout as in the descriptor); either pointer may be NULL.
+ * Takes effect at the next ieti_assemble. */
+ieti_status ieti_set_params(ieti_ctx* ctx, const double* nu_host,
+                            const double* source_params_host, int n_source_params);
+
+/* Eq. (3), batched over all patches of all subdomains: assembles, per
+ * subdomain k, the dense blocks K_rr^(k) (order [r_V, pad, r_I]), K_rp^(k),
+ * K_pp^(k) and the loads j_r^(k), j_p^(k) in FP64 on the device. */
+ieti_status ieti_assemble(ieti_ctx* ctx, void* stream);
+
+/* Sec. 2.1: batched Cholesky of every K_rr^(k) in the chosen precision; the
+ * interface Schur complement S_rIrI^(k) of Eq. (10) is taken from the factor
+ * after the r_V columns; Phi^(k) = K_rr^-1 K_rp; the coarse matrix
+ * S_Pi = -F (F of Eq. (7)) in FP64 and its Cholesky factor; the local
+ * interface operators (K_rr^-1)_II = S_rIrI^-1. Errors: SINGULAR_LOCAL (a
+ * non-positive pivot; the subdomain id is in the message), STATE (not
+ * assembled). Synchronises the stream. */
+ieti_status ieti_factor(ieti_ctx* ctx, ieti_precision prec, void* stream);
+
+/* Eq. (7): y = F_DP lam with F_DP = W - G F^-1 G^T = B_r K_rr^-1 B_r^T
+ * + G S_Pi^-1 G^T (the SPD negation of the paper's S). lam_dev, y_dev: m_r x
+ * nrhs FP64 device arrays (nrhs <= 64), not aliased. Uses the operators of the
+ * last ieti_factor (FP64 or FP32 storage). Errors: STATE, INVALID_ARG. */
+ieti_status ieti_apply_F(ieti_ctx* ctx, const double* lam_dev, double* y_dev, int nrhs,
+                         void* stream);
+
+/* Eq. (10): z = M_D^-1 r = sum_k D^(k) B_rI^(k) S_rIrI^(k) B_rI^(k)T D^(k) r,
+ * with D^(k) the rho-scaling weights nu_l / (nu_k + nu_l). r_dev, z_dev: m_r x
+ * nrhs FP64 device arrays, not aliased. */
+ieti_status ieti_apply_precond(ieti_ctx* ctx, const double* r_dev, double* z_dev, int nrhs,
+                               void* stream);
+
+/* Eqs. (7)-(9): right-hand side b = e - G F^-1 d, PCG with M_D^-1 on
+ * F_DP lam = b until ||b - F_DP lam|| <= tol ||b|| per load case (or maxit),
+ * coarse recovery a_p = C F^-1 (d - G^T lam) and local recovery
+ * a_r = K_rr^-1 (j_r - K_rp a_p - B_r^T lam). Under IETI_FP32_IR this is the
+ * inner solver of FP64 iterative refinement on the assembled system, repeated
+ * until the FP64 relative residual of the field is <= tol_field (default 1e-10
+ * when <= 0) or 8 refinement steps. lam0_dev: m_r x nrhs initial multipliers or
+ * NULL for zero. a_dev: nedge x nrhs output field (Dirichlet and tree DOFs are
+ * zero). lam_dev: optional m_r x nrhs output of the final multipliers.
+ * info: optional host struct. Synchronises the stream. Errors: STATE,
+ * NO_CONVERGENCE (info still filled, a_dev holds the last iterate). */
+ieti_status ieti_solve(ieti_ctx* ctx, const double* lam0_dev, double tol, int maxit,
+                       double tol_field, double* a_dev, double* lam_dev,
+                       ieti_solve_info* info, void* stream);
+
+/* Sizes of the problem and of the device data. */
+ieti_status ieti_query(const ieti_ctx* ctx, ieti_sizes* out);
+
+/* DOF maps for inspection (host copies). which:
+ *   0 tree flag per edge (nedge, int64 0/1)
+ *   1 edge weight 1..5 per edge (nedge)
+ *   2 primal edge ids (n_gp)
+ *   3 dual edge ids (m_r)
+ *   4 r_V edge ids of subdomain `sub`
+ *   5 r_I edge ids of subdomain `sub`
+ *   6 primal edge ids of subdomain `sub`
+ *   7 sign (+1/-1) of each r_I DOF of subdomain `sub`
+ * Writes min(count, cap) values to out_host and the count to *count. */
+ieti_status ieti_get_dofmap(const ieti_ctx* ctx, int which, int sub, int64_t* out_host,
+                            int64_t cap, int64_t* count);
+
+/* Copies a dense FP64 block of subdomain `sub` to the host, column-major with
+ * leading dimension `rows` as returned in *rows_out, *cols_out. which:
+ *   0 K_rr as assembled (rows/cols ordered [r_V, r_I], padding removed)
+ *   1 K_rp, 2 K_pp, 3 j_r (n_r x nrhs), 4 j_p,
+ *   5 S_rIrI (after ieti_factor), 6 (K_rr^-1)_II (after ieti_factor).
+ * out_host may be NULL to query the shape. Synchronises the device. */
+ieti_status ieti_get_block(ieti_ctx* ctx, int which, int sub, double* out_host, int64_t cap,
+                           int64_t* rows_out, int64_t* cols_out);
+
+/* The FP64 coarse matrix S_Pi = -F (n_gp x n_gp, host copy) after ieti_factor. */
+ieti_status ieti_get_coarse(ieti_ctx* ctx, double* out_host, int64_t cap);
+
+/* Interface right-hand side b = e - G F^-1 d (m_r x nrhs, device) for the
+ * current loads, from the last factorisation. */
+ieti_status ieti_interface_rhs(ieti_ctx* ctx, double* b_dev, void* stream);
+
+/* Number of kernel launches this context has issued so far. */
+int64_t ieti_launch_count(const ieti_ctx* ctx);
+
+void ieti_destroy(ieti_ctx* ctx);
+const char* ieti_last_error(const ieti_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IETI_H */

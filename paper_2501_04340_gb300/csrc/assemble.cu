@@ -1,0 +1,572 @@
+// Batched assembly of the subdomain stiffness blocks and loads, Eq. (3):
+//   (K)_ij = int nu curl w_j . curl w_i dV,  (j)_i = int J . w_i dV,
+// with covariant Piola push-forward w = DF^-T w_hat, curl w = DF curl_hat w_hat / det DF.
+//
+// Two paths produce K^(k) = sum of the patch contributions of subdomain k:
+//  * k_kron (axis-aligned affine patches): every dense entry is generated
+//    directly from 1D Gram matrices of the spline families {N, N', D}; with a
+//    constant diagonal Jacobian the Gauss quadrature of Eq. (3) factorises into
+//    these 1D integrals, so the value equals the quadrature result. One thread
+//    per dense entry, coalesced column-major stores, no atomics.
+//  * k_elem_K (any NURBS map): one CTA per knot-span element, Gauss quadrature
+//    with p+1 points per direction, element matrix in shared memory, atomic
+//    scatter into the dense blocks.
+// The loads always use the element path (k_elem_j).
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace ieti {
+
+struct AsmParams {
+  int p, nq, nsub, nrhs, source_kind, n_src;
+  int P0, P1, P2, N0, N1, N2, per0;
+  const SubDev* sd;
+  const DofDev* dof;
+  const int32_t* patch_code;
+  const int64_t* patch_code_off;
+  const int32_t* sub_of_patch;
+  const int32_t* elem;
+  const double* tabN[3];
+  const double* tabdN[3];
+  const double* tabD[3];
+  const double* wq;
+  const double* ctrl;
+  const double* nu;
+  const double* src;
+  const double* gq;
+  const double* gram[3];
+  int64_t gram_per[3];
+  int gram_nfun[3];
+  const int32_t* slab_of[3];
+  const int32_t* start[3];
+  const int32_t* nspan[3];
+  const int32_t* spanoff[3];
+  double* K64;
+  double* Kp;
+  double* Kpp;
+  double* jr;
+  double* jp;
+};
+
+// ---------------------------------------------------------------------------
+// shared device helpers
+// ---------------------------------------------------------------------------
+
+__device__ inline void patch_abc_d(const AsmParams& P, int q, int a[3]) {
+  a[0] = q % P.P0;
+  a[1] = (q / P.P0) % P.P1;
+  a[2] = q / (P.P0 * P.P1);
+}
+
+// curl of a reference edge function of direction d, component c != d:
+// sign and 1D families (0 = N, 1 = N', 2 = D) per direction
+__device__ inline int curl_term(int d, int c, int fam[3]) {
+  if (d == 0) {
+    if (c == 1) { fam[0] = 2; fam[1] = 0; fam[2] = 1; return +1; }
+    fam[0] = 2; fam[1] = 1; fam[2] = 0; return -1;           // c == 2
+  } else if (d == 1) {
+    if (c == 0) { fam[0] = 0; fam[1] = 2; fam[2] = 1; return -1; }
+    fam[0] = 1; fam[1] = 2; fam[2] = 0; return +1;           // c == 2
+  }
+  if (c == 0) { fam[0] = 0; fam[1] = 1; fam[2] = 2; return +1; }
+  fam[0] = 1; fam[1] = 0; fam[2] = 2; return -1;             // c == 1
+}
+
+__device__ inline void source_eval(const AsmParams& P, int q, const double X[3], double J[][3]) {
+  const double pi = 3.14159265358979323846;
+  if (P.source_kind == IETI_SOURCE_SINE) {
+    double sx = sin(pi * X[0]), sy = sin(pi * X[1]), sz = sin(pi * X[2]);
+    double b0 = 2 * pi * pi * sy * sz, b1 = 2 * pi * pi * sx * sz, b2 = 2 * pi * pi * sx * sy;
+    for (int r = 0; r < P.nrhs; ++r) {
+      double s = P.src[r];
+      J[r][0] = s * b0; J[r][1] = s * b1; J[r][2] = s * b2;
+    }
+  } else if (P.source_kind == IETI_SOURCE_FOURIER) {
+    int pos = 0;
+    for (int r = 0; r < P.nrhs; ++r) {
+      int nm = (int)P.src[pos++];
+      double a0 = 0, a1 = 0, a2 = 0;
+      for (int m = 0; m < nm; ++m) {
+        const double* M = P.src + pos;
+        pos += 9;
+        double th = 2 * pi * (M[0] * X[0] + M[1] * X[1] + M[2] * X[2]);
+        double cs = cos(th), sn = sin(th);
+        a0 += cs * M[3] - sn * M[6];
+        a1 += cs * M[4] - sn * M[7];
+        a2 += cs * M[5] - sn * M[8];
+      }
+      J[r][0] = a0; J[r][1] = a1; J[r][2] = a2;
+    }
+  } else {
+    int np = P.P0 * P.P1 * P.P2;
+    for (int r = 0; r < P.nrhs; ++r) {
+      const double* v = P.src + ((size_t)r * np + q) * 3;
+      J[r][0] = v[0]; J[r][1] = v[1]; J[r][2] = v[2];
+    }
+  }
+}
+
+// destination of the (ci, cj) entry of subdomain k (codes: [0,n) r, [n,n+nP) primal)
+__device__ inline void add_entry(const AsmParams& P, const SubDev& s, int ci, int cj, double v) {
+  if (ci < 0 || cj < 0) return;
+  if (ci < s.n) {
+    if (cj < s.n) atomicAdd(P.K64 + s.A + ci + (int64_t)s.n * cj, v);
+    else atomicAdd(P.Kp + s.Kp + ci + (int64_t)s.n * (cj - s.n), v);
+  } else if (cj >= s.n) {
+    atomicAdd(P.Kpp + s.Kpp + (ci - s.n) + (int64_t)s.nP * (cj - s.n), v);
+  }
+}
+
+// element setup common to the K and j kernels: 1D tables of the element's spans,
+// local control points, geometry at the Gauss points
+template <int PD>
+struct ElemShared {
+  static constexpr int NQ = PD + 1, NQ3 = NQ * NQ * NQ, NF = 3 * PD * (PD + 1) * (PD + 1);
+  double N[3][PD + 1][NQ], dN[3][PD + 1][NQ], D[3][PD][NQ];
+  double X[NQ3][3];
+  double DF[NQ3][9];
+  double det[NQ3], wt[NQ3];
+  int code[NF];
+};
+
+template <int PD>
+__device__ void elem_setup(const AsmParams& P, int e, ElemShared<PD>& sh, int& q, int& k) {
+  constexpr int NQ = PD + 1, NQ3 = NQ * NQ * NQ, NF = ElemShared<PD>::NF;
+  const int tid = threadIdx.x;
+  q = P.elem[4 * e];
+  int s[3] = {P.elem[4 * e + 1], P.elem[4 * e + 2], P.elem[4 * e + 3]};
+  int a[3];
+  patch_abc_d(P, q, a);
+  k = P.sub_of_patch[q];
+  int nsp[3], g[3], st[3];
+  for (int d = 0; d < 3; ++d) {
+    nsp[d] = P.nspan[d][a[d]];
+    g[d] = P.spanoff[d][a[d]] + s[d];
+    st[d] = P.start[d][a[d]];
+  }
+  for (int t = tid; t < 3 * (PD + 1) * NQ; t += blockDim.x) {
+    int d = t / ((PD + 1) * NQ), r = (t / NQ) % (PD + 1), x = t % NQ;
+    sh.N[d][r][x] = P.tabN[d][((int64_t)g[d] * (PD + 1) + r) * NQ + x];
+    sh.dN[d][r][x] = P.tabdN[d][((int64_t)g[d] * (PD + 1) + r) * NQ + x];
+  }
+  for (int t = tid; t < 3 * PD * NQ; t += blockDim.x) {
+    int d = t / (PD * NQ), r = (t / NQ) % PD, x = t % NQ;
+    sh.D[d][r][x] = P.tabD[d][((int64_t)g[d] * PD + r) * NQ + x];
+  }
+  // codes of the element functions (patch-local edge index -> local DOF)
+  for (int f = tid; f < NF; f += blockDim.x) {
+    constexpr int NFD = PD * (PD + 1) * (PD + 1);
+    int d = f / NFD, r = f % NFD;
+    int ext[3] = {PD + 1, PD + 1, PD + 1};
+    ext[d] = PD;
+    int la = r % ext[0], lb = (r / ext[0]) % ext[1], lc = r / (ext[0] * ext[1]);
+    // patch-local edge extents
+    int64_t doff = 0;
+    int pe[3];
+    for (int dd = 0; dd <= d; ++dd) {
+      for (int c = 0; c < 3; ++c) pe[c] = nsp[c] + PD - (c == dd ? 1 : 0);
+      if (dd < d) doff += (int64_t)pe[0] * pe[1] * pe[2];
+    }
+    int64_t li = doff + (s[0] + la) + (int64_t)pe[0] * ((s[1] + lb) + (int64_t)pe[1] * (s[2] + lc));
+    sh.code[f] = P.patch_code[P.patch_code_off[q] + li];
+  }
+  __syncthreads();
+  // geometry at the Gauss points
+  for (int t = tid; t < NQ3; t += blockDim.x) {
+    int x = t % NQ, y = (t / NQ) % NQ, z = t / (NQ * NQ);
+    double W = 0, dW[3] = {0, 0, 0}, S[3] = {0, 0, 0}, dS[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int c = 0; c <= PD; ++c)
+      for (int b = 0; b <= PD; ++b)
+        for (int aa = 0; aa <= PD; ++aa) {
+          int gi = st[0] + s[0] + aa;
+          if (P.per0) gi %= P.N0;
+          int gj = st[1] + s[1] + b, gk = st[2] + s[2] + c;
+          const double* cp = P.ctrl + (((int64_t)gk * P.N1 + gj) * P.N0 + gi) * 4;
+          double w = cp[3];
+          double B = sh.N[0][aa][x] * sh.N[1][b][y] * sh.N[2][c][z];
+          double B0 = sh.dN[0][aa][x] * sh.N[1][b][y] * sh.N[2][c][z];
+          double B1 = sh.N[0][aa][x] * sh.dN[1][b][y] * sh.N[2][c][z];
+          double B2 = sh.N[0][aa][x] * sh.N[1][b][y] * sh.dN[2][c][z];
+          W += w * B;
+          dW[0] += w * B0; dW[1] += w * B1; dW[2] += w * B2;
+          for (int r = 0; r < 3; ++r) {
+            double wp = w * cp[r];
+            S[r] += wp * B;
+            dS[r][0] += wp * B0; dS[r][1] += wp * B1; dS[r][2] += wp * B2;
+          }
+        }
+    double Xr[3];
+    for (int r = 0; r < 3; ++r) Xr[r] = S[r] / W;
+    double F[9];
+    for (int r = 0; r < 3; ++r)
+      for (int cc = 0; cc < 3; ++cc) F[r * 3 + cc] = (dS[r][cc] - Xr[r] * dW[cc]) / W;
+    double det = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+                 F[2] * (F[3] * F[7] - F[4] * F[6]);
+    for (int r = 0; r < 3; ++r) sh.X[t][r] = Xr[r];
+    for (int r = 0; r < 9; ++r) sh.DF[t][r] = F[r];
+    sh.det[t] = det;
+    sh.wt[t] = P.wq[x] * P.wq[y] * P.wq[z] / ((double)nsp[0] * nsp[1] * nsp[2]);
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// K: element quadrature (any geometry)
+// ---------------------------------------------------------------------------
+
+template <int PD>
+__global__ void __launch_bounds__(256) k_elem_K(AsmParams P) {
+  constexpr int NQ = PD + 1, NQ3 = NQ * NQ * NQ, NF = ElemShared<PD>::NF;
+  constexpr int NFD = PD * (PD + 1) * (PD + 1);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ElemShared<PD>& sh = *reinterpret_cast<ElemShared<PD>*>(smem_raw);
+  double* M = reinterpret_cast<double*>(smem_raw + sizeof(ElemShared<PD>));   // NQ3 x 9
+  double* C = M + NQ3 * 9;                                                      // NF x NQ3 x 2
+  const int e = blockIdx.x;
+  int q, k;
+  elem_setup<PD>(P, e, sh, q, k);
+  const SubDev s = P.sd[k];
+  const double nu = P.nu[q];
+  const int tid = threadIdx.x;
+  for (int t = tid; t < NQ3; t += blockDim.x) {
+    const double* F = sh.DF[t];
+    double f = nu * sh.wt[t] / sh.det[t];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        double v = 0;
+        for (int r = 0; r < 3; ++r) v += F[r * 3 + a] * F[r * 3 + b];
+        M[t * 9 + a * 3 + b] = f * v;
+      }
+  }
+  // reference curls, two nonzero components per function
+  for (int t = tid; t < NF * NQ3; t += blockDim.x) {
+    int f = t / NQ3, qq = t % NQ3;
+    int x = qq % NQ, y = (qq / NQ) % NQ, z = qq / (NQ * NQ);
+    int d = f / NFD, r = f % NFD;
+    int ext[3] = {PD + 1, PD + 1, PD + 1};
+    ext[d] = PD;
+    int la = r % ext[0], lb = (r / ext[0]) % ext[1], lc = r / (ext[0] * ext[1]);
+    double c0, c1;
+    if (d == 0) {        // D N N' , -D N' N   (components 1, 2)
+      c0 = sh.D[0][la][x] * sh.N[1][lb][y] * sh.dN[2][lc][z];
+      c1 = -sh.D[0][la][x] * sh.dN[1][lb][y] * sh.N[2][lc][z];
+    } else if (d == 1) { // -N D N' , N' D N   (components 0, 2)
+      c0 = -sh.N[0][la][x] * sh.D[1][lb][y] * sh.dN[2][lc][z];
+      c1 = sh.dN[0][la][x] * sh.D[1][lb][y] * sh.N[2][lc][z];
+    } else {             // N N' D , -N' N D   (components 0, 1)
+      c0 = sh.N[0][la][x] * sh.dN[1][lb][y] * sh.D[2][lc][z];
+      c1 = -sh.dN[0][la][x] * sh.N[1][lb][y] * sh.D[2][lc][z];
+    }
+    C[(f * NQ3 + qq) * 2 + 0] = c0;
+    C[(f * NQ3 + qq) * 2 + 1] = c1;
+  }
+  __syncthreads();
+  // 2x2 tiles (I <= J) of the symmetric element matrix
+  constexpr int NT = NF / 2;
+  constexpr int NTILE = NT * (NT + 1) / 2;
+  for (int t = tid; t < NTILE; t += blockDim.x) {
+    // decode t -> (I, J), I <= J, row-major over the upper triangle
+    int I = 0, rem = t;
+    while (rem >= NT - I) { rem -= NT - I; ++I; }
+    int J = I + rem;
+    int i0 = 2 * I, j0 = 2 * J;
+    int di = i0 / NFD, dj = j0 / NFD;
+    int ci[2] = {di == 0 ? 1 : 0, di == 2 ? 1 : 2};
+    int cj[2] = {dj == 0 ? 1 : 0, dj == 2 ? 1 : 2};
+    double e00 = 0, e01 = 0, e10 = 0, e11 = 0;
+    for (int qq = 0; qq < NQ3; ++qq) {
+      const double* Mq = M + qq * 9;
+      double m00 = Mq[ci[0] * 3 + cj[0]], m01 = Mq[ci[0] * 3 + cj[1]];
+      double m10 = Mq[ci[1] * 3 + cj[0]], m11 = Mq[ci[1] * 3 + cj[1]];
+      const double* a0 = C + ((i0 + 0) * NQ3 + qq) * 2;
+      const double* a1 = C + ((i0 + 1) * NQ3 + qq) * 2;
+      const double* b0 = C + ((j0 + 0) * NQ3 + qq) * 2;
+      const double* b1 = C + ((j0 + 1) * NQ3 + qq) * 2;
+      double y00 = m00 * b0[0] + m01 * b0[1], y01 = m10 * b0[0] + m11 * b0[1];
+      double y10 = m00 * b1[0] + m01 * b1[1], y11 = m10 * b1[0] + m11 * b1[1];
+      e00 += a0[0] * y00 + a0[1] * y01;
+      e01 += a0[0] * y10 + a0[1] * y11;
+      e10 += a1[0] * y00 + a1[1] * y01;
+      e11 += a1[0] * y10 + a1[1] * y11;
+    }
+    double ev[2][2] = {{e00, e01}, {e10, e11}};
+    for (int u = 0; u < 2; ++u)
+      for (int v = 0; v < 2; ++v) {
+        int fi = i0 + u, fj = j0 + v;
+        if (I == J && fj < fi) continue;
+        int cI = sh.code[fi], cJ = sh.code[fj];
+        add_entry(P, s, cI, cJ, ev[u][v]);
+        if (fi != fj) add_entry(P, s, cJ, cI, ev[u][v]);
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// j: element quadrature of int J . w_i (any geometry)
+// ---------------------------------------------------------------------------
+
+template <int PD>
+__global__ void __launch_bounds__(256) k_elem_j(AsmParams P) {
+  constexpr int NQ = PD + 1, NQ3 = NQ * NQ * NQ, NF = ElemShared<PD>::NF;
+  constexpr int NFD = PD * (PD + 1) * (PD + 1);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ElemShared<PD>& sh = *reinterpret_cast<ElemShared<PD>*>(smem_raw);
+  double* G = reinterpret_cast<double*>(smem_raw + sizeof(ElemShared<PD>));   // NQ3 x nrhs x 3
+  const int e = blockIdx.x;
+  int q, k;
+  elem_setup<PD>(P, e, sh, q, k);
+  const SubDev s = P.sd[k];
+  const int tid = threadIdx.x;
+  for (int t = tid; t < NQ3; t += blockDim.x) {
+    const double* F = sh.DF[t];
+    // inverse of DF times det (adjugate)
+    double A[9];
+    A[0] = F[4] * F[8] - F[5] * F[7]; A[1] = F[2] * F[7] - F[1] * F[8]; A[2] = F[1] * F[5] - F[2] * F[4];
+    A[3] = F[5] * F[6] - F[3] * F[8]; A[4] = F[0] * F[8] - F[2] * F[6]; A[5] = F[2] * F[3] - F[0] * F[5];
+    A[6] = F[3] * F[7] - F[4] * F[6]; A[7] = F[1] * F[6] - F[0] * F[7]; A[8] = F[0] * F[4] - F[1] * F[3];
+    double J[MAX_RHS][3];
+    source_eval(P, q, sh.X[t], J);
+    double w = sh.wt[t];
+    for (int r = 0; r < P.nrhs; ++r)
+      for (int a = 0; a < 3; ++a)
+        G[(t * P.nrhs + r) * 3 + a] = w * (A[a * 3 + 0] * J[r][0] + A[a * 3 + 1] * J[r][1] + A[a * 3 + 2] * J[r][2]);
+  }
+  __syncthreads();
+  for (int t = tid; t < NF * P.nrhs; t += blockDim.x) {
+    int f = t / P.nrhs, r = t % P.nrhs;
+    int cf = sh.code[f];
+    if (cf < 0) continue;
+    int d = f / NFD, rr = f % NFD;
+    int ext[3] = {PD + 1, PD + 1, PD + 1};
+    ext[d] = PD;
+    int la = rr % ext[0], lb = (rr / ext[0]) % ext[1], lc = rr / (ext[0] * ext[1]);
+    double acc = 0;
+    for (int qq = 0; qq < NQ3; ++qq) {
+      int x = qq % NQ, y = (qq / NQ) % NQ, z = qq / (NQ * NQ);
+      double v = (d == 0) ? sh.D[0][la][x] * sh.N[1][lb][y] * sh.N[2][lc][z]
+               : (d == 1) ? sh.N[0][la][x] * sh.D[1][lb][y] * sh.N[2][lc][z]
+                          : sh.N[0][la][x] * sh.N[1][lb][y] * sh.D[2][lc][z];
+      acc += v * G[(qq * P.nrhs + r) * 3 + d];
+    }
+    if (cf < s.n) atomicAdd(P.jr + RV(s, cf, r, P.nrhs), acc);
+    else atomicAdd(P.jp + PV(s, cf - s.n, r, P.nrhs), acc);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K: Kronecker generation of every dense entry (axis-aligned affine patches)
+// ---------------------------------------------------------------------------
+
+__device__ inline int slab_cands(const AsmParams& P, int c, int idx, bool isD, int out[2]) {
+  int Pc = (c == 0) ? P.P0 : (c == 1 ? P.P1 : P.P2);
+  int a = P.slab_of[c][idx];
+  int n = 0;
+  out[n++] = a;
+  if (!isD && idx == P.start[c][a]) {
+    if (a > 0) out[n++] = a - 1;
+    else if (c == 0 && P.per0) out[n++] = Pc - 1;
+  }
+  return n;
+}
+
+__device__ inline int local_index(const AsmParams& P, int c, int a, int idx, bool isD) {
+  int li = idx - P.start[c][a];
+  if (c == 0 && P.per0) li = ((li % P.N0) + P.N0) % P.N0;
+  int hi = P.nspan[c][a] + P.p - 1 - (isD ? 1 : 0);
+  return (li >= 0 && li <= hi) ? li : -1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_kron(AsmParams P, T* Lout) {
+  const int k = blockIdx.y;
+  const SubDev s = P.sd[k];
+  const int R = s.n + s.nP;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)R * R) return;
+  const int i = (int)(e % R), j = (int)(e / R);
+  if (i >= s.n && j < s.n) return;           // K_pr is not stored
+  const DofDev a = P.dof[s.dof + i];
+  const DofDev b = P.dof[s.dof + j];
+  double v = 0.0;
+  if (a.d < 0 || b.d < 0) {
+    v = (i == j) ? 1.0 : 0.0;
+  } else {
+    const int p = P.p;
+    int xa[3] = {a.i, a.j, a.k}, xb[3] = {b.i, b.j, b.k};
+    bool near = true;
+    for (int c = 0; c < 3; ++c) {
+      int dl = xa[c] - xb[c];
+      if (c == 0 && P.per0) {
+        dl = ((dl % P.N0) + P.N0) % P.N0;
+        if (dl > P.N0 / 2) dl -= P.N0;
+      }
+      if (dl > p || dl < -p) near = false;
+    }
+    if (near) {
+      int ca[3][2], cb[3][2], na[3], nb[3];
+      for (int c = 0; c < 3; ++c) {
+        na[c] = slab_cands(P, c, xa[c], a.d == c, ca[c]);
+        nb[c] = slab_cands(P, c, xb[c], b.d == c, cb[c]);
+      }
+      // common slabs per direction
+      int cs[3][2], ncs[3];
+      for (int c = 0; c < 3; ++c) {
+        ncs[c] = 0;
+        for (int u = 0; u < na[c]; ++u)
+          for (int w = 0; w < nb[c]; ++w)
+            if (ca[c][u] == cb[c][w]) cs[c][ncs[c]++] = ca[c][u];
+      }
+      for (int u0 = 0; u0 < ncs[0]; ++u0)
+        for (int u1 = 0; u1 < ncs[1]; ++u1)
+          for (int u2 = 0; u2 < ncs[2]; ++u2) {
+            int sl[3] = {cs[0][u0], cs[1][u1], cs[2][u2]};
+            int q = sl[0] + P.P0 * (sl[1] + P.P1 * sl[2]);
+            if (P.sub_of_patch[q] != k) continue;
+            int la[3], lb[3];
+            bool ok = true;
+            for (int c = 0; c < 3; ++c) {
+              la[c] = local_index(P, c, sl[c], xa[c], a.d == c);
+              lb[c] = local_index(P, c, sl[c], xb[c], b.d == c);
+              if (la[c] < 0 || lb[c] < 0) ok = false;
+            }
+            if (!ok) continue;
+            for (int comp = 0; comp < 3; ++comp) {
+              if (comp == a.d || comp == b.d) continue;
+              int fa[3], fb[3];
+              int sgn = curl_term(a.d, comp, fa) * curl_term(b.d, comp, fb);
+              double prod = P.gq[q * 3 + comp] * sgn;
+              for (int c = 0; c < 3; ++c) {
+                int off = lb[c] - la[c] + p;
+                if (off < 0 || off > 2 * p) { prod = 0; break; }
+                prod *= P.gram[c][P.gram_per[c] * sl[c] +
+                                  ((int64_t)(fa[c] * 3 + fb[c]) * P.gram_nfun[c] + la[c]) * (2 * p + 1) + off];
+              }
+              v += prod;
+            }
+          }
+    }
+  }
+  if (i < s.n) {
+    if (j < s.n) {
+      P.K64[s.A + i + (int64_t)s.n * j] = v;
+      if (Lout) Lout[s.A + i + (int64_t)s.n * j] = (T)v;
+    } else {
+      P.Kp[s.Kp + i + (int64_t)s.n * (j - s.n)] = v;
+    }
+  } else {
+    P.Kpp[s.Kpp + (i - s.n) + (int64_t)s.nP * (j - s.n)] = v;
+  }
+}
+
+__global__ void k_pad_diag(const SubDev* sd, const DofDev* dof, double* K64) {
+  const int k = blockIdx.y;
+  const SubDev s = sd[k];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s.n; i += gridDim.x * blockDim.x)
+    if (dof[s.dof + i].d < 0) K64[s.A + i + (int64_t)s.n * i] = 1.0;
+}
+
+template <typename T>
+__global__ void k_copy_convert(const double* __restrict__ src, T* __restrict__ dst, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (T)src[i];
+}
+
+// ---------------------------------------------------------------------------
+
+static AsmParams make_params(Ctx* c) {
+  AsmParams P;
+  P.p = c->mesh.p;
+  P.nq = c->tab.nq;
+  P.nsub = c->nsub;
+  P.nrhs = c->nrhs;
+  P.source_kind = c->source_kind;
+  P.n_src = (int)c->src.size();
+  P.P0 = c->mesh.P[0]; P.P1 = c->mesh.P[1]; P.P2 = c->mesh.P[2];
+  P.N0 = c->mesh.N[0]; P.N1 = c->mesh.N[1]; P.N2 = c->mesh.N[2];
+  P.per0 = c->mesh.per0 ? 1 : 0;
+  P.sd = c->d_sd;
+  P.dof = c->d_dof;
+  P.patch_code = c->d_patch_code;
+  P.patch_code_off = c->d_patch_code_off;
+  P.sub_of_patch = c->d_sub_of_patch;
+  P.elem = c->d_elem;
+  for (int d = 0; d < 3; ++d) {
+    P.tabN[d] = c->d_tabN[d];
+    P.tabdN[d] = c->d_tabdN[d];
+    P.tabD[d] = c->d_tabD[d];
+    P.gram[d] = c->d_gram[d];
+    P.gram_per[d] = c->gram[d].slab_off.size() > 1 ? c->gram[d].slab_off[1] : 0;
+    P.gram_nfun[d] = c->gram[d].nfun_max;
+    P.slab_of[d] = c->d_slab_of[d];
+    P.start[d] = c->d_start[d];
+    P.nspan[d] = c->d_nspan[d];
+    P.spanoff[d] = c->d_start[d] + c->mesh.P[d];   // stored right after start
+  }
+  P.wq = c->d_wq;
+  P.ctrl = c->d_ctrl;
+  P.nu = c->d_nu;
+  P.src = c->d_src;
+  P.gq = c->d_gq;
+  P.K64 = c->K64;
+  P.Kp = c->Kp64;
+  P.Kpp = c->Kpp64;
+  P.jr = c->jr;
+  P.jp = c->jp;
+  return P;
+}
+
+template <int PD>
+static ieti_status launch_elem(Ctx* c, const AsmParams& P, bool do_K, cudaStream_t st) {
+  constexpr int NQ3 = (PD + 1) * (PD + 1) * (PD + 1), NF = ElemShared<PD>::NF;
+  if (do_K) {
+    size_t smem = sizeof(ElemShared<PD>) + sizeof(double) * (NQ3 * 9 + (size_t)NF * NQ3 * 2);
+    IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_elem_K<PD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_elem_K<PD><<<(unsigned)c->nelem, 256, smem, st>>>(P);
+    IETI_LAUNCH_CHECK(c);
+  }
+  size_t smem = sizeof(ElemShared<PD>) + sizeof(double) * (size_t)NQ3 * c->nrhs * 3;
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_elem_j<PD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_elem_j<PD><<<(unsigned)c->nelem, 256, smem, st>>>(P);
+  IETI_LAUNCH_CHECK(c);
+  return IETI_OK;
+}
+
+ieti_status assemble_all(Ctx* c, cudaStream_t st) {
+  AsmParams P = make_params(c);
+  IETI_CUDA_TRY(c, cudaMemsetAsync(c->jr, 0, sizeof(double) * c->tot_rv * c->nrhs, st));
+  IETI_CUDA_TRY(c, cudaMemsetAsync(c->jp, 0, sizeof(double) * std::max<int64_t>(c->tot_pv, 1) * c->nrhs, st));
+  const bool kron = c->affine;
+  if (kron) {
+    int64_t R = c->max_n + c->max_nP;
+    dim3 grid((unsigned)ceil_div(R * R, 256), (unsigned)c->nsub);
+    k_kron<double><<<grid, 256, 0, st>>>(P, (double*)nullptr);
+    IETI_LAUNCH_CHECK(c);
+  } else {
+    IETI_CUDA_TRY(c, cudaMemsetAsync(c->K64, 0, sizeof(double) * c->tot_A, st));
+    IETI_CUDA_TRY(c, cudaMemsetAsync(c->Kp64, 0, sizeof(double) * std::max<int64_t>(c->tot_Kp, 1), st));
+    IETI_CUDA_TRY(c, cudaMemsetAsync(c->Kpp64, 0, sizeof(double) * std::max<int64_t>(c->tot_Kpp, 1), st));
+    k_pad_diag<<<dim3(8, c->nsub), 256, 0, st>>>(c->d_sd, c->d_dof, c->K64);
+    IETI_LAUNCH_CHECK(c);
+  }
+  ieti_status r;
+  switch (c->mesh.p) {
+    case 1: r = launch_elem<1>(c, P, !kron, st); break;
+    case 2: r = launch_elem<2>(c, P, !kron, st); break;
+    case 3: r = launch_elem<3>(c, P, !kron, st); break;
+    default: c->err = "degree p must be 1, 2 or 3"; return IETI_ERR_INVALID_ARG;
+  }
+  return r;
+}
+
+// conversion used by the factorisation set-up
+template <typename T>
+ieti_status convert_copy(Ctx* c, const double* src, T* dst, int64_t n, cudaStream_t st) {
+  k_copy_convert<T><<<1216, 256, 0, st>>>(src, dst, n);
+  IETI_LAUNCH_CHECK(c);
+  return IETI_OK;
+}
+template ieti_status convert_copy<float>(Ctx*, const double*, float*, int64_t, cudaStream_t);
+template ieti_status convert_copy<double>(Ctx*, const double*, double*, int64_t, cudaStream_t);
+
+}  // namespace ieti

@@ -1,0 +1,576 @@
+// Batched dense factorisations of the local blocks (Sec. 2.1: K_rr block
+// diagonal, "every K_rr^(k) invertible after tree and primal removal").
+//
+// Right-looking blocked Cholesky with NB x NB panels over all subdomains at
+// once (uneven sizes: a subdomain whose panel count is exhausted skips the
+// launch). The r DOFs are ordered [r_V, pad, r_I, pad]; right after the r_V
+// panels the trailing block is exactly S_rIrI = K_II - K_IV K_VV^-1 K_VI
+// (Eq. (10)), which is snapshotted. The inverses of the diagonal blocks are kept
+// so that every triangular solve is a sequence of small dense products.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "internal.h"
+
+namespace ieti {
+
+template <typename T>
+ieti_status convert_copy(Ctx* c, const double* src, T* dst, int64_t n, cudaStream_t st);
+
+struct SolveDesc {
+  int64_t boff;   // offset of this subdomain's RHS block
+  int b0;         // first panel of the solve range
+  int ldb;        // leading dimension (rows of the range)
+  int ncol;       // columns for this subdomain
+  int pad_;
+};
+
+// ---------------------------------------------------------------------------
+// Cholesky kernels
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_potrf_diag(const SubDev* sd, T* L, T* Linv, int b, int* err) {
+  const int k = blockIdx.x;
+  const SubDev s = sd[k];
+  if (b >= s.nblk) return;
+  __shared__ T a[NB][NB + 1];
+  __shared__ T inv[NB][NB + 1];
+  const int tid = threadIdx.x;
+  T* A = L + s.A + (int64_t)b * NB + (int64_t)s.n * b * NB;
+  for (int t = tid; t < NB * NB; t += blockDim.x) {
+    int i = t % NB, j = t / NB;
+    a[i][j] = A[i + (int64_t)s.n * j];
+  }
+  __shared__ int bad;
+  if (tid == 0) bad = 0;
+  for (int c = 0; c < NB; ++c) {
+    __syncthreads();
+    if (tid == 0) {
+      T v = a[c][c];
+      if (!(v > (T)0)) {
+        bad = 1;
+        v = (T)1;
+      }
+      a[c][c] = sqrt(v);
+    }
+    __syncthreads();
+    T piv = a[c][c];
+    for (int i = c + 1 + tid; i < NB; i += blockDim.x) a[i][c] /= piv;
+    __syncthreads();
+    const int m = NB - 1 - c;
+    for (int t = tid; t < m * m; t += blockDim.x) {
+      int i = c + 1 + t / m, l = c + 1 + t % m;
+      if (l <= i) a[i][l] -= a[i][c] * a[l][c];
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && bad) atomicCAS(err, 0, k + 1);
+  // inverse of the lower triangular diagonal block, one column per thread
+  if (tid < NB) {
+    const int j = tid;
+    for (int i = 0; i < j; ++i) inv[i][j] = (T)0;
+    inv[j][j] = (T)1 / a[j][j];
+    for (int i = j + 1; i < NB; ++i) {
+      T acc = 0;
+      for (int l = j; l < i; ++l) acc += a[i][l] * inv[l][j];
+      inv[i][j] = -acc / a[i][i];
+    }
+  }
+  __syncthreads();
+  T* Li = Linv + s.linv + (int64_t)b * NB * NB;
+  for (int t = tid; t < NB * NB; t += blockDim.x) {
+    int i = t % NB, j = t / NB;
+    A[i + (int64_t)s.n * j] = (i >= j) ? a[i][j] : (T)0;
+    Li[i + NB * j] = inv[i][j];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_trsm_panel(const SubDev* sd, T* L, const T* Linv, int b) {
+  const int k = blockIdx.y;
+  const SubDev s = sd[k];
+  const int r = b + 1 + blockIdx.x;
+  if (r >= s.nblk) return;
+  __shared__ T A[NB][NB + 1];
+  __shared__ T Li[NB][NB + 1];
+  const int tid = threadIdx.x;
+  T* Ab = L + s.A + (int64_t)r * NB + (int64_t)s.n * b * NB;
+  const T* Lb = Linv + s.linv + (int64_t)b * NB * NB;
+  for (int t = tid; t < NB * NB; t += blockDim.x) {
+    int i = t % NB, j = t / NB;
+    A[i][j] = Ab[i + (int64_t)s.n * j];
+    Li[i][j] = Lb[i + NB * j];
+  }
+  __syncthreads();
+  // X = A Linv^T: X[i][j] = sum_{l <= j} A[i][l] Linv[j][l]
+  const int i = tid % NB, jg = tid / NB;   // 4 groups of 16 columns
+  T acc[16];
+#pragma unroll
+  for (int u = 0; u < 16; ++u) acc[u] = 0;
+  for (int l = 0; l < NB; ++l) {
+    T av = A[i][l];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) acc[u] += av * Li[jg * 16 + u][l];
+  }
+#pragma unroll
+  for (int u = 0; u < 16; ++u) Ab[i + (int64_t)s.n * (jg * 16 + u)] = acc[u];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_syrk(const SubDev* sd, T* L, int b) {
+  const int k = blockIdx.y;
+  const SubDev s = sd[k];
+  const int Tk = s.nblk - b - 1;
+  // triangular decode of the tile index: rr >= cc
+  const int t = blockIdx.x;
+  int rr = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while (rr * (rr + 1) / 2 > t) --rr;
+  while ((rr + 1) * (rr + 2) / 2 <= t) ++rr;
+  const int cc = t - rr * (rr + 1) / 2;
+  if (rr >= Tk) return;
+  const int r = b + 1 + rr, c = b + 1 + cc;
+  __shared__ T Lr[NB][NB + 1];
+  __shared__ T Lc[NB][NB + 1];
+  const int tid = threadIdx.x;
+  const T* Pr = L + s.A + (int64_t)r * NB + (int64_t)s.n * b * NB;
+  const T* Pc = L + s.A + (int64_t)c * NB + (int64_t)s.n * b * NB;
+  for (int x = tid; x < NB * NB; x += blockDim.x) {
+    int i = x % NB, j = x / NB;
+    Lr[j][i] = Pr[i + (int64_t)s.n * j];   // transposed: Lr[l][i]
+    Lc[j][i] = Pc[i + (int64_t)s.n * j];
+  }
+  __syncthreads();
+  const int ti = tid % 16, tj = tid / 16;
+  T acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0;
+  for (int l = 0; l < NB; ++l) {
+    T x[4], y[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      x[u] = Lr[l][ti + 16 * u];
+      y[u] = Lc[l][tj + 16 * u];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] += x[u] * y[v];
+  }
+  T* Out = L + s.A + (int64_t)r * NB + (int64_t)s.n * c * NB;
+#pragma unroll
+  for (int v = 0; v < 4; ++v)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      int i = ti + 16 * u, j = tj + 16 * v;
+      Out[i + (int64_t)s.n * j] -= acc[u][v];
+    }
+}
+
+// S_rIrI snapshot: symmetrised copy of the lower trailing block at the r_I panel
+template <typename T>
+__global__ void k_snapshot(const SubDev* sd, const T* L, T* S, int b) {
+  const int k = blockIdx.y;
+  const SubDev s = sd[k];
+  if (s.nVp != b * NB || s.nI == 0) return;
+  const int64_t tot = (int64_t)s.nI * s.nI;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(t % s.nI), j = (int)(t / s.nI);
+    int hi = i > j ? i : j, lo = i > j ? j : i;
+    S[s.S + t] = L[s.A + (s.nVp + hi) + (int64_t)s.n * (s.nVp + lo)];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// triangular solves L Y = B (forward) and L^T X = Y (backward) on a panel range
+// ---------------------------------------------------------------------------
+
+constexpr int SOLVE_CT = 8;     // RHS columns per CTA
+constexpr int SOLVE_RC = 256;   // rows per CTA in the forward update
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fwd(const SubDev* sd, const SolveDesc* dsc, const T* L, const T* Linv,
+                                             T* B, T* Y, int b) {
+  const int k = blockIdx.z;
+  const SubDev s = sd[k];
+  const SolveDesc d = dsc[k];
+  if (b < d.b0 || b >= s.nblk || d.ncol == 0) return;
+  const int c0 = blockIdx.y * SOLVE_CT;
+  if (c0 >= d.ncol) return;
+  const int nc = min(SOLVE_CT, d.ncol - c0);
+  const int row0 = (b - d.b0) * NB;          // local row of panel b in the range
+  const int rows = s.n - d.b0 * NB;          // rows of the range
+  __shared__ T Li[NB][NB + 1];
+  __shared__ T Bb[NB][SOLVE_CT];
+  __shared__ T y[NB][SOLVE_CT];
+  const int tid = threadIdx.x;
+  const T* Lb = Linv + s.linv + (int64_t)b * NB * NB;
+  for (int t = tid; t < NB * NB; t += blockDim.x) Li[t % NB][t / NB] = Lb[t];
+  T* Bk = B + d.boff;
+  for (int t = tid; t < NB * SOLVE_CT; t += blockDim.x) {
+    int i = t % NB, cc = t / NB;
+    Bb[i][cc] = (cc < nc) ? Bk[row0 + i + (int64_t)d.ldb * (c0 + cc)] : (T)0;
+  }
+  __syncthreads();
+  for (int t = tid; t < NB * SOLVE_CT; t += blockDim.x) {
+    int i = t % NB, cc = t / NB;
+    T acc = 0;
+    for (int l = 0; l <= i; ++l) acc += Li[i][l] * Bb[l][cc];
+    y[i][cc] = acc;
+  }
+  __syncthreads();
+  if (blockIdx.x == 0) {
+    T* Yk = Y + d.boff;
+    for (int t = tid; t < NB * nc; t += blockDim.x) {
+      int i = t % NB, cc = t / NB;
+      Yk[row0 + i + (int64_t)d.ldb * (c0 + cc)] = y[i][cc];
+    }
+  }
+  // update the rows below the panel
+  const int r = row0 + NB + blockIdx.x * SOLVE_RC + tid;
+  if (r >= rows || tid >= SOLVE_RC) return;
+  T acc[SOLVE_CT];
+#pragma unroll
+  for (int cc = 0; cc < SOLVE_CT; ++cc) acc[cc] = 0;
+  const T* Lcol = L + s.A + (d.b0 * NB + r) + (int64_t)s.n * (b * NB);
+  for (int l = 0; l < NB; ++l) {
+    T lv = Lcol[(int64_t)s.n * l];
+#pragma unroll
+    for (int cc = 0; cc < SOLVE_CT; ++cc) acc[cc] += lv * y[l][cc];
+  }
+  for (int cc = 0; cc < nc; ++cc) Bk[r + (int64_t)d.ldb * (c0 + cc)] -= acc[cc];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_bwd(const SubDev* sd, const SolveDesc* dsc, const T* L, const T* Linv,
+                                             T* Y, T* X, int b) {
+  const int k = blockIdx.z;
+  const SubDev s = sd[k];
+  const SolveDesc d = dsc[k];
+  if (b < d.b0 || b >= s.nblk || d.ncol == 0) return;
+  const int c0 = blockIdx.y * SOLVE_CT;
+  if (c0 >= d.ncol) return;
+  const int nc = min(SOLVE_CT, d.ncol - c0);
+  const int row0 = (b - d.b0) * NB;
+  __shared__ T Li[NB][NB + 1];
+  __shared__ T Yb[NB][SOLVE_CT];
+  __shared__ T x[NB][SOLVE_CT];
+  const int tid = threadIdx.x;
+  const T* Lb = Linv + s.linv + (int64_t)b * NB * NB;
+  for (int t = tid; t < NB * NB; t += blockDim.x) Li[t % NB][t / NB] = Lb[t];
+  T* Yk = Y + d.boff;
+  for (int t = tid; t < NB * SOLVE_CT; t += blockDim.x) {
+    int i = t % NB, cc = t / NB;
+    Yb[i][cc] = (cc < nc) ? Yk[row0 + i + (int64_t)d.ldb * (c0 + cc)] : (T)0;
+  }
+  __syncthreads();
+  // x = Linv^T y: x[i] = sum_{l >= i} Li[l][i] y[l]
+  for (int t = tid; t < NB * SOLVE_CT; t += blockDim.x) {
+    int i = t % NB, cc = t / NB;
+    T acc = 0;
+    for (int l = i; l < NB; ++l) acc += Li[l][i] * Yb[l][cc];
+    x[i][cc] = acc;
+  }
+  __syncthreads();
+  if (blockIdx.x == 0) {
+    T* Xk = X + d.boff;
+    for (int t = tid; t < NB * nc; t += blockDim.x) {
+      int i = t % NB, cc = t / NB;
+      Xk[row0 + i + (int64_t)d.ldb * (c0 + cc)] = x[i][cc];
+    }
+  }
+  // update rows above: Y[c] -= sum_{r in panel b} L[r, c] x[r], one warp per column c
+  const int warp = tid / 32, lane = tid % 32;
+  const int ccol = blockIdx.x * 8 + warp;    // local row (= column of L) in the range
+  if (ccol >= row0) return;
+  const T* Lc = L + s.A + (int64_t)b * NB + (int64_t)s.n * (d.b0 * NB + ccol);
+  T l0 = Lc[lane], l1 = Lc[lane + 32];
+  for (int cc = 0; cc < nc; ++cc) {
+    T v = l0 * x[lane][cc] + l1 * x[lane + 32][cc];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) Yk[ccol + (int64_t)d.ldb * (c0 + cc)] -= v;
+  }
+}
+
+template <typename T>
+ieti_status tri_solve(Ctx* c, const SubDev* d_sd, int nsub, int max_nblk, int max_rows, int max_ncol,
+                      const SolveDesc* d_desc, int min_b0, const T* L, const T* Linv, T* B, T* Y, T* X,
+                      cudaStream_t st) {
+  if (max_ncol <= 0) return IETI_OK;
+  const int ctiles = (int)ceil_div(max_ncol, SOLVE_CT);
+  for (int b = min_b0; b < max_nblk; ++b) {
+    dim3 grid((unsigned)std::max<int64_t>(1, ceil_div(max_rows, SOLVE_RC)), ctiles, nsub);
+    k_fwd<T><<<grid, 256, 0, st>>>(d_sd, d_desc, L, Linv, B, Y, b);
+    IETI_LAUNCH_CHECK(c);
+  }
+  for (int b = max_nblk - 1; b >= min_b0; --b) {
+    dim3 grid((unsigned)std::max<int64_t>(1, ceil_div(max_rows, 8)), ctiles, nsub);
+    k_bwd<T><<<grid, 256, 0, st>>>(d_sd, d_desc, L, Linv, Y, X, b);
+    IETI_LAUNCH_CHECK(c);
+  }
+  return IETI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// helpers for the derived operators
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void k_identity_rhs(const SubDev* sd, const SolveDesc* dsc, T* B) {
+  const int k = blockIdx.y;
+  const SubDev s = sd[k];
+  const SolveDesc d = dsc[k];
+  const int64_t tot = (int64_t)d.ldb * d.ncol;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(t % d.ldb), j = (int)(t / d.ldb);
+    B[d.boff + t] = (i == j) ? (T)1 : (T)0;
+  }
+  (void)s;
+}
+
+template <typename T>
+__global__ void k_extract_W(const SubDev* sd, const SolveDesc* dsc, const T* X, T* W) {
+  const int k = blockIdx.y;
+  const SubDev s = sd[k];
+  const SolveDesc d = dsc[k];
+  const int64_t tot = (int64_t)s.nI * s.nI;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(t % s.nI), j = (int)(t / s.nI);
+    // symmetrise (the two triangles agree up to rounding)
+    T a = X[d.boff + i + (int64_t)d.ldb * j], bb = X[d.boff + j + (int64_t)d.ldb * i];
+    W[s.S + t] = (T)0.5 * (a + bb);
+  }
+}
+
+// B (n x nP, type T) <- K_rp
+template <typename T>
+__global__ void k_load_Kp(const SubDev* sd, const SolveDesc* dsc, const double* Kp, T* B) {
+  const int k = blockIdx.y;
+  const SubDev s = sd[k];
+  const SolveDesc d = dsc[k];
+  const int64_t tot = (int64_t)s.n * s.nP;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x)
+    B[d.boff + t] = (T)Kp[s.Kp + t];
+}
+
+template <typename T>
+__global__ void k_store_Phi(const SubDev* sd, const SolveDesc* dsc, const T* X, double* Phi) {
+  const int k = blockIdx.y;
+  const SubDev s = sd[k];
+  const SolveDesc d = dsc[k];
+  const int64_t tot = (int64_t)s.n * s.nP;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x)
+    Phi[s.Kp + t] = (double)X[d.boff + t];
+}
+
+// S_Pi += C^T (K_pp - K_rp^T Phi) C, one CTA per subdomain, FP64
+__global__ void k_coarse_assemble(const SubDev* sd, const double* Kp, const double* Kpp, const double* Phi,
+                                  const int32_t* P_glob, double* SPi, int ldc) {
+  const int k = blockIdx.x;
+  const SubDev s = sd[k];
+  const int np = s.nP;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  for (int t = warp; t < np * np; t += nw) {
+    int i = t % np, j = t / np;
+    const double* a = Kp + s.Kp + (int64_t)s.n * i;
+    const double* ph = Phi + s.Kp + (int64_t)s.n * j;
+    double acc = 0;
+    for (int r = lane; r < s.n; r += 32) acc += a[r] * ph[r];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      double v = Kpp[s.Kpp + i + (int64_t)np * j] - acc;
+      int gi = P_glob[s.pv + i], gj = P_glob[s.pv + j];
+      atomicAdd(SPi + gi + (int64_t)ldc * gj, v);
+    }
+  }
+}
+
+__global__ void k_pad_identity(double* A, int n0, int ld) {
+  for (int i = n0 + blockIdx.x * blockDim.x + threadIdx.x; i < ld; i += gridDim.x * blockDim.x)
+    A[i + (int64_t)ld * i] = 1.0;
+}
+
+// ---------------------------------------------------------------------------
+
+template <typename T>
+static ieti_status cholesky(Ctx* c, const SubDev* d_sd, const std::vector<SubDev>& sdh, T* L, T* Linv,
+                            T* S, bool snapshot, cudaStream_t st) {
+  int nsub = (int)sdh.size();
+  int max_nblk = 0;
+  for (auto& s : sdh) max_nblk = std::max(max_nblk, s.nblk);
+  for (int b = 0; b < max_nblk; ++b) {
+    if (snapshot) {
+      bool any = false;
+      for (auto& s : sdh) any |= (s.nVp == b * NB && s.nI > 0);
+      if (any) {
+        k_snapshot<T><<<dim3(256, nsub), 256, 0, st>>>(d_sd, L, S, b);
+        IETI_LAUNCH_CHECK(c);
+      }
+    }
+    k_potrf_diag<T><<<nsub, 256, 0, st>>>(d_sd, L, Linv, b, c->d_err);
+    IETI_LAUNCH_CHECK(c);
+    const int Tm = max_nblk - b - 1;
+    if (Tm > 0) {
+      k_trsm_panel<T><<<dim3(Tm, nsub), 256, 0, st>>>(d_sd, L, Linv, b);
+      IETI_LAUNCH_CHECK(c);
+      k_syrk<T><<<dim3(Tm * (Tm + 1) / 2, nsub), 256, 0, st>>>(d_sd, L, b);
+      IETI_LAUNCH_CHECK(c);
+    }
+  }
+  return IETI_OK;
+}
+
+template <typename T>
+static ieti_status factor_t(Ctx* c, cudaStream_t st) {
+  T* L = (T*)c->L;
+  T* Linv = (T*)c->Linv;
+  T* S = (T*)c->S;
+  T* W = (T*)c->W;
+  ieti_status r;
+  // factor buffer <- K_rr
+  if ((r = convert_copy<T>(c, c->K64, L, c->tot_A, st)) != IETI_OK) return r;
+  IETI_CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
+  if ((r = cholesky<T>(c, c->d_sd, c->sd_host, L, Linv, S, true, st)) != IETI_OK) return r;
+  IETI_CUDA_TRY(c, cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  IETI_CUDA_TRY(c, cudaStreamSynchronize(st));
+  if (*c->h_err) {
+    c->err = "non-positive pivot in the factorisation of subdomain " + std::to_string(*c->h_err - 1);
+    return IETI_ERR_SINGULAR_LOCAL;
+  }
+  const int nsub = c->nsub;
+  T* B = (T*)c->wr[0];
+  T* Y = (T*)c->wr[1];
+  T* X = (T*)c->wr[2];
+  // --- W = S_rIrI^-1 from the trailing factor block (identity right-hand sides)
+  {
+    std::vector<SolveDesc> dh(nsub);
+    int64_t off = 0;
+    int min_b0 = 1 << 30, max_rows = 0, max_col = 0;
+    for (int k = 0; k < nsub; ++k) {
+      const SubDev& s = c->sd_host[k];
+      dh[k].boff = off;
+      dh[k].b0 = s.nVp / NB;
+      dh[k].ldb = s.n - s.nVp;
+      dh[k].ncol = s.nI;
+      off += (int64_t)dh[k].ldb * dh[k].ncol;
+      min_b0 = std::min(min_b0, dh[k].b0);
+      max_rows = std::max(max_rows, dh[k].ldb);
+      max_col = std::max(max_col, s.nI);
+    }
+    SolveDesc* dd = (SolveDesc*)c->d_descbuf;   // scratch for descriptors (host-sized)
+    IETI_CUDA_TRY(c, cudaMemcpyAsync(dd, dh.data(), sizeof(SolveDesc) * nsub, cudaMemcpyHostToDevice, st));
+    k_identity_rhs<T><<<dim3(256, nsub), 256, 0, st>>>(c->d_sd, dd, B);
+    IETI_LAUNCH_CHECK(c);
+    if ((r = tri_solve<T>(c, c->d_sd, nsub, c->max_nblk, max_rows, max_col, dd, min_b0, L, Linv, B, Y, X, st)) != IETI_OK)
+      return r;
+    k_extract_W<T><<<dim3(256, nsub), 256, 0, st>>>(c->d_sd, dd, X, W);
+    IETI_LAUNCH_CHECK(c);
+    IETI_CUDA_TRY(c, cudaStreamSynchronize(st));
+  }
+  // --- Phi = K_rr^-1 K_rp (FP64 storage)
+  if (c->max_nP > 0) {
+    std::vector<SolveDesc> dh(nsub);
+    int64_t off = 0;
+    for (int k = 0; k < nsub; ++k) {
+      const SubDev& s = c->sd_host[k];
+      dh[k].boff = off;
+      dh[k].b0 = 0;
+      dh[k].ldb = s.n;
+      dh[k].ncol = s.nP;
+      off += (int64_t)s.n * s.nP;
+    }
+    SolveDesc* dd = (SolveDesc*)c->d_descbuf;
+    IETI_CUDA_TRY(c, cudaMemcpyAsync(dd, dh.data(), sizeof(SolveDesc) * nsub, cudaMemcpyHostToDevice, st));
+    k_load_Kp<T><<<dim3(256, nsub), 256, 0, st>>>(c->d_sd, dd, c->Kp64, B);
+    IETI_LAUNCH_CHECK(c);
+    if ((r = tri_solve<T>(c, c->d_sd, nsub, c->max_nblk, c->max_n, c->max_nP, dd, 0, L, Linv, B, Y, X, st)) != IETI_OK)
+      return r;
+    k_store_Phi<T><<<dim3(256, nsub), 256, 0, st>>>(c->d_sd, dd, X, c->Phi);
+    IETI_LAUNCH_CHECK(c);
+    IETI_CUDA_TRY(c, cudaStreamSynchronize(st));
+  }
+  return IETI_OK;
+}
+
+// coarse S_Pi (always FP64): assemble, factor, explicit inverse
+static ieti_status coarse_factor(Ctx* c, cudaStream_t st) {
+  const int ngp = (int)c->n_gp;
+  if (ngp == 0) return IETI_OK;
+  const int ldc = (int)(ceil_div(ngp, NB) * NB);
+  IETI_CUDA_TRY(c, cudaMemsetAsync(c->SPi, 0, sizeof(double) * ldc * ldc, st));
+  k_coarse_assemble<<<c->nsub, 256, 0, st>>>(c->d_sd, c->Kp64, c->Kpp64, c->Phi, c->d_P_glob,
+                                             c->SPi, ldc);
+  IETI_LAUNCH_CHECK(c);
+  k_pad_identity<<<1, 256, 0, st>>>(c->SPi, ngp, ldc);
+  IETI_LAUNCH_CHECK(c);
+  // one "subdomain" holding the coarse matrix; its factor lives in SPiInv's second half
+  SubDev cs{};
+  cs.A = 0;
+  cs.n = ldc;
+  cs.nblk = ldc / NB;
+  cs.nVp = 0;
+  cs.nI = 0;
+  cs.linv = 0;
+  std::vector<SubDev> csh{cs};
+  double* Lc = c->SPiInv + (int64_t)ldc * ldc;          // factor
+  double* Lci = Lc + (int64_t)ldc * ldc;                 // diagonal-block inverses
+  double* Bc = Lci + (int64_t)ldc * NB;
+  double* Yc = Bc + (int64_t)ldc * ldc;
+  SubDev* d_cs = (SubDev*)(Yc + (int64_t)ldc * ldc);
+  SolveDesc* d_desc = (SolveDesc*)(d_cs + 1);
+  IETI_CUDA_TRY(c, cudaMemcpyAsync(d_cs, &cs, sizeof(SubDev), cudaMemcpyHostToDevice, st));
+  IETI_CUDA_TRY(c, cudaMemcpyAsync(Lc, c->SPi, sizeof(double) * ldc * ldc, cudaMemcpyDeviceToDevice, st));
+  IETI_CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
+  ieti_status r;
+  if ((r = cholesky<double>(c, d_cs, csh, Lc, Lci, nullptr, false, st)) != IETI_OK) return r;
+  SolveDesc dh{0, 0, ldc, ldc, 0};
+  IETI_CUDA_TRY(c, cudaMemcpyAsync(d_desc, &dh, sizeof(SolveDesc), cudaMemcpyHostToDevice, st));
+  k_identity_rhs<double><<<dim3(64, 1), 256, 0, st>>>(d_cs, d_desc, Bc);
+  IETI_LAUNCH_CHECK(c);
+  if ((r = tri_solve<double>(c, d_cs, 1, cs.nblk, ldc, ldc, d_desc, 0, Lc, Lci, Bc, Yc, c->SPiInv, st)) != IETI_OK)
+    return r;
+  IETI_CUDA_TRY(c, cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  IETI_CUDA_TRY(c, cudaStreamSynchronize(st));
+  if (*c->h_err) {
+    c->err = "coarse matrix S_Pi is not positive definite";
+    return IETI_ERR_SINGULAR_LOCAL;
+  }
+  return IETI_OK;
+}
+
+ieti_status factor_all(Ctx* c, cudaStream_t st) {
+  ieti_status r = (c->prec == IETI_FP64) ? factor_t<double>(c, st) : factor_t<float>(c, st);
+  if (r != IETI_OK) return r;
+  return coarse_factor(c, st);
+}
+
+// full local solves on r-vectors (used by the solver), type T buffers
+template <typename T>
+ieti_status local_solve(Ctx* c, T* B, T* Y, int ncol, int blk0, int which, cudaStream_t st) {
+  (void)blk0;
+  (void)which;
+  std::vector<SolveDesc> dh(c->nsub);
+  for (int k = 0; k < c->nsub; ++k) {
+    const SubDev& s = c->sd_host[k];
+    dh[k].boff = s.rv * ncol;
+    dh[k].b0 = 0;
+    dh[k].ldb = s.n;
+    dh[k].ncol = ncol;
+  }
+  SolveDesc* dd = (SolveDesc*)c->d_descbuf;
+  IETI_CUDA_TRY(c, cudaMemcpyAsync(dd, dh.data(), sizeof(SolveDesc) * c->nsub, cudaMemcpyHostToDevice, st));
+  T* X = (T*)c->wr[2];
+  ieti_status r = tri_solve<T>(c, c->d_sd, c->nsub, c->max_nblk, c->max_n, ncol, dd, 0, (const T*)c->L,
+                               (const T*)c->Linv, B, Y, X, st);
+  return r;
+}
+template ieti_status local_solve<float>(Ctx*, float*, float*, int, int, int, cudaStream_t);
+template ieti_status local_solve<double>(Ctx*, double*, double*, int, int, int, cudaStream_t);
+
+}  // namespace ieti

@@ -1,0 +1,189 @@
+// Internal declarations of the GB300 IETI-DP library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/ieti.h"
+#include "model.h"
+
+namespace ieti {
+
+constexpr int NB = 64;            // panel width of the dense factorisations
+constexpr int MAX_RHS = 64;
+
+// Per-subdomain offsets (in elements) into the concatenated device buffers.
+// Local r DOFs of subdomain k are ordered [r_V, pad, r_I, pad] with the r_I
+// block starting at nVp (a multiple of NB) and n a multiple of NB; padding
+// DOFs are decoupled identity rows. The dense blocks are column-major with
+// leading dimension n.
+struct SubDev {
+  int64_t A;      // K_rr (n x n) in K64 and in the factor buffer
+  int64_t Kp;     // K_rp (n x nP)
+  int64_t Kpp;    // K_pp (nP x nP)
+  int64_t S;      // S_rIrI and W = S_rIrI^-1 (nI x nI)
+  int64_t linv;   // inverses of the NB x NB diagonal blocks of the factor
+  int64_t dof;    // local DOF table, n + nP entries
+  int64_t rv;     // r-vectors (n rows)
+  int64_t pv;     // p-vectors (nP rows)
+  int64_t iv;     // interface vectors (nI rows)
+  int n, nVp, nI, nP, nblk, pad;
+};
+
+// local DOF: direction d and global control-grid index (i, j, k) of its edge;
+// d = -1 for padding
+struct DofDev {
+  int d, i, j, k;
+};
+
+struct DeviceBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct Ctx {
+  Mesh mesh;
+  Tables1D tab;
+  Gram1D gram[3];
+  Topology topo;
+  std::vector<int> sub_of_patch;
+  std::vector<double> nu, ctrl, src;
+  int source_kind = 0, nrhs = 1;
+  bool affine = false;
+  std::string err;
+  int64_t launches = 0;
+
+  // sizes
+  int nsub = 0;
+  int64_t m_r = 0, n_gp = 0;
+  int max_n = 0, max_nI = 0, max_nP = 0, max_nblk = 0;
+  int64_t tot_A = 0, tot_Kp = 0, tot_Kpp = 0, tot_S = 0, tot_linv = 0, tot_dof = 0;
+  int64_t tot_rv = 0, tot_pv = 0, tot_iv = 0;
+  std::vector<SubDev> sd_host;
+  std::vector<double> gq_host;           // per patch: nu * L_c^2 / vol (affine path)
+  std::vector<int> elem_host;            // per element: q, s0, s1, s2
+  int64_t nelem = 0;
+
+  // device memory
+  std::vector<DeviceBuf> allocs;
+  SubDev* d_sd = nullptr;
+  DofDev* d_dof = nullptr;
+  int64_t* d_r_edge = nullptr;           // global edge id of each local r / p DOF (-1 pad)
+  int32_t* d_I_dual = nullptr;           // per interface DOF: multiplier index
+  double* d_I_sign = nullptr;
+  double* d_I_scale = nullptr;           // rho-scaling D^(k)
+  int32_t* d_P_glob = nullptr;           // per primal DOF: coarse index
+  int32_t* d_pair = nullptr;             // per multiplier: k1, i1, k2, i2
+  int32_t* d_patch_code = nullptr;       // per patch-local edge: local DOF index, -1 dropped
+  int64_t* d_patch_code_off = nullptr;
+  int32_t* d_sub_of_patch = nullptr;
+  int32_t* d_elem = nullptr;
+  double* d_tabN[3] = {nullptr, nullptr, nullptr};
+  double* d_tabdN[3] = {nullptr, nullptr, nullptr};
+  double* d_tabD[3] = {nullptr, nullptr, nullptr};
+  double* d_wq = nullptr;
+  double* d_ctrl = nullptr;
+  double* d_nu = nullptr;
+  double* d_src = nullptr;
+  double* d_gq = nullptr;
+  double* d_gram[3] = {nullptr, nullptr, nullptr};
+  int32_t* d_slab_of[3] = {nullptr, nullptr, nullptr};
+  int32_t* d_start[3] = {nullptr, nullptr, nullptr};
+  int32_t* d_nspan[3] = {nullptr, nullptr, nullptr};
+
+  double* K64 = nullptr;                 // assembled K_rr (kept for FP64 residuals)
+  double* Kp64 = nullptr;
+  double* Kpp64 = nullptr;
+  double* jr = nullptr;                  // loads (n x nrhs per subdomain)
+  double* jp = nullptr;
+  void* L = nullptr;                     // factor (double or float)
+  void* Linv = nullptr;
+  void* S = nullptr;                     // S_rIrI (nI x nI, full)
+  void* W = nullptr;                     // S_rIrI^-1
+  double* Phi = nullptr;                 // K_rr^-1 K_rp (n x nP), FP64 storage
+  double* SPi = nullptr;                 // coarse S_Pi (n_gp x n_gp)
+  double* SPiInv = nullptr;              // its inverse
+  int* d_err = nullptr;                  // device error word (subdomain id + 1 of a bad pivot)
+  int* h_err = nullptr;                  // pinned mirror
+
+  // work buffers
+  void* wr[3] = {nullptr, nullptr, nullptr};   // r-vector work (T or double), max_rhs columns
+  double* wr64[3] = {nullptr, nullptr, nullptr};
+  double* wp64 = nullptr;                // p-vector work
+  double* wi[2] = {nullptr, nullptr};    // interface work (nI x nrhs)
+  double* wq_part = nullptr;             // per subdomain primal partials
+  double* wc[2] = {nullptr, nullptr};    // coarse vectors
+  double* wlam[8] = {};                  // PCG vectors (m_r x nrhs)
+  double* wscal = nullptr;               // PCG scalars
+  double* wred = nullptr;                // reduction partials
+  int* wflag = nullptr;
+  double* wglob = nullptr;               // global edge vectors (nedge x nrhs)
+  double* whist = nullptr;               // PCG alpha/beta history of column 0
+  double* wnorm = nullptr;               // column norms
+  void* d_descbuf = nullptr;             // triangular-solve descriptors
+  int2* d_pcsr = nullptr;                // contributors (k, c) of each coarse DOF
+  int64_t* d_pcsr_off = nullptr;
+  int64_t* d_primal_edges = nullptr;
+  double* wres_r = nullptr;              // local residual r-vectors
+  double* wres_p = nullptr;
+  double* wlam_acc = nullptr;            // accumulated multipliers
+
+  bool assembled = false, factored = false, host_only = false;
+  ieti_precision prec = IETI_FP64;
+};
+
+// error helpers
+#define IETI_CUDA_TRY(ctx, call)                                                   \
+  do {                                                                             \
+    cudaError_t e__ = (call);                                                      \
+    if (e__ != cudaSuccess) {                                                      \
+      (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e__);            \
+      return IETI_ERR_CUDA;                                                        \
+    }                                                                              \
+  } while (0)
+
+#define IETI_LAUNCH_CHECK(ctx)                                                     \
+  do {                                                                             \
+    (ctx)->launches++;                                                             \
+    cudaError_t e__ = cudaGetLastError();                                          \
+    if (e__ != cudaSuccess) {                                                      \
+      (ctx)->err = std::string("kernel launch: ") + cudaGetErrorString(e__) +      \
+                   " at " + __FILE__ + ":" + std::to_string(__LINE__);             \
+      return IETI_ERR_CUDA;                                                        \
+    }                                                                              \
+  } while (0)
+
+// assembly
+ieti_status assemble_all(Ctx* c, cudaStream_t s);
+// factorisation
+ieti_status factor_all(Ctx* c, cudaStream_t s);
+// triangular solves with the local factors on the r-vectors in c->wr[...]
+template <typename T>
+ieti_status local_solve(Ctx* c, T* B, T* Y, int ncol, int blk0, int which, cudaStream_t s);
+// solver
+ieti_status apply_F(Ctx* c, const double* lam, double* y, int nrhs, bool fp32_ops, cudaStream_t s);
+ieti_status apply_precond(Ctx* c, const double* r, double* z, int nrhs, bool fp32_ops, cudaStream_t s);
+ieti_status interface_rhs(Ctx* c, const double* jr, const double* jp, double* b, double* dprime,
+                          int nrhs, cudaStream_t s);
+ieti_status solve_all(Ctx* c, const double* lam0, double tol, int maxit, double tol_field,
+                      double* a, double* lam_out, ieti_solve_info* info, cudaStream_t s);
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// multi-column per-subdomain vectors: subdomain k's block of an nrhs-column
+// vector starts at (offset_k * nrhs), column stride = local size
+__host__ __device__ inline int64_t RV(const SubDev& s, int i, int col, int nrhs) {
+  return s.rv * nrhs + i + (int64_t)s.n * col;
+}
+__host__ __device__ inline int64_t PV(const SubDev& s, int c, int col, int nrhs) {
+  return s.pv * nrhs + c + (int64_t)s.nP * col;
+}
+__host__ __device__ inline int64_t IV(const SubDev& s, int i, int col, int nrhs) {
+  return s.iv * nrhs + i + (int64_t)s.nI * col;
+}
+
+}  // namespace ieti

@@ -1,0 +1,858 @@
+// Interface operator, Dirichlet preconditioner, PCG, right-hand side and
+// recovery of the dual-primal method (Eqs. (7)-(10)).
+//
+// With the r DOFs ordered [r_V, r_I] the jump operator only touches r_I, and
+// B_r K_rr^-1 B_r^T = sum_k B_k (K_rr^-1)_II B_k^T with (K_rr^-1)_II = S_rIrI^-1.
+// Both the F-apply and the preconditioner are therefore batched dense products
+// with the per-subdomain interface blocks W_k = S_rIrI^-1 and S_rIrI:
+//   y = F_DP lam = sum_k B_k W_k B_k^T lam + G S_Pi^-1 G^T lam,
+//   G = sum_k B_k Phi_I^(k) C_k,
+// followed by a deterministic gather over the two subdomains of each multiplier.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+
+namespace ieti {
+
+constexpr int LOC_CT = 8;      // RHS columns per CTA in the local products
+constexpr int LOC_ROWS = 32;   // rows of W per CTA (4 per warp)
+constexpr int RED_BLOCKS = 304;
+constexpr int SC = 16;         // PCG scalars per column
+
+// ---------------------------------------------------------------------------
+// local interface products: t_k = M_k u_k, u_k = sign * scale * x[dual]
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_local(const SubDev* sd, const T* M, const int32_t* I_dual,
+                                               const double* I_sign, const double* I_scale,
+                                               const double* x, int64_t ldx, double* t, int nrhs) {
+  const int k = blockIdx.z;
+  const SubDev s = sd[k];
+  const int nI = s.nI;
+  const int r0 = blockIdx.x * LOC_ROWS;
+  if (r0 >= nI) return;
+  const int c0 = blockIdx.y * LOC_CT;
+  if (c0 >= nrhs) return;
+  const int nc = min(LOC_CT, nrhs - c0);
+  extern __shared__ __align__(16) unsigned char sm[];
+  T* u = reinterpret_cast<T*>(sm);             // nI x LOC_CT
+  for (int i = threadIdx.x; i < nI; i += blockDim.x) {
+    double w = I_sign[s.iv + i] * (I_scale ? I_scale[s.iv + i] : 1.0);
+    int l = I_dual[s.iv + i];
+#pragma unroll
+    for (int cc = 0; cc < LOC_CT; ++cc) u[i * LOC_CT + cc] = (cc < nc) ? (T)(w * x[l + ldx * (c0 + cc)]) : (T)0;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const T* Mk = M + s.S;
+  for (int rr = warp; rr < LOC_ROWS; rr += 8) {
+    const int i = r0 + rr;
+    if (i >= nI) break;
+    const T* col = Mk + (int64_t)nI * i;     // symmetric: column i = row i
+    T acc[LOC_CT];
+#pragma unroll
+    for (int cc = 0; cc < LOC_CT; ++cc) acc[cc] = 0;
+    for (int j = lane; j < nI; j += 32) {
+      T m = col[j];
+      const T* uj = u + j * LOC_CT;
+#pragma unroll
+      for (int cc = 0; cc < LOC_CT; ++cc) acc[cc] += m * uj[cc];
+    }
+#pragma unroll
+    for (int cc = 0; cc < LOC_CT; ++cc) {
+      T v = acc[cc];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      acc[cc] = v;
+    }
+    if (lane < nc) {
+      T v = acc[0];
+#pragma unroll
+      for (int cc = 1; cc < LOC_CT; ++cc)
+        if (lane == cc) v = acc[cc];
+      t[IV(s, i, c0 + lane, nrhs)] = (double)v;
+    }
+  }
+}
+
+// primal partials q_k = Phi_I^(k)T B_k^T x (per subdomain, FP64)
+__global__ void k_phiT(const SubDev* sd, const double* Phi, const int32_t* I_dual, const double* I_sign,
+                       const double* x, int64_t ldx, double* qpart, int nrhs) {
+  const int k = blockIdx.x;
+  const SubDev s = sd[k];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  for (int t = warp; t < s.nP * nrhs; t += nw) {
+    int c = t % s.nP, col = t / s.nP;
+    const double* ph = Phi + s.Kp + s.nVp + (int64_t)s.n * c;
+    double acc = 0;
+    for (int i = lane; i < s.nI; i += 32) acc += ph[i] * I_sign[s.iv + i] * x[I_dual[s.iv + i] + ldx * col];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) qpart[PV(s, c, col, nrhs)] = acc;
+  }
+}
+
+// coarse: q_g = sum of the contributors (k, c) of coarse DOF g, yc = S_Pi^-1 q
+__global__ void k_coarse(const SubDev* sd, const int64_t* pcsr_off, const int2* pcsr, const double* qpart,
+                         const double* SPiInv, int ngp, int ldc, double* yc, int nrhs) {
+  extern __shared__ double q[];                 // ngp x nrhs
+  for (int t = threadIdx.x; t < ngp * nrhs; t += blockDim.x) {
+    int g = t % ngp, col = t / ngp;
+    double acc = 0.0;
+    for (int64_t e = pcsr_off[g]; e < pcsr_off[g + 1]; ++e) {
+      int2 kc = pcsr[e];
+      acc += qpart[PV(sd[kc.x], kc.y, col, nrhs)];
+    }
+    q[t] = acc;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  for (int t = blockIdx.x * nw + warp; t < ngp * nrhs; t += gridDim.x * nw) {
+    int g = t % ngp, col = t / ngp;
+    double acc = 0;
+    for (int h = lane; h < ngp; h += 32) acc += SPiInv[h + (int64_t)ldc * g] * q[h + ngp * col];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) yc[t] = acc;
+  }
+}
+
+__device__ inline double block_sum(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  return red[0];
+}
+
+// y[l] = e_sign e[l] + sum_sides sign (t_sign t_k[i] + phi_sign Phi_I^(k)[i,:] yc[C_k])
+// and an optional per-block partial of <y, dotv>
+__global__ void __launch_bounds__(256) k_gather_F(const SubDev* sd, const int32_t* pair, const double* t,
+                                                  const double* Phi, const int32_t* P_glob, const double* yc,
+                                                  int ngp, int64_t m_r, int nrhs, double* y, const double* dotv,
+                                                  double* part, const double* e_in, double phi_sign) {
+  __shared__ double red[256];
+  const int col = blockIdx.y;
+  double mydot = 0;
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < m_r; l += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0;
+    for (int side = 0; side < 2; ++side) {
+      int k = pair[l * 4 + 2 * side], i = pair[l * 4 + 2 * side + 1];
+      const SubDev s = sd[k];
+      double w = t ? t[IV(s, i, col, nrhs)] : 0.0;
+      if (yc) {
+        const double* ph = Phi + s.Kp + s.nVp + i;
+        double g = 0;
+        for (int c = 0; c < s.nP; ++c) g += ph[(int64_t)s.n * c] * yc[P_glob[s.pv + c] + (int64_t)ngp * col];
+        w += phi_sign * g;
+      }
+      v += (side == 0) ? w : -w;
+    }
+    if (e_in) v += e_in[l + m_r * col];
+    y[l + m_r * col] = v;
+    if (dotv) mydot += v * dotv[l + m_r * col];
+  }
+  if (part) {
+    double s = block_sum(mydot, red);
+    if (threadIdx.x == 0) part[blockIdx.x + gridDim.x * col] = s;
+  }
+}
+
+// preconditioner gather: z[l] = sum_sides sign * scale * t_k[i]; optional partial <z, dotv>
+__global__ void __launch_bounds__(256) k_gather_P(const SubDev* sd, const int32_t* pair, const double* I_scale,
+                                                  const double* t, int64_t m_r, int nrhs, double* z,
+                                                  const double* dotv, double* part) {
+  __shared__ double red[256];
+  const int col = blockIdx.y;
+  double mydot = 0;
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < m_r; l += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0;
+    for (int side = 0; side < 2; ++side) {
+      int k = pair[l * 4 + 2 * side], i = pair[l * 4 + 2 * side + 1];
+      const SubDev s = sd[k];
+      double w = I_scale[s.iv + i] * t[IV(s, i, col, nrhs)];
+      v += (side == 0) ? w : -w;
+    }
+    z[l + m_r * col] = v;
+    if (dotv) mydot += v * dotv[l + m_r * col];
+  }
+  if (part) {
+    double s = block_sum(mydot, red);
+    if (threadIdx.x == 0) part[blockIdx.x + gridDim.x * col] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// PCG pieces: FP64 vectors, device-side scalars, one column per load case.
+// scalars per column (stride SC): 0 rz, 1 pq, 2 rr, 3 bb, 4 alpha, 5 beta,
+// 7 done (0/1), 8 iterations
+// ---------------------------------------------------------------------------
+
+__global__ void k_dot_part(const double* a, const double* b, int64_t m, double* part) {
+  __shared__ double red[256];
+  const int col = blockIdx.y;
+  double acc = 0;
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < m; l += (int64_t)gridDim.x * blockDim.x)
+    acc += a[l + m * col] * b[l + m * col];
+  double s = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x + gridDim.x * col] = s;
+}
+
+__device__ inline double sum_parts(const double* part, int nb, int col) {
+  double s = 0;
+  for (int i = 0; i < nb; ++i) s += part[i + nb * col];
+  return s;
+}
+
+// which: 0 rz <- sum; 1 alpha from pq; 2 rr & convergence (counts an iteration);
+//        3 beta from rz_new; 4 bb <- sum; 5 rr & convergence (initial, no count)
+__global__ void k_scalar(double* scal, const double* part, int nb, int nrhs, int which, double tol2,
+                         double* hist, int hist_cap) {
+  const int col = threadIdx.x;
+  if (col >= nrhs) return;
+  double* S = scal + SC * col;
+  double v = sum_parts(part, nb, col);
+  if (which == 0) {
+    S[0] = v;
+  } else if (which == 4) {
+    S[3] = v;
+  } else if (which == 1) {
+    S[1] = v;
+    S[4] = (S[7] != 0.0 || v == 0.0) ? 0.0 : S[0] / v;
+  } else if (which == 2 || which == 5) {
+    if (S[7] == 0.0) {
+      S[2] = v;
+      if (which == 2) {
+        S[8] += 1.0;
+        int it = (int)S[8];
+        if (col == 0 && hist && it <= hist_cap) hist[2 * (it - 1)] = S[4];
+      }
+      if (v <= tol2 * S[3]) S[7] = 1.0;
+    }
+  } else if (which == 3) {
+    if (S[7] == 0.0) {
+      S[5] = (S[0] != 0.0) ? v / S[0] : 0.0;
+      S[0] = v;
+      int it = (int)S[8];
+      if (col == 0 && hist && it >= 1 && it <= hist_cap) hist[2 * (it - 1) + 1] = S[5];
+    }
+  }
+}
+
+// x += alpha p ; r -= alpha q ; partial <r, r>
+__global__ void k_axpy2(double* x, double* r, const double* p, const double* q, const double* scal, int64_t m,
+                        double* part) {
+  __shared__ double red[256];
+  const int col = blockIdx.y;
+  const double alpha = scal[SC * col + 4];
+  const bool done = scal[SC * col + 7] != 0.0;
+  double acc = 0;
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < m; l += (int64_t)gridDim.x * blockDim.x) {
+    int64_t o = l + m * col;
+    double rv = r[o];
+    if (!done) {
+      x[o] += alpha * p[o];
+      rv -= alpha * q[o];
+      r[o] = rv;
+    }
+    acc += rv * rv;
+  }
+  double s = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x + gridDim.x * col] = s;
+}
+
+// p = z + beta p (first: p = z)
+__global__ void k_update_p(double* p, const double* z, const double* scal, int64_t m, int first) {
+  const int col = blockIdx.y;
+  const double beta = first ? 0.0 : scal[SC * col + 5];
+  const bool done = scal[SC * col + 7] != 0.0;
+  if (done && !first) return;
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < m; l += (int64_t)gridDim.x * blockDim.x) {
+    int64_t o = l + m * col;
+    p[o] = z[o] + beta * p[o];
+  }
+}
+
+__global__ void k_sub(double* r, const double* b, const double* y, int64_t n) {
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x)
+    r[l] = b[l] - y[l];
+}
+
+__global__ void k_add(double* a, const double* b, int64_t n) {
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x)
+    a[l] += b[l];
+}
+
+__global__ void k_all_done(const double* scal, int nrhs, int* flag) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int all = 1;
+    for (int c = 0; c < nrhs; ++c) all &= scal[SC * c + 7] != 0.0 ? 1 : 0;
+    *flag = all;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// r-vector kernels (loads, recovery, residual)
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void k_rvec_to_T(const SubDev* sd, const double* src, T* dst, int nrhs) {
+  const int k = blockIdx.y;
+  const SubDev s = sd[k];
+  const int64_t tot = (int64_t)s.n * nrhs;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x)
+    dst[s.rv * nrhs + t] = (T)src[s.rv * nrhs + t];
+}
+
+template <typename T>
+__global__ void k_rvec_from_T(const SubDev* sd, const T* src, double* dst, int nrhs) {
+  const int k = blockIdx.y;
+  const SubDev s = sd[k];
+  const int64_t tot = (int64_t)s.n * nrhs;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x)
+    dst[s.rv * nrhs + t] = (double)src[s.rv * nrhs + t];
+}
+
+// e[l] = v_k1[I] - v_k2[I] (r_I rows of the r-vectors)
+__global__ void k_gather_e(const SubDev* sd, const int32_t* pair, const double* v, int64_t m_r, int nrhs,
+                           double* e) {
+  const int col = blockIdx.y;
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < m_r; l += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0;
+    for (int side = 0; side < 2; ++side) {
+      int k = pair[l * 4 + 2 * side], i = pair[l * 4 + 2 * side + 1];
+      const SubDev s = sd[k];
+      double w = v[RV(s, s.nVp + i, col, nrhs)];
+      acc += (side == 0) ? w : -w;
+    }
+    e[l + m_r * col] = acc;
+  }
+}
+
+// part_k = j_p - K_rp^T v  (p rows of each subdomain)
+__global__ void k_dprime_part(const SubDev* sd, const double* Kp, const double* jp, const double* v, int nrhs,
+                              double* part) {
+  const int k = blockIdx.x;
+  const SubDev s = sd[k];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  for (int t = warp; t < s.nP * nrhs; t += nw) {
+    int c = t % s.nP, col = t / s.nP;
+    const double* a = Kp + s.Kp + (int64_t)s.n * c;
+    const double* vv = v + RV(s, 0, col, nrhs);
+    double acc = 0;
+    for (int i = lane; i < s.n; i += 32) acc += a[i] * vv[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) part[PV(s, c, col, nrhs)] = jp[PV(s, c, col, nrhs)] - acc;
+  }
+}
+
+// rhs_k = j_r - K_rp (p1 + p2)_k - B_k^T lam  (FP64, n rows per subdomain)
+__global__ void k_recover_rhs(const SubDev* sd, const double* Kp, const double* jr, const double* p1,
+                              const double* p2, int ngp, const int32_t* P_glob, const int32_t* I_dual,
+                              const double* I_sign, const double* lam, int64_t m_r, int nrhs, double* out) {
+  const int k = blockIdx.y;
+  const SubDev s = sd[k];
+  const int64_t tot = (int64_t)s.n * nrhs;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(t % s.n), col = (int)(t / s.n);
+    double v = jr[RV(s, i, col, nrhs)];
+    for (int c = 0; c < s.nP; ++c) {
+      int64_t g = P_glob[s.pv + c] + (int64_t)ngp * col;
+      v -= Kp[s.Kp + i + (int64_t)s.n * c] * (p1[g] + p2[g]);
+    }
+    int ii = i - s.nVp;
+    if (ii >= 0 && ii < s.nI) v -= I_sign[s.iv + ii] * lam[I_dual[s.iv + ii] + m_r * col];
+    out[RV(s, i, col, nrhs)] = v;
+  }
+}
+
+// global field from the local solution: r_V DOFs and the "+" copy of r_I DOFs
+__global__ void k_scatter_a(const SubDev* sd, const int64_t* r_edge, const double* I_sign, const double* ar,
+                            int64_t nedge, int nrhs, double* a, int accumulate) {
+  const int k = blockIdx.y;
+  const SubDev s = sd[k];
+  const int64_t tot = (int64_t)s.n * nrhs;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(t % s.n), col = (int)(t / s.n);
+    int64_t e = r_edge[s.dof + i];
+    if (e < 0) continue;
+    int ii = i - s.nVp;
+    if (ii >= 0 && ii < s.nI && I_sign[s.iv + ii] < 0) continue;
+    double v = ar[RV(s, i, col, nrhs)];
+    if (accumulate) a[e + nedge * col] += v;
+    else a[e + nedge * col] = v;
+  }
+}
+
+__global__ void k_scatter_primal(const int64_t* primal_edges, const double* p1, const double* p2, int ngp,
+                                 int64_t nedge, int nrhs, double* a, int accumulate) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ngp * nrhs; t += gridDim.x * blockDim.x) {
+    int g = t % ngp, col = t / ngp;
+    double v = p1[t] + p2[t];
+    int64_t o = primal_edges[g] + nedge * col;
+    if (accumulate) a[o] += v;
+    else a[o] = v;
+  }
+}
+
+// local residual r^(k) = j^(k) - K^(k) x^(k) - B_k^T lam, x gathered from the
+// global field. The multiplier term cancels in the assembled sum but must be
+// removed from the local loads of a refinement step: otherwise those loads
+// carry the full multipliers, and a PCG tolerance relative to them never gets
+// below the first solve's absolute error. The assembled residual
+// sum_k R_k^T (j^(k) - K^(k) x^(k)) is scatter-added into R when given.
+__global__ void __launch_bounds__(256) k_residual(const SubDev* sd, const int64_t* r_edge, const double* K64,
+                                                  const double* Kp, const double* Kpp, const double* jr,
+                                                  const double* jp, const double* a, int64_t nedge, int nrhs,
+                                                  const int32_t* I_dual, const double* I_sign, const double* lam,
+                                                  int64_t m_r, double* rr_out, double* rp_out, double* R) {
+  const int k = blockIdx.y;
+  const SubDev s = sd[k];
+  const int Rn = s.n + s.nP;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int row = blockIdx.x * 8 + warp;
+  if (row >= Rn) return;
+  const int64_t e_row = r_edge[s.dof + row];
+  for (int col = 0; col < nrhs; ++col) {
+    double acc = 0;
+    const double* kc;
+    const double* kpc;
+    int64_t kp_stride;
+    if (row < s.n) {
+      kc = K64 + s.A + (int64_t)s.n * row;         // symmetric: column = row
+      kpc = Kp + s.Kp + row;
+      kp_stride = s.n;
+    } else {
+      const int c = row - s.n;
+      kc = Kp + s.Kp + (int64_t)s.n * c;
+      kpc = Kpp + s.Kpp + c;
+      kp_stride = s.nP;
+    }
+    for (int j = lane; j < s.n; j += 32) {
+      int64_t e = r_edge[s.dof + j];
+      if (e >= 0) acc += kc[j] * a[e + nedge * col];
+    }
+    for (int j = lane; j < s.nP; j += 32) {
+      int64_t e = r_edge[s.dof + s.n + j];
+      acc += kpc[kp_stride * j] * a[e + nedge * col];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      double v;
+      if (row < s.n) {
+        v = (e_row < 0) ? 0.0 : jr[RV(s, row, col, nrhs)] - acc;
+        double vl = v;
+        const int ii = row - s.nVp;
+        if (ii >= 0 && ii < s.nI) vl -= I_sign[s.iv + ii] * lam[I_dual[s.iv + ii] + m_r * col];
+        rr_out[RV(s, row, col, nrhs)] = vl;
+      } else {
+        v = jp[PV(s, row - s.n, col, nrhs)] - acc;
+        rp_out[PV(s, row - s.n, col, nrhs)] = v;
+      }
+      if (R && e_row >= 0) atomicAdd(R + e_row + nedge * col, v);
+    }
+  }
+}
+
+__global__ void k_colnorm2(const double* v, int64_t m, double* out) {
+  __shared__ double red[256];
+  const int col = blockIdx.x;
+  double acc = 0;
+  for (int64_t l = threadIdx.x; l < m; l += blockDim.x) acc += v[l + m * col] * v[l + m * col];
+  double s = block_sum(acc, red);
+  if (threadIdx.x == 0) out[col] = s;
+}
+
+// ---------------------------------------------------------------------------
+// host orchestration
+// ---------------------------------------------------------------------------
+
+template <typename T>
+static ieti_status launch_local(Ctx* c, const T* M, const double* x, const double* scale, double* t, int nrhs,
+                                cudaStream_t st) {
+  if (c->max_nI == 0) return IETI_OK;
+  size_t smem = (size_t)c->max_nI * LOC_CT * sizeof(T);
+  if (smem > 48 * 1024)
+    IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_local<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((unsigned)ceil_div(c->max_nI, LOC_ROWS), (unsigned)ceil_div(nrhs, LOC_CT), (unsigned)c->nsub);
+  k_local<T><<<grid, 256, smem, st>>>(c->d_sd, M, c->d_I_dual, c->d_I_sign, scale, x, c->m_r, t, nrhs);
+  IETI_LAUNCH_CHECK(c);
+  return IETI_OK;
+}
+
+static int gather_blocks(Ctx* c) {
+  return (int)std::min<int64_t>(RED_BLOCKS, std::max<int64_t>(1, ceil_div(c->m_r, 256)));
+}
+
+static ieti_status coarse_solve(Ctx* c, const double* qpart, double* yc, int nrhs, cudaStream_t st) {
+  const int ngp = (int)c->n_gp;
+  if (ngp == 0) return IETI_OK;
+  const int ldc = (int)(ceil_div(ngp, NB) * NB);
+  size_t smem = sizeof(double) * ngp * nrhs;
+  if (smem > 48 * 1024)
+    IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int blocks = (int)std::min<int64_t>(64, std::max<int64_t>(1, ceil_div((int64_t)ngp * nrhs, 8)));
+  k_coarse<<<blocks, 256, smem, st>>>(c->d_sd, c->d_pcsr_off, c->d_pcsr, qpart, c->SPiInv, ngp, ldc, yc, nrhs);
+  IETI_LAUNCH_CHECK(c);
+  return IETI_OK;
+}
+
+// y = F_DP lam (+ optional partial <y, dotv> per gather block)
+static ieti_status apply_F_ex(Ctx* c, const double* lam, double* y, int nrhs, bool fp32, const double* dotv,
+                              double* part, cudaStream_t st) {
+  ieti_status r;
+  double* t = c->wi[0];
+  if (fp32) r = launch_local<float>(c, (const float*)c->W, lam, nullptr, t, nrhs, st);
+  else r = launch_local<double>(c, (const double*)c->W, lam, nullptr, t, nrhs, st);
+  if (r != IETI_OK) return r;
+  const bool coarse = c->n_gp > 0;
+  if (coarse) {
+    k_phiT<<<c->nsub, 256, 0, st>>>(c->d_sd, c->Phi, c->d_I_dual, c->d_I_sign, lam, c->m_r, c->wq_part, nrhs);
+    IETI_LAUNCH_CHECK(c);
+    if ((r = coarse_solve(c, c->wq_part, c->wc[0], nrhs, st)) != IETI_OK) return r;
+  }
+  k_gather_F<<<dim3(gather_blocks(c), nrhs), 256, 0, st>>>(c->d_sd, c->d_pair, t, c->Phi, c->d_P_glob,
+                                                          coarse ? c->wc[0] : nullptr, (int)c->n_gp, c->m_r, nrhs,
+                                                          y, dotv, part, nullptr, 1.0);
+  IETI_LAUNCH_CHECK(c);
+  return IETI_OK;
+}
+
+ieti_status apply_F(Ctx* c, const double* lam, double* y, int nrhs, bool fp32, cudaStream_t st) {
+  return apply_F_ex(c, lam, y, nrhs, fp32, nullptr, nullptr, st);
+}
+
+static ieti_status apply_precond_ex(Ctx* c, const double* rv, double* z, int nrhs, bool fp32, const double* dotv,
+                                    double* part, cudaStream_t st) {
+  ieti_status r;
+  double* t = c->wi[1];
+  if (fp32) r = launch_local<float>(c, (const float*)c->S, rv, c->d_I_scale, t, nrhs, st);
+  else r = launch_local<double>(c, (const double*)c->S, rv, c->d_I_scale, t, nrhs, st);
+  if (r != IETI_OK) return r;
+  k_gather_P<<<dim3(gather_blocks(c), nrhs), 256, 0, st>>>(c->d_sd, c->d_pair, c->d_I_scale, t, c->m_r, nrhs, z,
+                                                          dotv, part);
+  IETI_LAUNCH_CHECK(c);
+  return IETI_OK;
+}
+
+ieti_status apply_precond(Ctx* c, const double* rv, double* z, int nrhs, bool fp32, cudaStream_t st) {
+  return apply_precond_ex(c, rv, z, nrhs, fp32, nullptr, nullptr, st);
+}
+
+// full local solves x = K_rr^-1 b on r-vectors (FP64 in, FP64 out)
+static ieti_status full_solve(Ctx* c, const double* b, double* x, int nrhs, cudaStream_t st) {
+  dim3 g(256, c->nsub);
+  ieti_status r;
+  if (c->prec == IETI_FP64) {
+    double* B = (double*)c->wr[0];
+    k_rvec_to_T<double><<<g, 256, 0, st>>>(c->d_sd, b, B, nrhs);
+    IETI_LAUNCH_CHECK(c);
+    if ((r = local_solve<double>(c, B, (double*)c->wr[1], nrhs, 0, 0, st)) != IETI_OK) return r;
+    k_rvec_from_T<double><<<g, 256, 0, st>>>(c->d_sd, (const double*)c->wr[2], x, nrhs);
+  } else {
+    float* B = (float*)c->wr[0];
+    k_rvec_to_T<float><<<g, 256, 0, st>>>(c->d_sd, b, B, nrhs);
+    IETI_LAUNCH_CHECK(c);
+    if ((r = local_solve<float>(c, B, (float*)c->wr[1], nrhs, 0, 0, st)) != IETI_OK) return r;
+    k_rvec_from_T<float><<<g, 256, 0, st>>>(c->d_sd, (const float*)c->wr[2], x, nrhs);
+  }
+  IETI_LAUNCH_CHECK(c);
+  return IETI_OK;
+}
+
+// b = e - G S_Pi^-1 d' from local loads (jr, jp); ycr <- S_Pi^-1 d' (kept for recovery)
+ieti_status interface_rhs(Ctx* c, const double* jr, const double* jp, double* b, double* ycr, int nrhs,
+                          cudaStream_t st) {
+  ieti_status r;
+  double* v = c->wr64[0];
+  if ((r = full_solve(c, jr, v, nrhs, st)) != IETI_OK) return r;
+  const int gb = gather_blocks(c);
+  double* e = c->wlam[7];
+  k_gather_e<<<dim3(gb, nrhs), 256, 0, st>>>(c->d_sd, c->d_pair, v, c->m_r, nrhs, e);
+  IETI_LAUNCH_CHECK(c);
+  const bool coarse = c->n_gp > 0;
+  if (coarse) {
+    k_dprime_part<<<c->nsub, 256, 0, st>>>(c->d_sd, c->Kp64, jp, v, nrhs, c->wq_part);
+    IETI_LAUNCH_CHECK(c);
+    if ((r = coarse_solve(c, c->wq_part, ycr, nrhs, st)) != IETI_OK) return r;
+  }
+  k_gather_F<<<dim3(gb, nrhs), 256, 0, st>>>(c->d_sd, c->d_pair, nullptr, c->Phi, c->d_P_glob,
+                                            coarse ? ycr : nullptr, (int)c->n_gp, c->m_r, nrhs, b, nullptr,
+                                            nullptr, e, -1.0);
+  IETI_LAUNCH_CHECK(c);
+  return IETI_OK;
+}
+
+// PCG on F_DP lam = b (lam holds the initial guess on entry, or zero)
+static ieti_status pcg(Ctx* c, const double* b, double* lam, bool zero_start, double tol, int maxit, bool fp32,
+                       int* iters, double* relres, double* kappa, cudaStream_t st) {
+  const int nrhs = c->nrhs;
+  const int64_t m = c->m_r;
+  double* r = c->wlam[0];
+  double* z = c->wlam[1];
+  double* p = c->wlam[2];
+  double* q = c->wlam[3];
+  double* part = c->wred;
+  double* scal = c->wscal;
+  const int gb = gather_blocks(c);
+  const dim3 vg(gb, nrhs);
+  const double tol2 = tol * tol;
+  const int hist_cap = 4096;
+  ieti_status e;
+  IETI_CUDA_TRY(c, cudaMemsetAsync(scal, 0, sizeof(double) * SC * nrhs, st));
+  if (zero_start) {
+    IETI_CUDA_TRY(c, cudaMemsetAsync(lam, 0, sizeof(double) * m * nrhs, st));
+    IETI_CUDA_TRY(c, cudaMemcpyAsync(r, b, sizeof(double) * m * nrhs, cudaMemcpyDeviceToDevice, st));
+  } else {
+    if ((e = apply_F_ex(c, lam, q, nrhs, fp32, nullptr, nullptr, st)) != IETI_OK) return e;
+    k_sub<<<1216, 256, 0, st>>>(r, b, q, m * nrhs);
+    IETI_LAUNCH_CHECK(c);
+  }
+  k_dot_part<<<vg, 256, 0, st>>>(b, b, m, part);
+  IETI_LAUNCH_CHECK(c);
+  k_scalar<<<1, 64, 0, st>>>(scal, part, gb, nrhs, 4, tol2, nullptr, 0);
+  IETI_LAUNCH_CHECK(c);
+  k_dot_part<<<vg, 256, 0, st>>>(r, r, m, part);
+  IETI_LAUNCH_CHECK(c);
+  k_scalar<<<1, 64, 0, st>>>(scal, part, gb, nrhs, 5, tol2, nullptr, 0);
+  IETI_LAUNCH_CHECK(c);
+  if ((e = apply_precond_ex(c, r, z, nrhs, fp32, r, part, st)) != IETI_OK) return e;
+  k_scalar<<<1, 64, 0, st>>>(scal, part, gb, nrhs, 0, tol2, nullptr, 0);
+  IETI_LAUNCH_CHECK(c);
+  k_update_p<<<vg, 256, 0, st>>>(p, z, scal, m, 1);
+  IETI_LAUNCH_CHECK(c);
+  const int check_every = 4;
+  int it = 0;
+  for (; it < maxit; ++it) {
+    if (it % check_every == 0) {
+      k_all_done<<<1, 32, 0, st>>>(scal, nrhs, c->wflag);
+      IETI_LAUNCH_CHECK(c);
+      IETI_CUDA_TRY(c, cudaMemcpyAsync(c->h_err, c->wflag, sizeof(int), cudaMemcpyDeviceToHost, st));
+      IETI_CUDA_TRY(c, cudaStreamSynchronize(st));
+      if (*c->h_err) break;
+    }
+    if ((e = apply_F_ex(c, p, q, nrhs, fp32, p, part, st)) != IETI_OK) return e;
+    k_scalar<<<1, 64, 0, st>>>(scal, part, gb, nrhs, 1, tol2, nullptr, 0);
+    IETI_LAUNCH_CHECK(c);
+    k_axpy2<<<vg, 256, 0, st>>>(lam, r, p, q, scal, m, part);
+    IETI_LAUNCH_CHECK(c);
+    k_scalar<<<1, 64, 0, st>>>(scal, part, gb, nrhs, 2, tol2, c->whist, hist_cap);
+    IETI_LAUNCH_CHECK(c);
+    if ((e = apply_precond_ex(c, r, z, nrhs, fp32, r, part, st)) != IETI_OK) return e;
+    k_scalar<<<1, 64, 0, st>>>(scal, part, gb, nrhs, 3, tol2, c->whist, hist_cap);
+    IETI_LAUNCH_CHECK(c);
+    k_update_p<<<vg, 256, 0, st>>>(p, z, scal, m, 0);
+    IETI_LAUNCH_CHECK(c);
+  }
+  std::vector<double> hs(SC * nrhs);
+  IETI_CUDA_TRY(c, cudaMemcpyAsync(hs.data(), scal, sizeof(double) * SC * nrhs, cudaMemcpyDeviceToHost, st));
+  IETI_CUDA_TRY(c, cudaStreamSynchronize(st));
+  int itmax = 0;
+  double rel = 0;
+  bool conv = true;
+  for (int col = 0; col < nrhs; ++col) {
+    itmax = std::max(itmax, (int)hs[SC * col + 8]);
+    double bb = hs[SC * col + 3];
+    double rr = hs[SC * col + 2];
+    rel = std::max(rel, bb > 0 ? std::sqrt(rr / bb) : 0.0);
+    conv &= hs[SC * col + 7] != 0.0;
+  }
+  *iters = itmax;
+  *relres = rel;
+  // Lanczos estimate of kappa(M^-1 F) from the CG coefficients of column 0
+  int n = std::min((int)hs[8], hist_cap);
+  *kappa = 0;
+  if (n >= 2) {
+    std::vector<double> h(2 * n);
+    IETI_CUDA_TRY(c, cudaMemcpy(h.data(), c->whist, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost));
+    // tridiagonal T: diag 1/a_j + b_{j-1}/a_{j-1}, off sqrt(b_j)/a_j; extreme eigenvalues by bisection
+    std::vector<double> dg(n), of(n, 0.0);
+    for (int j = 0; j < n; ++j) {
+      dg[j] = 1.0 / h[2 * j] + (j > 0 ? h[2 * (j - 1) + 1] / h[2 * (j - 1)] : 0.0);
+      if (j + 1 < n) of[j] = std::sqrt(std::max(h[2 * j + 1], 0.0)) / h[2 * j];
+    }
+    auto count_below = [&](double x) {   // Sturm count of eigenvalues < x
+      int cnt = 0;
+      double d = 1.0;
+      for (int j = 0; j < n; ++j) {
+        double o = (j > 0) ? of[j - 1] : 0.0;
+        d = dg[j] - x - ((j > 0) ? o * o / d : 0.0);
+        if (d == 0.0) d = -1e-300;
+        if (d < 0) ++cnt;
+      }
+      return cnt;
+    };
+    double lo = 0, hi = 0;
+    for (int j = 0; j < n; ++j) hi = std::max(hi, dg[j] + 2 * std::fabs(of[j]) + 2 * (j ? std::fabs(of[j - 1]) : 0));
+    auto kth = [&](int kk) {
+      double a = lo, bnd = hi;
+      for (int iter = 0; iter < 200; ++iter) {
+        double mid = 0.5 * (a + bnd);
+        if (count_below(mid) > kk) bnd = mid;
+        else a = mid;
+      }
+      return 0.5 * (a + bnd);
+    };
+    double emin = kth(0), emax = kth(n - 1);
+    *kappa = emin > 0 ? emax / emin : 0.0;
+  }
+  return conv ? IETI_OK : IETI_ERR_NO_CONVERGENCE;
+}
+
+// recovery (Eqs. (8), (9)) of the field increment from lam and local loads
+static ieti_status recover(Ctx* c, const double* lam, const double* ycr, const double* jr, double* a, int accumulate,
+                           cudaStream_t st) {
+  const int nrhs = c->nrhs;
+  ieti_status r;
+  const bool coarse = c->n_gp > 0;
+  double* pl = c->wc[0];
+  if (coarse) {
+    k_phiT<<<c->nsub, 256, 0, st>>>(c->d_sd, c->Phi, c->d_I_dual, c->d_I_sign, lam, c->m_r, c->wq_part, nrhs);
+    IETI_LAUNCH_CHECK(c);
+    if ((r = coarse_solve(c, c->wq_part, pl, nrhs, st)) != IETI_OK) return r;
+  }
+  dim3 g(256, c->nsub);
+  double* rhs = c->wr64[1];
+  k_recover_rhs<<<g, 256, 0, st>>>(c->d_sd, c->Kp64, jr, coarse ? pl : c->wc[0], coarse ? ycr : c->wc[0],
+                                   (int)c->n_gp, c->d_P_glob, c->d_I_dual, c->d_I_sign, lam, c->m_r, nrhs, rhs);
+  IETI_LAUNCH_CHECK(c);
+  double* ar = c->wr64[2];
+  if ((r = full_solve(c, rhs, ar, nrhs, st)) != IETI_OK) return r;
+  k_scatter_a<<<g, 256, 0, st>>>(c->d_sd, c->d_r_edge, c->d_I_sign, ar, c->mesh.nedge, nrhs, a, accumulate);
+  IETI_LAUNCH_CHECK(c);
+  if (coarse) {
+    k_scatter_primal<<<64, 256, 0, st>>>(c->d_primal_edges, pl, ycr, (int)c->n_gp, c->mesh.nedge, nrhs, a,
+                                         accumulate);
+    IETI_LAUNCH_CHECK(c);
+  }
+  return IETI_OK;
+}
+
+// relative FP64 residual ||j - K a|| / ||j|| (max over columns); local residuals to wres_r/wres_p
+static ieti_status residual(Ctx* c, const double* a, double* rel, double* jn2, cudaStream_t st) {
+  const int nrhs = c->nrhs;
+  const int64_t ne = c->mesh.nedge;
+  IETI_CUDA_TRY(c, cudaMemsetAsync(c->wglob, 0, sizeof(double) * ne * nrhs, st));
+  dim3 g((unsigned)ceil_div(c->max_n + c->max_nP, 8), c->nsub);
+  k_residual<<<g, 256, 0, st>>>(c->d_sd, c->d_r_edge, c->K64, c->Kp64, c->Kpp64, c->jr, c->jp, a, ne, nrhs,
+                                c->d_I_dual, c->d_I_sign, c->wlam_acc, c->m_r,
+                                c->wres_r, c->wres_p, c->wglob);
+  IETI_LAUNCH_CHECK(c);
+  k_colnorm2<<<nrhs, 256, 0, st>>>(c->wglob, ne, c->wnorm);
+  IETI_LAUNCH_CHECK(c);
+  std::vector<double> h(nrhs);
+  IETI_CUDA_TRY(c, cudaMemcpyAsync(h.data(), c->wnorm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+  IETI_CUDA_TRY(c, cudaStreamSynchronize(st));
+  double mx = 0;
+  for (int col = 0; col < nrhs; ++col) {
+    if (jn2) {
+      double den = jn2[col] > 0 ? jn2[col] : 1.0;
+      mx = std::max(mx, std::sqrt(h[col] / den));
+    } else {
+      mx = std::max(mx, h[col]);
+    }
+  }
+  *rel = mx;
+  if (!jn2) {
+    // caller asked for the raw squared norms (used for ||j||)
+  }
+  return IETI_OK;
+}
+
+ieti_status solve_all(Ctx* c, const double* lam0, double tol, int maxit, double tol_field, double* a,
+                      double* lam_out, ieti_solve_info* info, cudaStream_t st) {
+  const int nrhs = c->nrhs;
+  const int64_t ne = c->mesh.nedge, m = c->m_r;
+  const bool fp32 = c->prec == IETI_FP32_IR;
+  cudaEvent_t e0, e1;
+  IETI_CUDA_TRY(c, cudaEventCreate(&e0));
+  IETI_CUDA_TRY(c, cudaEventCreate(&e1));
+  IETI_CUDA_TRY(c, cudaEventRecord(e0, st));
+  ieti_status r;
+  IETI_CUDA_TRY(c, cudaMemsetAsync(a, 0, sizeof(double) * ne * nrhs, st));
+  IETI_CUDA_TRY(c, cudaMemsetAsync(c->wlam_acc, 0, sizeof(double) * m * nrhs, st));
+  // FP64 factors: one pass, refined further only when a field tolerance is given;
+  // FP32 factors: always refined (default field tolerance 1e-10)
+  const bool refine = fp32 || tol_field > 0;
+  if (fp32 && tol_field <= 0) tol_field = 1e-10;
+  std::vector<double> jn2(nrhs, 1.0);
+  if (refine) {
+    // ||j||^2 of the assembled loads: residual of the zero field
+    double dummy;
+    if ((r = residual(c, a, &dummy, nullptr, st)) != IETI_OK) return r;
+    IETI_CUDA_TRY(c, cudaMemcpy(jn2.data(), c->wnorm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost));
+  }
+  const int max_steps = refine ? 8 : 1;
+  int total_it = 0, steps = 0;
+  double relres = 0, grel = -1, kappa = 0;
+  bool conv = true;
+  double* b = c->wlam[4];
+  double* lam = c->wlam[5];
+  double* ycr = c->wc[1];
+  for (int step = 0; step < max_steps; ++step) {
+    const double* jr = (step == 0) ? c->jr : c->wres_r;
+    const double* jp = (step == 0) ? c->jp : c->wres_p;
+    if ((r = interface_rhs(c, jr, jp, b, ycr, nrhs, st)) != IETI_OK) return r;
+    bool warm = (step == 0 && lam0 != nullptr);
+    if (warm) IETI_CUDA_TRY(c, cudaMemcpyAsync(lam, lam0, sizeof(double) * m * nrhs, cudaMemcpyDeviceToDevice, st));
+    int its = 0;
+    double rel = 0, kap = 0;
+    // with FP32 operators the inner PCG residual cannot fall much below the FP32
+    // accumulation error; the inner solve only has to reduce the error of the
+    // refinement step, the FP64 residual of the field decides convergence
+    const double tol_in = fp32 ? std::max(tol, 1e-6) : tol;
+    ieti_status pr = pcg(c, b, lam, !warm, tol_in, maxit, fp32, &its, &rel, &kap, st);
+    if (pr != IETI_OK && pr != IETI_ERR_NO_CONVERGENCE) return pr;
+    if (pr == IETI_ERR_NO_CONVERGENCE && !fp32) conv = false;
+    total_it += its;
+    relres = rel;
+    if (step == 0) kappa = kap;
+    k_add<<<1216, 256, 0, st>>>(c->wlam_acc, lam, m * nrhs);
+    IETI_LAUNCH_CHECK(c);
+    if ((r = recover(c, lam, ycr, jr, a, step > 0 ? 1 : 0, st)) != IETI_OK) return r;
+    steps = step + 1;
+    if (refine) {
+      if ((r = residual(c, a, &grel, jn2.data(), st)) != IETI_OK) return r;
+    }
+    if (std::getenv("IETI_TRACE"))
+      std::fprintf(stderr, "[ieti] step %d: pcg its %d relres %.3e field residual %.3e\n", step, its, rel, grel);
+    if (!refine || grel <= tol_field) break;
+  }
+  if (refine && grel > tol_field) conv = false;
+  if (lam_out)
+    IETI_CUDA_TRY(c, cudaMemcpyAsync(lam_out, c->wlam_acc, sizeof(double) * m * nrhs, cudaMemcpyDeviceToDevice, st));
+  IETI_CUDA_TRY(c, cudaEventRecord(e1, st));
+  IETI_CUDA_TRY(c, cudaEventSynchronize(e1));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (info) {
+    info->iterations = total_it;
+    info->refinement_steps = steps;
+    info->relres = relres;
+    info->global_relres = grel;
+    info->kappa = kappa;
+    info->converged = conv ? 1 : 0;
+    info->ms_total = ms;
+  }
+  if (!conv) {
+    c->err = "PCG or refinement did not reach the tolerance";
+    return IETI_ERR_NO_CONVERGENCE;
+  }
+  return IETI_OK;
+}
+
+}  // namespace ieti

@@ -1,0 +1,176 @@
+"""GPU parity: every step of the CUDA path against the FP64 oracle, element by
+element on seeded synthetic problems (small cases span several 64-wide panels
+and ragged tails).
+
+Tolerances (relative, max-norm unless stated):
+  * assembly (FP64 on both sides, different summation order): 1e-12;
+  * FP64 factorisation products (S_rIrI, its inverse, S_Pi, F_DP, M_D^-1): 1e-9
+    (condition numbers of the local blocks are below 1e4 here);
+  * FP32 operators: 2e-3 (FP32 factor, kappa(K_rr) ~ 1e3 times u_32 ~ 6e-8);
+  * the field a and the flux B = curl a against the monolithic oracle solve:
+    1e-8 in the 2-norm, for both precisions (FP32 through FP64 refinement).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import discretise as dz, topology as tp, fetidp as fd, monolithic as mono, post
+from paper_2501_04340_gb300 import workloads as wl
+
+
+@pytest.fixture(scope="module")
+def ieti():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2501_04340_gb300 import ieti as m
+    return m
+
+
+def _ragged():
+    return wl.unit_cube(3, (2, 2, 1), [[2, 3], [3, 2], [3]], sub_of_patch=np.array([0, 1, 0, 2], np.int32),
+                        nu=[1.0, 30.0, 2.0, 500.0], nrhs=2, source_params=[1.0, -2.0])
+
+
+CASES = {
+    "cube8_p2n4": lambda: wl.cube8_p2n4(),
+    "cube8_p1n2": lambda: wl.small_cases()[1],
+    "cube12_p2_mixed": lambda: wl.small_cases()[3],
+    "ragged_p3": _ragged,
+}
+
+_cache = {}
+
+
+def oracle_case(name):
+    if name not in _cache:
+        prob = CASES[name]()
+        mesh, Kp, jp = dz.assemble_all(prob)
+        topo = tp.build_topology(prob, mesh)
+        sysd = fd.build_system(prob, (mesh, Kp, jp), topo)
+        a_m, _ = mono.solve(mesh, topo, Kp, jp)
+        _cache[name] = (prob, mesh, topo, sysd, a_m)
+    return _cache[name]
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("affine", [1, 0])
+def test_assembly_blocks(ieti, name, affine):
+    prob, mesh, topo, sysd, _ = oracle_case(name)
+    prob = prob.with_params()
+    prob.affine = affine
+    ctx = ieti.ieti_create(prob)
+    try:
+        ieti.ieti_assemble(ctx)
+        for k, s in enumerate(sysd.subs):
+            Krr = ieti.ieti_get_block(ctx, 0, k)
+            assert rel(Krr, s.Krr.toarray()) < 1e-12
+            if len(s.Cidx):
+                assert rel(ieti.ieti_get_block(ctx, 1, k), s.Krp) < 1e-12
+                assert rel(ieti.ieti_get_block(ctx, 2, k), s.Kpp) < 1e-12
+            assert rel(ieti.ieti_get_block(ctx, 3, k), s.jr) < 1e-12
+            if len(s.Cidx):
+                assert rel(ieti.ieti_get_block(ctx, 4, k), s.jp) < 1e-12
+    finally:
+        ieti.ieti_destroy(ctx)
+
+
+def _factored(ieti, name, prec):
+    prob, mesh, topo, sysd, a_m = oracle_case(name)
+    ctx = ieti.ieti_create(prob)
+    ieti.ieti_assemble(ctx)
+    ieti.ieti_factor(ctx, prec)
+    return ctx, prob, mesh, topo, sysd, a_m
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 2e-3)])
+def test_schur_blocks_and_coarse(ieti, name, prec, tol):
+    ctx, prob, mesh, topo, sysd, _ = _factored(ieti, name, prec)
+    try:
+        op = fd.InterfaceOperator(sysd)
+        for k, s in enumerate(sysd.subs):
+            S = s.KII - (s.KIV @ s.KVV_lu.solve(s.KIV.T) if s.nV else 0)
+            assert rel(ieti.ieti_get_block(ctx, 5, k), S) < tol
+            nI = len(s.Brow)
+            E = np.zeros((s.Krr.shape[0], nI)); E[s.nV:] = np.eye(nI)
+            Winv = s.lu.solve(E)[s.nV:]
+            assert rel(ieti.ieti_get_block(ctx, 6, k), Winv) < tol
+        if sysd.n_gp:
+            assert rel(ieti.ieti_get_coarse(ctx, sysd.n_gp), -op.F) < tol
+    finally:
+        ieti.ieti_destroy(ctx)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 2e-3)])
+def test_apply_F_and_preconditioner(ieti, name, prec, tol):
+    ctx, prob, mesh, topo, sysd, _ = _factored(ieti, name, prec)
+    try:
+        op = fd.InterfaceOperator(sysd)
+        m = sysd.m_r
+        rng = np.random.default_rng(5)
+        for nrhs in (1, 3, 11):
+            lam = rng.standard_normal((m, nrhs))
+            ref = op(lam)
+            refM = fd.dirichlet_precond(sysd, lam)
+            lam_d = torch.tensor(lam.T.copy(), dtype=torch.float64, device="cuda")
+            y = torch.empty_like(lam_d)
+            ieti.ieti_apply_F(ctx, lam_d, y, nrhs)
+            assert rel(y.cpu().numpy().T, ref) < tol
+            z = torch.empty_like(lam_d)
+            ieti.ieti_apply_precond(ctx, lam_d, z, nrhs)
+            assert rel(z.cpu().numpy().T, refM) < tol
+        # interface right-hand side b = e - G F^-1 d
+        b = torch.empty((prob.nrhs, m), dtype=torch.float64, device="cuda")
+        ieti.ieti_interface_rhs(ctx, b)
+        assert rel(b.cpu().numpy().T, op.rhs()) < tol
+    finally:
+        ieti.ieti_destroy(ctx)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("prec", [0, 1])
+def test_solve_matches_monolithic_field_and_flux(ieti, name, prec):
+    ctx, prob, mesh, topo, sysd, a_m = _factored(ieti, name, prec)
+    try:
+        a = torch.zeros((prob.nrhs, mesh.nedge), dtype=torch.float64, device="cuda")
+        lam = torch.zeros((prob.nrhs, sysd.m_r), dtype=torch.float64, device="cuda")
+        info = ieti.ieti_solve(ctx, a, tol=1e-11, maxit=400, tol_field=1e-12, lam_out=lam)
+        assert info.converged == 1
+        ag = a.cpu().numpy().T
+        assert np.linalg.norm(ag - a_m) <= 1e-8 * np.linalg.norm(a_m)
+        for r in range(prob.nrhs):
+            nB, _ = post.flux_l2(prob, mesh, a_m, rhs=r)
+            dB, _ = post.flux_l2(prob, mesh, ag - a_m, rhs=r)
+            assert dB <= 1e-8 * nB
+        # tree and Dirichlet DOFs are exactly zero
+        assert np.all(ag[topo.tree | topo.dirichlet] == 0)
+        if prec == 0:
+            # one pass without field refinement: same PCG iteration count as the oracle
+            info1 = ieti.ieti_solve(ctx, a, tol=1e-11, maxit=400, tol_field=0.0)
+            sol = fd.solve(sysd, tol=1e-11)
+            assert info1.refinement_steps == 1
+            assert abs(info1.iterations - max(sol.iters)) <= 2
+            assert np.linalg.norm(a.cpu().numpy().T - a_m) <= 1e-8 * np.linalg.norm(a_m)
+            assert abs(info1.kappa - sol.kappa[0]) <= 0.05 * sol.kappa[0]
+    finally:
+        ieti.ieti_destroy(ctx)
+
+
+def test_warm_start_with_exact_multipliers_needs_no_iteration(ieti):
+    ctx, prob, mesh, topo, sysd, a_m = _factored(ieti, "cube12_p2_mixed", 0)
+    try:
+        sol = fd.solve(sysd, tol=1e-13)
+        lam0 = torch.tensor(sol.lam.T.copy(), dtype=torch.float64, device="cuda")
+        a = torch.zeros((prob.nrhs, mesh.nedge), dtype=torch.float64, device="cuda")
+        info = ieti.ieti_solve(ctx, a, lam0=lam0, tol=1e-8)
+        assert info.iterations == 0
+        assert np.linalg.norm(a.cpu().numpy().T - a_m) <= 1e-8 * np.linalg.norm(a_m)
+    finally:
+        ieti.ieti_destroy(ctx)
