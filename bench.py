@@ -1,0 +1,395 @@
+"""Benchmark of the dual-primal (FETI-DP / IETI-DP) solve on GB300.
+
+One step = the whole hot path for one problem instance: batched assembly of
+the local curl-curl blocks, batched factorisation (FP32 Cholesky, the chosen
+form), coarse matrix, interface right-hand side, PCG with the Dirichlet
+preconditioner on the interface problem, recovery, and FP64 refinement of the
+field. Workload: unit cube of 4x4x4 affine patches, p = 3, 8 spans per patch
+direction, 16 subdomains of 2x2x1 patches, per-patch reluctivity log-uniform
+in [1, 1e3] (seed 2), manufactured sine source; all inputs synthetic.
+
+Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle on
+a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FETI-DP solve s to 1e-8 rel. residual; F-applies/s; chosen vs plain FP64"
+WORKLOAD = "cube64_p3n8_sub16"
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for name, v in zip(names, r[4:8]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("IETI_BENCH_GLOO") is None else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(world, x):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
+# algorithmic work of the kernel classes (per timed launch group)
+# ----------------------------------------------------------------------------
+
+def syrk_flops(n_list, nb=64):
+    """Trailing symmetric updates of the right-looking blocked Cholesky: every
+    lower tile (r >= c > b) of step b gets nb^3 multiply-adds."""
+    tot = 0
+    for n in n_list:
+        nblk = n // nb
+        for b in range(nblk):
+            t = nblk - b - 1
+            tot += t * (t + 1) // 2 * 2 * nb ** 3
+    return tot
+
+
+def ours(args):
+    import torch
+    from paper_2501_04340_gb300 import ieti, workloads as wl
+
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prob = wl.cube64_p3n8_sub16()
+    ctx = ieti.ieti_create(prob)
+    q = ieti.ieti_query(ctx)
+    nedge, m_r = q["nedge"], q["m_r"]
+    tol, tol_field = 1e-8, 1e-9
+
+    # ---- reference field (FP64 factors, tight tolerances; untimed)
+    ieti.ieti_assemble(ctx)
+    ieti.ieti_factor(ctx, ieti.IETI_FP64)
+    a_ref = torch.zeros((prob.nrhs, nedge), dtype=torch.float64, device=dev)
+    ieti.ieti_solve(ctx, a_ref, tol=1e-12, maxit=2000, tol_field=1e-13, allow_no_convergence=True)
+    nref = torch.linalg.norm(a_ref).item()
+
+    # ---- apply_F throughput with FP64 operators (factors of the reference)
+    lam = torch.randn((1, m_r), dtype=torch.float64, device=dev)
+    y = torch.empty_like(lam)
+    flush = torch.empty(int(256e6) // 4, dtype=torch.float32, device=dev)
+
+    def apply_rate(napply=200, flush_l2=False):
+        for _ in range(5):
+            ieti.ieti_apply_F(ctx, lam, y, 1)
+        torch.cuda.synchronize()
+        tot = 0.0
+        if flush_l2:
+            for _ in range(napply // 4):
+                flush.fill_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                ieti.ieti_apply_F(ctx, lam, y, 1)
+                e1.record()
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+            return (napply // 4) / (tot / 1e3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(napply):
+            ieti.ieti_apply_F(ctx, lam, y, 1)
+        e1.record()
+        torch.cuda.synchronize()
+        return napply / (e0.elapsed_time(e1) / 1e3)
+
+    apply64 = apply_rate()
+    apply64_cold = apply_rate(flush_l2=True)
+
+    # ---- plain FP64 arm: one full step (assemble + FP64 factor + solve to 1e-8)
+    a = torch.zeros_like(a_ref)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ieti.ieti_assemble(ctx)
+    ieti.ieti_factor(ctx, ieti.IETI_FP64)
+    info64 = ieti.ieti_solve(ctx, a, tol=tol, maxit=2000, tol_field=0.0, allow_no_convergence=True)
+    e1.record()
+    torch.cuda.synchronize()
+    plain_s = e0.elapsed_time(e1) / 1e3
+    plain_err = (torch.linalg.norm(a - a_ref) / nref).item()
+    plain_solve_s = info64.ms_total / 1e3
+
+    # ---- chosen form: FP32 factors + FP64 refinement
+    def step():
+        ieti.ieti_assemble(ctx)
+        ieti.ieti_factor(ctx, ieti.IETI_FP32_IR)
+        return ieti.ieti_solve(ctx, a, tol=tol, maxit=2000, tol_field=tol_field, allow_no_convergence=True)
+
+    for _ in range(args.warmup):
+        step()
+    apply32 = apply_rate()
+    apply32_cold = apply_rate(flush_l2=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    l0 = ieti.ieti_launch_count(ctx)
+    ieti.ieti_profile(ctx, True)
+    infos = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            infos.append(step())
+        e1.record()
+        torch.cuda.synchronize()
+    barrier(world)
+    t_ms = allmax(world, e0.elapsed_time(e1))
+    prof = ieti.ieti_profile_read(ctx)
+    ieti.ieti_profile(ctx, False)
+    launches = ieti.ieti_launch_count(ctx) - l0
+    chosen_err = (torch.linalg.norm(a - a_ref) / nref).item()
+    ms_per_step = t_ms / args.steps
+    value = t_ms / 1e3 / (args.steps * world)      # seconds per solved problem, whole job
+
+    # ---- end to end through the C ABI with host buffers (parameters in, field out)
+    nu_host = torch.tensor(prob.nu, dtype=torch.float64).pin_memory()
+    a_host = torch.empty((prob.nrhs, nedge), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ieti.ieti_set_params(ctx, nu=nu_host.numpy())
+        step()
+        a_host.copy_(a, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_s = allmax(world, e2e_s) / world
+
+    # ---- roofline of the dominant kernel class of the step
+    dom = max(prof, key=lambda k: prof[k][0])
+    peaks = _peaks()
+    sub_n = []
+    for k in range(q["nsub"]):
+        nV = len(ieti.ieti_get_dofmap(ctx, 4, k))
+        nI = len(ieti.ieti_get_dofmap(ctx, 5, k))
+        sub_n.append(((nV + 63) // 64 + (nI + 63) // 64) * 64)
+    roof = None
+    if dom == "syrk_update":
+        flops = syrk_flops(sub_n) * args.steps
+        achieved = flops / (prof[dom][0] / 1e3) / 1e12
+        peak = 152 * 128 * 2 * 2.07e9 / 1e12     # FP32 FMA lanes x 2 flops x max SM clock
+        roof = {"kernel": "k_syrk<float> (trailing update of the FP32 Cholesky)", "bound": "alu",
+                "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+    else:
+        roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"),
+                "unit": "GB/s", "frac": None, "traffic": None}
+    # local_W apply roofline (algorithmic bytes: FP32 interface blocks + vectors)
+    sumI2 = q["sum_nI2"]
+    bytes32 = sumI2 * 4 + m_r * 8 * 3
+    apply_roof = {"bound": "hbm", "bytes_per_apply": bytes32,
+                  "achieved_gbs_l2_cold": round(bytes32 * apply32_cold / 1e9, 1),
+                  "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                  "frac_l2_cold": round(bytes32 * apply32_cold / 1e9 / peaks.get("hbm_gbs", 6787.6), 3)}
+
+    out = {
+        "metric": METRIC, "value": round(value, 5), "unit": "s", "higher_is_better": False,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 factors + f64 refinement",
+        "data": "synthetic", "impl": "ours",
+        "config": {"workload": WORKLOAD, "patches": 64, "subdomains": 16, "p": 3, "spans": 8,
+                   "nu": "log-uniform [1,1e3] seed 2", "dofs_gauged": q["n_gauged"], "m_r": m_r,
+                   "n_gp": q["n_gp"], "tol_interface": tol, "tol_field": tol_field,
+                   "l2": "each step writes > 10 GB (assembly of the dense blocks): inputs larger than L2",
+                   "parallelism": f"replicas x{world}"},
+        "chosen": {"pcg_iterations": infos[-1].iterations, "refinement_steps": infos[-1].refinement_steps,
+                   "field_residual": infos[-1].global_relres, "rel_err_vs_fp64_ref": chosen_err,
+                   "kappa": round(infos[-1].kappa, 2)},
+        "plain_fp64": {"s": round(plain_s, 4), "solve_only_s": round(plain_solve_s, 4),
+                       "pcg_iterations": info64.iterations, "rel_err_vs_fp64_ref": plain_err},
+        "chosen_vs_plain_speedup": round(plain_s / (ms_per_step / 1e3), 3),
+        "apply_F_per_s": {"fp32_ops_l2_warm": round(apply32, 1), "fp32_ops_l2_cold": round(apply32_cold, 1),
+                          "fp64_ops_l2_warm": round(apply64, 1), "fp64_ops_l2_cold": round(apply64_cold, 1)},
+        "apply_F_roofline": apply_roof,
+        "kernel_ms": {k: round(v[0] / args.steps, 3) for k, v in prof.items() if v[1]},
+        "roofline": roof,
+        "e2e": {"value": round(e2e_s, 5), "unit": "s", "h2d_bytes_per_step": int(prob.nu.nbytes),
+                "d2h_bytes_per_step": int(a_host.numel() * 8)},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.skip_cpu:
+        out["cpu_baseline"] = cpu_sample(info64.iterations)
+    ieti.ieti_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------
+# oracle (CPU) timing on a bounded sample
+# ----------------------------------------------------------------------------
+
+def cpu_sample(pcg_iters):
+    """The FP64 CPU oracle, as it stands, timed on subdomain 0 of the workload
+    (assembly of its 4 patches, sparse LU of its K_rr, 10 local solves); the
+    full solve time is extrapolated: 16 subdomains' assembly and factorisation
+    (K_rr and K_VV), and per PCG iteration 32 local solves (F-apply and
+    preconditioner), plus 2 x 16 solves for right-hand side and recovery."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+
+    from oracle import discretise as dz, topology as tp
+    from paper_2501_04340_gb300 import workloads as wl
+
+    prob = wl.cube64_p3n8_sub16()
+    t_all = time.perf_counter()
+    mesh = dz.build_mesh(prob)
+    t0 = time.perf_counter()
+    topo = tp.build_topology(prob, mesh)
+    t_topo = time.perf_counter() - t0
+    pats = [q for q in range(prob.npatch_total) if prob.sub_of_patch[q] == 0]
+    t0 = time.perf_counter()
+    K = None
+    for q in pats:
+        r, c, v, _, _ = dz.assemble_patch(prob, mesh, q)
+        Kq = sp.csr_matrix((v, (r, c)), shape=(mesh.nedge, mesh.nedge))
+        K = Kq if K is None else K + Kq
+    t_asm = time.perf_counter() - t0
+    r_ids = np.concatenate([topo.V[0], topo.I[0]])
+    Krr = K[r_ids][:, r_ids].tocsc()
+    t0 = time.perf_counter()
+    lu = spla.splu(Krr)
+    t_fac = time.perf_counter() - t0
+    b = np.ones(Krr.shape[0])
+    t0 = time.perf_counter()
+    for _ in range(10):
+        lu.solve(b)
+    t_sol = (time.perf_counter() - t0) / 10
+    nsub = prob.nsub
+    est = (t_topo + nsub * t_asm + 2 * nsub * t_fac + (pcg_iters * 2 + 2) * nsub * t_sol)
+    return {"value": round(est, 2), "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"subdomain 0 of {nsub}: assembly of its {len(pats)} patches {t_asm:.2f} s, SuperLU "
+                       f"of K_rr ({Krr.shape[0]} rows) {t_fac:.2f} s, local solve {t_sol * 1e3:.1f} ms; "
+                       f"extrapolated to {nsub} subdomains x (assembly + 2 factorisations) + "
+                       f"{pcg_iters} PCG iterations x 2 x {nsub} local solves; sample wall "
+                       f"{time.perf_counter() - t_all:.1f} s; SuperLU single-threaded, BLAS on all cores")}
+
+
+def reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        pass   # the oracle has no warm-up state; keep the run bounded
+    t0 = time.perf_counter()
+    samples = []
+    for _ in range(args.steps):
+        samples.append(cpu_sample(152))
+    per = (time.perf_counter() - t0) / args.steps
+    v = float(np.median([s["value"] for s in samples]))
+    out = {"metric": METRIC, "value": round(v, 2), "unit": "s", "higher_is_better": False, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per * 1e3, 1), "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD, "patches": 64, "subdomains": 16, "p": 3, "spans": 8},
+           "cpu_baseline": {"value": round(v, 2), "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": samples[0]["sample"]},
+           "e2e": {"value": round(v, 2), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle sample")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

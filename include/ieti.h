@@ -214,6 +214,20 @@ ieti_status ieti_interface_rhs(ieti_ctx* ctx, double* b_dev, void* stream);
 /* Number of kernel launches this context has issued so far. */
 int64_t ieti_launch_count(const ieti_ctx* ctx);
 
+/* Per-kernel-class device timing with CUDA events recorded around each launch
+ * group on the launching stream (enable = 1) or off (0); resets the totals.
+ * Classes, in order: 0 assembly of K, 1 assembly of j, 2 diagonal-block
+ * Cholesky, 3 panel triangular solve, 4 trailing symmetric update, 5 forward
+ * substitution sweeps, 6 backward substitution sweeps, 7 local products with
+ * W = S_rIrI^-1 (F-apply), 8 local products with S_rIrI (preconditioner),
+ * 9 multiplier gathers, 10 coarse solves, 11 PCG vector kernels,
+ * 12 FP64 field residual, 13 other. */
+ieti_status ieti_profile(ieti_ctx* ctx, int enable);
+
+/* Totals since the last ieti_profile call: milliseconds and number of timed
+ * launch groups per class (first n classes). Synchronises the device. */
+ieti_status ieti_profile_read(ieti_ctx* ctx, double* ms_host, int64_t* calls_host, int n);
+
 void ieti_destroy(ieti_ctx* ctx);
 const char* ieti_last_error(const ieti_ctx* ctx);
 

@@ -157,7 +157,9 @@ ieti_status build(Ctx* c, const ieti_problem_desc* desc, bool device) {
     d.A = oA; oA += (int64_t)d.n * d.n;
     d.Kp = oKp; oKp += (int64_t)d.n * d.nP;
     d.Kpp = oKpp; oKpp += (int64_t)d.nP * d.nP;
-    d.S = oS; oS += (int64_t)d.nI * d.nI;
+    d.ldI = (int)(ceil_div(d.nI, 4) * 4);
+    d.S = oS; oS += (int64_t)d.ldI * d.nI;
+    c->max_ldI = std::max(c->max_ldI, d.ldI);
     d.linv = oL; oL += (int64_t)d.nblk * NB * NB;
     d.dof = oD; oD += d.n + d.nP;
     d.rv = orv; orv += d.n;
@@ -269,6 +271,17 @@ ieti_status build(Ctx* c, const ieti_problem_desc* desc, bool device) {
 
   c->host_only = !device;
   if (!device) return IETI_OK;
+  {
+    int dev = 0, optin = 48 * 1024;
+    IETI_CUDA_TRY(c, cudaGetDevice(&dev));
+    IETI_CUDA_TRY(c, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    TRY(assemble_kernel_attrs(c, optin));
+    TRY(solve_kernel_attrs(c, optin));
+    if ((size_t)c->max_ldI * 8 * sizeof(double) > (size_t)optin) {
+      c->err = "interface block too large for the shared-memory staging of the local products";
+      return IETI_ERR_INVALID_ARG;
+    }
+  }
   // ---- device uploads
   TRY(upload(c, &c->d_sd, c->sd_host));
   TRY(upload(c, &c->d_dof, dof));
@@ -606,8 +619,9 @@ ieti_status ieti_get_block(ieti_ctx* x, int which, int sub, double* out, int64_t
     std::memcpy(out, tmp.data(), sizeof(double) * R * C);
   } else {
     const void* base = (which == 5) ? c->S : c->W;
-    if ((r = fetch(base, s.S, (int64_t)nI * nI, c->prec == IETI_FP32_IR)) != IETI_OK) return r;
-    std::memcpy(out, tmp.data(), sizeof(double) * R * C);
+    if ((r = fetch(base, s.S, (int64_t)s.ldI * nI, c->prec == IETI_FP32_IR)) != IETI_OK) return r;
+    for (int64_t j = 0; j < C; ++j)
+      for (int64_t i = 0; i < R; ++i) out[i + R * j] = tmp[i + (int64_t)s.ldI * j];
   }
   return IETI_OK;
 }
@@ -626,6 +640,29 @@ ieti_status ieti_get_coarse(ieti_ctx* x, double* out, int64_t cap) {
 }
 
 int64_t ieti_launch_count(const ieti_ctx* x) { return x ? x->c.launches : 0; }
+
+ieti_status ieti_profile(ieti_ctx* x, int enable) {
+  if (!x) return IETI_ERR_INVALID_ARG;
+  Ctx* c = &x->c;
+  prof_collect(c);
+  c->prof.on = enable != 0;
+  for (int i = 0; i < PROF_NCAT; ++i) {
+    c->prof.ms[i] = 0;
+    c->prof.calls[i] = 0;
+  }
+  return IETI_OK;
+}
+
+ieti_status ieti_profile_read(ieti_ctx* x, double* ms_host, int64_t* calls_host, int n) {
+  if (!x || !ms_host || !calls_host) return IETI_ERR_INVALID_ARG;
+  Ctx* c = &x->c;
+  prof_collect(c);
+  for (int i = 0; i < n && i < PROF_NCAT; ++i) {
+    ms_host[i] = c->prof.ms[i];
+    calls_host[i] = c->prof.calls[i];
+  }
+  return IETI_OK;
+}
 
 void ieti_destroy(ieti_ctx* x) {
   if (!x) return;

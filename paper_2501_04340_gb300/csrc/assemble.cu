@@ -521,14 +521,27 @@ static ieti_status launch_elem(Ctx* c, const AsmParams& P, bool do_K, cudaStream
   constexpr int NQ3 = (PD + 1) * (PD + 1) * (PD + 1), NF = ElemShared<PD>::NF;
   if (do_K) {
     size_t smem = sizeof(ElemShared<PD>) + sizeof(double) * (NQ3 * 9 + (size_t)NF * NQ3 * 2);
-    IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_elem_K<PD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cudaEvent_t p0 = prof_begin(c, st);
     k_elem_K<PD><<<(unsigned)c->nelem, 256, smem, st>>>(P);
+    prof_end(c, PROF_ASM_K, p0, st);
     IETI_LAUNCH_CHECK(c);
   }
   size_t smem = sizeof(ElemShared<PD>) + sizeof(double) * (size_t)NQ3 * c->nrhs * 3;
-  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_elem_j<PD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaEvent_t p0 = prof_begin(c, st);
   k_elem_j<PD><<<(unsigned)c->nelem, 256, smem, st>>>(P);
+  prof_end(c, PROF_ASM_J, p0, st);
   IETI_LAUNCH_CHECK(c);
+  return IETI_OK;
+}
+
+// raises the dynamic shared-memory limit of the element kernels
+ieti_status assemble_kernel_attrs(Ctx* c, int smem_max) {
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_elem_K<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_elem_K<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_elem_K<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_elem_j<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_elem_j<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_elem_j<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
   return IETI_OK;
 }
 
@@ -540,7 +553,9 @@ ieti_status assemble_all(Ctx* c, cudaStream_t st) {
   if (kron) {
     int64_t R = c->max_n + c->max_nP;
     dim3 grid((unsigned)ceil_div(R * R, 256), (unsigned)c->nsub);
+    cudaEvent_t p0 = prof_begin(c, st);
     k_kron<double><<<grid, 256, 0, st>>>(P, (double*)nullptr);
+    prof_end(c, PROF_ASM_K, p0, st);
     IETI_LAUNCH_CHECK(c);
   } else {
     IETI_CUDA_TRY(c, cudaMemsetAsync(c->K64, 0, sizeof(double) * c->tot_A, st));

@@ -177,9 +177,13 @@ __global__ void k_snapshot(const SubDev* sd, const T* L, T* S, int b) {
   const int k = blockIdx.y;
   const SubDev s = sd[k];
   if (s.nVp != b * NB || s.nI == 0) return;
-  const int64_t tot = (int64_t)s.nI * s.nI;
+  const int64_t tot = (int64_t)s.ldI * s.nI;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
-    int i = (int)(t % s.nI), j = (int)(t / s.nI);
+    int i = (int)(t % s.ldI), j = (int)(t / s.ldI);
+    if (i >= s.nI) {
+      S[s.S + t] = (T)0;
+      continue;
+    }
     int hi = i > j ? i : j, lo = i > j ? j : i;
     S[s.S + t] = L[s.A + (s.nVp + hi) + (int64_t)s.n * (s.nVp + lo)];
   }
@@ -303,16 +307,20 @@ ieti_status tri_solve(Ctx* c, const SubDev* d_sd, int nsub, int max_nblk, int ma
                       cudaStream_t st) {
   if (max_ncol <= 0) return IETI_OK;
   const int ctiles = (int)ceil_div(max_ncol, SOLVE_CT);
+  cudaEvent_t p0 = prof_begin(c, st);
   for (int b = min_b0; b < max_nblk; ++b) {
     dim3 grid((unsigned)std::max<int64_t>(1, ceil_div(max_rows, SOLVE_RC)), ctiles, nsub);
     k_fwd<T><<<grid, 256, 0, st>>>(d_sd, d_desc, L, Linv, B, Y, b);
     IETI_LAUNCH_CHECK(c);
   }
+  prof_end(c, PROF_FWD, p0, st);
+  p0 = prof_begin(c, st);
   for (int b = max_nblk - 1; b >= min_b0; --b) {
     dim3 grid((unsigned)std::max<int64_t>(1, ceil_div(max_rows, 8)), ctiles, nsub);
     k_bwd<T><<<grid, 256, 0, st>>>(d_sd, d_desc, L, Linv, Y, X, b);
     IETI_LAUNCH_CHECK(c);
   }
+  prof_end(c, PROF_BWD, p0, st);
   return IETI_OK;
 }
 
@@ -338,9 +346,13 @@ __global__ void k_extract_W(const SubDev* sd, const SolveDesc* dsc, const T* X, 
   const int k = blockIdx.y;
   const SubDev s = sd[k];
   const SolveDesc d = dsc[k];
-  const int64_t tot = (int64_t)s.nI * s.nI;
+  const int64_t tot = (int64_t)s.ldI * s.nI;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
-    int i = (int)(t % s.nI), j = (int)(t / s.nI);
+    int i = (int)(t % s.ldI), j = (int)(t / s.ldI);
+    if (i >= s.nI) {
+      W[s.S + t] = (T)0;
+      continue;
+    }
     // symmetrise (the two triangles agree up to rounding)
     T a = X[d.boff + i + (int64_t)d.ldb * j], bb = X[d.boff + j + (int64_t)d.ldb * i];
     W[s.S + t] = (T)0.5 * (a + bb);
@@ -413,13 +425,19 @@ static ieti_status cholesky(Ctx* c, const SubDev* d_sd, const std::vector<SubDev
         IETI_LAUNCH_CHECK(c);
       }
     }
+    cudaEvent_t p0 = prof_begin(c, st);
     k_potrf_diag<T><<<nsub, 256, 0, st>>>(d_sd, L, Linv, b, c->d_err);
+    prof_end(c, PROF_POTRF, p0, st);
     IETI_LAUNCH_CHECK(c);
     const int Tm = max_nblk - b - 1;
     if (Tm > 0) {
+      p0 = prof_begin(c, st);
       k_trsm_panel<T><<<dim3(Tm, nsub), 256, 0, st>>>(d_sd, L, Linv, b);
+      prof_end(c, PROF_TRSM, p0, st);
       IETI_LAUNCH_CHECK(c);
+      p0 = prof_begin(c, st);
       k_syrk<T><<<dim3(Tm * (Tm + 1) / 2, nsub), 256, 0, st>>>(d_sd, L, b);
+      prof_end(c, PROF_SYRK, p0, st);
       IETI_LAUNCH_CHECK(c);
     }
   }

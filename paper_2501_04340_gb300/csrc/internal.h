@@ -25,13 +25,28 @@ struct SubDev {
   int64_t A;      // K_rr (n x n) in K64 and in the factor buffer
   int64_t Kp;     // K_rp (n x nP)
   int64_t Kpp;    // K_pp (nP x nP)
-  int64_t S;      // S_rIrI and W = S_rIrI^-1 (nI x nI)
+  int64_t S;      // S_rIrI and W = S_rIrI^-1 (ldI x nI, ldI = nI rounded up to 4)
   int64_t linv;   // inverses of the NB x NB diagonal blocks of the factor
   int64_t dof;    // local DOF table, n + nP entries
   int64_t rv;     // r-vectors (n rows)
   int64_t pv;     // p-vectors (nP rows)
   int64_t iv;     // interface vectors (nI rows)
-  int n, nVp, nI, nP, nblk, pad;
+  int n, nVp, nI, nP, nblk, ldI;
+};
+
+// kernel classes timed with CUDA events when profiling is enabled
+enum ProfCat {
+  PROF_ASM_K = 0, PROF_ASM_J, PROF_POTRF, PROF_TRSM, PROF_SYRK, PROF_FWD, PROF_BWD, PROF_LOCAL_W,
+  PROF_LOCAL_S, PROF_GATHER, PROF_COARSE, PROF_PCG, PROF_RESID, PROF_OTHER, PROF_NCAT
+};
+
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+  double ms[PROF_NCAT] = {};
+  int64_t calls[PROF_NCAT] = {};
 };
 
 // local DOF: direction d and global control-grid index (i, j, k) of its edge;
@@ -60,7 +75,8 @@ struct Ctx {
   // sizes
   int nsub = 0;
   int64_t m_r = 0, n_gp = 0;
-  int max_n = 0, max_nI = 0, max_nP = 0, max_nblk = 0;
+  int max_n = 0, max_nI = 0, max_nP = 0, max_nblk = 0, max_ldI = 0;
+  Prof prof;
   int64_t tot_A = 0, tot_Kp = 0, tot_Kpp = 0, tot_S = 0, tot_linv = 0, tot_dof = 0;
   int64_t tot_rv = 0, tot_pv = 0, tot_iv = 0;
   std::vector<SubDev> sd_host;
@@ -157,8 +173,33 @@ struct Ctx {
     }                                                                              \
   } while (0)
 
+// profiling marks (no-ops unless enabled)
+inline cudaEvent_t prof_begin(Ctx* c, cudaStream_t st) {
+  if (!c->prof.on) return nullptr;
+  if (c->prof.used + 2 > c->prof.pool.size()) {
+    for (int i = 0; i < 256; ++i) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      c->prof.pool.push_back(e);
+    }
+  }
+  cudaEvent_t e = c->prof.pool[c->prof.used++];
+  cudaEventRecord(e, st);
+  return e;
+}
+inline void prof_end(Ctx* c, int cat, cudaEvent_t e0, cudaStream_t st) {
+  if (!c->prof.on || !e0) return;
+  cudaEvent_t e1 = c->prof.pool[c->prof.used++];
+  cudaEventRecord(e1, st);
+  c->prof.marks.push_back({cat, {e0, e1}});
+}
+// folds the recorded marks into per-class totals (synchronises)
+void prof_collect(Ctx* c);
+
 // assembly
 ieti_status assemble_all(Ctx* c, cudaStream_t s);
+ieti_status assemble_kernel_attrs(Ctx* c, int smem_max);
+ieti_status solve_kernel_attrs(Ctx* c, int smem_max);
 // factorisation
 ieti_status factor_all(Ctx* c, cudaStream_t s);
 // triangular solves with the local factors on the r-vectors in c->wr[...]

@@ -30,44 +30,65 @@ constexpr int SC = 16;         // PCG scalars per column
 // local interface products: t_k = M_k u_k, u_k = sign * scale * x[dual]
 // ---------------------------------------------------------------------------
 
-template <typename T>
+// CT = right-hand-side columns handled per CTA (1, 2, 4 or 8). Rows of M are
+// stored with a leading dimension ldI (a multiple of 4 elements) so that each
+// lane streams 16-byte vectors of its row.
+template <typename T, int CT>
 __global__ void __launch_bounds__(256) k_local(const SubDev* sd, const T* M, const int32_t* I_dual,
                                                const double* I_sign, const double* I_scale,
                                                const double* x, int64_t ldx, double* t, int nrhs) {
+  constexpr int VEC = 16 / sizeof(T);
   const int k = blockIdx.z;
   const SubDev s = sd[k];
   const int nI = s.nI;
   const int r0 = blockIdx.x * LOC_ROWS;
   if (r0 >= nI) return;
-  const int c0 = blockIdx.y * LOC_CT;
+  const int c0 = blockIdx.y * CT;
   if (c0 >= nrhs) return;
-  const int nc = min(LOC_CT, nrhs - c0);
+  const int nc = min(CT, nrhs - c0);
   extern __shared__ __align__(16) unsigned char sm[];
-  T* u = reinterpret_cast<T*>(sm);             // nI x LOC_CT
-  for (int i = threadIdx.x; i < nI; i += blockDim.x) {
-    double w = I_sign[s.iv + i] * (I_scale ? I_scale[s.iv + i] : 1.0);
-    int l = I_dual[s.iv + i];
+  T* u = reinterpret_cast<T*>(sm);             // ldI x CT (zero beyond nI)
+  for (int i = threadIdx.x; i < s.ldI; i += blockDim.x) {
+    if (i < nI) {
+      double w = I_sign[s.iv + i] * (I_scale ? I_scale[s.iv + i] : 1.0);
+      int l = I_dual[s.iv + i];
 #pragma unroll
-    for (int cc = 0; cc < LOC_CT; ++cc) u[i * LOC_CT + cc] = (cc < nc) ? (T)(w * x[l + ldx * (c0 + cc)]) : (T)0;
+      for (int cc = 0; cc < CT; ++cc) u[i * CT + cc] = (cc < nc) ? (T)(w * x[l + ldx * (c0 + cc)]) : (T)0;
+    } else {
+#pragma unroll
+      for (int cc = 0; cc < CT; ++cc) u[i * CT + cc] = (T)0;
+    }
   }
   __syncthreads();
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const T* Mk = M + s.S;
+  const int nv = s.ldI / VEC;
   for (int rr = warp; rr < LOC_ROWS; rr += 8) {
     const int i = r0 + rr;
     if (i >= nI) break;
-    const T* col = Mk + (int64_t)nI * i;     // symmetric: column i = row i
-    T acc[LOC_CT];
+    const T* row = Mk + (int64_t)s.ldI * i;     // symmetric: row i = column i
+    T acc[CT];
 #pragma unroll
-    for (int cc = 0; cc < LOC_CT; ++cc) acc[cc] = 0;
-    for (int j = lane; j < nI; j += 32) {
-      T m = col[j];
-      const T* uj = u + j * LOC_CT;
+    for (int cc = 0; cc < CT; ++cc) acc[cc] = 0;
+#pragma unroll 4
+    for (int jv = lane; jv < nv; jv += 32) {
+      T m[VEC];
+      if constexpr (VEC == 4) {
+        float4 q = reinterpret_cast<const float4*>(row)[jv];
+        m[0] = q.x; m[1] = q.y; m[2] = q.z; m[3] = q.w;
+      } else {
+        double2 q = reinterpret_cast<const double2*>(row)[jv];
+        m[0] = q.x; m[1] = q.y;
+      }
 #pragma unroll
-      for (int cc = 0; cc < LOC_CT; ++cc) acc[cc] += m * uj[cc];
+      for (int e = 0; e < VEC; ++e) {
+        const T* uj = u + (jv * VEC + e) * CT;
+#pragma unroll
+        for (int cc = 0; cc < CT; ++cc) acc[cc] += m[e] * uj[cc];
+      }
     }
 #pragma unroll
-    for (int cc = 0; cc < LOC_CT; ++cc) {
+    for (int cc = 0; cc < CT; ++cc) {
       T v = acc[cc];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -76,7 +97,7 @@ __global__ void __launch_bounds__(256) k_local(const SubDev* sd, const T* M, con
     if (lane < nc) {
       T v = acc[0];
 #pragma unroll
-      for (int cc = 1; cc < LOC_CT; ++cc)
+      for (int cc = 1; cc < CT; ++cc)
         if (lane == cc) v = acc[cc];
       t[IV(s, i, c0 + lane, nrhs)] = (double)v;
     }
@@ -479,16 +500,40 @@ __global__ void k_colnorm2(const double* v, int64_t m, double* out) {
 // host orchestration
 // ---------------------------------------------------------------------------
 
+template <typename T, int CT>
+static ieti_status launch_local_ct(Ctx* c, const T* M, const double* x, const double* scale, double* t, int nrhs,
+                                   int cat, cudaStream_t st) {
+  size_t smem = (size_t)c->max_ldI * CT * sizeof(T);
+  dim3 grid((unsigned)ceil_div(c->max_nI, LOC_ROWS), (unsigned)ceil_div(nrhs, CT), (unsigned)c->nsub);
+  cudaEvent_t p0 = prof_begin(c, st);
+  k_local<T, CT><<<grid, 256, smem, st>>>(c->d_sd, M, c->d_I_dual, c->d_I_sign, scale, x, c->m_r, t, nrhs);
+  prof_end(c, cat, p0, st);
+  IETI_LAUNCH_CHECK(c);
+  return IETI_OK;
+}
+
 template <typename T>
 static ieti_status launch_local(Ctx* c, const T* M, const double* x, const double* scale, double* t, int nrhs,
                                 cudaStream_t st) {
   if (c->max_nI == 0) return IETI_OK;
-  size_t smem = (size_t)c->max_nI * LOC_CT * sizeof(T);
-  if (smem > 48 * 1024)
-    IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_local<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid((unsigned)ceil_div(c->max_nI, LOC_ROWS), (unsigned)ceil_div(nrhs, LOC_CT), (unsigned)c->nsub);
-  k_local<T><<<grid, 256, smem, st>>>(c->d_sd, M, c->d_I_dual, c->d_I_sign, scale, x, c->m_r, t, nrhs);
-  IETI_LAUNCH_CHECK(c);
+  const int cat = scale ? PROF_LOCAL_S : PROF_LOCAL_W;
+  if (nrhs == 1) return launch_local_ct<T, 1>(c, M, x, scale, t, nrhs, cat, st);
+  if (nrhs == 2) return launch_local_ct<T, 2>(c, M, x, scale, t, nrhs, cat, st);
+  if (nrhs <= 4) return launch_local_ct<T, 4>(c, M, x, scale, t, nrhs, cat, st);
+  return launch_local_ct<T, 8>(c, M, x, scale, t, nrhs, cat, st);
+}
+
+// raises the dynamic shared-memory limit of the kernels that need more than 48 KB
+ieti_status solve_kernel_attrs(Ctx* c, int smem_max) {
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_local<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_local<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_local<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_local<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_local<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_local<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_local<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_local<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
   return IETI_OK;
 }
 
@@ -501,10 +546,10 @@ static ieti_status coarse_solve(Ctx* c, const double* qpart, double* yc, int nrh
   if (ngp == 0) return IETI_OK;
   const int ldc = (int)(ceil_div(ngp, NB) * NB);
   size_t smem = sizeof(double) * ngp * nrhs;
-  if (smem > 48 * 1024)
-    IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int blocks = (int)std::min<int64_t>(64, std::max<int64_t>(1, ceil_div((int64_t)ngp * nrhs, 8)));
+  cudaEvent_t p0 = prof_begin(c, st);
   k_coarse<<<blocks, 256, smem, st>>>(c->d_sd, c->d_pcsr_off, c->d_pcsr, qpart, c->SPiInv, ngp, ldc, yc, nrhs);
+  prof_end(c, PROF_COARSE, p0, st);
   IETI_LAUNCH_CHECK(c);
   return IETI_OK;
 }
@@ -523,9 +568,11 @@ static ieti_status apply_F_ex(Ctx* c, const double* lam, double* y, int nrhs, bo
     IETI_LAUNCH_CHECK(c);
     if ((r = coarse_solve(c, c->wq_part, c->wc[0], nrhs, st)) != IETI_OK) return r;
   }
+  cudaEvent_t p0 = prof_begin(c, st);
   k_gather_F<<<dim3(gather_blocks(c), nrhs), 256, 0, st>>>(c->d_sd, c->d_pair, t, c->Phi, c->d_P_glob,
                                                           coarse ? c->wc[0] : nullptr, (int)c->n_gp, c->m_r, nrhs,
                                                           y, dotv, part, nullptr, 1.0);
+  prof_end(c, PROF_GATHER, p0, st);
   IETI_LAUNCH_CHECK(c);
   return IETI_OK;
 }
@@ -541,10 +588,26 @@ static ieti_status apply_precond_ex(Ctx* c, const double* rv, double* z, int nrh
   if (fp32) r = launch_local<float>(c, (const float*)c->S, rv, c->d_I_scale, t, nrhs, st);
   else r = launch_local<double>(c, (const double*)c->S, rv, c->d_I_scale, t, nrhs, st);
   if (r != IETI_OK) return r;
+  cudaEvent_t p0 = prof_begin(c, st);
   k_gather_P<<<dim3(gather_blocks(c), nrhs), 256, 0, st>>>(c->d_sd, c->d_pair, c->d_I_scale, t, c->m_r, nrhs, z,
                                                           dotv, part);
+  prof_end(c, PROF_GATHER, p0, st);
   IETI_LAUNCH_CHECK(c);
   return IETI_OK;
+}
+
+void prof_collect(Ctx* c) {
+  if (c->prof.marks.empty()) return;
+  cudaDeviceSynchronize();
+  for (auto& m : c->prof.marks) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, m.second.first, m.second.second) == cudaSuccess) {
+      c->prof.ms[m.first] += ms;
+      c->prof.calls[m.first] += 1;
+    }
+  }
+  c->prof.marks.clear();
+  c->prof.used = 0;
 }
 
 ieti_status apply_precond(Ctx* c, const double* rv, double* z, int nrhs, bool fp32, cudaStream_t st) {
@@ -746,9 +809,11 @@ static ieti_status residual(Ctx* c, const double* a, double* rel, double* jn2, c
   const int64_t ne = c->mesh.nedge;
   IETI_CUDA_TRY(c, cudaMemsetAsync(c->wglob, 0, sizeof(double) * ne * nrhs, st));
   dim3 g((unsigned)ceil_div(c->max_n + c->max_nP, 8), c->nsub);
+  cudaEvent_t p0 = prof_begin(c, st);
   k_residual<<<g, 256, 0, st>>>(c->d_sd, c->d_r_edge, c->K64, c->Kp64, c->Kpp64, c->jr, c->jp, a, ne, nrhs,
                                 c->d_I_dual, c->d_I_sign, c->wlam_acc, c->m_r,
                                 c->wres_r, c->wres_p, c->wglob);
+  prof_end(c, PROF_RESID, p0, st);
   IETI_LAUNCH_CHECK(c);
   k_colnorm2<<<nrhs, 256, 0, st>>>(c->wglob, ne, c->wnorm);
   IETI_LAUNCH_CHECK(c);

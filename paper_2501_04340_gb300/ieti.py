@@ -72,6 +72,8 @@ _sig = {
     "ieti_get_coarse": (C.c_int, [_vp, C.POINTER(C.c_double), C.c_int64]),
     "ieti_interface_rhs": (C.c_int, [_vp, _vp, _vp]),
     "ieti_launch_count": (C.c_int64, [_vp]),
+    "ieti_profile": (C.c_int, [_vp, C.c_int]),
+    "ieti_profile_read": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]),
     "ieti_destroy": (None, [_vp]),
     "ieti_last_error": (C.c_char_p, [_vp]),
 }
@@ -220,6 +222,22 @@ def ieti_get_coarse(ctx, n_gp):
 
 def ieti_launch_count(ctx):
     return int(_lib.ieti_launch_count(ctx))
+
+
+PROFILE_CLASSES = ["assemble_K", "assemble_j", "potrf_diag", "trsm_panel", "syrk_update", "trsv_fwd",
+                   "trsv_bwd", "local_W", "local_S", "gather", "coarse", "pcg_vec", "residual", "other"]
+
+
+def ieti_profile(ctx, enable=True):
+    _check(ctx, _lib.ieti_profile(ctx, 1 if enable else 0))
+
+
+def ieti_profile_read(ctx):
+    n = len(PROFILE_CLASSES)
+    ms = (C.c_double * n)()
+    calls = (C.c_int64 * n)()
+    _check(ctx, _lib.ieti_profile_read(ctx, ms, calls, n))
+    return {name: (ms[i], calls[i]) for i, name in enumerate(PROFILE_CLASSES)}
 
 
 def ieti_destroy(ctx):
