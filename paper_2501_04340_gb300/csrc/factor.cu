@@ -195,6 +195,7 @@ __global__ void k_snapshot(const SubDev* sd, const T* L, T* S, int b) {
 
 constexpr int SOLVE_CT = 8;     // RHS columns per CTA
 constexpr int SOLVE_RC = 256;   // rows per CTA in the forward update
+constexpr int BWD_COLS = 64;    // rows above the panel per CTA in the backward update
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_fwd(const SubDev* sd, const SolveDesc* dsc, const T* L, const T* Linv,
@@ -208,6 +209,8 @@ __global__ void __launch_bounds__(256) k_fwd(const SubDev* sd, const SolveDesc* 
   const int nc = min(SOLVE_CT, d.ncol - c0);
   const int row0 = (b - d.b0) * NB;          // local row of panel b in the range
   const int rows = s.n - d.b0 * NB;          // rows of the range
+  // CTAs without rows below the panel have nothing to do (CTA 0 writes y_b)
+  if (blockIdx.x != 0 && row0 + NB + blockIdx.x * SOLVE_RC >= rows) return;
   __shared__ T Li[NB][NB + 1];
   __shared__ T Bb[NB][SOLVE_CT];
   __shared__ T y[NB][SOLVE_CT];
@@ -260,6 +263,8 @@ __global__ void __launch_bounds__(256) k_bwd(const SubDev* sd, const SolveDesc* 
   if (c0 >= d.ncol) return;
   const int nc = min(SOLVE_CT, d.ncol - c0);
   const int row0 = (b - d.b0) * NB;
+  // each CTA updates BWD_COLS rows above the panel; CTA 0 also writes x_b
+  if (blockIdx.x != 0 && blockIdx.x * BWD_COLS >= row0) return;
   __shared__ T Li[NB][NB + 1];
   __shared__ T Yb[NB][SOLVE_CT];
   __shared__ T x[NB][SOLVE_CT];
@@ -287,17 +292,20 @@ __global__ void __launch_bounds__(256) k_bwd(const SubDev* sd, const SolveDesc* 
       Xk[row0 + i + (int64_t)d.ldb * (c0 + cc)] = x[i][cc];
     }
   }
-  // update rows above: Y[c] -= sum_{r in panel b} L[r, c] x[r], one warp per column c
+  // update rows above: Y[c] -= sum_{r in panel b} L[r, c] x[r]; each warp takes
+  // columns c of L (64 contiguous entries of panel b) in turn
   const int warp = tid / 32, lane = tid % 32;
-  const int ccol = blockIdx.x * 8 + warp;    // local row (= column of L) in the range
-  if (ccol >= row0) return;
-  const T* Lc = L + s.A + (int64_t)b * NB + (int64_t)s.n * (d.b0 * NB + ccol);
-  T l0 = Lc[lane], l1 = Lc[lane + 32];
-  for (int cc = 0; cc < nc; ++cc) {
-    T v = l0 * x[lane][cc] + l1 * x[lane + 32][cc];
+  for (int w = warp; w < BWD_COLS; w += 8) {
+    const int ccol = blockIdx.x * BWD_COLS + w;    // local row (= column of L) in the range
+    if (ccol >= row0) break;
+    const T* Lc = L + s.A + (int64_t)b * NB + (int64_t)s.n * (d.b0 * NB + ccol);
+    T l0 = Lc[lane], l1 = Lc[lane + 32];
+    for (int cc = 0; cc < nc; ++cc) {
+      T v = l0 * x[lane][cc] + l1 * x[lane + 32][cc];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) Yk[ccol + (int64_t)d.ldb * (c0 + cc)] -= v;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) Yk[ccol + (int64_t)d.ldb * (c0 + cc)] -= v;
+    }
   }
 }
 
@@ -316,7 +324,7 @@ ieti_status tri_solve(Ctx* c, const SubDev* d_sd, int nsub, int max_nblk, int ma
   prof_end(c, PROF_FWD, p0, st);
   p0 = prof_begin(c, st);
   for (int b = max_nblk - 1; b >= min_b0; --b) {
-    dim3 grid((unsigned)std::max<int64_t>(1, ceil_div(max_rows, 8)), ctiles, nsub);
+    dim3 grid((unsigned)std::max<int64_t>(1, ceil_div(max_rows, BWD_COLS)), ctiles, nsub);
     k_bwd<T><<<grid, 256, 0, st>>>(d_sd, d_desc, L, Linv, Y, X, b);
     IETI_LAUNCH_CHECK(c);
   }
