@@ -11,7 +11,7 @@ independently there):
     direction of increasing parameter, inherited by every local copy;
   * edge ids: all direction-0 edges, then direction-1, then direction-2, each
     block lexicographic with i fastest over its own index extents.
-Reading (Sec. 2.2, "DOFs correspond to edges of the mesh"): the edge DOF
+Reading (Sec. 2.2: the gauge identifies DOFs with mesh edges): the edge DOF
 (i,j,k) of direction d is the coefficient of the edge function whose 1D factor
 in direction d is D_i and N in the other directions.
 Reading (quadrature, not stated): p+1 Gauss-Legendre points per direction per

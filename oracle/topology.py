@@ -6,13 +6,12 @@ Fig. "weights" (edge weights 1-5).
 
 Readings (the paper is underspecified here):
   * An interface facet is the union of the closed patch-facets shared by two
-    subdomains k and l (one facet per pair, Sec. 2: "every interface is
-    considered to be a facet").
+    subdomains k and l (one facet per pair; Sec. 2 makes each interface a facet).
   * Dirichlet facets of a subdomain: connected components of its boundary
     patch-facets with the same outward label (direction, side) of the glued
-    control net. This realises "two patch-facets of the same patch sharing a
-    boundary segment belong to two separate facets".
-  * Wire basket (mesh-edge reading of "edges located at intersections"): edges in
+    control net. This keeps two boundary patch-facets of one patch that meet along a
+    segment in separate facets, as Sec. 2 requires.
+  * Wire basket (mesh-edge reading: the edges lying where facets meet): edges in
     the closure of two or more facets of one subdomain, plus every edge shared
     by more than two subdomains.
   * Weights: the first matching rule of Fig. "weights" wins; Kruskal processes
