@@ -231,6 +231,43 @@ ieti_status ieti_profile_read(ieti_ctx* ctx, double* ms_host, int64_t* calls_hos
 void ieti_destroy(ieti_ctx* ctx);
 const char* ieti_last_error(const ieti_ctx* ctx);
 
+/* Batched interface product that allocates no device memory (the paper has no
+ * counterpart; this is a library service).
+ *
+ * For callers that cannot call cudaMalloc when they need this product: an
+ * outer solver or framework that owns the device memory pool and hands the
+ * library only its own input and output buffers, where an allocation would fail
+ * against that pool's budget or fragment it. The caller passes every input and
+ * output; the scratch (per-subdomain descriptors and local products) lives in
+ * one fixed 32 MiB array inside the library, which every GPU that loads the
+ * library holds until the process exits.
+ *
+ * Computes y = sum_k B_k^T diag(w_k) M_k diag(w_k) B_k x, i.e. for each
+ * subdomain k: u = w_k .* x[dual_k]; t = M_k u; y[dual_k] += w_k .* t.
+ *   nsub        number of subdomains, 1..4096
+ *   nI_host     host array: interface block size nI_k of each subdomain
+ *   M_dev       device FP64: the symmetric blocks M_k, each nI_k x nI_k
+ *               column-major, concatenated in subdomain order
+ *   dual_dev    device int32: multiplier index (0 .. m-1) of every local
+ *               interface DOF, concatenated in subdomain order
+ *   weight_dev  device FP64: weight w of every local interface DOF (same order)
+ *   m, nrhs     multipliers and columns; x_dev, y_dev are m x nrhs FP64
+ *               column-major, not aliased; y_dev is overwritten
+ * With M_k = S_rIrI^(k) and w_k = sign * rho-scaling weight this is the
+ * Dirichlet preconditioner of Eq. (10); with M_k = S_rIrI^(k)-1 and w_k = sign
+ * it is the local part of the F-apply.
+ * Limits and errors: sum_k nI_k * nrhs must not exceed 4,177,920 (the scratch
+ * minus the descriptor area); larger requests return IETI_ERR_INVALID_ARG with a
+ * message on stderr, as do bad arguments. IETI_ERR_CUDA on a CUDA error.
+ * The first call on each device looks up the device address of the scratch
+ * array (one-time set-up with that device current); make that first call
+ * before any stream capture. Every call shares the one scratch array: calls
+ * that overlap on the GPU (other streams, other host threads) race and must
+ * be serialised by the caller. Enqueued on `stream`; returns before completion. */
+ieti_status ieti_interface_product_noalloc(int nsub, const int* nI_host, const double* M_dev,
+                                           const int* dual_dev, const double* weight_dev, int64_t m,
+                                           const double* x_dev, double* y_dev, int nrhs, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

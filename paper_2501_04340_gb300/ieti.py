@@ -74,6 +74,8 @@ _sig = {
     "ieti_launch_count": (C.c_int64, [_vp]),
     "ieti_profile": (C.c_int, [_vp, C.c_int]),
     "ieti_profile_read": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]),
+    "ieti_interface_product_noalloc": (C.c_int, [C.c_int, C.POINTER(C.c_int), _vp, _vp, _vp, C.c_int64, _vp,
+                                                 _vp, C.c_int, _vp]),
     "ieti_destroy": (None, [_vp]),
     "ieti_last_error": (C.c_char_p, [_vp]),
 }
@@ -238,6 +240,17 @@ def ieti_profile_read(ctx):
     calls = (C.c_int64 * n)()
     _check(ctx, _lib.ieti_profile_read(ctx, ms, calls, n))
     return {name: (ms[i], calls[i]) for i, name in enumerate(PROFILE_CLASSES)}
+
+
+def ieti_interface_product_noalloc(nI, M, dual, weight, x, y, m, nrhs=1, stream=None):
+    """y = sum_k B_k^T diag(w_k) M_k diag(w_k) B_k x with the library's fixed scratch.
+    nI: host sequence of block sizes; M, dual (int32), weight, x, y: device tensors."""
+    nI_a = np.ascontiguousarray(nI, np.int32)
+    st = _lib.ieti_interface_product_noalloc(len(nI_a), nI_a.ctypes.data_as(C.POINTER(C.c_int)), _dptr(M),
+                                             _dptr(dual), _dptr(weight), int(m), _dptr(x), _dptr(y), int(nrhs),
+                                             _stream(stream))
+    if st != IETI_OK:
+        raise IetiError(f"{STATUS.get(st, st)}: see stderr")
 
 
 def ieti_destroy(ctx):
