@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -271,6 +272,8 @@ ieti_status build(Ctx* c, const ieti_problem_desc* desc, bool device) {
 
   c->host_only = !device;
   if (!device) return IETI_OK;
+  c->no_coop = std::getenv("IETI_NO_COOP") != nullptr;
+  c->coop_trsv = !c->no_coop && std::getenv("IETI_COOP_TRSV") != nullptr;
   {
     int dev = 0, optin = 48 * 1024;
     IETI_CUDA_TRY(c, cudaGetDevice(&dev));

@@ -19,13 +19,6 @@ namespace ieti {
 template <typename T>
 ieti_status convert_copy(Ctx* c, const double* src, T* dst, int64_t n, cudaStream_t st);
 
-struct SolveDesc {
-  int64_t boff;   // offset of this subdomain's RHS block
-  int b0;         // first panel of the solve range
-  int ldb;        // leading dimension (rows of the range)
-  int ncol;       // columns for this subdomain
-  int pad_;
-};
 
 // ---------------------------------------------------------------------------
 // Cholesky kernels
@@ -197,33 +190,33 @@ constexpr int SOLVE_CT = 8;     // RHS columns per CTA
 constexpr int SOLVE_RC = 256;   // rows per CTA in the forward update
 constexpr int BWD_COLS = 64;    // rows above the panel per CTA in the backward update
 
-template <typename T>
+template <typename T, int CT>
 __global__ void __launch_bounds__(256) k_fwd(const SubDev* sd, const SolveDesc* dsc, const T* L, const T* Linv,
                                              T* B, T* Y, int b) {
   const int k = blockIdx.z;
   const SubDev s = sd[k];
   const SolveDesc d = dsc[k];
   if (b < d.b0 || b >= s.nblk || d.ncol == 0) return;
-  const int c0 = blockIdx.y * SOLVE_CT;
+  const int c0 = blockIdx.y * CT;
   if (c0 >= d.ncol) return;
-  const int nc = min(SOLVE_CT, d.ncol - c0);
+  const int nc = min(CT, d.ncol - c0);
   const int row0 = (b - d.b0) * NB;          // local row of panel b in the range
   const int rows = s.n - d.b0 * NB;          // rows of the range
   // CTAs without rows below the panel have nothing to do (CTA 0 writes y_b)
   if (blockIdx.x != 0 && row0 + NB + blockIdx.x * SOLVE_RC >= rows) return;
   __shared__ T Li[NB][NB + 1];
-  __shared__ T Bb[NB][SOLVE_CT];
-  __shared__ T y[NB][SOLVE_CT];
+  __shared__ T Bb[NB][CT];
+  __shared__ T y[NB][CT];
   const int tid = threadIdx.x;
   const T* Lb = Linv + s.linv + (int64_t)b * NB * NB;
   for (int t = tid; t < NB * NB; t += blockDim.x) Li[t % NB][t / NB] = Lb[t];
   T* Bk = B + d.boff;
-  for (int t = tid; t < NB * SOLVE_CT; t += blockDim.x) {
+  for (int t = tid; t < NB * CT; t += blockDim.x) {
     int i = t % NB, cc = t / NB;
     Bb[i][cc] = (cc < nc) ? Bk[row0 + i + (int64_t)d.ldb * (c0 + cc)] : (T)0;
   }
   __syncthreads();
-  for (int t = tid; t < NB * SOLVE_CT; t += blockDim.x) {
+  for (int t = tid; t < NB * CT; t += blockDim.x) {
     int i = t % NB, cc = t / NB;
     T acc = 0;
     for (int l = 0; l <= i; ++l) acc += Li[i][l] * Bb[l][cc];
@@ -240,45 +233,45 @@ __global__ void __launch_bounds__(256) k_fwd(const SubDev* sd, const SolveDesc* 
   // update the rows below the panel
   const int r = row0 + NB + blockIdx.x * SOLVE_RC + tid;
   if (r >= rows || tid >= SOLVE_RC) return;
-  T acc[SOLVE_CT];
+  T acc[CT];
 #pragma unroll
-  for (int cc = 0; cc < SOLVE_CT; ++cc) acc[cc] = 0;
+  for (int cc = 0; cc < CT; ++cc) acc[cc] = 0;
   const T* Lcol = L + s.A + (d.b0 * NB + r) + (int64_t)s.n * (b * NB);
   for (int l = 0; l < NB; ++l) {
     T lv = Lcol[(int64_t)s.n * l];
 #pragma unroll
-    for (int cc = 0; cc < SOLVE_CT; ++cc) acc[cc] += lv * y[l][cc];
+    for (int cc = 0; cc < CT; ++cc) acc[cc] += lv * y[l][cc];
   }
   for (int cc = 0; cc < nc; ++cc) Bk[r + (int64_t)d.ldb * (c0 + cc)] -= acc[cc];
 }
 
-template <typename T>
+template <typename T, int CT>
 __global__ void __launch_bounds__(256) k_bwd(const SubDev* sd, const SolveDesc* dsc, const T* L, const T* Linv,
                                              T* Y, T* X, int b) {
   const int k = blockIdx.z;
   const SubDev s = sd[k];
   const SolveDesc d = dsc[k];
   if (b < d.b0 || b >= s.nblk || d.ncol == 0) return;
-  const int c0 = blockIdx.y * SOLVE_CT;
+  const int c0 = blockIdx.y * CT;
   if (c0 >= d.ncol) return;
-  const int nc = min(SOLVE_CT, d.ncol - c0);
+  const int nc = min(CT, d.ncol - c0);
   const int row0 = (b - d.b0) * NB;
   // each CTA updates BWD_COLS rows above the panel; CTA 0 also writes x_b
   if (blockIdx.x != 0 && blockIdx.x * BWD_COLS >= row0) return;
   __shared__ T Li[NB][NB + 1];
-  __shared__ T Yb[NB][SOLVE_CT];
-  __shared__ T x[NB][SOLVE_CT];
+  __shared__ T Yb[NB][CT];
+  __shared__ T x[NB][CT];
   const int tid = threadIdx.x;
   const T* Lb = Linv + s.linv + (int64_t)b * NB * NB;
   for (int t = tid; t < NB * NB; t += blockDim.x) Li[t % NB][t / NB] = Lb[t];
   T* Yk = Y + d.boff;
-  for (int t = tid; t < NB * SOLVE_CT; t += blockDim.x) {
+  for (int t = tid; t < NB * CT; t += blockDim.x) {
     int i = t % NB, cc = t / NB;
     Yb[i][cc] = (cc < nc) ? Yk[row0 + i + (int64_t)d.ldb * (c0 + cc)] : (T)0;
   }
   __syncthreads();
   // x = Linv^T y: x[i] = sum_{l >= i} Li[l][i] y[l]
-  for (int t = tid; t < NB * SOLVE_CT; t += blockDim.x) {
+  for (int t = tid; t < NB * CT; t += blockDim.x) {
     int i = t % NB, cc = t / NB;
     T acc = 0;
     for (int l = i; l < NB; ++l) acc += Li[l][i] * Yb[l][cc];
@@ -314,18 +307,27 @@ ieti_status tri_solve(Ctx* c, const SubDev* d_sd, int nsub, int max_nblk, int ma
                       const SolveDesc* d_desc, int min_b0, const T* L, const T* Linv, T* B, T* Y, T* X,
                       cudaStream_t st) {
   if (max_ncol <= 0) return IETI_OK;
-  const int ctiles = (int)ceil_div(max_ncol, SOLVE_CT);
+  if (c->coop_trsv) {
+    // one persistent launch for both sweeps; the per-panel launches below are
+    // kept for devices without cooperative launch
+    ieti_status r = tri_solve_coop<T>(c, d_sd, nsub, max_nblk, min_b0, max_ncol, d_desc, L, Linv, B, Y, X, st);
+    if (r != IETI_ERR_STATE) return r;
+  }
+  const bool one = max_ncol == 1;   // single right-hand side: one-column kernels
+  const int ctiles = one ? 1 : (int)ceil_div(max_ncol, SOLVE_CT);
   cudaEvent_t p0 = prof_begin(c, st);
   for (int b = min_b0; b < max_nblk; ++b) {
     dim3 grid((unsigned)std::max<int64_t>(1, ceil_div(max_rows, SOLVE_RC)), ctiles, nsub);
-    k_fwd<T><<<grid, 256, 0, st>>>(d_sd, d_desc, L, Linv, B, Y, b);
+    if (one) k_fwd<T, 1><<<grid, 256, 0, st>>>(d_sd, d_desc, L, Linv, B, Y, b);
+    else k_fwd<T, SOLVE_CT><<<grid, 256, 0, st>>>(d_sd, d_desc, L, Linv, B, Y, b);
     IETI_LAUNCH_CHECK(c);
   }
   prof_end(c, PROF_FWD, p0, st);
   p0 = prof_begin(c, st);
   for (int b = max_nblk - 1; b >= min_b0; --b) {
     dim3 grid((unsigned)std::max<int64_t>(1, ceil_div(max_rows, BWD_COLS)), ctiles, nsub);
-    k_bwd<T><<<grid, 256, 0, st>>>(d_sd, d_desc, L, Linv, Y, X, b);
+    if (one) k_bwd<T, 1><<<grid, 256, 0, st>>>(d_sd, d_desc, L, Linv, Y, X, b);
+    else k_bwd<T, SOLVE_CT><<<grid, 256, 0, st>>>(d_sd, d_desc, L, Linv, Y, X, b);
     IETI_LAUNCH_CHECK(c);
   }
   prof_end(c, PROF_BWD, p0, st);

@@ -49,6 +49,22 @@ struct Prof {
   int64_t calls[PROF_NCAT] = {};
 };
 
+// one subdomain's right-hand-side block of a batched triangular solve
+struct SolveDesc {
+  int64_t boff;   // offset of this subdomain's RHS block
+  int b0;         // first panel of the solve range
+  int ldb;        // leading dimension (rows of the range)
+  int ncol;       // columns for this subdomain
+  int pad_;
+};
+
+struct Ctx;
+// persistent (cooperative) triangular solves L Y = B, L^T X = Y over all
+// subdomains in one launch; returns IETI_ERR_STATE if the device cannot run it
+template <typename T>
+ieti_status tri_solve_coop(Ctx* c, const SubDev* d_sd, int nsub, int max_nblk, int min_b0, int max_ncol,
+                           const SolveDesc* d_desc, const T* L, const T* Linv, T* B, T* Y, T* X, cudaStream_t st);
+
 // local DOF: direction d and global control-grid index (i, j, k) of its edge;
 // d = -1 for padding
 struct DofDev {
@@ -149,6 +165,8 @@ struct Ctx {
   double* wlam_acc = nullptr;            // accumulated multipliers
 
   bool assembled = false, factored = false, host_only = false;
+  bool no_coop = false;                  // IETI_NO_COOP=1: per-phase launches instead of the persistent PCG
+  bool coop_trsv = false;                // IETI_COOP_TRSV=1: persistent substitution sweeps (slower on GB300)
   ieti_precision prec = IETI_FP64;
 };
 
@@ -206,6 +224,9 @@ ieti_status factor_all(Ctx* c, cudaStream_t s);
 template <typename T>
 ieti_status local_solve(Ctx* c, T* B, T* Y, int ncol, int blk0, int which, cudaStream_t s);
 // solver
+// persistent PCG loop (state prepared by the caller); IETI_ERR_STATE if unavailable
+ieti_status pcg_coop(Ctx* c, double* lam, double* r, double* z, double* p, double* q, double tol2, int maxit,
+                     bool fp32, cudaStream_t st);
 ieti_status apply_F(Ctx* c, const double* lam, double* y, int nrhs, bool fp32_ops, cudaStream_t s);
 ieti_status apply_precond(Ctx* c, const double* r, double* z, int nrhs, bool fp32_ops, cudaStream_t s);
 ieti_status interface_rhs(Ctx* c, const double* jr, const double* jp, double* b, double* dprime,

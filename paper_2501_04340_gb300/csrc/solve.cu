@@ -696,9 +696,16 @@ static ieti_status pcg(Ctx* c, const double* b, double* lam, bool zero_start, do
   IETI_LAUNCH_CHECK(c);
   k_update_p<<<vg, 256, 0, st>>>(p, z, scal, m, 1);
   IETI_LAUNCH_CHECK(c);
+  bool persistent = false;
+  if (!c->no_coop && nrhs <= 8) {
+    // the whole iteration loop in one cooperative launch
+    ieti_status pr = pcg_coop(c, lam, r, z, p, q, tol2, maxit, fp32, st);
+    if (pr == IETI_OK) persistent = true;
+    else if (pr != IETI_ERR_STATE) return pr;
+  }
   const int check_every = 4;
   int it = 0;
-  for (; it < maxit; ++it) {
+  for (; !persistent && it < maxit; ++it) {
     if (it % check_every == 0) {
       k_all_done<<<1, 32, 0, st>>>(scal, nrhs, c->wflag);
       IETI_LAUNCH_CHECK(c);
