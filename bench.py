@@ -140,7 +140,7 @@ def ours(args):
     ctx = ieti.ieti_create(prob)
     q = ieti.ieti_query(ctx)
     nedge, m_r = q["nedge"], q["m_r"]
-    tol, tol_field = 1e-8, 1e-9
+    tol, tol_field = 1e-8, 1e-8
 
     # ---- reference field (FP64 factors, tight tolerances; untimed)
     ieti.ieti_assemble(ctx)

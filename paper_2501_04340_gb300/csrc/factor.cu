@@ -125,29 +125,40 @@ __global__ void __launch_bounds__(256) k_syrk(const SubDev* sd, T* L, int b) {
   const int cc = t - rr * (rr + 1) / 2;
   if (rr >= Tk) return;
   const int r = b + 1 + rr, c = b + 1 + cc;
-  __shared__ T Lr[NB][NB + 1];
-  __shared__ T Lc[NB][NB + 1];
+  // panels stored transposed (Lr[l][i] = L[r-block row i, panel column l]) with
+  // 16-byte aligned rows, so a thread reads its 4 rows / 4 columns as vectors
+  constexpr int LDS = NB + 16 / (int)sizeof(T);
+  __shared__ __align__(16) T Lr[NB][LDS];
+  __shared__ __align__(16) T Lc[NB][LDS];
   const int tid = threadIdx.x;
   const T* Pr = L + s.A + (int64_t)r * NB + (int64_t)s.n * b * NB;
   const T* Pc = L + s.A + (int64_t)c * NB + (int64_t)s.n * b * NB;
   for (int x = tid; x < NB * NB; x += blockDim.x) {
     int i = x % NB, j = x / NB;
-    Lr[j][i] = Pr[i + (int64_t)s.n * j];   // transposed: Lr[l][i]
+    Lr[j][i] = Pr[i + (int64_t)s.n * j];
     Lc[j][i] = Pc[i + (int64_t)s.n * j];
   }
   __syncthreads();
-  const int ti = tid % 16, tj = tid / 16;
+  const int ti = tid % 16, tj = tid / 16;   // rows 4ti..4ti+3, columns 4tj..4tj+3
   T acc[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc[u][v] = 0;
+#pragma unroll 8
   for (int l = 0; l < NB; ++l) {
     T x[4], y[4];
+    if constexpr (sizeof(T) == 4) {
+      float4 xv = *reinterpret_cast<const float4*>(&Lr[l][4 * ti]);
+      float4 yv = *reinterpret_cast<const float4*>(&Lc[l][4 * tj]);
+      x[0] = xv.x; x[1] = xv.y; x[2] = xv.z; x[3] = xv.w;
+      y[0] = yv.x; y[1] = yv.y; y[2] = yv.z; y[3] = yv.w;
+    } else {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      x[u] = Lr[l][ti + 16 * u];
-      y[u] = Lc[l][tj + 16 * u];
+      for (int u = 0; u < 4; ++u) {
+        x[u] = Lr[l][4 * ti + u];
+        y[u] = Lc[l][4 * tj + u];
+      }
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u)
@@ -159,7 +170,7 @@ __global__ void __launch_bounds__(256) k_syrk(const SubDev* sd, T* L, int b) {
   for (int v = 0; v < 4; ++v)
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      int i = ti + 16 * u, j = tj + 16 * v;
+      int i = 4 * ti + u, j = 4 * tj + v;
       Out[i + (int64_t)s.n * j] -= acc[u][v];
     }
 }
@@ -302,6 +313,92 @@ __global__ void __launch_bounds__(256) k_bwd(const SubDev* sd, const SolveDesc* 
   }
 }
 
+// Single right-hand side: the diagonal solve reads the stored block inverse
+// directly (coalesced, no shared-memory staging) and the update of the rows
+// below spreads each row's 64-term dot product over 4 threads, so a launch has
+// 4x more CTAs in flight for the same rows.
+constexpr int FWD1_ROWS = 64;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fwd1(const SubDev* sd, const SolveDesc* dsc, const T* L, const T* Linv,
+                                              T* B, T* Y, int b) {
+  const int k = blockIdx.y;
+  const SubDev s = sd[k];
+  const SolveDesc d = dsc[k];
+  if (b < d.b0 || b >= s.nblk || d.ncol == 0) return;
+  const int row0 = (b - d.b0) * NB;
+  const int rows = s.n - d.b0 * NB;
+  const int rbeg = row0 + NB + blockIdx.x * FWD1_ROWS;
+  if (blockIdx.x != 0 && rbeg >= rows) return;
+  __shared__ T y[NB], bb[NB];
+  const int tid = threadIdx.x;
+  T* Bk = B + d.boff;
+  if (tid < NB) bb[tid] = Bk[row0 + tid];
+  __syncthreads();
+  {
+    // y_i = sum_{l <= i} Linv[i][l] b_l: 4 threads per row i, 16 terms each
+    const T* Lb = Linv + s.linv + (int64_t)b * NB * NB;
+    const int i = tid / 4, part = tid % 4;
+    T acc = 0;
+#pragma unroll
+    for (int l = part * 16; l < part * 16 + 16; ++l) acc += Lb[i + NB * l] * bb[l];   // Linv[i][l] = 0 for l > i
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (part == 0) {
+      y[i] = acc;
+      if (blockIdx.x == 0) Y[d.boff + row0 + i] = acc;
+    }
+  }
+  __syncthreads();
+  const int r = rbeg + tid / 4, part = tid % 4;
+  T acc = 0;
+  if (r < rows) {
+    const T* Lrow = L + s.A + (d.b0 * NB + r) + (int64_t)s.n * (b * NB + part * 16);
+#pragma unroll
+    for (int l = 0; l < 16; ++l) acc += Lrow[(int64_t)s.n * l] * y[part * 16 + l];
+  }
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  if (r < rows && part == 0) Bk[r] -= acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_bwd1(const SubDev* sd, const SolveDesc* dsc, const T* L, const T* Linv,
+                                              T* Y, T* X, int b) {
+  const int k = blockIdx.y;
+  const SubDev s = sd[k];
+  const SolveDesc d = dsc[k];
+  if (b < d.b0 || b >= s.nblk || d.ncol == 0) return;
+  const int row0 = (b - d.b0) * NB;
+  if (blockIdx.x != 0 && blockIdx.x * BWD_COLS >= row0) return;
+  __shared__ T x[NB];
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  T* Yk = Y + d.boff;
+  {
+    // x_i = sum_{l >= i} Linv[l][i] y_l: warp w computes x_i for i = w, w+8, ...
+    const T* Lb = Linv + s.linv + (int64_t)b * NB * NB;
+    const T y0 = Yk[row0 + lane], y1 = Yk[row0 + lane + 32];
+#pragma unroll
+    for (int i = warp; i < NB; i += 8) {
+      T v = (lane >= i ? Lb[lane + NB * i] * y0 : (T)0) + (lane + 32 >= i ? Lb[lane + 32 + NB * i] * y1 : (T)0);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) x[i] = v;
+    }
+  }
+  __syncthreads();
+  if (blockIdx.x == 0 && tid < NB) X[d.boff + row0 + tid] = x[tid];
+  for (int w = warp; w < BWD_COLS; w += 8) {
+    const int ccol = blockIdx.x * BWD_COLS + w;
+    if (ccol >= row0) break;
+    const T* Lc = L + s.A + (int64_t)b * NB + (int64_t)s.n * (d.b0 * NB + ccol);
+    T v = Lc[lane] * x[lane] + Lc[lane + 32] * x[lane + 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) Yk[ccol] -= v;
+  }
+}
+
 template <typename T>
 ieti_status tri_solve(Ctx* c, const SubDev* d_sd, int nsub, int max_nblk, int max_rows, int max_ncol,
                       const SolveDesc* d_desc, int min_b0, const T* L, const T* Linv, T* B, T* Y, T* X,
@@ -318,7 +415,9 @@ ieti_status tri_solve(Ctx* c, const SubDev* d_sd, int nsub, int max_nblk, int ma
   cudaEvent_t p0 = prof_begin(c, st);
   for (int b = min_b0; b < max_nblk; ++b) {
     dim3 grid((unsigned)std::max<int64_t>(1, ceil_div(max_rows, SOLVE_RC)), ctiles, nsub);
-    if (one) k_fwd<T, 1><<<grid, 256, 0, st>>>(d_sd, d_desc, L, Linv, B, Y, b);
+    if (one)
+      k_fwd1<T><<<dim3((unsigned)std::max<int64_t>(1, ceil_div(max_rows, FWD1_ROWS)), nsub), 256, 0, st>>>(
+          d_sd, d_desc, L, Linv, B, Y, b);
     else k_fwd<T, SOLVE_CT><<<grid, 256, 0, st>>>(d_sd, d_desc, L, Linv, B, Y, b);
     IETI_LAUNCH_CHECK(c);
   }
@@ -326,7 +425,9 @@ ieti_status tri_solve(Ctx* c, const SubDev* d_sd, int nsub, int max_nblk, int ma
   p0 = prof_begin(c, st);
   for (int b = max_nblk - 1; b >= min_b0; --b) {
     dim3 grid((unsigned)std::max<int64_t>(1, ceil_div(max_rows, BWD_COLS)), ctiles, nsub);
-    if (one) k_bwd<T, 1><<<grid, 256, 0, st>>>(d_sd, d_desc, L, Linv, Y, X, b);
+    if (one)
+      k_bwd1<T><<<dim3((unsigned)std::max<int64_t>(1, ceil_div(max_rows, BWD_COLS)), nsub), 256, 0, st>>>(
+          d_sd, d_desc, L, Linv, Y, X, b);
     else k_bwd<T, SOLVE_CT><<<grid, 256, 0, st>>>(d_sd, d_desc, L, Linv, Y, X, b);
     IETI_LAUNCH_CHECK(c);
   }

@@ -226,20 +226,21 @@ struct PcgArgs {
   int u_ld;         // rows of the staged u (>= every ldI)
 };
 
-constexpr int PC_ROWS = 32;    // rows of a local block per work item
+constexpr int PC_ROWS = 16;    // rows of a local block per work item
 constexpr int PCG_COOP_MAX_GRID = 1024;
 constexpr int PC_SC = 16;
 
+// CTA sum in a fixed order: butterfly within each warp (lane 0's value), then
+// the warp sums in warp order; every thread returns the same value
 __device__ inline double cta_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  __syncthreads();   // red is free
+  if (lane == 0) red[warp] = v;
   __syncthreads();
-  red[threadIdx.x] = v;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  double s = red[0];
-  __syncthreads();
+  double s = 0;
+  for (int w = 0; w < (int)(blockDim.x / 32); ++w) s += red[w];
   return s;
 }
 
@@ -254,11 +255,11 @@ __device__ inline double sum_part(const double* part, int col, double* red) {
 // local products of one work item: rows [r0, r0 + PC_ROWS) of M_k times u_k
 template <typename T, int CT>
 __device__ void pc_local(const PcgArgs& A, const T* M, const double* src, bool scaled, double* out, int k, int chunk,
-                         T* u) {
+                         T* u, bool gather) {
   const SubDev s = A.sd[k];
   const int nI = s.nI;
   __syncthreads();
-  for (int i = threadIdx.x; i < s.ldI; i += blockDim.x) {
+  for (int i = threadIdx.x; gather && i < s.ldI; i += blockDim.x) {
     if (i < nI) {
       const double w = A.I_sign[s.iv + i] * (scaled ? A.I_scale[s.iv + i] : 1.0);
       const int l = A.I_dual[s.iv + i];
@@ -332,16 +333,24 @@ __global__ void __launch_bounds__(256) k_pcg_coop(PcgArgs A) {
     bool all = true;
     for (int cc = 0; cc < A.nrhs; ++cc) all &= done[cc] != 0;
     if (all) break;
-    // ---- A: local products with W and primal partials
-    for (int item = blockIdx.x; item < A.total_items; item += gridDim.x) {
-      int k = 0, base = 0;
-      for (; k < A.nsub; ++k) {
-        const int nch = (A.sd[k].nI + PC_ROWS - 1) / PC_ROWS;
-        if (item < base + nch) break;
-        base += nch;
+    // ---- A: local products with W and primal partials. Each CTA takes a
+    // contiguous run of items (ordered by subdomain) and stages u_k once per
+    // subdomain of the run.
+    const int per = (A.total_items + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int ibeg = blockIdx.x * per, iend = min(A.total_items, ibeg + per);
+    int k0 = 0, base0 = 0;
+    while (k0 < A.nsub && ibeg >= base0 + (A.sd[k0].nI + PC_ROWS - 1) / PC_ROWS) {
+      base0 += (A.sd[k0].nI + PC_ROWS - 1) / PC_ROWS;
+      ++k0;
+    }
+    for (int item = ibeg, k = k0, base = base0, lastk = -1; item < iend; ++item) {
+      while (item >= base + (A.sd[k].nI + PC_ROWS - 1) / PC_ROWS) {
+        base += (A.sd[k].nI + PC_ROWS - 1) / PC_ROWS;
+        ++k;
       }
       const int chunk = item - base;
-      pc_local<T, CT>(A, (const T*)A.W, A.p, false, A.t1, k, chunk, u);
+      pc_local<T, CT>(A, (const T*)A.W, A.p, false, A.t1, k, chunk, u, k != lastk);
+      lastk = k;
       if (chunk == 0) {
         const SubDev s = A.sd[k];
         const int warp = tid / 32, lane = tid % 32;
@@ -447,14 +456,13 @@ __global__ void __launch_bounds__(256) k_pcg_coop(PcgArgs A) {
       if (blockIdx.x == 0 && A.hist && its <= A.hist_cap) A.hist[2 * (its - 1)] = alpha[0];
     }
     __syncthreads();
-    for (int item = blockIdx.x; item < A.total_items; item += gridDim.x) {
-      int k = 0, base = 0;
-      for (; k < A.nsub; ++k) {
-        const int nch = (A.sd[k].nI + PC_ROWS - 1) / PC_ROWS;
-        if (item < base + nch) break;
-        base += nch;
+    for (int item = ibeg, k = k0, base = base0, lastk = -1; item < iend; ++item) {
+      while (item >= base + (A.sd[k].nI + PC_ROWS - 1) / PC_ROWS) {
+        base += (A.sd[k].nI + PC_ROWS - 1) / PC_ROWS;
+        ++k;
       }
-      pc_local<T, CT>(A, (const T*)A.S, A.r, true, A.t2, k, item - base, u);
+      pc_local<T, CT>(A, (const T*)A.S, A.r, true, A.t2, k, item - base, u, k != lastk);
+      lastk = k;
     }
     grid.sync();
     // ---- E: z = preconditioned r, partial <r, z>
