@@ -268,6 +268,84 @@ ieti_status ieti_interface_product_noalloc(int nsub, const int* nI_host, const d
                                            const int* dual_dev, const double* weight_dev, int64_t m,
                                            const double* x_dev, double* y_dev, int nrhs, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned warm start for the interface multipliers (the paper has no learned
+ * component; this is an extension). A 3-layer perceptron maps a parameter
+ * vector of a problem instance (for example log nu per patch and the source
+ * amplitudes) to an initial guess lambda0 for ieti_solve. PCG on Eq. (7) keeps
+ * its own stopping test, so the guess changes iteration counts, not accuracy.
+ *
+ * Network: x' = (x - shift) .* scale; Z1 = x' W1^T + b1, A1 = relu(Z1);
+ * Z2 = A1 W2^T + b2, A2 = relu(Z2); y = A2 W3^T + b3; lambda0 = out_scale * y.
+ * GEMM operands are rounded to bfloat16 (round to nearest even), products are
+ * accumulated in FP32 on the tensor cores; biases, master weights, gradients
+ * and Adam moments are FP32. W_l is (out x in) row-major.
+ * Parameter vector layout (FP32, host): W1 | b1 | W2 | b2 | W3 | b3, sizes
+ * h*n_in, h, h*h, h, n_out*h, n_out.
+ * Loss: mean over the batch and outputs of (y - t/out_scale)^2 (targets t in
+ * multiplier units). Adam: beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected.
+ * Batches are row-major (batch x n_in / batch x n_out) FP32 device arrays.
+ * ------------------------------------------------------------------------- */
+typedef struct ieti_mlp ieti_mlp;
+
+/* Allocates parameters (zero), moments, activations for up to max_batch rows.
+ * IETI_ERR_INVALID_ARG on sizes < 1, IETI_ERR_OOM if allocation fails (the
+ * handle is still returned and must be destroyed). Synchronous. */
+ieti_status ieti_mlp_create(int n_in, int n_hidden, int n_out, int max_batch, ieti_mlp** out);
+/* sizes4 = {n_in, n_hidden, n_out, max_batch}; *nparam = parameter count. */
+ieti_status ieti_mlp_query(const ieti_mlp* m, int* sizes4, int64_t* nparam);
+/* Copies all parameters from the host (count must equal the parameter count),
+ * resets the Adam moments and step counter. Synchronous. */
+ieti_status ieti_mlp_set_params(ieti_mlp* m, const float* params_host, int64_t count);
+/* Input normalisation (n_in entries each, host) and output scale (> 0). */
+ieti_status ieti_mlp_set_scaling(ieti_mlp* m, const float* shift_host, const float* scale_host,
+                                 float out_scale);
+/* which = 0: parameters, 1: gradients of the last backward pass, 2: the input
+ * shift (n_in), input scale (n_in) and out_scale (1). *count is set to the
+ * number of values; with out_host == NULL nothing is copied, else cap must be
+ * >= *count. IETI_ERR_INVALID_ARG for another `which`. Synchronous. */
+ieti_status ieti_mlp_get(ieti_mlp* m, int which, float* out_host, int64_t cap, int64_t* count);
+/* lambda0 (batch x n_out) for inputs x (batch x n_in); 1 <= batch <= max_batch.
+ * Enqueued on `stream`. */
+ieti_status ieti_mlp_forward(ieti_mlp* m, const float* x_dev, float* y_dev, int batch, void* stream);
+/* As ieti_mlp_forward, but lambda0 is written in FP64: row b of lam_dev
+ * (batch x n_out row-major) is the initial guess of load case / instance b, the
+ * multi-column layout ieti_solve takes for lam0_dev. */
+ieti_status ieti_mlp_forward_f64(ieti_mlp* m, const float* x_dev, double* lam_dev, int batch,
+                                 void* stream);
+/* Source-linear head: the outputs of a row are read as ncoef blocks of
+ * m = n_out / ncoef values (the responses to ncoef unit sources, which the
+ * solution depends on linearly) and combined with that row's coefficients:
+ *   lam[b, j] = out_scale * sum_c coef[b, c] * y[b, c m + j]   (FP64 sum)
+ * coef_dev: batch x ncoef FP64 row-major; lam_dev: batch x m FP64 row-major
+ * (the lam0 layout of ieti_solve). IETI_ERR_INVALID_ARG unless ncoef divides
+ * n_out. Enqueued on `stream`. */
+ieti_status ieti_mlp_forward_combine(ieti_mlp* m, const float* x_dev, const double* coef_dev, int ncoef,
+                                     double* lam_dev, int batch, void* stream);
+/* Forward + loss + gradients of all parameters for targets t (batch x n_out).
+ * If loss_host is not NULL, the loss is copied there and the stream is
+ * synchronised; otherwise returns before completion. */
+ieti_status ieti_mlp_backward(ieti_mlp* m, const float* x_dev, const float* t_dev, int batch,
+                              float* loss_host, void* stream);
+/* One Adam step with learning rate lr > 0 on the last gradients; refreshes the
+ * bfloat16 weight copies. Enqueued on `stream`. */
+ieti_status ieti_mlp_adam(ieti_mlp* m, float lr, void* stream);
+/* Mini-batch training on n_samples pairs (X_dev: n_samples x n_in, T_dev:
+ * n_samples x n_out, FP32 row-major, device). With normalise != 0 the input
+ * shift/scale are first set to the per-feature mean and 1/std of X and
+ * out_scale to the root mean square of T (1 if that is 0). Each epoch visits
+ * the samples in an order drawn by a Fisher-Yates shuffle from splitmix64
+ * seeded with (seed, epoch); batches of `batch` rows (the last one ragged),
+ * one backward pass and one Adam step each, learning rate lr * decay^epoch
+ * (0 < decay <= 1). loss_host (optional) receives the mean batch loss of the
+ * last epoch. Synchronises the stream at the start (normalise) and at the end
+ * (loss_host); IETI_ERR_INVALID_ARG on bad sizes. */
+ieti_status ieti_mlp_fit(ieti_mlp* m, const float* X_dev, const float* T_dev, int n_samples, int batch,
+                         int epochs, float lr, float decay, unsigned long long seed, int normalise,
+                         float* loss_host, void* stream);
+void ieti_mlp_destroy(ieti_mlp* m);
+const char* ieti_mlp_last_error(const ieti_mlp* m);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,6 +78,20 @@ _sig = {
                                                  _vp, C.c_int, _vp]),
     "ieti_destroy": (None, [_vp]),
     "ieti_last_error": (C.c_char_p, [_vp]),
+    "ieti_mlp_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(_vp)]),
+    "ieti_mlp_query": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
+    "ieti_mlp_set_params": (C.c_int, [_vp, C.POINTER(C.c_float), C.c_int64]),
+    "ieti_mlp_set_scaling": (C.c_int, [_vp, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_float]),
+    "ieti_mlp_get": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_float), C.c_int64, C.POINTER(C.c_int64)]),
+    "ieti_mlp_forward": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp]),
+    "ieti_mlp_backward": (C.c_int, [_vp, _vp, _vp, C.c_int, C.POINTER(C.c_float), _vp]),
+    "ieti_mlp_adam": (C.c_int, [_vp, C.c_float, _vp]),
+    "ieti_mlp_forward_f64": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp]),
+    "ieti_mlp_forward_combine": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp, C.c_int, _vp]),
+    "ieti_mlp_fit": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, C.c_float, C.c_float, C.c_ulonglong,
+                               C.c_int, C.POINTER(C.c_float), _vp]),
+    "ieti_mlp_destroy": (None, [_vp]),
+    "ieti_mlp_last_error": (C.c_char_p, [_vp]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -259,3 +273,103 @@ def ieti_destroy(ctx):
 
 def ieti_last_error(ctx):
     return _lib.ieti_last_error(ctx).decode()
+
+
+# --- learned warm start (3-layer BF16 perceptron) --------------------------------
+
+def _mcheck(m, st):
+    if st != IETI_OK:
+        msg = _lib.ieti_mlp_last_error(m).decode() if m else ""
+        raise IetiError(f"{STATUS.get(st, st)}: {msg}")
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, np.float32)
+
+
+def ieti_mlp_create(n_in, n_hidden, n_out, max_batch):
+    m = C.c_void_p()
+    st = _lib.ieti_mlp_create(int(n_in), int(n_hidden), int(n_out), int(max_batch), C.byref(m))
+    if st != IETI_OK:
+        if m:
+            _lib.ieti_mlp_destroy(m)
+        _mcheck(None, st)
+    return m
+
+
+def ieti_mlp_query(m):
+    sz = (C.c_int * 4)()
+    npar = C.c_int64()
+    _mcheck(m, _lib.ieti_mlp_query(m, sz, C.byref(npar)))
+    return {"n_in": sz[0], "n_hidden": sz[1], "n_out": sz[2], "max_batch": sz[3], "nparam": npar.value}
+
+
+def ieti_mlp_set_params(m, params):
+    """params: flat host vector W1|b1|W2|b2|W3|b3 (or a list of those arrays)."""
+    if isinstance(params, (list, tuple)):
+        params = np.concatenate([np.ravel(p) for p in params])
+    p = _f32(params)
+    _mcheck(m, _lib.ieti_mlp_set_params(m, p.ctypes.data_as(C.POINTER(C.c_float)), p.size))
+
+
+def ieti_mlp_set_scaling(m, shift, scale, out_scale=1.0):
+    a, b = _f32(shift), _f32(scale)
+    _mcheck(m, _lib.ieti_mlp_set_scaling(m, a.ctypes.data_as(C.POINTER(C.c_float)),
+                                         b.ctypes.data_as(C.POINTER(C.c_float)), float(out_scale)))
+
+
+def ieti_mlp_get(m, which=0):
+    n = C.c_int64()
+    _mcheck(m, _lib.ieti_mlp_get(m, int(which), None, 0, C.byref(n)))
+    out = np.empty(n.value, np.float32)
+    _mcheck(m, _lib.ieti_mlp_get(m, int(which), out.ctypes.data_as(C.POINTER(C.c_float)), n.value, C.byref(n)))
+    return out
+
+
+def ieti_mlp_forward(m, x, y, batch=None, stream=None):
+    """x: (batch, n_in) float32 CUDA tensor; y: (batch, n_out) float32 CUDA tensor."""
+    b = x.shape[0] if batch is None else batch
+    _mcheck(m, _lib.ieti_mlp_forward(m, _dptr(x), _dptr(y), int(b), _stream(stream)))
+
+
+def ieti_mlp_forward_f64(m, x, lam, batch=None, stream=None):
+    """lam: (batch, n_out) float64 CUDA tensor (the lam0 layout of ieti_solve)."""
+    b = x.shape[0] if batch is None else batch
+    _mcheck(m, _lib.ieti_mlp_forward_f64(m, _dptr(x), _dptr(lam), int(b), _stream(stream)))
+
+
+def ieti_mlp_forward_combine(m, x, coef, lam, batch=None, stream=None):
+    """x (batch, n_in) float32, coef (batch, ncoef) float64, lam (batch, n_out/ncoef)
+    float64: CUDA tensors."""
+    b = x.shape[0] if batch is None else batch
+    _mcheck(m, _lib.ieti_mlp_forward_combine(m, _dptr(x), _dptr(coef), int(coef.shape[1]), _dptr(lam), int(b),
+                                             _stream(stream)))
+
+
+def ieti_mlp_fit(m, X, T, batch, epochs, lr, decay=1.0, seed=0, normalise=True, stream=None):
+    """Trains on all rows of X (n, n_in) / T (n, n_out), float32 CUDA tensors;
+    returns the mean batch loss of the last epoch."""
+    loss = C.c_float(float("nan"))
+    _mcheck(m, _lib.ieti_mlp_fit(m, _dptr(X), _dptr(T), int(X.shape[0]), int(batch), int(epochs), float(lr),
+                                 float(decay), int(seed), int(bool(normalise)), C.byref(loss), _stream(stream)))
+    return loss.value
+
+
+def ieti_mlp_backward(m, x, t, batch=None, want_loss=True, stream=None):
+    b = x.shape[0] if batch is None else batch
+    loss = C.c_float(float("nan"))
+    _mcheck(m, _lib.ieti_mlp_backward(m, _dptr(x), _dptr(t), int(b), C.byref(loss) if want_loss else None,
+                                      _stream(stream)))
+    return loss.value if want_loss else None
+
+
+def ieti_mlp_adam(m, lr, stream=None):
+    _mcheck(m, _lib.ieti_mlp_adam(m, float(lr), _stream(stream)))
+
+
+def ieti_mlp_destroy(m):
+    _lib.ieti_mlp_destroy(m)
+
+
+def ieti_mlp_last_error(m):
+    return _lib.ieti_mlp_last_error(m).decode()

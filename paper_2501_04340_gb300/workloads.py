@@ -365,3 +365,77 @@ def small_cases():
                          sub_of_patch=np.array([0, 0, 1, 2, 2, 1, 3, 3, 4, 5, 5, 4], np.int32),
                          nu=10.0 ** rng.uniform(0, 3, 12), name="cube12_p2_mixed"))
     return out
+
+
+# ----------------------------------------------------------------------------
+# parameter family for the learned warm start
+# ----------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class WarmstartFamily:
+    """Instances of one mesh that differ in the per-patch reluctivity and in 16
+    source coefficients: nu_q = 10^(3 u_q), u_q ~ U(0, 1) per patch, and
+    J = sum_m (a_{2m} cos(2 pi k_m.x) - a_{2m+1} sin(2 pi k_m.x)) e_m with 8
+    fixed modes k_m, fixed unit directions e_m orthogonal to k_m (so J is
+    divergence free) and a ~ N(0, 1)^16. The network input of an instance is
+    x = [log10 nu (npatch values), a (16 values)]."""
+    base: Problem
+    modes: np.ndarray        # (8, 3) integer wave vectors
+    dirs: np.ndarray         # (8, 3) unit vectors, dirs[m] . modes[m] = 0
+    log_nu: np.ndarray       # (n, npatch)
+    coef: np.ndarray         # (n, 16)
+
+    @property
+    def n(self) -> int:
+        return int(self.log_nu.shape[0])
+
+    def inputs(self) -> np.ndarray:
+        return np.concatenate([self.log_nu, self.coef], axis=1).astype(np.float32)
+
+    def nu(self, i: int) -> np.ndarray:
+        return 10.0 ** self.log_nu[i]
+
+    def source_params(self, i: int) -> np.ndarray:
+        """SOURCE_FOURIER parameters of instance i (one load case)."""
+        return self.source_params_for(self.coef[i])
+
+    def source_params_for(self, coef) -> np.ndarray:
+        """SOURCE_FOURIER parameters of one load case with coefficients `coef` (16)."""
+        col = [float(len(self.modes))]
+        for m, (k, e) in enumerate(zip(self.modes, self.dirs)):
+            col.extend(list(k) + list(coef[2 * m] * e) + list(coef[2 * m + 1] * e))
+        return np.array(col)
+
+    def basis_source_params(self) -> np.ndarray:
+        """16 load cases, load case c with coefficient vector e_c: the solution of
+        an instance with coefficients a is sum_c a_c times the solution of load
+        case c (the source enters Eq. (3) linearly)."""
+        return np.concatenate([self.source_params_for(np.eye(16)[c]) for c in range(16)])
+
+
+def warmstart_family(n: int, seed: int, patches=(4, 4, 4), block=(2, 2, 2), spans: int = 2,
+                     p: int = 2, kmax: int = 2) -> WarmstartFamily:
+    """n seeded instances on the unit cube split into `patches` affine patches,
+    grouped into equal subdomains of `block` patches."""
+    rng = np.random.default_rng(seed)
+    # modes and directions are fixed by a generator of their own so that every
+    # seed shares them
+    frng = np.random.default_rng(12345)
+    modes, dirs = [], []
+    while len(modes) < 8:
+        k = frng.integers(-kmax, kmax + 1, size=3)
+        if not k.any() or any((k == q).all() or (k == -q).all() for q in modes):
+            continue
+        e = frng.standard_normal(3)
+        e = e - (e @ k) * k / (k @ k)
+        modes.append(k)
+        dirs.append(e / np.linalg.norm(e))
+    npt = int(np.prod(patches))
+    sub = block_partition(tuple(patches), tuple(block))
+    fam = WarmstartFamily(base=None, modes=np.array(modes, np.float64), dirs=np.array(dirs),
+                          log_nu=rng.uniform(0.0, 3.0, size=(n, npt)),
+                          coef=rng.standard_normal((n, 16)))
+    fam.base = unit_cube(p, tuple(patches), spans, sub_of_patch=sub, nu=fam.nu(0),
+                         name=f"warmstart_{patches[0]}x{patches[1]}x{patches[2]}_p{p}n{spans}",
+                         source_kind=SOURCE_FOURIER, source_params=fam.source_params(0), nrhs=1)
+    return fam
