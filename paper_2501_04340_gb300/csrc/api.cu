@@ -280,7 +280,7 @@ ieti_status build(Ctx* c, const ieti_problem_desc* desc, bool device) {
     IETI_CUDA_TRY(c, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     TRY(assemble_kernel_attrs(c, optin));
     TRY(solve_kernel_attrs(c, optin));
-    if ((size_t)c->max_ldI * 8 * sizeof(double) > (size_t)optin) {
+    if ((size_t)c->max_ldI * sizeof(double) * 2 > (size_t)optin) {
       c->err = "interface block too large for the shared-memory staging of the local products";
       return IETI_ERR_INVALID_ARG;
     }
@@ -363,6 +363,7 @@ ieti_status build(Ctx* c, const ieti_problem_desc* desc, bool device) {
   TRY(dalloc(c, &c->SPiInv, 5 * ldc * ldc + ldc * NB + 64));
   TRY(dalloc(c, &c->d_err, 4));
   IETI_CUDA_TRY(c, cudaMallocHost(&c->h_err, sizeof(int) * 4));
+  TRY(iface_alloc(c));
   return IETI_OK;
 }
 

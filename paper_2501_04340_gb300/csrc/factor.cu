@@ -676,7 +676,8 @@ static ieti_status coarse_factor(Ctx* c, cudaStream_t st) {
 ieti_status factor_all(Ctx* c, cudaStream_t st) {
   ieti_status r = (c->prec == IETI_FP64) ? factor_t<double>(c, st) : factor_t<float>(c, st);
   if (r != IETI_OK) return r;
-  return coarse_factor(c, st);
+  if ((r = coarse_factor(c, st)) != IETI_OK) return r;
+  return iface_prepare(c, st);
 }
 
 // full local solves on r-vectors (used by the solver), type T buffers

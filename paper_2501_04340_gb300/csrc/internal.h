@@ -71,6 +71,16 @@ struct DofDev {
   int d, i, j, k;
 };
 
+// tile table of the streamed interface products (one per precision and operator)
+struct StreamPlan {
+  bool built = false;
+  bool incomplete = false;   // a subdomain without interface rows has primal rows (not streamed)
+  int ntiles = 0, grid = 0, stage_bytes = 0;
+  int64_t bytes = 0;         // bytes streamed per column group
+  void* d_tiles = nullptr;
+  int* d_cta = nullptr;      // first tile of every CTA (grid + 1 entries)
+};
+
 struct DeviceBuf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -164,6 +174,24 @@ struct Ctx {
   double* wres_p = nullptr;
   double* wlam_acc = nullptr;            // accumulated multipliers
 
+  // streamed interface products (iface.cu)
+  int sm_count = 0, smem_optin = 0;
+  StreamPlan splan[2][2];                // [FP32 operators][with the Phi_I^T rows]
+  void* PhiT = nullptr;                  // rows of Phi_I^(k)T in the factor precision (nP x ldI)
+  std::vector<int64_t> phio;             // their offsets
+  int64_t* d_phio = nullptr;
+  int4* d_gs = nullptr;                  // per multiplier: iv and i of both sides
+  int2* d_gn = nullptr;                  // per multiplier: nI of both sides
+  int2* d_gu = nullptr;                  // per multiplier: positions of both sides in the u vectors
+  std::vector<int64_t> uoff;             // per subdomain: offset of u_k (ldI_k entries)
+  int64_t utot = 0;                      // column stride of the u vectors
+  void* uall = nullptr;                  // prepared u vectors (factor precision, MAX_RHS columns)
+  int32_t* d_gell_i = nullptr;           // coarse part of the F gather (ELL, m_r x gell_E)
+  double* d_gell_v = nullptr;
+  int gell_E = 0;
+  int4* d_pcon = nullptr;                // contributors of each coarse DOF: (pv_k, c, nP_k)
+  int* d_stream_err = nullptr;           // set when a bulk-copy wait times out
+
   bool assembled = false, factored = false, host_only = false;
   bool no_coop = false;                  // IETI_NO_COOP=1: per-phase launches instead of the persistent PCG
   bool coop_trsv = false;                // IETI_COOP_TRSV=1: persistent substitution sweeps (slower on GB300)
@@ -223,6 +251,17 @@ ieti_status factor_all(Ctx* c, cudaStream_t s);
 // triangular solves with the local factors on the r-vectors in c->wr[...]
 template <typename T>
 ieti_status local_solve(Ctx* c, T* B, T* Y, int ncol, int blk0, int which, cudaStream_t s);
+// streamed interface products (iface.cu)
+ieti_status iface_alloc(Ctx* c);
+ieti_status iface_prepare(Ctx* c, cudaStream_t s);
+ieti_status iface_local(Ctx* c, bool fp32, bool with_phi, const double* x, const double* scale, double* t,
+                        double* qpart, int nrhs, cudaStream_t s);
+bool iface_coarse_fused(const Ctx* c);
+ieti_status iface_gather_F(Ctx* c, const double* t, const double* qpart, const double* yc, int nrhs, double* y,
+                           const double* dotv, double* part, int blocks, cudaStream_t s);
+ieti_status iface_gather_P(Ctx* c, const double* t, int nrhs, double* z, const double* dotv, double* part,
+                           int blocks, cudaStream_t s);
+ieti_status iface_check(Ctx* c, cudaStream_t s);
 // solver
 // persistent PCG loop (state prepared by the caller); IETI_ERR_STATE if unavailable
 ieti_status pcg_coop(Ctx* c, double* lam, double* r, double* z, double* p, double* q, double tol2, int maxit,

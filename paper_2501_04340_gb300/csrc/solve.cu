@@ -517,9 +517,10 @@ static ieti_status launch_local(Ctx* c, const T* M, const double* x, const doubl
                                 cudaStream_t st) {
   if (c->max_nI == 0) return IETI_OK;
   const int cat = scale ? PROF_LOCAL_S : PROF_LOCAL_W;
-  if (nrhs == 1) return launch_local_ct<T, 1>(c, M, x, scale, t, nrhs, cat, st);
-  if (nrhs == 2) return launch_local_ct<T, 2>(c, M, x, scale, t, nrhs, cat, st);
-  if (nrhs <= 4) return launch_local_ct<T, 4>(c, M, x, scale, t, nrhs, cat, st);
+  const int64_t fit = c->smem_optin / ((int64_t)c->max_ldI * sizeof(T));   // columns u can hold
+  if (nrhs == 1 || fit < 2) return launch_local_ct<T, 1>(c, M, x, scale, t, nrhs, cat, st);
+  if (nrhs == 2 || fit < 4) return launch_local_ct<T, 2>(c, M, x, scale, t, nrhs, cat, st);
+  if (nrhs <= 4 || fit < 8) return launch_local_ct<T, 4>(c, M, x, scale, t, nrhs, cat, st);
   return launch_local_ct<T, 8>(c, M, x, scale, t, nrhs, cat, st);
 }
 
@@ -559,10 +560,20 @@ static ieti_status apply_F_ex(Ctx* c, const double* lam, double* y, int nrhs, bo
                               double* part, cudaStream_t st) {
   ieti_status r;
   double* t = c->wi[0];
+  const bool coarse = c->n_gp > 0;
+  // streamed path: W_k and Phi_I^(k)T rows in one pass, then the coarse solve
+  // and the gather with the coarse part as an ELL matrix
+  r = iface_local(c, fp32, true, lam, nullptr, t, c->wq_part, nrhs, st);
+  if (r == IETI_OK) {
+    const bool fused = iface_coarse_fused(c);
+    if (coarse && !fused && (r = coarse_solve(c, c->wq_part, c->wc[0], nrhs, st)) != IETI_OK) return r;
+    return iface_gather_F(c, t, c->wq_part, (coarse && !fused) ? c->wc[0] : nullptr, nrhs, y, dotv, part,
+                          gather_blocks(c), st);
+  }
+  if (r != IETI_ERR_STATE) return r;
   if (fp32) r = launch_local<float>(c, (const float*)c->W, lam, nullptr, t, nrhs, st);
   else r = launch_local<double>(c, (const double*)c->W, lam, nullptr, t, nrhs, st);
   if (r != IETI_OK) return r;
-  const bool coarse = c->n_gp > 0;
   if (coarse) {
     k_phiT<<<c->nsub, 256, 0, st>>>(c->d_sd, c->Phi, c->d_I_dual, c->d_I_sign, lam, c->m_r, c->wq_part, nrhs);
     IETI_LAUNCH_CHECK(c);
@@ -585,6 +596,9 @@ static ieti_status apply_precond_ex(Ctx* c, const double* rv, double* z, int nrh
                                     double* part, cudaStream_t st) {
   ieti_status r;
   double* t = c->wi[1];
+  r = iface_local(c, fp32, false, rv, c->d_I_scale, t, nullptr, nrhs, st);
+  if (r == IETI_OK) return iface_gather_P(c, t, nrhs, z, dotv, part, gather_blocks(c), st);
+  if (r != IETI_ERR_STATE) return r;
   if (fp32) r = launch_local<float>(c, (const float*)c->S, rv, c->d_I_scale, t, nrhs, st);
   else r = launch_local<double>(c, (const double*)c->S, rv, c->d_I_scale, t, nrhs, st);
   if (r != IETI_OK) return r;

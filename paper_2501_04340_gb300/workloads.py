@@ -222,50 +222,39 @@ def is_simply_connected_union(npatch, members) -> bool:
 
 
 def greedy_partition(npatch, sizes_lo: int, sizes_hi: int, nsub: int, seed: int,
-                     max_tries: int = 200) -> np.ndarray:
-    """Uneven partition of the patch grid into ``nsub`` simply connected subdomains
-    with sizes in [sizes_lo, sizes_hi] (seeded BFS region growing; a draw whose
-    parts are not all simply connected is rejected and redrawn)."""
+                     moves: int = 600) -> np.ndarray:
+    """Uneven partition of the patch grid into ``nsub`` simply connected
+    subdomains with sizes in [sizes_lo, sizes_hi]: start from the aligned block
+    partition into nsub equal blocks and apply seeded boundary moves (a patch
+    joins the subdomain of a face neighbour); a move is kept only if both
+    subdomains stay within the size bounds and simply connected."""
     total = int(np.prod(npatch))
+    per = total // nsub
+    side = round(per ** (1.0 / 3.0))
+    if side ** 3 * nsub != total or any(n % side for n in npatch):
+        raise ValueError("the start partition needs nsub equal cubic blocks")
+    sub = block_partition(tuple(npatch), (side, side, side))
+    size = np.bincount(sub, minlength=nsub)
     rng = np.random.default_rng(seed)
-    for _ in range(max_tries):
-        # seeded sizes summing to total
-        sizes = rng.integers(sizes_lo, sizes_hi + 1, size=nsub)
-        while sizes.sum() != total:
-            i = int(rng.integers(nsub))
-            if sizes.sum() > total and sizes[i] > sizes_lo:
-                sizes[i] -= 1
-            elif sizes.sum() < total and sizes[i] < sizes_hi:
-                sizes[i] += 1
-        sub = -np.ones(total, np.int32)
-        ok = True
-        for s in range(nsub):
-            free = np.flatnonzero(sub < 0)
-            # start at the free patch with the smallest index (sweeps the grid)
-            start = int(free[0])
-            region = [start]
-            sub[start] = s
-            frontier = [n for n in _patch_neighbours(npatch, start) if sub[n] < 0]
-            while len(region) < sizes[s]:
-                frontier = [n for n in dict.fromkeys(frontier) if sub[n] < 0]
-                if not frontier:
-                    ok = False
-                    break
-                # prefer the most compact growth: frontier patch with most region neighbours
-                scores = [sum(1 for m in _patch_neighbours(npatch, n) if sub[m] == s) for n in frontier]
-                best = max(scores)
-                cands = [n for n, sc in zip(frontier, scores) if sc == best]
-                n = int(cands[int(rng.integers(len(cands)))])
-                sub[n] = s
-                region.append(n)
-                frontier.extend(m for m in _patch_neighbours(npatch, n) if sub[m] < 0)
-            if not ok:
-                break
-        if not ok or (sub < 0).any():
+    done, attempts = 0, 0
+    while done < moves and attempts < 50 * moves:
+        attempts += 1
+        q = int(rng.integers(total))
+        nbrs = [n for n in _patch_neighbours(npatch, q) if sub[n] != sub[q]]
+        if not nbrs:
             continue
-        if all(is_simply_connected_union(npatch, np.flatnonzero(sub == s)) for s in range(nsub)):
-            return sub
-    raise RuntimeError("no simply connected partition found")
+        src, dst = int(sub[q]), int(sub[nbrs[int(rng.integers(len(nbrs)))]])
+        if size[src] - 1 < sizes_lo or size[dst] + 1 > sizes_hi:
+            continue
+        sub[q] = dst
+        if (is_simply_connected_union(npatch, np.flatnonzero(sub == src))
+                and is_simply_connected_union(npatch, np.flatnonzero(sub == dst))):
+            size[src] -= 1
+            size[dst] += 1
+            done += 1
+        else:
+            sub[q] = src
+    return sub
 
 
 # ----------------------------------------------------------------------------
