@@ -409,6 +409,7 @@ ieti_status iface_alloc(Ctx* c) {
       const SubDev& sk = c->sd_host[pc[e].x];
       pcon[e] = make_int4((int)sk.pv, pc[e].y, sk.nP, 0);
     }
+    c->pcon_count = po.back();
     if ((r = alloc_dev(c, &c->d_pcon, pcon.size())) != IETI_OK) return r;
     IETI_CUDA_TRY(c, cudaMemcpy(c->d_pcon, pcon.data(), sizeof(int4) * pcon.size(), cudaMemcpyHostToDevice));
   }

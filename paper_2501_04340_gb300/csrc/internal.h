@@ -190,6 +190,7 @@ struct Ctx {
   double* d_gell_v = nullptr;
   int gell_E = 0;
   int4* d_pcon = nullptr;                // contributors of each coarse DOF: (pv_k, c, nP_k)
+  int64_t pcon_count = 0;
   int* d_stream_err = nullptr;           // set when a bulk-copy wait times out
 
   bool assembled = false, factored = false, host_only = false;
@@ -262,6 +263,10 @@ ieti_status iface_gather_F(Ctx* c, const double* t, const double* qpart, const d
 ieti_status iface_gather_P(Ctx* c, const double* t, int nrhs, double* z, const double* dotv, double* part,
                            int blocks, cudaStream_t s);
 ieti_status iface_check(Ctx* c, cudaStream_t s);
+// the PCG loop in one cooperative launch on the streamed products (pcg_stream.cu);
+// IETI_ERR_STATE when that form does not apply
+ieti_status pcg_stream(Ctx* c, double* lam, double* r, double* z, double* p, double* q, double tol2, int maxit,
+                       bool fp32, cudaStream_t st);
 // solver
 // persistent PCG loop (state prepared by the caller); IETI_ERR_STATE if unavailable
 ieti_status pcg_coop(Ctx* c, double* lam, double* r, double* z, double* p, double* q, double tol2, int maxit,

@@ -712,8 +712,10 @@ static ieti_status pcg(Ctx* c, const double* b, double* lam, bool zero_start, do
   IETI_LAUNCH_CHECK(c);
   bool persistent = false;
   if (!c->no_coop && nrhs <= 8) {
-    // the whole iteration loop in one cooperative launch
-    ieti_status pr = pcg_coop(c, lam, r, z, p, q, tol2, maxit, fp32, st);
+    // the whole iteration loop in one cooperative launch: on the streamed
+    // products if they apply, else with per-item local products
+    ieti_status pr = pcg_stream(c, lam, r, z, p, q, tol2, maxit, fp32, st);
+    if (pr == IETI_ERR_STATE) pr = pcg_coop(c, lam, r, z, p, q, tol2, maxit, fp32, st);
     if (pr == IETI_OK) persistent = true;
     else if (pr != IETI_ERR_STATE) return pr;
   }

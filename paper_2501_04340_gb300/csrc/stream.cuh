@@ -181,6 +181,59 @@ __device__ __forceinline__ void stream_init_bars(unsigned char* smem, int stages
   __syncthreads();
 }
 
+// Producer warp only: copies the descriptors of the first WIN tiles of
+// [tb, te) into window 0 and issues the bulk copies of the first `stages`
+// tiles (they do not depend on u), so that a later stream_tiles call with the
+// same range, seq and npre = the return value finds them in flight. The
+// consumers of the previous range must be done with the window and the
+// stages they used (the caller places a barrier in between). Returns the
+// number of tiles issued (0 after a timed-out wait, which sets the abort flag).
+template <typename T>
+__device__ int stream_prefetch(const StreamCtx& C, int tb, int te, unsigned char* smem, uint32_t seq, int ct) {
+  const int n = te - tb;
+  if (n <= 0) return 0;
+  StreamBars B(smem);
+  LTile* win = reinterpret_cast<LTile*>(smem + BAR_BYTES);
+  const size_t ubytes = ((sizeof(T) * (size_t)C.u_ld * ct + 127) / 128) * 128;
+  unsigned char* stage_base = smem + stream_hdr(ct) + 2 * ubytes;
+  const int lane = threadIdx.x % 32;
+  const uint32_t S = (uint32_t)C.stages;
+  if (lane < n && lane < WIN) win[lane] = C.tiles[tb + lane];
+  __syncwarp();
+  int npre = 0;
+  if (lane == 0) {
+    const int want = min(n, (int)S);
+    for (int j = 0; j < want && !*B.abort_flag; ++j) {
+      const LTile tl = win[j];
+      const uint32_t sq = seq + (uint32_t)j;
+      const uint32_t st = sq % S, use = sq / S;
+      if (use > 0 && !mbar_wait(&B.empty[st], (use - 1) & 1u)) {
+        atomicExch(C.err, 1);
+        *B.abort_flag = 1;
+        break;
+      }
+      const T* src = (tl.kind ? (const T*)C.PhiT : (const T*)C.M) + tl.src;
+      mbar_expect_tx(&B.full[st], (uint32_t)tl.bytes);
+      bulk_load(stage_base + (size_t)st * C.stage_bytes, src, (uint32_t)tl.bytes, &B.full[st]);
+      npre = j + 1;
+    }
+  }
+  return __shfl_sync(0xffffffffu, npre, 0);
+}
+
+// Producer warp only: waits (bounded) for tiles issued by stream_prefetch that
+// will not be consumed (the loop ended), so that no copy is in flight when the
+// CTA exits.
+__device__ inline void stream_drain(unsigned char* smem, uint32_t seq, int npre, int stages) {
+  StreamBars B(smem);
+  if (threadIdx.x % 32 == 0)
+    for (int j = 0; j < npre; ++j) {
+      const uint32_t sq = seq + (uint32_t)j;
+      mbar_wait(&B.full[sq % (uint32_t)stages], (sq / (uint32_t)stages) & 1u);
+    }
+  __syncwarp();
+}
+
 // Streams tiles [tb, te) and writes t (kind 0) and qpart (kind 1) for columns
 // col0 .. col0+nc-1 of an nrhs-column layout. Called by all STREAM_THREADS
 // threads: warps 0-7 consume, warp 8 (lane 0) issues the bulk copies: u_k at
@@ -201,7 +254,8 @@ __device__ __forceinline__ void stream_init_bars(unsigned char* smem, int stages
 // sum over the 8 warps.
 template <typename T, int CT, bool ROWS = false>
 __device__ void stream_tiles(const StreamCtx& C, int tb, int te, unsigned char* smem, uint32_t& seq,
-                             uint32_t& useq, double* t, double* qpart, int nrhs, int col0, int nc) {
+                             uint32_t& useq, double* t, double* qpart, int nrhs, int col0, int nc,
+                             int npre = 0) {
   constexpr int VEC = 16 / sizeof(T);
   constexpr int V = RMAX * CT;
   const int n = te - tb;
@@ -224,7 +278,7 @@ __device__ void stream_tiles(const StreamCtx& C, int tb, int te, unsigned char* 
     int issued = 0, pk = -1;
     bool stop = false;
     for (int j = 0; j < n && !stop; ++j) {
-      if (j % WIN == 0) {
+      if (j % WIN == 0 && !(j == 0 && npre > 0)) {   // window 0 is filled by stream_prefetch
         const int jj = j + lane;
         if (jj < n) win[((j / WIN) & 1) * WIN + lane] = C.tiles[tb + jj];
         __syncwarp();
@@ -248,7 +302,9 @@ __device__ void stream_tiles(const StreamCtx& C, int tb, int te, unsigned char* 
             pk = tl.k;
           }
         }
-        if (!stop) {
+        if (!stop && j < npre) {
+          issued = j + 1;   // copied ahead by stream_prefetch
+        } else if (!stop) {
           const uint32_t sq = seq + (uint32_t)j;
           const uint32_t st = sq % S, use = sq / S;
           if (use > 0 && !mbar_wait(&B.empty[st], (use - 1) & 1u)) {
