@@ -404,9 +404,9 @@ ieti_status tri_solve(Ctx* c, const SubDev* d_sd, int nsub, int max_nblk, int ma
                       const SolveDesc* d_desc, int min_b0, const T* L, const T* Linv, T* B, T* Y, T* X,
                       cudaStream_t st) {
   if (max_ncol <= 0) return IETI_OK;
-  if (c->coop_trsv) {
-    // one persistent launch for both sweeps; the per-panel launches below are
-    // kept for devices without cooperative launch
+  if (!c->no_coop) {
+    // one persistent launch per sweep (single column, or any width when opted
+    // in); the per-panel launches below serve devices without cooperative launch
     ieti_status r = tri_solve_coop<T>(c, d_sd, nsub, max_nblk, min_b0, max_ncol, d_desc, L, Linv, B, Y, X, st);
     if (r != IETI_ERR_STATE) return r;
   }

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -180,11 +181,170 @@ static ieti_status launch_coop(Ctx* c, const SubDev* d_sd, int nsub, int max_nbl
   return IETI_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Single-column sweeps as one persistent launch each: the panel loop runs
+// inside the kernel with a grid barrier per panel. Every CTA that owns work in
+// a subdomain forms that panel's 64-entry solution itself (from the stored
+// inverse of the diagonal block), so one barrier per panel suffices. A thread
+// issues all 64 loads of its row (forward) or column (backward) before the
+// panel's solution is needed.
+// ---------------------------------------------------------------------------
+
+constexpr int SW_ROWS = 256;   // rows (forward) or columns (backward) per work item
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sweep1_fwd(const SubDev* sd, const SolveDesc* dsc, int nsub, int max_nblk,
+                                                    int min_b0, const T* L, const T* Linv, T* B, T* Y) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ T bb[NB], y[NB];
+  const int tid = threadIdx.x;
+  for (int b = min_b0; b < max_nblk; ++b) {
+    int item = blockIdx.x, base = 0;
+    for (int k = 0; k < nsub; ++k) {
+      const SubDev s = sd[k];
+      const SolveDesc d = dsc[k];
+      if (b < d.b0 || b >= s.nblk || d.ncol <= 0) continue;
+      const int rows = s.n - d.b0 * NB, row0 = (b - d.b0) * NB;
+      const int below = rows - row0 - NB;
+      const int cnt = below > 0 ? (below + SW_ROWS - 1) / SW_ROWS : 1;
+      for (; item < base + cnt; item += gridDim.x) {
+        const int ch = item - base;
+        T* Bk = B + d.boff;
+        const int r = row0 + NB + ch * SW_ROWS + tid;
+        const bool valid = r < rows;
+        T lv[NB];
+        const T* Lrow = L + s.A + (d.b0 * NB + r) + (int64_t)s.n * (b * NB);
+#pragma unroll
+        for (int l = 0; l < NB; ++l) lv[l] = valid ? Lrow[(int64_t)s.n * l] : (T)0;
+        const T* Lb = Linv + s.linv + (int64_t)b * NB * NB;
+        const int i = tid / 4, part = tid % 4;
+        T li[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) li[q] = Lb[i + NB * (part * 16 + q)];   // zero above the diagonal
+        __syncthreads();   // the previous item is done with bb and y
+        if (tid < NB) bb[tid] = Bk[row0 + tid];
+        __syncthreads();
+        T acc = 0;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) acc += li[q] * bb[part * 16 + q];
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        if (part == 0) {
+          y[i] = acc;
+          if (ch == 0) Y[d.boff + row0 + i] = acc;
+        }
+        __syncthreads();
+        if (valid) {
+          T u = 0;
+#pragma unroll
+          for (int l = 0; l < NB; ++l) u += lv[l] * y[l];
+          Bk[r] -= u;
+        }
+      }
+      base += cnt;
+    }
+    grid.sync();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sweep1_bwd(const SubDev* sd, const SolveDesc* dsc, int nsub, int max_nblk,
+                                                    int min_b0, const T* L, const T* Linv, T* Y, T* X) {
+  cg::grid_group grid = cg::this_grid();
+  using V2 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  constexpr int VL = 16 / sizeof(T);
+  __shared__ T yb[NB], x[NB];
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  for (int b = max_nblk - 1; b >= min_b0; --b) {
+    int item = blockIdx.x, base = 0;
+    for (int k = 0; k < nsub; ++k) {
+      const SubDev s = sd[k];
+      const SolveDesc d = dsc[k];
+      if (b < d.b0 || b >= s.nblk || d.ncol <= 0) continue;
+      const int row0 = (b - d.b0) * NB;
+      const int cnt = row0 > 0 ? (row0 + SW_ROWS - 1) / SW_ROWS : 1;
+      for (; item < base + cnt; item += gridDim.x) {
+        const int ch = item - base;
+        T* Yk = Y + d.boff;
+        // this thread's column: the 64 entries of row block b, contiguous
+        const int ccol = ch * SW_ROWS + tid;
+        const bool valid = ccol < row0;
+        V2 lv[NB / VL];
+        const V2* Lc = reinterpret_cast<const V2*>(L + s.A + (d.b0 * NB + row0) + (int64_t)s.n * (d.b0 * NB + ccol));
+#pragma unroll
+        for (int q = 0; q < NB / VL; ++q) {
+          if (valid) lv[q] = Lc[q];
+          else if constexpr (VL == 4) lv[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+          else lv[q] = make_double2(0.0, 0.0);
+        }
+        // x_i = sum_{l >= i} Linv[l][i] y_l: warp w computes x_i for i = w, w + 8, ...
+        const T* Lb = Linv + s.linv + (int64_t)b * NB * NB;
+        __syncthreads();   // the previous item is done with yb and x
+        if (tid < NB) yb[tid] = Yk[row0 + tid];
+        __syncthreads();
+        for (int i = warp; i < NB; i += 8) {
+          T v = (lane >= i ? Lb[lane + NB * i] * yb[lane] : (T)0) +
+                (lane + 32 >= i ? Lb[lane + 32 + NB * i] * yb[lane + 32] : (T)0);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (lane == 0) x[i] = v;
+        }
+        __syncthreads();
+        if (ch == 0 && tid < NB) X[d.boff + row0 + tid] = x[tid];
+        if (valid) {
+          T u = 0;
+#pragma unroll
+          for (int q = 0; q < NB / VL; ++q) {
+            if constexpr (VL == 4) {
+              u += lv[q].x * x[4 * q] + lv[q].y * x[4 * q + 1] + lv[q].z * x[4 * q + 2] + lv[q].w * x[4 * q + 3];
+            } else {
+              u += lv[q].x * x[2 * q] + lv[q].y * x[2 * q + 1];
+            }
+          }
+          Yk[ccol] -= u;
+        }
+      }
+      base += cnt;
+    }
+    grid.sync();
+  }
+}
+
+template <typename T>
+static ieti_status launch_sweep1(Ctx* c, const SubDev* d_sd, int nsub, int max_nblk, int min_b0,
+                                 const SolveDesc* d_desc, const T* L, const T* Linv, T* B, T* Y, T* X,
+                                 cudaStream_t st) {
+  int dev = 0, sms = 0, pf = 0, pb = 0, coop = 0;
+  IETI_CUDA_TRY(c, cudaGetDevice(&dev));
+  IETI_CUDA_TRY(c, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) return IETI_ERR_STATE;
+  IETI_CUDA_TRY(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  IETI_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pf, k_sweep1_fwd<T>, 256, 0));
+  IETI_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pb, k_sweep1_bwd<T>, 256, 0));
+  const int per_sm = std::min(std::min(pf, pb), 4);
+  if (per_sm < 1) return IETI_ERR_STATE;
+  const dim3 grid(sms * per_sm);
+  void* fa[] = {(void*)&d_sd, (void*)&d_desc, (void*)&nsub, (void*)&max_nblk, (void*)&min_b0,
+                (void*)&L, (void*)&Linv, (void*)&B, (void*)&Y};
+  cudaEvent_t p0 = prof_begin(c, st);
+  IETI_CUDA_TRY(c, cudaLaunchCooperativeKernel((void*)k_sweep1_fwd<T>, grid, dim3(256), fa, 0, st));
+  prof_end(c, PROF_FWD, p0, st);
+  IETI_LAUNCH_CHECK(c);
+  void* ba[] = {(void*)&d_sd, (void*)&d_desc, (void*)&nsub, (void*)&max_nblk, (void*)&min_b0,
+                (void*)&L, (void*)&Linv, (void*)&Y, (void*)&X};
+  p0 = prof_begin(c, st);
+  IETI_CUDA_TRY(c, cudaLaunchCooperativeKernel((void*)k_sweep1_bwd<T>, grid, dim3(256), ba, 0, st));
+  prof_end(c, PROF_BWD, p0, st);
+  IETI_LAUNCH_CHECK(c);
+  return IETI_OK;
+}
+
 template <typename T>
 ieti_status tri_solve_coop(Ctx* c, const SubDev* d_sd, int nsub, int max_nblk, int min_b0, int max_ncol,
                            const SolveDesc* d_desc, const T* L, const T* Linv, T* B, T* Y, T* X, cudaStream_t st) {
   if (max_ncol <= 0) return IETI_OK;
-  if (max_ncol == 1) return launch_coop<T, 1>(c, d_sd, nsub, max_nblk, min_b0, d_desc, L, Linv, B, Y, X, st);
+  if (max_ncol == 1) return launch_sweep1<T>(c, d_sd, nsub, max_nblk, min_b0, d_desc, L, Linv, B, Y, X, st);
+  if (!c->coop_trsv) return IETI_ERR_STATE;   // multi-column: per-panel launches unless opted in
   return launch_coop<T, 8>(c, d_sd, nsub, max_nblk, min_b0, d_desc, L, Linv, B, Y, X, st);
 }
 
