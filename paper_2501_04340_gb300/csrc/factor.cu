@@ -197,120 +197,124 @@ __global__ void k_snapshot(const SubDev* sd, const T* L, T* S, int b) {
 // triangular solves L Y = B (forward) and L^T X = Y (backward) on a panel range
 // ---------------------------------------------------------------------------
 
-constexpr int SOLVE_CT = 8;     // RHS columns per CTA
-constexpr int SOLVE_RC = 256;   // rows per CTA in the forward update
-constexpr int BWD_COLS = 64;    // rows above the panel per CTA in the backward update
+// Many right-hand sides (W = S_rIrI^-1 from identity columns, Phi from K_rp):
+// blocked substitution whose work is 64 x 64 x 64 tile products. Forward,
+// panel b: Y_b = Linv_b B_b, then B_below -= L_below,b Y_b. Backward, panel b:
+// X_b = Linv_b^T Y_b, then Y_above -= L_b,above^T X_b. One CTA per 64 x 64 output
+// tile, 4 x 4 outputs per thread from shared-memory copies of both operands.
 
-template <typename T, int CT>
-__global__ void __launch_bounds__(256) k_fwd(const SubDev* sd, const SolveDesc* dsc, const T* L, const T* Linv,
-                                             T* B, T* Y, int b) {
-  const int k = blockIdx.z;
-  const SubDev s = sd[k];
-  const SolveDesc d = dsc[k];
-  if (b < d.b0 || b >= s.nblk || d.ncol == 0) return;
-  const int c0 = blockIdx.y * CT;
-  if (c0 >= d.ncol) return;
-  const int nc = min(CT, d.ncol - c0);
-  const int row0 = (b - d.b0) * NB;          // local row of panel b in the range
-  const int rows = s.n - d.b0 * NB;          // rows of the range
-  // CTAs without rows below the panel have nothing to do (CTA 0 writes y_b)
-  if (blockIdx.x != 0 && row0 + NB + blockIdx.x * SOLVE_RC >= rows) return;
-  __shared__ T Li[NB][NB + 1];
-  __shared__ T Bb[NB][CT];
-  __shared__ T y[NB][CT];
+constexpr int BWD_COLS = 64;    // single-column backward: rows above the panel per CTA
+
+// C(i, j) = (or -=) sum_l P(i, l) Q(l, j) on one 64 x 64 tile with K = 64;
+// P(i, l) = P[i pi + l pl], Q(l, j) = Q[l ql + j qj], C(i, j) = C[i + j ldc];
+// rows i >= mi and columns j >= nj are not touched (their operands read as 0)
+template <typename T, bool SUB>
+__device__ __forceinline__ void tile_gemm64(const T* P, int64_t pi, int64_t pl, int mi, const T* Q, int64_t ql,
+                                            int64_t qj, int nj, T* C, int64_t ldc) {
+  constexpr int LDS = NB + 16 / (int)sizeof(T);
+  __shared__ __align__(16) T Ps[NB][LDS];
+  __shared__ __align__(16) T Qs[NB][LDS];
   const int tid = threadIdx.x;
-  const T* Lb = Linv + s.linv + (int64_t)b * NB * NB;
-  for (int t = tid; t < NB * NB; t += blockDim.x) Li[t % NB][t / NB] = Lb[t];
-  T* Bk = B + d.boff;
-  for (int t = tid; t < NB * CT; t += blockDim.x) {
-    int i = t % NB, cc = t / NB;
-    Bb[i][cc] = (cc < nc) ? Bk[row0 + i + (int64_t)d.ldb * (c0 + cc)] : (T)0;
+  // the index with unit stride runs fastest over the threads (coalesced loads)
+  const bool p_i_fast = pi == 1, q_l_fast = ql == 1;
+  for (int x = tid; x < NB * NB; x += blockDim.x) {
+    const int i = p_i_fast ? x % NB : x / NB, l = p_i_fast ? x / NB : x % NB;
+    Ps[l][i] = i < mi ? P[i * pi + l * pl] : (T)0;
+    const int lq = q_l_fast ? x % NB : x / NB, j = q_l_fast ? x / NB : x % NB;
+    Qs[lq][j] = j < nj ? Q[lq * ql + j * qj] : (T)0;
   }
   __syncthreads();
-  for (int t = tid; t < NB * CT; t += blockDim.x) {
-    int i = t % NB, cc = t / NB;
-    T acc = 0;
-    for (int l = 0; l <= i; ++l) acc += Li[i][l] * Bb[l][cc];
-    y[i][cc] = acc;
-  }
-  __syncthreads();
-  if (blockIdx.x == 0) {
-    T* Yk = Y + d.boff;
-    for (int t = tid; t < NB * nc; t += blockDim.x) {
-      int i = t % NB, cc = t / NB;
-      Yk[row0 + i + (int64_t)d.ldb * (c0 + cc)] = y[i][cc];
-    }
-  }
-  // update the rows below the panel
-  const int r = row0 + NB + blockIdx.x * SOLVE_RC + tid;
-  if (r >= rows || tid >= SOLVE_RC) return;
-  T acc[CT];
+  const int ti = tid % 16, tj = tid / 16;
+  T acc[4][4];
 #pragma unroll
-  for (int cc = 0; cc < CT; ++cc) acc[cc] = 0;
-  const T* Lcol = L + s.A + (d.b0 * NB + r) + (int64_t)s.n * (b * NB);
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0;
+#pragma unroll 8
   for (int l = 0; l < NB; ++l) {
-    T lv = Lcol[(int64_t)s.n * l];
+    T x[4], y[4];
+    if constexpr (sizeof(T) == 4) {
+      const float4 xv = *reinterpret_cast<const float4*>(&Ps[l][4 * ti]);
+      const float4 yv = *reinterpret_cast<const float4*>(&Qs[l][4 * tj]);
+      x[0] = xv.x; x[1] = xv.y; x[2] = xv.z; x[3] = xv.w;
+      y[0] = yv.x; y[1] = yv.y; y[2] = yv.z; y[3] = yv.w;
+    } else {
 #pragma unroll
-    for (int cc = 0; cc < CT; ++cc) acc[cc] += lv * y[l][cc];
+      for (int u = 0; u < 4; ++u) {
+        x[u] = Ps[l][4 * ti + u];
+        y[u] = Qs[l][4 * tj + u];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] += x[u] * y[v];
   }
-  for (int cc = 0; cc < nc; ++cc) Bk[r + (int64_t)d.ldb * (c0 + cc)] -= acc[cc];
+#pragma unroll
+  for (int v = 0; v < 4; ++v)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = 4 * ti + u, j = 4 * tj + v;
+      if (i < mi && j < nj) {
+        if (SUB) C[i + j * ldc] -= acc[u][v];
+        else C[i + j * ldc] = acc[u][v];
+      }
+    }
 }
 
-template <typename T, int CT>
-__global__ void __launch_bounds__(256) k_bwd(const SubDev* sd, const SolveDesc* dsc, const T* L, const T* Linv,
-                                             T* Y, T* X, int b) {
+// diagonal block of panel b for column tile blockIdx.x: Dst_b = Linv_b Src_b
+// (forward) or Linv_b^T Src_b (backward)
+template <typename T, bool TRANS>
+__global__ void __launch_bounds__(256) k_tsolve_diag(const SubDev* sd, const SolveDesc* dsc, const T* Linv,
+                                                     const T* Src, T* Dst, int b) {
+  const int k = blockIdx.y;
+  const SubDev s = sd[k];
+  const SolveDesc d = dsc[k];
+  if (b < d.b0 || b >= s.nblk || d.ncol == 0) return;
+  const int j0 = blockIdx.x * NB;
+  if (j0 >= d.ncol) return;
+  const int row0 = (b - d.b0) * NB;
+  const T* Lb = Linv + s.linv + (int64_t)b * NB * NB;
+  const int64_t o = d.boff + row0 + (int64_t)d.ldb * j0;
+  if (TRANS) tile_gemm64<T, false>(Lb, NB, 1, NB, Src + o, 1, d.ldb, min(NB, d.ncol - j0), Dst + o, d.ldb);
+  else tile_gemm64<T, false>(Lb, 1, NB, NB, Src + o, 1, d.ldb, min(NB, d.ncol - j0), Dst + o, d.ldb);
+}
+
+// forward update of panel b: B[rows below] -= L[rows below, panel b] Y_b
+template <typename T>
+__global__ void __launch_bounds__(256) k_tsolve_fwd(const SubDev* sd, const SolveDesc* dsc, const T* L, T* B,
+                                                    const T* Y, int b) {
   const int k = blockIdx.z;
   const SubDev s = sd[k];
   const SolveDesc d = dsc[k];
   if (b < d.b0 || b >= s.nblk || d.ncol == 0) return;
-  const int c0 = blockIdx.y * CT;
-  if (c0 >= d.ncol) return;
-  const int nc = min(CT, d.ncol - c0);
+  const int j0 = blockIdx.y * NB;
+  if (j0 >= d.ncol) return;
+  const int row0 = (b - d.b0) * NB, rows = s.n - d.b0 * NB;
+  const int r0 = row0 + NB + blockIdx.x * NB;
+  if (r0 >= rows) return;
+  const T* P = L + s.A + (d.b0 * NB + r0) + (int64_t)s.n * (b * NB);
+  tile_gemm64<T, true>(P, 1, s.n, min(NB, rows - r0), Y + d.boff + row0 + (int64_t)d.ldb * j0, 1, d.ldb,
+                       min(NB, d.ncol - j0), B + d.boff + r0 + (int64_t)d.ldb * j0, d.ldb);
+}
+
+// backward update of panel b: Y[rows above] -= L[panel b, rows above]^T X_b
+template <typename T>
+__global__ void __launch_bounds__(256) k_tsolve_bwd(const SubDev* sd, const SolveDesc* dsc, const T* L, T* Y,
+                                                    const T* X, int b) {
+  const int k = blockIdx.z;
+  const SubDev s = sd[k];
+  const SolveDesc d = dsc[k];
+  if (b < d.b0 || b >= s.nblk || d.ncol == 0) return;
+  const int j0 = blockIdx.y * NB;
+  if (j0 >= d.ncol) return;
   const int row0 = (b - d.b0) * NB;
-  // each CTA updates BWD_COLS rows above the panel; CTA 0 also writes x_b
-  if (blockIdx.x != 0 && blockIdx.x * BWD_COLS >= row0) return;
-  __shared__ T Li[NB][NB + 1];
-  __shared__ T Yb[NB][CT];
-  __shared__ T x[NB][CT];
-  const int tid = threadIdx.x;
-  const T* Lb = Linv + s.linv + (int64_t)b * NB * NB;
-  for (int t = tid; t < NB * NB; t += blockDim.x) Li[t % NB][t / NB] = Lb[t];
-  T* Yk = Y + d.boff;
-  for (int t = tid; t < NB * CT; t += blockDim.x) {
-    int i = t % NB, cc = t / NB;
-    Yb[i][cc] = (cc < nc) ? Yk[row0 + i + (int64_t)d.ldb * (c0 + cc)] : (T)0;
-  }
-  __syncthreads();
-  // x = Linv^T y: x[i] = sum_{l >= i} Li[l][i] y[l]
-  for (int t = tid; t < NB * CT; t += blockDim.x) {
-    int i = t % NB, cc = t / NB;
-    T acc = 0;
-    for (int l = i; l < NB; ++l) acc += Li[l][i] * Yb[l][cc];
-    x[i][cc] = acc;
-  }
-  __syncthreads();
-  if (blockIdx.x == 0) {
-    T* Xk = X + d.boff;
-    for (int t = tid; t < NB * nc; t += blockDim.x) {
-      int i = t % NB, cc = t / NB;
-      Xk[row0 + i + (int64_t)d.ldb * (c0 + cc)] = x[i][cc];
-    }
-  }
-  // update rows above: Y[c] -= sum_{r in panel b} L[r, c] x[r]; each warp takes
-  // columns c of L (64 contiguous entries of panel b) in turn
-  const int warp = tid / 32, lane = tid % 32;
-  for (int w = warp; w < BWD_COLS; w += 8) {
-    const int ccol = blockIdx.x * BWD_COLS + w;    // local row (= column of L) in the range
-    if (ccol >= row0) break;
-    const T* Lc = L + s.A + (int64_t)b * NB + (int64_t)s.n * (d.b0 * NB + ccol);
-    T l0 = Lc[lane], l1 = Lc[lane + 32];
-    for (int cc = 0; cc < nc; ++cc) {
-      T v = l0 * x[lane][cc] + l1 * x[lane + 32][cc];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) Yk[ccol + (int64_t)d.ldb * (c0 + cc)] -= v;
-    }
-  }
+  const int a0 = blockIdx.x * NB;
+  if (a0 >= row0) return;
+  // P(i, l) = L[b NB + l, d.b0 NB + a0 + i]
+  const T* P = L + s.A + (int64_t)b * NB + (int64_t)s.n * (d.b0 * NB + a0);
+  tile_gemm64<T, true>(P, s.n, 1, min(NB, row0 - a0), X + d.boff + row0 + (int64_t)d.ldb * j0, 1, d.ldb,
+                       min(NB, d.ncol - j0), Y + d.boff + a0 + (int64_t)d.ldb * j0, d.ldb);
 }
 
 // Single right-hand side: the diagonal solve reads the stored block inverse
@@ -411,25 +415,34 @@ ieti_status tri_solve(Ctx* c, const SubDev* d_sd, int nsub, int max_nblk, int ma
     if (r != IETI_ERR_STATE) return r;
   }
   const bool one = max_ncol == 1;   // single right-hand side: one-column kernels
-  const int ctiles = one ? 1 : (int)ceil_div(max_ncol, SOLVE_CT);
+  const unsigned ctiles = (unsigned)ceil_div(max_ncol, NB);
+  const unsigned rtiles = (unsigned)std::max<int64_t>(1, ceil_div(max_rows, NB));
   cudaEvent_t p0 = prof_begin(c, st);
   for (int b = min_b0; b < max_nblk; ++b) {
-    dim3 grid((unsigned)std::max<int64_t>(1, ceil_div(max_rows, SOLVE_RC)), ctiles, nsub);
-    if (one)
+    if (one) {
       k_fwd1<T><<<dim3((unsigned)std::max<int64_t>(1, ceil_div(max_rows, FWD1_ROWS)), nsub), 256, 0, st>>>(
           d_sd, d_desc, L, Linv, B, Y, b);
-    else k_fwd<T, SOLVE_CT><<<grid, 256, 0, st>>>(d_sd, d_desc, L, Linv, B, Y, b);
-    IETI_LAUNCH_CHECK(c);
+      IETI_LAUNCH_CHECK(c);
+    } else {
+      k_tsolve_diag<T, false><<<dim3(ctiles, nsub), 256, 0, st>>>(d_sd, d_desc, Linv, B, Y, b);
+      IETI_LAUNCH_CHECK(c);
+      k_tsolve_fwd<T><<<dim3(rtiles, ctiles, nsub), 256, 0, st>>>(d_sd, d_desc, L, B, Y, b);
+      IETI_LAUNCH_CHECK(c);
+    }
   }
   prof_end(c, PROF_FWD, p0, st);
   p0 = prof_begin(c, st);
   for (int b = max_nblk - 1; b >= min_b0; --b) {
-    dim3 grid((unsigned)std::max<int64_t>(1, ceil_div(max_rows, BWD_COLS)), ctiles, nsub);
-    if (one)
+    if (one) {
       k_bwd1<T><<<dim3((unsigned)std::max<int64_t>(1, ceil_div(max_rows, BWD_COLS)), nsub), 256, 0, st>>>(
           d_sd, d_desc, L, Linv, Y, X, b);
-    else k_bwd<T, SOLVE_CT><<<grid, 256, 0, st>>>(d_sd, d_desc, L, Linv, Y, X, b);
-    IETI_LAUNCH_CHECK(c);
+      IETI_LAUNCH_CHECK(c);
+    } else {
+      k_tsolve_diag<T, true><<<dim3(ctiles, nsub), 256, 0, st>>>(d_sd, d_desc, Linv, Y, X, b);
+      IETI_LAUNCH_CHECK(c);
+      k_tsolve_bwd<T><<<dim3(rtiles, ctiles, nsub), 256, 0, st>>>(d_sd, d_desc, L, Y, X, b);
+      IETI_LAUNCH_CHECK(c);
+    }
   }
   prof_end(c, PROF_BWD, p0, st);
   return IETI_OK;
