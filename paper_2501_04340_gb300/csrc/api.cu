@@ -280,6 +280,7 @@ ieti_status build(Ctx* c, const ieti_problem_desc* desc, bool device) {
     IETI_CUDA_TRY(c, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     TRY(assemble_kernel_attrs(c, optin));
     TRY(solve_kernel_attrs(c, optin));
+    TRY(factor_kernel_attrs(c));
     if ((size_t)c->max_ldI * sizeof(double) * 2 > (size_t)optin) {
       c->err = "interface block too large for the shared-memory staging of the local products";
       return IETI_ERR_INVALID_ARG;

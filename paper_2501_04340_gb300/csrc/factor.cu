@@ -175,6 +175,94 @@ __global__ void __launch_bounds__(256) k_syrk(const SubDev* sd, T* L, int b) {
     }
 }
 
+// FP32 trailing update on 128 x 128 tiles: the tile covers block rows r0, r0+1
+// and block columns c0, c0+1 of the trailing matrix (pairs counted from b+1);
+// 256 threads with 8 x 8 outputs each, both panels staged transposed in shared
+// memory. Sub-blocks above the block diagonal are skipped.
+constexpr int S2_LDS = 128 + 4;
+constexpr int S2_SMEM = 2 * NB * S2_LDS * 4;
+
+__global__ void __launch_bounds__(256, 2) k_syrk2(const SubDev* sd, float* L, int b) {
+  const int k = blockIdx.y;
+  const SubDev s = sd[k];
+  const int Tk = s.nblk - b - 1;
+  if (Tk <= 0) return;
+  const int Tt = (Tk + 1) / 2;   // block pairs
+  // triangular decode of the pair-tile index: R >= C
+  const int t = blockIdx.x;
+  int R = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while (R * (R + 1) / 2 > t) --R;
+  while ((R + 1) * (R + 2) / 2 <= t) ++R;
+  const int C = t - R * (R + 1) / 2;
+  if (R >= Tt) return;
+  const int r0 = b + 1 + 2 * R, c0 = b + 1 + 2 * C;
+  const int nr = min(2, s.nblk - r0), nc = min(2, s.nblk - c0);   // blocks present (1 or 2)
+  extern __shared__ __align__(16) float s2[];
+  float(*Pr)[S2_LDS] = reinterpret_cast<float(*)[S2_LDS]>(s2);
+  float(*Pc)[S2_LDS] = reinterpret_cast<float(*)[S2_LDS]>(s2 + NB * S2_LDS);
+  const int tid = threadIdx.x;
+  const int64_t n = s.n;
+  const float* P = L + s.A + (int64_t)n * b * NB;
+  const int ti = tid % 16, tj = tid / 16;   // rows 8 ti .. 8 ti + 7, columns 8 tj .. 8 tj + 7
+  const int rb = r0 + (8 * ti) / NB, cb = c0 + (8 * tj) / NB;
+  const bool writes = (8 * ti) / NB < nr && (8 * tj) / NB < nc && rb >= cb;
+  float* Out = L + s.A + (int64_t)r0 * NB + 8 * ti + n * ((int64_t)c0 * NB + 8 * tj);
+  // both panels, 4 consecutive rows per vector load, stored transposed
+  float4 pr[8], pc[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int x = tid + 256 * q;                  // 2048 vectors of 4 rows: i4 = x % 32, l = x / 32
+    const int i = 4 * (x % 32), l = x / 32;
+    pr[q] = (i < nr * NB) ? *reinterpret_cast<const float4*>(P + (int64_t)r0 * NB + i + n * l)
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+    pc[q] = (i < nc * NB) ? *reinterpret_cast<const float4*>(P + (int64_t)c0 * NB + i + n * l)
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int x = tid + 256 * q;
+    const int i = 4 * (x % 32), l = x / 32;
+    *reinterpret_cast<float4*>(&Pr[l][i]) = pr[q];
+    *reinterpret_cast<float4*>(&Pc[l][i]) = pc[q];
+  }
+  __syncthreads();
+  float acc[8][8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+#pragma unroll
+    for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
+#pragma unroll 4
+  for (int l = 0; l < NB; ++l) {
+    const float4 x0 = *reinterpret_cast<const float4*>(&Pr[l][8 * ti]);
+    const float4 x1 = *reinterpret_cast<const float4*>(&Pr[l][8 * ti + 4]);
+    const float4 y0 = *reinterpret_cast<const float4*>(&Pc[l][8 * tj]);
+    const float4 y1 = *reinterpret_cast<const float4*>(&Pc[l][8 * tj + 4]);
+    const float x[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+    const float y[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(x[u], y[v], acc[u][v]);
+  }
+  if (!writes) return;   // beyond the trailing matrix or above the block diagonal
+  float4 cv[16];         // all loads of the C tile in flight together
+#pragma unroll
+  for (int v = 0; v < 8; ++v) {
+    const float4* o = reinterpret_cast<const float4*>(Out + n * v);
+    cv[2 * v] = o[0];
+    cv[2 * v + 1] = o[1];
+  }
+#pragma unroll
+  for (int v = 0; v < 8; ++v) {
+    float4* o = reinterpret_cast<float4*>(Out + n * v);
+    float4 a = cv[2 * v], c = cv[2 * v + 1];
+    a.x -= acc[0][v]; a.y -= acc[1][v]; a.z -= acc[2][v]; a.w -= acc[3][v];
+    c.x -= acc[4][v]; c.y -= acc[5][v]; c.z -= acc[6][v]; c.w -= acc[7][v];
+    o[0] = a;
+    o[1] = c;
+  }
+}
+
 // S_rIrI snapshot: symmetrised copy of the lower trailing block at the r_I panel
 template <typename T>
 __global__ void k_snapshot(const SubDev* sd, const T* L, T* S, int b) {
@@ -534,6 +622,11 @@ __global__ void k_pad_identity(double* A, int n0, int ld) {
 
 // ---------------------------------------------------------------------------
 
+ieti_status factor_kernel_attrs(Ctx* c) {
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_syrk2, cudaFuncAttributeMaxDynamicSharedMemorySize, S2_SMEM));
+  return IETI_OK;
+}
+
 template <typename T>
 static ieti_status cholesky(Ctx* c, const SubDev* d_sd, const std::vector<SubDev>& sdh, T* L, T* Linv,
                             T* S, bool snapshot, cudaStream_t st) {
@@ -560,7 +653,12 @@ static ieti_status cholesky(Ctx* c, const SubDev* d_sd, const std::vector<SubDev
       prof_end(c, PROF_TRSM, p0, st);
       IETI_LAUNCH_CHECK(c);
       p0 = prof_begin(c, st);
-      k_syrk<T><<<dim3(Tm * (Tm + 1) / 2, nsub), 256, 0, st>>>(d_sd, L, b);
+      if constexpr (sizeof(T) == 4) {
+        const int Tp = (Tm + 1) / 2;   // block pairs
+        k_syrk2<<<dim3(Tp * (Tp + 1) / 2, nsub), 256, S2_SMEM, st>>>(d_sd, (float*)L, b);
+      } else {
+        k_syrk<T><<<dim3(Tm * (Tm + 1) / 2, nsub), 256, 0, st>>>(d_sd, L, b);
+      }
       prof_end(c, PROF_SYRK, p0, st);
       IETI_LAUNCH_CHECK(c);
     }

@@ -249,6 +249,7 @@ ieti_status assemble_kernel_attrs(Ctx* c, int smem_max);
 ieti_status solve_kernel_attrs(Ctx* c, int smem_max);
 // factorisation
 ieti_status factor_all(Ctx* c, cudaStream_t s);
+ieti_status factor_kernel_attrs(Ctx* c);
 // triangular solves with the local factors on the r-vectors in c->wr[...]
 template <typename T>
 ieti_status local_solve(Ctx* c, T* B, T* Y, int ncol, int blk0, int which, cudaStream_t s);
