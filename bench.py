@@ -260,7 +260,7 @@ def ours(args):
         flops = syrk_flops(sub_n) * args.steps
         achieved = flops / (prof[dom][0] / 1e3) / 1e12
         peak = 152 * 128 * 2 * 2.07e9 / 1e12     # FP32 FMA lanes x 2 flops x max SM clock
-        roof = {"kernel": "k_syrk<float> (trailing update of the FP32 Cholesky)", "bound": "alu",
+        roof = {"kernel": "k_syrk2 (128x128 register-blocked trailing update of the FP32 Cholesky)", "bound": "alu",
                 "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}

@@ -274,6 +274,7 @@ ieti_status build(Ctx* c, const ieti_problem_desc* desc, bool device) {
   if (!device) return IETI_OK;
   c->no_coop = std::getenv("IETI_NO_COOP") != nullptr;
   c->coop_trsv = !c->no_coop && std::getenv("IETI_COOP_TRSV") != nullptr;
+  c->syrk_tc = std::getenv("IETI_SYRK_TC") != nullptr;
   {
     int dev = 0, optin = 48 * 1024;
     IETI_CUDA_TRY(c, cudaGetDevice(&dev));
@@ -281,6 +282,7 @@ ieti_status build(Ctx* c, const ieti_problem_desc* desc, bool device) {
     TRY(assemble_kernel_attrs(c, optin));
     TRY(solve_kernel_attrs(c, optin));
     TRY(factor_kernel_attrs(c));
+    TRY(syrk_tc_attrs(c));
     if ((size_t)c->max_ldI * sizeof(double) * 2 > (size_t)optin) {
       c->err = "interface block too large for the shared-memory staging of the local products";
       return IETI_ERR_INVALID_ARG;
@@ -365,6 +367,7 @@ ieti_status build(Ctx* c, const ieti_problem_desc* desc, bool device) {
   TRY(dalloc(c, &c->d_err, 4));
   IETI_CUDA_TRY(c, cudaMallocHost(&c->h_err, sizeof(int) * 4));
   TRY(iface_alloc(c));
+  TRY(syrk_tc_alloc(c));
   return IETI_OK;
 }
 

@@ -654,8 +654,15 @@ static ieti_status cholesky(Ctx* c, const SubDev* d_sd, const std::vector<SubDev
       IETI_LAUNCH_CHECK(c);
       p0 = prof_begin(c, st);
       if constexpr (sizeof(T) == 4) {
-        const int Tp = (Tm + 1) / 2;   // block pairs
-        k_syrk2<<<dim3(Tp * (Tp + 1) / 2, nsub), 256, S2_SMEM, st>>>(d_sd, (float*)L, b);
+        if (c->syrk_tc) {
+          // opt-in: split TF32 products on the tensor cores (slower than the
+          // CUDA-core kernel at this panel width, see syrk_tc.cu)
+          ieti_status r = syrk_tc(c, d_sd, (float*)L, b, max_nblk, nsub, st);
+          if (r != IETI_OK) return r;
+        } else {
+          const int Tp = (Tm + 1) / 2;   // block pairs
+          k_syrk2<<<dim3(Tp * (Tp + 1) / 2, nsub), 256, S2_SMEM, st>>>(d_sd, (float*)L, b);
+        }
       } else {
         k_syrk<T><<<dim3(Tm * (Tm + 1) / 2, nsub), 256, 0, st>>>(d_sd, L, b);
       }
@@ -788,7 +795,8 @@ ieti_status factor_all(Ctx* c, cudaStream_t st) {
   ieti_status r = (c->prec == IETI_FP64) ? factor_t<double>(c, st) : factor_t<float>(c, st);
   if (r != IETI_OK) return r;
   if ((r = coarse_factor(c, st)) != IETI_OK) return r;
-  return iface_prepare(c, st);
+  if ((r = iface_prepare(c, st)) != IETI_OK) return r;
+  return iface_check(c, st);   // timed-out waits of the tensor-core update
 }
 
 // full local solves on r-vectors (used by the solver), type T buffers

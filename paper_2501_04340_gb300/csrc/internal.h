@@ -191,7 +191,10 @@ struct Ctx {
   int gell_E = 0;
   int4* d_pcon = nullptr;                // contributors of each coarse DOF: (pv_k, c, nP_k)
   int64_t pcon_count = 0;
-  int* d_stream_err = nullptr;           // set when a bulk-copy wait times out
+  int* d_stream_err = nullptr;           // set when a bulk-copy or tensor-core wait times out
+  float* tc_img = nullptr;               // TF32 term images of the current panel (syrk_tc.cu)
+  int* d_grp_off = nullptr;              // per subdomain: first 128-row group in tc_img
+  bool syrk_tc = false;                  // IETI_SYRK_TC=1: FP32 trailing update with split TF32 tensor-core products
 
   bool assembled = false, factored = false, host_only = false;
   bool no_coop = false;                  // IETI_NO_COOP=1: per-phase launches instead of the persistent PCG
@@ -250,6 +253,10 @@ ieti_status solve_kernel_attrs(Ctx* c, int smem_max);
 // factorisation
 ieti_status factor_all(Ctx* c, cudaStream_t s);
 ieti_status factor_kernel_attrs(Ctx* c);
+// FP32 trailing update on the tensor cores (syrk_tc.cu)
+ieti_status syrk_tc_attrs(Ctx* c);
+ieti_status syrk_tc_alloc(Ctx* c);
+ieti_status syrk_tc(Ctx* c, const SubDev* d_sd, float* L, int b, int max_nblk, int nsub, cudaStream_t st);
 // triangular solves with the local factors on the r-vectors in c->wr[...]
 template <typename T>
 ieti_status local_solve(Ctx* c, T* B, T* Y, int ncol, int blk0, int which, cudaStream_t s);

@@ -203,3 +203,21 @@ def test_per_panel_launch_path_matches_persistent(ieti, prec, monkeypatch):
     assert abs(i1 - i2) <= max(1, 0.1 * i2)
     assert np.linalg.norm(a1 - a2) <= 1e-9 * np.linalg.norm(a2)
     assert np.linalg.norm(a1 - a_m) <= 1e-8 * np.linalg.norm(a_m)
+
+
+def test_tensor_core_trailing_update_path(ieti, monkeypatch):
+    """The opt-in FP32 trailing update on the tensor cores (split TF32 products)
+    gives a factor good enough for the FP64 refinement: the field matches the
+    monolithic oracle solve to 1e-8, like the CUDA-core update."""
+    prob, mesh, topo, sysd, a_m = oracle_case("cube12_p2_mixed")
+    monkeypatch.setenv("IETI_SYRK_TC", "1")
+    ctx = ieti.ieti_create(prob)
+    try:
+        ieti.ieti_assemble(ctx)
+        ieti.ieti_factor(ctx, 1)
+        a = torch.zeros((prob.nrhs, mesh.nedge), dtype=torch.float64, device="cuda")
+        info = ieti.ieti_solve(ctx, a, tol=1e-10, maxit=400, tol_field=1e-12)
+        assert info.converged == 1
+        assert np.linalg.norm(a.cpu().numpy().T - a_m) <= 1e-8 * np.linalg.norm(a_m)
+    finally:
+        ieti.ieti_destroy(ctx)
