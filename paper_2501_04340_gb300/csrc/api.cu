@@ -358,6 +358,7 @@ ieti_status build(Ctx* c, const ieti_problem_desc* desc, bool device) {
   TRY(dalloc(c, &c->wnorm, MAX_RHS));
   TRY(dalloc(c, &c->wres_r, c->tot_rv * nr));
   TRY(dalloc(c, &c->wres_p, std::max<int64_t>(c->tot_pv, 1) * nr));
+  TRY(dalloc(c, &c->wxp, std::max<int64_t>(c->tot_pv, 1) * nr));
   char* desc_buf;
   TRY(dalloc(c, &desc_buf, 64 * (size_t)c->nsub + 64));
   c->d_descbuf = desc_buf;

@@ -14,6 +14,8 @@
 // The loads always use the element path (k_elem_j).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace ieti {
@@ -378,13 +380,21 @@ __device__ inline int local_index(const AsmParams& P, int c, int a, int idx, boo
 }
 
 template <typename T>
+__device__ __forceinline__ void kron_entry(const AsmParams& P, T* Lout, int k, const SubDev& s, int i, int j);
+
+template <typename T>
 __global__ void __launch_bounds__(256) k_kron(AsmParams P, T* Lout) {
-  const int k = blockIdx.y;
+  // grid: (row chunks of 256, column groups, subdomain); columns j = blockIdx.y + gridDim.y t
+  const int k = blockIdx.z;
   const SubDev s = P.sd[k];
   const int R = s.n + s.nP;
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)R * R) return;
-  const int i = (int)(e % R), j = (int)(e / R);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= R) return;
+  for (int j = blockIdx.y; j < R; j += gridDim.y) kron_entry<T>(P, Lout, k, s, i, j);
+}
+
+template <typename T>
+__device__ __forceinline__ void kron_entry(const AsmParams& P, T* Lout, int k, const SubDev& s, int i, int j) {
   if (i >= s.n && j < s.n) return;           // K_pr is not stored
   const DofDev a = P.dof[s.dof + i];
   const DofDev b = P.dof[s.dof + j];
@@ -551,8 +561,8 @@ ieti_status assemble_all(Ctx* c, cudaStream_t st) {
   IETI_CUDA_TRY(c, cudaMemsetAsync(c->jp, 0, sizeof(double) * std::max<int64_t>(c->tot_pv, 1) * c->nrhs, st));
   const bool kron = c->affine;
   if (kron) {
-    int64_t R = c->max_n + c->max_nP;
-    dim3 grid((unsigned)ceil_div(R * R, 256), (unsigned)c->nsub);
+    const int64_t R = c->max_n + c->max_nP;
+    dim3 grid((unsigned)ceil_div(R, 256), (unsigned)std::min<int64_t>(R, 65535), (unsigned)c->nsub);
     cudaEvent_t p0 = prof_begin(c, st);
     k_kron<double><<<grid, 256, 0, st>>>(P, (double*)nullptr);
     prof_end(c, PROF_ASM_K, p0, st);

@@ -172,6 +172,7 @@ struct Ctx {
   int64_t* d_primal_edges = nullptr;
   double* wres_r = nullptr;              // local residual r-vectors
   double* wres_p = nullptr;
+  double* wxp = nullptr;                 // the field at the local p DOFs (residual)
   double* wlam_acc = nullptr;            // accumulated multipliers
 
   // streamed interface products (iface.cu)

@@ -193,13 +193,15 @@ static ieti_status launch_coop(Ctx* c, const SubDev* d_sd, int nsub, int max_nbl
 constexpr int SW_ROWS = 256;   // rows (forward) or columns (backward) per work item
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_sweep1_fwd(const SubDev* sd, const SolveDesc* dsc, int nsub, int max_nblk,
-                                                    int min_b0, const T* L, const T* Linv, T* B, T* Y) {
+__global__ void __launch_bounds__(256, 1) k_sweep1_fwd(const SubDev* sd, const SolveDesc* dsc, int nsub,
+                                                       int max_nblk, int min_b0, const T* L, const T* Linv, T* B,
+                                                       T* Y) {
   cg::grid_group grid = cg::this_grid();
   __shared__ T bb[NB], y[NB];
   const int tid = threadIdx.x;
   for (int b = min_b0; b < max_nblk; ++b) {
     int item = blockIdx.x, base = 0;
+    int yk = -1;   // subdomain whose panel solution y currently holds
     for (int k = 0; k < nsub; ++k) {
       const SubDev s = sd[k];
       const SolveDesc d = dsc[k];
@@ -216,24 +218,30 @@ __global__ void __launch_bounds__(256) k_sweep1_fwd(const SubDev* sd, const Solv
         const T* Lrow = L + s.A + (d.b0 * NB + r) + (int64_t)s.n * (b * NB);
 #pragma unroll
         for (int l = 0; l < NB; ++l) lv[l] = valid ? Lrow[(int64_t)s.n * l] : (T)0;
-        const T* Lb = Linv + s.linv + (int64_t)b * NB * NB;
-        const int i = tid / 4, part = tid % 4;
-        T li[16];
+        if (yk != k) {
+          // y_b = Linv_b b_b, once per subdomain and panel in this CTA
+          const T* Lb = Linv + s.linv + (int64_t)b * NB * NB;
+          const int i = tid / 4, part = tid % 4;
+          T li[16];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) li[q] = Lb[i + NB * (part * 16 + q)];   // zero above the diagonal
-        __syncthreads();   // the previous item is done with bb and y
-        if (tid < NB) bb[tid] = Bk[row0 + tid];
-        __syncthreads();
-        T acc = 0;
+          for (int q = 0; q < 16; ++q) li[q] = Lb[i + NB * (part * 16 + q)];   // zero above the diagonal
+          __syncthreads();   // the previous item is done with bb and y
+          if (tid < NB) bb[tid] = Bk[row0 + tid];
+          __syncthreads();
+          T acc = 0;
 #pragma unroll
-        for (int q = 0; q < 16; ++q) acc += li[q] * bb[part * 16 + q];
-        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-        if (part == 0) {
-          y[i] = acc;
-          if (ch == 0) Y[d.boff + row0 + i] = acc;
+          for (int q = 0; q < 16; ++q) acc += li[q] * bb[part * 16 + q];
+          acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+          acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+          if (part == 0) {
+            y[i] = acc;
+            if (ch == 0) Y[d.boff + row0 + i] = acc;
+          }
+          __syncthreads();
+          yk = k;
+        } else if (ch == 0 && tid < NB) {
+          Y[d.boff + row0 + tid] = y[tid];
         }
-        __syncthreads();
         if (valid) {
           T u = 0;
 #pragma unroll
@@ -248,8 +256,9 @@ __global__ void __launch_bounds__(256) k_sweep1_fwd(const SubDev* sd, const Solv
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_sweep1_bwd(const SubDev* sd, const SolveDesc* dsc, int nsub, int max_nblk,
-                                                    int min_b0, const T* L, const T* Linv, T* Y, T* X) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_sweep1_bwd(const SubDev* sd, const SolveDesc* dsc, int nsub,
+                                                       int max_nblk, int min_b0, const T* L, const T* Linv, T* Y,
+                                                       T* X) {
   cg::grid_group grid = cg::this_grid();
   using V2 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
   constexpr int VL = 16 / sizeof(T);
@@ -257,6 +266,7 @@ __global__ void __launch_bounds__(256) k_sweep1_bwd(const SubDev* sd, const Solv
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   for (int b = max_nblk - 1; b >= min_b0; --b) {
     int item = blockIdx.x, base = 0;
+    int xk = -1;   // subdomain whose panel solution x currently holds
     for (int k = 0; k < nsub; ++k) {
       const SubDev s = sd[k];
       const SolveDesc d = dsc[k];
@@ -277,19 +287,22 @@ __global__ void __launch_bounds__(256) k_sweep1_bwd(const SubDev* sd, const Solv
           else if constexpr (VL == 4) lv[q] = make_float4(0.f, 0.f, 0.f, 0.f);
           else lv[q] = make_double2(0.0, 0.0);
         }
-        // x_i = sum_{l >= i} Linv[l][i] y_l: warp w computes x_i for i = w, w + 8, ...
-        const T* Lb = Linv + s.linv + (int64_t)b * NB * NB;
-        __syncthreads();   // the previous item is done with yb and x
-        if (tid < NB) yb[tid] = Yk[row0 + tid];
-        __syncthreads();
-        for (int i = warp; i < NB; i += 8) {
-          T v = (lane >= i ? Lb[lane + NB * i] * yb[lane] : (T)0) +
-                (lane + 32 >= i ? Lb[lane + 32 + NB * i] * yb[lane + 32] : (T)0);
+        if (xk != k) {
+          // x_i = sum_{l >= i} Linv[l][i] y_l: warp w computes x_i for i = w, w + 8, ...
+          const T* Lb = Linv + s.linv + (int64_t)b * NB * NB;
+          __syncthreads();   // the previous item is done with yb and x
+          if (tid < NB) yb[tid] = Yk[row0 + tid];
+          __syncthreads();
+          for (int i = warp; i < NB; i += 8) {
+            T v = (lane >= i ? Lb[lane + NB * i] * yb[lane] : (T)0) +
+                  (lane + 32 >= i ? Lb[lane + 32 + NB * i] * yb[lane + 32] : (T)0);
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-          if (lane == 0) x[i] = v;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) x[i] = v;
+          }
+          __syncthreads();
+          xk = k;
         }
-        __syncthreads();
         if (ch == 0 && tid < NB) X[d.boff + row0 + tid] = x[tid];
         if (valid) {
           T u = 0;

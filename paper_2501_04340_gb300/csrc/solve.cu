@@ -433,11 +433,29 @@ __global__ void k_scatter_primal(const int64_t* primal_edges, const double* p1, 
 // carry the full multipliers, and a PCG tolerance relative to them never gets
 // below the first solve's absolute error. The assembled residual
 // sum_k R_k^T (j^(k) - K^(k) x^(k)) is scatter-added into R when given.
-__global__ void __launch_bounds__(256) k_residual(const SubDev* sd, const int64_t* r_edge, const double* K64,
-                                                  const double* Kp, const double* Kpp, const double* jr,
-                                                  const double* jp, const double* a, int64_t nedge, int nrhs,
-                                                  const int32_t* I_dual, const double* I_sign, const double* lam,
-                                                  int64_t m_r, double* rr_out, double* rp_out, double* R) {
+// the field at every local r and p DOF (0 at Dirichlet, tree and padding DOFs)
+__global__ void k_gather_x(const SubDev* sd, const int64_t* r_edge, const double* a, int64_t nedge, int nrhs,
+                           double* xr, double* xp) {
+  const int k = blockIdx.y;
+  const SubDev s = sd[k];
+  const int Rn = s.n + s.nP;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < Rn * nrhs; t += gridDim.x * blockDim.x) {
+    const int i = t % Rn, col = t / Rn;
+    const int64_t e = r_edge[s.dof + i];
+    const double v = e >= 0 ? a[e + nedge * col] : 0.0;
+    if (i < s.n) xr[RV(s, i, col, nrhs)] = v;
+    else xp[PV(s, i - s.n, col, nrhs)] = v;
+  }
+}
+
+// residual rows with the gathered field: a dense product over contiguous
+// columns of the symmetric K_rr (16-byte loads, four in flight per lane)
+__global__ void __launch_bounds__(256) k_residual2(const SubDev* sd, const int64_t* r_edge, const double* K64,
+                                                   const double* Kp, const double* Kpp, const double* jr,
+                                                   const double* jp, const double* xr, const double* xp,
+                                                   int64_t nedge, int nrhs, const int32_t* I_dual,
+                                                   const double* I_sign, const double* lam, int64_t m_r,
+                                                   double* rr_out, double* rp_out, double* R) {
   const int k = blockIdx.y;
   const SubDev s = sd[k];
   const int Rn = s.n + s.nP;
@@ -446,7 +464,6 @@ __global__ void __launch_bounds__(256) k_residual(const SubDev* sd, const int64_
   if (row >= Rn) return;
   const int64_t e_row = r_edge[s.dof + row];
   for (int col = 0; col < nrhs; ++col) {
-    double acc = 0;
     const double* kc;
     const double* kpc;
     int64_t kp_stride;
@@ -460,14 +477,17 @@ __global__ void __launch_bounds__(256) k_residual(const SubDev* sd, const int64_
       kpc = Kpp + s.Kpp + c;
       kp_stride = s.nP;
     }
-    for (int j = lane; j < s.n; j += 32) {
-      int64_t e = r_edge[s.dof + j];
-      if (e >= 0) acc += kc[j] * a[e + nedge * col];
+    const double2* k2 = reinterpret_cast<const double2*>(kc);
+    const double2* x2 = reinterpret_cast<const double2*>(xr + RV(s, 0, col, nrhs));
+    double acc0 = 0, acc1 = 0;
+#pragma unroll 4
+    for (int j = lane; j < s.n / 2; j += 32) {
+      const double2 kv = k2[j], xv = x2[j];
+      acc0 = fma(kv.x, xv.x, acc0);
+      acc1 = fma(kv.y, xv.y, acc1);
     }
-    for (int j = lane; j < s.nP; j += 32) {
-      int64_t e = r_edge[s.dof + s.n + j];
-      acc += kpc[kp_stride * j] * a[e + nedge * col];
-    }
+    double acc = acc0 + acc1;
+    for (int j = lane; j < s.nP; j += 32) acc += kpc[kp_stride * j] * xp[PV(s, j, col, nrhs)];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) {
@@ -833,9 +853,11 @@ static ieti_status residual(Ctx* c, const double* a, double* rel, double* jn2, c
   IETI_CUDA_TRY(c, cudaMemsetAsync(c->wglob, 0, sizeof(double) * ne * nrhs, st));
   dim3 g((unsigned)ceil_div(c->max_n + c->max_nP, 8), c->nsub);
   cudaEvent_t p0 = prof_begin(c, st);
-  k_residual<<<g, 256, 0, st>>>(c->d_sd, c->d_r_edge, c->K64, c->Kp64, c->Kpp64, c->jr, c->jp, a, ne, nrhs,
-                                c->d_I_dual, c->d_I_sign, c->wlam_acc, c->m_r,
-                                c->wres_r, c->wres_p, c->wglob);
+  k_gather_x<<<dim3(64, c->nsub), 256, 0, st>>>(c->d_sd, c->d_r_edge, a, ne, nrhs, c->wr64[2], c->wxp);
+  IETI_LAUNCH_CHECK(c);
+  k_residual2<<<g, 256, 0, st>>>(c->d_sd, c->d_r_edge, c->K64, c->Kp64, c->Kpp64, c->jr, c->jp, c->wr64[2],
+                                 c->wxp, ne, nrhs, c->d_I_dual, c->d_I_sign, c->wlam_acc, c->m_r,
+                                 c->wres_r, c->wres_p, c->wglob);
   prof_end(c, PROF_RESID, p0, st);
   IETI_LAUNCH_CHECK(c);
   k_colnorm2<<<nrhs, 256, 0, st>>>(c->wglob, ne, c->wnorm);
