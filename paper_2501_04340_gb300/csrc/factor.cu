@@ -39,37 +39,45 @@ __global__ void __launch_bounds__(256) k_potrf_diag(const SubDev* sd, T* L, T* L
   }
   __shared__ int bad;
   if (tid == 0) bad = 0;
+  __syncthreads();
   for (int c = 0; c < NB; ++c) {
+    // every thread forms the pivot itself; the threads below it scale column c
+    // (a[c][c] itself is written after the barrier, once nobody reads it)
+    const T v0 = a[c][c];
+    const T piv = sqrt(v0 > (T)0 ? v0 : (T)1);
+    if (tid > c && tid < NB) a[tid][c] /= piv;
     __syncthreads();
     if (tid == 0) {
-      T v = a[c][c];
-      if (!(v > (T)0)) {
-        bad = 1;
-        v = (T)1;
-      }
-      a[c][c] = sqrt(v);
+      if (!(v0 > (T)0)) bad = 1;
+      a[c][c] = piv;
     }
-    __syncthreads();
-    T piv = a[c][c];
-    for (int i = c + 1 + tid; i < NB; i += blockDim.x) a[i][c] /= piv;
-    __syncthreads();
     const int m = NB - 1 - c;
     for (int t = tid; t < m * m; t += blockDim.x) {
       int i = c + 1 + t / m, l = c + 1 + t % m;
       if (l <= i) a[i][l] -= a[i][c] * a[l][c];
     }
+    __syncthreads();
   }
-  __syncthreads();
   if (tid == 0 && bad) atomicCAS(err, 0, k + 1);
-  // inverse of the lower triangular diagonal block, one column per thread
-  if (tid < NB) {
-    const int j = tid;
-    for (int i = 0; i < j; ++i) inv[i][j] = (T)0;
-    inv[j][j] = (T)1 / a[j][j];
-    for (int i = j + 1; i < NB; ++i) {
+  // inverse of the lower triangular diagonal block: column j by the four
+  // threads 4 j .. 4 j + 3 of one warp, each summing every fourth term
+  {
+    const int j = tid / 4, part = tid % 4;
+    for (int i = 0; i < j; ++i)
+      if (part == 0) inv[i][j] = (T)0;
+    const T djj = (T)1 / a[j][j];
+    if (part == 0) inv[j][j] = djj;
+    __syncwarp();
+    // the same trip count in every lane (rows i <= j contribute nothing), so the
+    // shuffles stay warp-uniform
+    for (int i = 1; i < NB; ++i) {
       T acc = 0;
-      for (int l = j; l < i; ++l) acc += a[i][l] * inv[l][j];
-      inv[i][j] = -acc / a[i][i];
+      if (i > j)
+        for (int l = j + part; l < i; l += 4) acc += a[i][l] * inv[l][j];
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      if (part == 0 && i > j) inv[i][j] = -acc / a[i][i];
+      __syncwarp();
     }
   }
   __syncthreads();
