@@ -329,6 +329,9 @@ ieti_status build(Ctx* c, const ieti_problem_desc* desc, bool device) {
   c->Linv = Li;
   TRY(dalloc(c, &c->Kp64, c->tot_Kp));
   TRY(dalloc(c, &c->Phi, c->tot_Kp));
+  double* psi;
+  TRY(dalloc(c, &psi, std::max<int64_t>(c->tot_Kp, 1)));
+  c->Psi = psi;
   TRY(dalloc(c, &c->Kpp64, c->tot_Kpp));
   double *Sb, *Wb;
   TRY(dalloc(c, &Sb, c->tot_S));
@@ -359,6 +362,23 @@ ieti_status build(Ctx* c, const ieti_problem_desc* desc, bool device) {
   TRY(dalloc(c, &c->wres_r, c->tot_rv * nr));
   TRY(dalloc(c, &c->wres_p, std::max<int64_t>(c->tot_pv, 1) * nr));
   TRY(dalloc(c, &c->wxp, std::max<int64_t>(c->tot_pv, 1) * nr));
+  double* wyk;
+  TRY(dalloc(c, &wyk, c->tot_rv * nr));
+  c->wyk = wyk;
+  {
+    // sweep ranges of the r-vector solves: the whole r range, and the r_I rows
+    // (panels from nVp / 64 on; a subdomain without r_I DOFs takes no part)
+    std::vector<SolveDesc> dh(2 * (size_t)c->nsub);
+    int min_b0 = 1 << 30;
+    for (int k = 0; k < c->nsub; ++k) {
+      const SubDev& s = c->sd_host[k];
+      dh[k] = SolveDesc{s.rv * nr, 0, s.n, nr, 0};
+      dh[c->nsub + k] = SolveDesc{s.rv * nr + s.nVp, s.nVp / NB, s.n, s.nI > 0 ? nr : 0, 0};
+      if (s.nI > 0) min_b0 = std::min(min_b0, s.nVp / NB);
+    }
+    c->min_b0_I = min_b0 == (1 << 30) ? c->max_nblk : min_b0;
+    TRY(upload(c, &c->d_desc_rv, dh));
+  }
   char* desc_buf;
   TRY(dalloc(c, &desc_buf, 64 * (size_t)c->nsub + 64));
   c->d_descbuf = desc_buf;

@@ -502,19 +502,20 @@ __global__ void __launch_bounds__(256) k_bwd1(const SubDev* sd, const SolveDesc*
 template <typename T>
 ieti_status tri_solve(Ctx* c, const SubDev* d_sd, int nsub, int max_nblk, int max_rows, int max_ncol,
                       const SolveDesc* d_desc, int min_b0, const T* L, const T* Linv, T* B, T* Y, T* X,
-                      cudaStream_t st) {
+                      cudaStream_t st, int which = SWEEP_BOTH) {
   if (max_ncol <= 0) return IETI_OK;
   if (!c->no_coop) {
     // one persistent launch per sweep (single column, or any width when opted
     // in); the per-panel launches below serve devices without cooperative launch
-    ieti_status r = tri_solve_coop<T>(c, d_sd, nsub, max_nblk, min_b0, max_ncol, d_desc, L, Linv, B, Y, X, st);
+    ieti_status r =
+        tri_solve_coop<T>(c, d_sd, nsub, max_nblk, min_b0, max_ncol, d_desc, L, Linv, B, Y, X, which, st);
     if (r != IETI_ERR_STATE) return r;
   }
   const bool one = max_ncol == 1;   // single right-hand side: one-column kernels
   const unsigned ctiles = (unsigned)ceil_div(max_ncol, NB);
   const unsigned rtiles = (unsigned)std::max<int64_t>(1, ceil_div(max_rows, NB));
   cudaEvent_t p0 = prof_begin(c, st);
-  for (int b = min_b0; b < max_nblk; ++b) {
+  for (int b = min_b0; (which & SWEEP_FWD) && b < max_nblk; ++b) {
     if (one) {
       k_fwd1<T><<<dim3((unsigned)std::max<int64_t>(1, ceil_div(max_rows, FWD1_ROWS)), nsub), 256, 0, st>>>(
           d_sd, d_desc, L, Linv, B, Y, b);
@@ -528,7 +529,7 @@ ieti_status tri_solve(Ctx* c, const SubDev* d_sd, int nsub, int max_nblk, int ma
   }
   prof_end(c, PROF_FWD, p0, st);
   p0 = prof_begin(c, st);
-  for (int b = max_nblk - 1; b >= min_b0; --b) {
+  for (int b = max_nblk - 1; (which & SWEEP_BWD) && b >= min_b0; --b) {
     if (one) {
       k_bwd1<T><<<dim3((unsigned)std::max<int64_t>(1, ceil_div(max_rows, BWD_COLS)), nsub), 256, 0, st>>>(
           d_sd, d_desc, L, Linv, Y, X, b);
@@ -598,6 +599,18 @@ __global__ void k_store_Phi(const SubDev* sd, const SolveDesc* dsc, const T* X, 
   const int64_t tot = (int64_t)s.n * s.nP;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x)
     Phi[s.Kp + t] = (double)X[d.boff + t];
+}
+
+// Psi = L^-1 K_rp (the forward sweep of the Phi solve), kept in the factor
+// precision for the recovery of the local field
+template <typename T>
+__global__ void k_store_Psi(const SubDev* sd, const SolveDesc* dsc, const T* Y, T* Psi) {
+  const int k = blockIdx.y;
+  const SubDev s = sd[k];
+  const SolveDesc d = dsc[k];
+  const int64_t tot = (int64_t)s.n * s.nP;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x)
+    Psi[s.Kp + t] = Y[d.boff + t];
 }
 
 // S_Pi += C^T (K_pp - K_rp^T Phi) C, one CTA per subdomain, FP64
@@ -744,7 +757,13 @@ static ieti_status factor_t(Ctx* c, cudaStream_t st) {
     IETI_CUDA_TRY(c, cudaMemcpyAsync(dd, dh.data(), sizeof(SolveDesc) * nsub, cudaMemcpyHostToDevice, st));
     k_load_Kp<T><<<dim3(256, nsub), 256, 0, st>>>(c->d_sd, dd, c->Kp64, B);
     IETI_LAUNCH_CHECK(c);
-    if ((r = tri_solve<T>(c, c->d_sd, nsub, c->max_nblk, c->max_n, c->max_nP, dd, 0, L, Linv, B, Y, X, st)) != IETI_OK)
+    if ((r = tri_solve<T>(c, c->d_sd, nsub, c->max_nblk, c->max_n, c->max_nP, dd, 0, L, Linv, B, Y, X, st,
+                          SWEEP_FWD)) != IETI_OK)
+      return r;
+    k_store_Psi<T><<<dim3(256, nsub), 256, 0, st>>>(c->d_sd, dd, Y, (T*)c->Psi);
+    IETI_LAUNCH_CHECK(c);
+    if ((r = tri_solve<T>(c, c->d_sd, nsub, c->max_nblk, c->max_n, c->max_nP, dd, 0, L, Linv, B, Y, X, st,
+                          SWEEP_BWD)) != IETI_OK)
       return r;
     k_store_Phi<T><<<dim3(256, nsub), 256, 0, st>>>(c->d_sd, dd, X, c->Phi);
     IETI_LAUNCH_CHECK(c);
@@ -807,27 +826,15 @@ ieti_status factor_all(Ctx* c, cudaStream_t st) {
   return iface_check(c, st);   // timed-out waits of the tensor-core update
 }
 
-// full local solves on r-vectors (used by the solver), type T buffers
+// sweeps on nrhs-column r-vectors with the range descriptors built at creation
 template <typename T>
-ieti_status local_solve(Ctx* c, T* B, T* Y, int ncol, int blk0, int which, cudaStream_t st) {
-  (void)blk0;
-  (void)which;
-  std::vector<SolveDesc> dh(c->nsub);
-  for (int k = 0; k < c->nsub; ++k) {
-    const SubDev& s = c->sd_host[k];
-    dh[k].boff = s.rv * ncol;
-    dh[k].b0 = 0;
-    dh[k].ldb = s.n;
-    dh[k].ncol = ncol;
-  }
-  SolveDesc* dd = (SolveDesc*)c->d_descbuf;
-  IETI_CUDA_TRY(c, cudaMemcpyAsync(dd, dh.data(), sizeof(SolveDesc) * c->nsub, cudaMemcpyHostToDevice, st));
-  T* X = (T*)c->wr[2];
-  ieti_status r = tri_solve<T>(c, c->d_sd, c->nsub, c->max_nblk, c->max_n, ncol, dd, 0, (const T*)c->L,
-                               (const T*)c->Linv, B, Y, X, st);
-  return r;
+ieti_status rv_solve(Ctx* c, int range, int which, T* B, T* Y, T* X, cudaStream_t st) {
+  const bool irange = range == RV_IRANGE;
+  const SolveDesc* dd = c->d_desc_rv + (irange ? c->nsub : 0);
+  return tri_solve<T>(c, c->d_sd, c->nsub, c->max_nblk, c->max_n, c->nrhs, dd, irange ? c->min_b0_I : 0,
+                      (const T*)c->L, (const T*)c->Linv, B, Y, X, st, which);
 }
-template ieti_status local_solve<float>(Ctx*, float*, float*, int, int, int, cudaStream_t);
-template ieti_status local_solve<double>(Ctx*, double*, double*, int, int, int, cudaStream_t);
+template ieti_status rv_solve<float>(Ctx*, int, int, float*, float*, float*, cudaStream_t);
+template ieti_status rv_solve<double>(Ctx*, int, int, double*, double*, double*, cudaStream_t);
 
 }  // namespace ieti

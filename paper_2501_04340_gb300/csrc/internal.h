@@ -59,11 +59,16 @@ struct SolveDesc {
 };
 
 struct Ctx;
+// which sweeps of a triangular solve to run
+constexpr int SWEEP_FWD = 1;    // L Y = B (B is overwritten)
+constexpr int SWEEP_BWD = 2;    // L^T X = Y (Y is overwritten)
+constexpr int SWEEP_BOTH = 3;
 // persistent (cooperative) triangular solves L Y = B, L^T X = Y over all
-// subdomains in one launch; returns IETI_ERR_STATE if the device cannot run it
+// subdomains, one launch per sweep; returns IETI_ERR_STATE if the device cannot run it
 template <typename T>
 ieti_status tri_solve_coop(Ctx* c, const SubDev* d_sd, int nsub, int max_nblk, int min_b0, int max_ncol,
-                           const SolveDesc* d_desc, const T* L, const T* Linv, T* B, T* Y, T* X, cudaStream_t st);
+                           const SolveDesc* d_desc, const T* L, const T* Linv, T* B, T* Y, T* X, int which,
+                           cudaStream_t st);
 
 // local DOF: direction d and global control-grid index (i, j, k) of its edge;
 // d = -1 for padding
@@ -147,6 +152,10 @@ struct Ctx {
   void* S = nullptr;                     // S_rIrI (nI x nI, full)
   void* W = nullptr;                     // S_rIrI^-1
   double* Phi = nullptr;                 // K_rr^-1 K_rp (n x nP), FP64 storage
+  void* Psi = nullptr;                   // L^-1 K_rp (n x nP), factor precision
+  void* wyk = nullptr;                   // L^-1 j_r of the last interface right-hand side (factor precision)
+  SolveDesc* d_desc_rv = nullptr;        // r-vector sweep ranges: [0, nsub) full, [nsub, 2 nsub) r_I rows
+  int min_b0_I = 0;                      // first panel of the r_I range over all subdomains
   double* SPi = nullptr;                 // coarse S_Pi (n_gp x n_gp)
   double* SPiInv = nullptr;              // its inverse
   int* d_err = nullptr;                  // device error word (subdomain id + 1 of a bad pivot)
@@ -258,9 +267,14 @@ ieti_status factor_kernel_attrs(Ctx* c);
 ieti_status syrk_tc_attrs(Ctx* c);
 ieti_status syrk_tc_alloc(Ctx* c);
 ieti_status syrk_tc(Ctx* c, const SubDev* d_sd, float* L, int b, int max_nblk, int nsub, cudaStream_t st);
-// triangular solves with the local factors on the r-vectors in c->wr[...]
+// triangular sweeps with the local factors on nrhs-column r-vectors: over the
+// whole r range (RV_FULL) or over the r_I rows only (RV_IRANGE; the forward
+// sweep of a right-hand side that vanishes on the r_V rows, or the backward
+// sweep that yields the r_I rows of the solution)
+constexpr int RV_FULL = 0;
+constexpr int RV_IRANGE = 1;
 template <typename T>
-ieti_status local_solve(Ctx* c, T* B, T* Y, int ncol, int blk0, int which, cudaStream_t s);
+ieti_status rv_solve(Ctx* c, int range, int which, T* B, T* Y, T* X, cudaStream_t s);
 // streamed interface products (iface.cu)
 ieti_status iface_alloc(Ctx* c);
 ieti_status iface_prepare(Ctx* c, cudaStream_t s);

@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_sweep1_bwd(cons
 template <typename T>
 static ieti_status launch_sweep1(Ctx* c, const SubDev* d_sd, int nsub, int max_nblk, int min_b0,
                                  const SolveDesc* d_desc, const T* L, const T* Linv, T* B, T* Y, T* X,
-                                 cudaStream_t st) {
+                                 int which, cudaStream_t st) {
   int dev = 0, sms = 0, pf = 0, pb = 0, coop = 0;
   IETI_CUDA_TRY(c, cudaGetDevice(&dev));
   IETI_CUDA_TRY(c, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
@@ -337,27 +337,33 @@ static ieti_status launch_sweep1(Ctx* c, const SubDev* d_sd, int nsub, int max_n
   const int per_sm = std::min(std::min(pf, pb), 4);
   if (per_sm < 1) return IETI_ERR_STATE;
   const dim3 grid(sms * per_sm);
-  void* fa[] = {(void*)&d_sd, (void*)&d_desc, (void*)&nsub, (void*)&max_nblk, (void*)&min_b0,
-                (void*)&L, (void*)&Linv, (void*)&B, (void*)&Y};
-  cudaEvent_t p0 = prof_begin(c, st);
-  IETI_CUDA_TRY(c, cudaLaunchCooperativeKernel((void*)k_sweep1_fwd<T>, grid, dim3(256), fa, 0, st));
-  prof_end(c, PROF_FWD, p0, st);
-  IETI_LAUNCH_CHECK(c);
-  void* ba[] = {(void*)&d_sd, (void*)&d_desc, (void*)&nsub, (void*)&max_nblk, (void*)&min_b0,
-                (void*)&L, (void*)&Linv, (void*)&Y, (void*)&X};
-  p0 = prof_begin(c, st);
-  IETI_CUDA_TRY(c, cudaLaunchCooperativeKernel((void*)k_sweep1_bwd<T>, grid, dim3(256), ba, 0, st));
-  prof_end(c, PROF_BWD, p0, st);
-  IETI_LAUNCH_CHECK(c);
+  if (which & SWEEP_FWD) {
+    void* fa[] = {(void*)&d_sd, (void*)&d_desc, (void*)&nsub, (void*)&max_nblk, (void*)&min_b0,
+                  (void*)&L, (void*)&Linv, (void*)&B, (void*)&Y};
+    cudaEvent_t p0 = prof_begin(c, st);
+    IETI_CUDA_TRY(c, cudaLaunchCooperativeKernel((void*)k_sweep1_fwd<T>, grid, dim3(256), fa, 0, st));
+    prof_end(c, PROF_FWD, p0, st);
+    IETI_LAUNCH_CHECK(c);
+  }
+  if (which & SWEEP_BWD) {
+    void* ba[] = {(void*)&d_sd, (void*)&d_desc, (void*)&nsub, (void*)&max_nblk, (void*)&min_b0,
+                  (void*)&L, (void*)&Linv, (void*)&Y, (void*)&X};
+    cudaEvent_t p0 = prof_begin(c, st);
+    IETI_CUDA_TRY(c, cudaLaunchCooperativeKernel((void*)k_sweep1_bwd<T>, grid, dim3(256), ba, 0, st));
+    prof_end(c, PROF_BWD, p0, st);
+    IETI_LAUNCH_CHECK(c);
+  }
   return IETI_OK;
 }
 
 template <typename T>
 ieti_status tri_solve_coop(Ctx* c, const SubDev* d_sd, int nsub, int max_nblk, int min_b0, int max_ncol,
-                           const SolveDesc* d_desc, const T* L, const T* Linv, T* B, T* Y, T* X, cudaStream_t st) {
+                           const SolveDesc* d_desc, const T* L, const T* Linv, T* B, T* Y, T* X, int which,
+                           cudaStream_t st) {
   if (max_ncol <= 0) return IETI_OK;
-  if (max_ncol == 1) return launch_sweep1<T>(c, d_sd, nsub, max_nblk, min_b0, d_desc, L, Linv, B, Y, X, st);
-  if (!c->coop_trsv) return IETI_ERR_STATE;   // multi-column: per-panel launches unless opted in
+  if (max_ncol == 1) return launch_sweep1<T>(c, d_sd, nsub, max_nblk, min_b0, d_desc, L, Linv, B, Y, X, which, st);
+  // multi-column: per-panel launches unless opted in (the opt-in kernel runs both sweeps)
+  if (!c->coop_trsv || which != SWEEP_BOTH) return IETI_ERR_STATE;
   return launch_coop<T, 8>(c, d_sd, nsub, max_nblk, min_b0, d_desc, L, Linv, B, Y, X, st);
 }
 
@@ -751,8 +757,9 @@ ieti_status pcg_coop(Ctx* c, double* lam, double* r, double* z, double* p, doubl
 }
 
 template ieti_status tri_solve_coop<float>(Ctx*, const SubDev*, int, int, int, int, const SolveDesc*, const float*,
-                                           const float*, float*, float*, float*, cudaStream_t);
+                                           const float*, float*, float*, float*, int, cudaStream_t);
 template ieti_status tri_solve_coop<double>(Ctx*, const SubDev*, int, int, int, int, const SolveDesc*,
-                                            const double*, const double*, double*, double*, double*, cudaStream_t);
+                                            const double*, const double*, double*, double*, double*, int,
+                                            cudaStream_t);
 
 }  // namespace ieti

@@ -335,25 +335,16 @@ __global__ void k_rvec_to_T(const SubDev* sd, const double* src, T* dst, int nrh
     dst[s.rv * nrhs + t] = (T)src[s.rv * nrhs + t];
 }
 
-template <typename T>
-__global__ void k_rvec_from_T(const SubDev* sd, const T* src, double* dst, int nrhs) {
-  const int k = blockIdx.y;
-  const SubDev s = sd[k];
-  const int64_t tot = (int64_t)s.n * nrhs;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x)
-    dst[s.rv * nrhs + t] = (double)src[s.rv * nrhs + t];
-}
-
 // e[l] = v_k1[I] - v_k2[I] (r_I rows of the r-vectors)
-__global__ void k_gather_e(const SubDev* sd, const int32_t* pair, const double* v, int64_t m_r, int nrhs,
-                           double* e) {
+template <typename T>
+__global__ void k_gather_e(const SubDev* sd, const int32_t* pair, const T* v, int64_t m_r, int nrhs, double* e) {
   const int col = blockIdx.y;
   for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < m_r; l += (int64_t)gridDim.x * blockDim.x) {
     double acc = 0;
     for (int side = 0; side < 2; ++side) {
       int k = pair[l * 4 + 2 * side], i = pair[l * 4 + 2 * side + 1];
       const SubDev s = sd[k];
-      double w = v[RV(s, s.nVp + i, col, nrhs)];
+      const double w = (double)v[RV(s, s.nVp + i, col, nrhs)];
       acc += (side == 0) ? w : -w;
     }
     e[l + m_r * col] = acc;
@@ -378,28 +369,48 @@ __global__ void k_dprime_part(const SubDev* sd, const double* Kp, const double* 
   }
 }
 
-// rhs_k = j_r - K_rp (p1 + p2)_k - B_k^T lam  (FP64, n rows per subdomain)
-__global__ void k_recover_rhs(const SubDev* sd, const double* Kp, const double* jr, const double* p1,
-                              const double* p2, int ngp, const int32_t* P_glob, const int32_t* I_dual,
-                              const double* I_sign, const double* lam, int64_t m_r, int nrhs, double* out) {
+// B <- -B_k^T lam on the r_I rows (zero on their padding), the right-hand side
+// of the forward sweep over the r_I range
+template <typename T>
+__global__ void k_dual_rhs(const SubDev* sd, const int32_t* I_dual, const double* I_sign, const double* lam,
+                           int64_t m_r, int nrhs, T* B) {
+  const int k = blockIdx.y;
+  const SubDev s = sd[k];
+  const int rows = s.n - s.nVp;
+  const int64_t tot = (int64_t)rows * nrhs;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % rows), col = (int)(t / rows);
+    const double v = i < s.nI ? -I_sign[s.iv + i] * lam[I_dual[s.iv + i] + m_r * col] : 0.0;
+    B[RV(s, s.nVp + i, col, nrhs)] = (T)v;
+  }
+}
+
+// Y <- L^-1 (j_r - K_rp p - B_k^T lam) = L^-1 j_r - Psi p + [0; Z_I], with
+// p = p1 + p2 the primal values, L^-1 j_r kept from the interface right-hand
+// side and Z_I = L_II^-1 (-B_k^T lam) in the r_I rows of Y on entry (the
+// forward sweep of a right-hand side that vanishes on the r_V rows stays there)
+template <typename T>
+__global__ void k_recover_mid(const SubDev* sd, const T* yk, const T* Psi, const double* p1, const double* p2,
+                              int ngp, const int32_t* P_glob, int nrhs, T* Y) {
   const int k = blockIdx.y;
   const SubDev s = sd[k];
   const int64_t tot = (int64_t)s.n * nrhs;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
-    int i = (int)(t % s.n), col = (int)(t / s.n);
-    double v = jr[RV(s, i, col, nrhs)];
+    const int i = (int)(t % s.n), col = (int)(t / s.n);
+    const int64_t o = RV(s, i, col, nrhs);
+    double v = (double)yk[o];
     for (int c = 0; c < s.nP; ++c) {
-      int64_t g = P_glob[s.pv + c] + (int64_t)ngp * col;
-      v -= Kp[s.Kp + i + (int64_t)s.n * c] * (p1[g] + p2[g]);
+      const int64_t g = P_glob[s.pv + c] + (int64_t)ngp * col;
+      v -= (double)Psi[s.Kp + i + (int64_t)s.n * c] * (p1[g] + p2[g]);
     }
-    int ii = i - s.nVp;
-    if (ii >= 0 && ii < s.nI) v -= I_sign[s.iv + ii] * lam[I_dual[s.iv + ii] + m_r * col];
-    out[RV(s, i, col, nrhs)] = v;
+    if (i >= s.nVp) v += (double)Y[o];
+    Y[o] = (T)v;
   }
 }
 
 // global field from the local solution: r_V DOFs and the "+" copy of r_I DOFs
-__global__ void k_scatter_a(const SubDev* sd, const int64_t* r_edge, const double* I_sign, const double* ar,
+template <typename T>
+__global__ void k_scatter_a(const SubDev* sd, const int64_t* r_edge, const double* I_sign, const T* ar,
                             int64_t nedge, int nrhs, double* a, int accumulate) {
   const int k = blockIdx.y;
   const SubDev s = sd[k];
@@ -410,7 +421,7 @@ __global__ void k_scatter_a(const SubDev* sd, const int64_t* r_edge, const doubl
     if (e < 0) continue;
     int ii = i - s.nVp;
     if (ii >= 0 && ii < s.nI && I_sign[s.iv + ii] < 0) continue;
-    double v = ar[RV(s, i, col, nrhs)];
+    const double v = (double)ar[RV(s, i, col, nrhs)];
     if (accumulate) a[e + nedge * col] += v;
     else a[e + nedge * col] = v;
   }
@@ -648,40 +659,30 @@ ieti_status apply_precond(Ctx* c, const double* rv, double* z, int nrhs, bool fp
   return apply_precond_ex(c, rv, z, nrhs, fp32, nullptr, nullptr, st);
 }
 
-// full local solves x = K_rr^-1 b on r-vectors (FP64 in, FP64 out)
-static ieti_status full_solve(Ctx* c, const double* b, double* x, int nrhs, cudaStream_t st) {
-  dim3 g(256, c->nsub);
+// b = e - G S_Pi^-1 d' from local loads (jr, jp); ycr <- S_Pi^-1 d' (kept for
+// recovery). e reads only the r_I rows of v = K_rr^-1 j_r, so after the full
+// forward sweep (its result L^-1 j_r is kept for the recovery) the backward
+// sweep runs over the r_I panels alone; d' = j_p - K_pr K_rr^-1 j_r is
+// j_p - Phi^T j_r and takes no solve.
+template <typename T>
+static ieti_status interface_rhs_t(Ctx* c, const double* jr, const double* jp, double* b, double* ycr, int nrhs,
+                                   cudaStream_t st) {
   ieti_status r;
-  if (c->prec == IETI_FP64) {
-    double* B = (double*)c->wr[0];
-    k_rvec_to_T<double><<<g, 256, 0, st>>>(c->d_sd, b, B, nrhs);
-    IETI_LAUNCH_CHECK(c);
-    if ((r = local_solve<double>(c, B, (double*)c->wr[1], nrhs, 0, 0, st)) != IETI_OK) return r;
-    k_rvec_from_T<double><<<g, 256, 0, st>>>(c->d_sd, (const double*)c->wr[2], x, nrhs);
-  } else {
-    float* B = (float*)c->wr[0];
-    k_rvec_to_T<float><<<g, 256, 0, st>>>(c->d_sd, b, B, nrhs);
-    IETI_LAUNCH_CHECK(c);
-    if ((r = local_solve<float>(c, B, (float*)c->wr[1], nrhs, 0, 0, st)) != IETI_OK) return r;
-    k_rvec_from_T<float><<<g, 256, 0, st>>>(c->d_sd, (const float*)c->wr[2], x, nrhs);
-  }
+  T* B = (T*)c->wr[0];
+  T* Y = (T*)c->wr[1];
+  T* X = (T*)c->wr[2];
+  k_rvec_to_T<T><<<dim3(256, c->nsub), 256, 0, st>>>(c->d_sd, jr, B, nrhs);
   IETI_LAUNCH_CHECK(c);
-  return IETI_OK;
-}
-
-// b = e - G S_Pi^-1 d' from local loads (jr, jp); ycr <- S_Pi^-1 d' (kept for recovery)
-ieti_status interface_rhs(Ctx* c, const double* jr, const double* jp, double* b, double* ycr, int nrhs,
-                          cudaStream_t st) {
-  ieti_status r;
-  double* v = c->wr64[0];
-  if ((r = full_solve(c, jr, v, nrhs, st)) != IETI_OK) return r;
+  if ((r = rv_solve<T>(c, RV_FULL, SWEEP_FWD, B, Y, X, st)) != IETI_OK) return r;
+  IETI_CUDA_TRY(c, cudaMemcpyAsync(c->wyk, Y, sizeof(T) * c->tot_rv * nrhs, cudaMemcpyDeviceToDevice, st));
+  if ((r = rv_solve<T>(c, RV_IRANGE, SWEEP_BWD, B, Y, X, st)) != IETI_OK) return r;
   const int gb = gather_blocks(c);
   double* e = c->wlam[7];
-  k_gather_e<<<dim3(gb, nrhs), 256, 0, st>>>(c->d_sd, c->d_pair, v, c->m_r, nrhs, e);
+  k_gather_e<T><<<dim3(gb, nrhs), 256, 0, st>>>(c->d_sd, c->d_pair, X, c->m_r, nrhs, e);
   IETI_LAUNCH_CHECK(c);
   const bool coarse = c->n_gp > 0;
   if (coarse) {
-    k_dprime_part<<<c->nsub, 256, 0, st>>>(c->d_sd, c->Kp64, jp, v, nrhs, c->wq_part);
+    k_dprime_part<<<c->nsub, 256, 0, st>>>(c->d_sd, c->Phi, jp, jr, nrhs, c->wq_part);
     IETI_LAUNCH_CHECK(c);
     if ((r = coarse_solve(c, c->wq_part, ycr, nrhs, st)) != IETI_OK) return r;
   }
@@ -690,6 +691,12 @@ ieti_status interface_rhs(Ctx* c, const double* jr, const double* jp, double* b,
                                             nullptr, e, -1.0);
   IETI_LAUNCH_CHECK(c);
   return IETI_OK;
+}
+
+ieti_status interface_rhs(Ctx* c, const double* jr, const double* jp, double* b, double* ycr, int nrhs,
+                          cudaStream_t st) {
+  return c->prec == IETI_FP64 ? interface_rhs_t<double>(c, jr, jp, b, ycr, nrhs, st)
+                              : interface_rhs_t<float>(c, jr, jp, b, ycr, nrhs, st);
 }
 
 // PCG on F_DP lam = b (lam holds the initial guess on entry, or zero)
@@ -817,9 +824,15 @@ static ieti_status pcg(Ctx* c, const double* b, double* lam, bool zero_start, do
   return conv ? IETI_OK : IETI_ERR_NO_CONVERGENCE;
 }
 
-// recovery (Eqs. (8), (9)) of the field increment from lam and local loads
-static ieti_status recover(Ctx* c, const double* lam, const double* ycr, const double* jr, double* a, int accumulate,
-                           cudaStream_t st) {
+// recovery (Eqs. (8), (9)) of the field increment from lam: the primal values
+// p = S_Pi^-1 (d' + Phi_I^T B^T lam) and a_r = K_rr^-1 (j_r - K_rp p - B_r^T lam),
+// the latter as L^-T (L^-1 j_r - Psi p + L^-1 [0; -B_r^T lam]). The last term
+// needs the forward sweep over the r_I panels only, L^-1 j_r is kept from the
+// interface right-hand side of the same loads and Psi = L^-1 K_rp from the
+// factorisation, so one full backward sweep remains.
+template <typename T>
+static ieti_status recover_t(Ctx* c, const double* lam, const double* ycr, double* a, int accumulate,
+                             cudaStream_t st) {
   const int nrhs = c->nrhs;
   ieti_status r;
   const bool coarse = c->n_gp > 0;
@@ -829,14 +842,18 @@ static ieti_status recover(Ctx* c, const double* lam, const double* ycr, const d
     IETI_LAUNCH_CHECK(c);
     if ((r = coarse_solve(c, c->wq_part, pl, nrhs, st)) != IETI_OK) return r;
   }
-  dim3 g(256, c->nsub);
-  double* rhs = c->wr64[1];
-  k_recover_rhs<<<g, 256, 0, st>>>(c->d_sd, c->Kp64, jr, coarse ? pl : c->wc[0], coarse ? ycr : c->wc[0],
-                                   (int)c->n_gp, c->d_P_glob, c->d_I_dual, c->d_I_sign, lam, c->m_r, nrhs, rhs);
+  const dim3 g(256, c->nsub);
+  T* B = (T*)c->wr[0];
+  T* Y = (T*)c->wr[1];
+  T* X = (T*)c->wr[2];
+  k_dual_rhs<T><<<g, 256, 0, st>>>(c->d_sd, c->d_I_dual, c->d_I_sign, lam, c->m_r, nrhs, B);
   IETI_LAUNCH_CHECK(c);
-  double* ar = c->wr64[2];
-  if ((r = full_solve(c, rhs, ar, nrhs, st)) != IETI_OK) return r;
-  k_scatter_a<<<g, 256, 0, st>>>(c->d_sd, c->d_r_edge, c->d_I_sign, ar, c->mesh.nedge, nrhs, a, accumulate);
+  if ((r = rv_solve<T>(c, RV_IRANGE, SWEEP_FWD, B, Y, X, st)) != IETI_OK) return r;
+  k_recover_mid<T><<<g, 256, 0, st>>>(c->d_sd, (const T*)c->wyk, (const T*)c->Psi, coarse ? pl : c->wc[0],
+                                      coarse ? ycr : c->wc[0], (int)c->n_gp, c->d_P_glob, nrhs, Y);
+  IETI_LAUNCH_CHECK(c);
+  if ((r = rv_solve<T>(c, RV_FULL, SWEEP_BWD, B, Y, X, st)) != IETI_OK) return r;
+  k_scatter_a<T><<<g, 256, 0, st>>>(c->d_sd, c->d_r_edge, c->d_I_sign, X, c->mesh.nedge, nrhs, a, accumulate);
   IETI_LAUNCH_CHECK(c);
   if (coarse) {
     k_scatter_primal<<<64, 256, 0, st>>>(c->d_primal_edges, pl, ycr, (int)c->n_gp, c->mesh.nedge, nrhs, a,
@@ -844,6 +861,12 @@ static ieti_status recover(Ctx* c, const double* lam, const double* ycr, const d
     IETI_LAUNCH_CHECK(c);
   }
   return IETI_OK;
+}
+
+static ieti_status recover(Ctx* c, const double* lam, const double* ycr, double* a, int accumulate,
+                           cudaStream_t st) {
+  return c->prec == IETI_FP64 ? recover_t<double>(c, lam, ycr, a, accumulate, st)
+                              : recover_t<float>(c, lam, ycr, a, accumulate, st);
 }
 
 // relative FP64 residual ||j - K a|| / ||j|| (max over columns); local residuals to wres_r/wres_p
@@ -933,7 +956,7 @@ ieti_status solve_all(Ctx* c, const double* lam0, double tol, int maxit, double 
     if (step == 0) kappa = kap;
     k_add<<<1216, 256, 0, st>>>(c->wlam_acc, lam, m * nrhs);
     IETI_LAUNCH_CHECK(c);
-    if ((r = recover(c, lam, ycr, jr, a, step > 0 ? 1 : 0, st)) != IETI_OK) return r;
+    if ((r = recover(c, lam, ycr, a, step > 0 ? 1 : 0, st)) != IETI_OK) return r;
     steps = step + 1;
     if (refine) {
       if ((r = residual(c, a, &grel, jn2.data(), st)) != IETI_OK) return r;
