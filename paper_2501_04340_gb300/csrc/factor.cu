@@ -183,74 +183,87 @@ __global__ void __launch_bounds__(256) k_syrk(const SubDev* sd, T* L, int b) {
     }
 }
 
-// FP32 trailing update on 128 x 128 tiles: the tile covers block rows r0, r0+1
-// and block columns c0, c0+1 of the trailing matrix (pairs counted from b+1);
-// 256 threads with 8 x 8 outputs each, both panels staged transposed in shared
-// memory. Sub-blocks above the block diagonal are skipped.
+// FP32 trailing update on 128 x 128 tiles with the kb panels b .. b+kb-1
+// (K = 64 kb): the tile covers block rows r0, r0+1 and block columns c0, c0+1
+// of the trailing matrix (pairs counted from b+kb); 256 threads with 8 x 8
+// outputs each, each 64-wide panel chunk staged transposed in shared memory in
+// turn. Sub-blocks above the block diagonal are skipped. With col_only the
+// update covers block column b+kb alone (one tile column, blockIdx.x = R).
 constexpr int S2_LDS = 128 + 4;
 constexpr int S2_SMEM = 2 * NB * S2_LDS * 4;
 
-__global__ void __launch_bounds__(256, 2) k_syrk2(const SubDev* sd, float* L, int b) {
+// 16-byte global -> shared copy that bypasses registers; valid == false
+// writes zeros (no bytes are read from src)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  const int bytes = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(src), "r"(bytes) : "memory");
+}
+
+__global__ void __launch_bounds__(256, 2) k_syrk2(const SubDev* sd, float* L, int b, int kb, int col_only) {
   const int k = blockIdx.y;
   const SubDev s = sd[k];
-  const int Tk = s.nblk - b - 1;
+  const int t0 = b + kb;          // first trailing block
+  const int Tk = s.nblk - t0;
   if (Tk <= 0) return;
   const int Tt = (Tk + 1) / 2;   // block pairs
-  // triangular decode of the pair-tile index: R >= C
-  const int t = blockIdx.x;
-  int R = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-  while (R * (R + 1) / 2 > t) --R;
-  while ((R + 1) * (R + 2) / 2 <= t) ++R;
-  const int C = t - R * (R + 1) / 2;
+  int R, C;
+  if (col_only) {
+    R = blockIdx.x;
+    C = 0;
+  } else {
+    // triangular decode of the pair-tile index: R >= C
+    const int t = blockIdx.x;
+    R = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    while (R * (R + 1) / 2 > t) --R;
+    while ((R + 1) * (R + 2) / 2 <= t) ++R;
+    C = t - R * (R + 1) / 2;
+  }
   if (R >= Tt) return;
-  const int r0 = b + 1 + 2 * R, c0 = b + 1 + 2 * C;
-  const int nr = min(2, s.nblk - r0), nc = min(2, s.nblk - c0);   // blocks present (1 or 2)
+  const int r0 = t0 + 2 * R, c0 = t0 + 2 * C;
+  const int nr = min(2, s.nblk - r0), nc = col_only ? 1 : min(2, s.nblk - c0);   // blocks present (1 or 2)
   extern __shared__ __align__(16) float s2[];
   float(*Pr)[S2_LDS] = reinterpret_cast<float(*)[S2_LDS]>(s2);
   float(*Pc)[S2_LDS] = reinterpret_cast<float(*)[S2_LDS]>(s2 + NB * S2_LDS);
   const int tid = threadIdx.x;
   const int64_t n = s.n;
-  const float* P = L + s.A + (int64_t)n * b * NB;
   const int ti = tid % 16, tj = tid / 16;   // rows 8 ti .. 8 ti + 7, columns 8 tj .. 8 tj + 7
   const int rb = r0 + (8 * ti) / NB, cb = c0 + (8 * tj) / NB;
   const bool writes = (8 * ti) / NB < nr && (8 * tj) / NB < nc && rb >= cb;
   float* Out = L + s.A + (int64_t)r0 * NB + 8 * ti + n * ((int64_t)c0 * NB + 8 * tj);
-  // both panels, 4 consecutive rows per vector load, stored transposed
-  float4 pr[8], pc[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int x = tid + 256 * q;                  // 2048 vectors of 4 rows: i4 = x % 32, l = x / 32
-    const int i = 4 * (x % 32), l = x / 32;
-    pr[q] = (i < nr * NB) ? *reinterpret_cast<const float4*>(P + (int64_t)r0 * NB + i + n * l)
-                          : make_float4(0.f, 0.f, 0.f, 0.f);
-    pc[q] = (i < nc * NB) ? *reinterpret_cast<const float4*>(P + (int64_t)c0 * NB + i + n * l)
-                          : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int x = tid + 256 * q;
-    const int i = 4 * (x % 32), l = x / 32;
-    *reinterpret_cast<float4*>(&Pr[l][i]) = pr[q];
-    *reinterpret_cast<float4*>(&Pc[l][i]) = pc[q];
-  }
-  __syncthreads();
   float acc[8][8];
 #pragma unroll
   for (int u = 0; u < 8; ++u)
 #pragma unroll
     for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
+  for (int ch = 0; ch < kb; ++ch) {
+    const float* P = L + s.A + (int64_t)n * (b + ch) * NB;
+    if (ch > 0) __syncthreads();   // every thread is done with the previous chunk
+    // both panels, 4 consecutive rows per 16-byte asynchronous copy (zero
+    // filled past the blocks present), stored transposed
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int x = tid + 256 * q;                  // 2048 vectors of 4 rows: i4 = x % 32, l = x / 32
+      const int i = 4 * (x % 32), l = x / 32;
+      const bool vr = i < nr * NB, vc = i < nc * NB;
+      cp_async16(&Pr[l][i], vr ? P + (int64_t)r0 * NB + i + n * l : P, vr);
+      cp_async16(&Pc[l][i], vc ? P + (int64_t)c0 * NB + i + n * l : P, vc);
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
 #pragma unroll 4
-  for (int l = 0; l < NB; ++l) {
-    const float4 x0 = *reinterpret_cast<const float4*>(&Pr[l][8 * ti]);
-    const float4 x1 = *reinterpret_cast<const float4*>(&Pr[l][8 * ti + 4]);
-    const float4 y0 = *reinterpret_cast<const float4*>(&Pc[l][8 * tj]);
-    const float4 y1 = *reinterpret_cast<const float4*>(&Pc[l][8 * tj + 4]);
-    const float x[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-    const float y[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+    for (int l = 0; l < NB; ++l) {
+      const float4 x0 = *reinterpret_cast<const float4*>(&Pr[l][8 * ti]);
+      const float4 x1 = *reinterpret_cast<const float4*>(&Pr[l][8 * ti + 4]);
+      const float4 y0 = *reinterpret_cast<const float4*>(&Pc[l][8 * tj]);
+      const float4 y1 = *reinterpret_cast<const float4*>(&Pc[l][8 * tj + 4]);
+      const float x[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+      const float y[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
+      for (int u = 0; u < 8; ++u)
 #pragma unroll
-      for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(x[u], y[v], acc[u][v]);
+        for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(x[u], y[v], acc[u][v]);
+    }
   }
   if (!writes) return;   // beyond the trailing matrix or above the block diagonal
   float4 cv[16];         // all loads of the C tile in flight together
@@ -654,15 +667,13 @@ static ieti_status cholesky(Ctx* c, const SubDev* d_sd, const std::vector<SubDev
   int nsub = (int)sdh.size();
   int max_nblk = 0;
   for (auto& s : sdh) max_nblk = std::max(max_nblk, s.nblk);
-  for (int b = 0; b < max_nblk; ++b) {
-    if (snapshot) {
-      bool any = false;
-      for (auto& s : sdh) any |= (s.nVp == b * NB && s.nI > 0);
-      if (any) {
-        k_snapshot<T><<<dim3(256, nsub), 256, 0, st>>>(d_sd, L, S, b);
-        IETI_LAUNCH_CHECK(c);
-      }
-    }
+  auto snap_at = [&](int b) {
+    bool any = false;
+    for (auto& s : sdh) any |= (s.nVp == b * NB && s.nI > 0);
+    return snapshot && any;
+  };
+  // diagonal block b and the panel below it
+  auto panel = [&](int b) -> ieti_status {
     cudaEvent_t p0 = prof_begin(c, st);
     k_potrf_diag<T><<<nsub, 256, 0, st>>>(d_sd, L, Linv, b, c->d_err);
     prof_end(c, PROF_POTRF, p0, st);
@@ -673,16 +684,41 @@ static ieti_status cholesky(Ctx* c, const SubDev* d_sd, const std::vector<SubDev
       k_trsm_panel<T><<<dim3(Tm, nsub), 256, 0, st>>>(d_sd, L, Linv, b);
       prof_end(c, PROF_TRSM, p0, st);
       IETI_LAUNCH_CHECK(c);
-      p0 = prof_begin(c, st);
+    }
+    return IETI_OK;
+  };
+  for (int b = 0; b < max_nblk;) {
+    if (snap_at(b)) {
+      k_snapshot<T><<<dim3(256, nsub), 256, 0, st>>>(d_sd, L, S, b);
+      IETI_LAUNCH_CHECK(c);
+    }
+    // FP32: two panels per trailing update (K = 128 halves the passes over
+    // the trailing matrix), unless the S_rIrI snapshot falls between them
+    int kb = 1;
+    if constexpr (sizeof(T) == 4) kb = (!c->syrk_tc && b + 2 < max_nblk && !snap_at(b + 1)) ? 2 : 1;
+    ieti_status r;
+    if ((r = panel(b)) != IETI_OK) return r;
+    if (kb == 2) {
+      // block column b+1 takes panel b's update before its own factorisation
+      const int Tp1 = (max_nblk - b - 1 + 1) / 2;
+      cudaEvent_t p0 = prof_begin(c, st);
+      k_syrk2<<<dim3(Tp1, nsub), 256, S2_SMEM, st>>>(d_sd, (float*)L, b, 1, 1);
+      prof_end(c, PROF_SYRK, p0, st);
+      IETI_LAUNCH_CHECK(c);
+      if ((r = panel(b + 1)) != IETI_OK) return r;
+    }
+    const int Tm = max_nblk - b - kb;
+    if (Tm > 0) {
+      cudaEvent_t p0 = prof_begin(c, st);
       if constexpr (sizeof(T) == 4) {
         if (c->syrk_tc) {
           // opt-in: split TF32 products on the tensor cores (slower than the
           // CUDA-core kernel at this panel width, see syrk_tc.cu)
-          ieti_status r = syrk_tc(c, d_sd, (float*)L, b, max_nblk, nsub, st);
-          if (r != IETI_OK) return r;
+          ieti_status r2 = syrk_tc(c, d_sd, (float*)L, b, max_nblk, nsub, st);
+          if (r2 != IETI_OK) return r2;
         } else {
           const int Tp = (Tm + 1) / 2;   // block pairs
-          k_syrk2<<<dim3(Tp * (Tp + 1) / 2, nsub), 256, S2_SMEM, st>>>(d_sd, (float*)L, b);
+          k_syrk2<<<dim3(Tp * (Tp + 1) / 2, nsub), 256, S2_SMEM, st>>>(d_sd, (float*)L, b, kb, 0);
         }
       } else {
         k_syrk<T><<<dim3(Tm * (Tm + 1) / 2, nsub), 256, 0, st>>>(d_sd, L, b);
@@ -690,6 +726,7 @@ static ieti_status cholesky(Ctx* c, const SubDev* d_sd, const std::vector<SubDev
       prof_end(c, PROF_SYRK, p0, st);
       IETI_LAUNCH_CHECK(c);
     }
+    b += kb;
   }
   return IETI_OK;
 }
