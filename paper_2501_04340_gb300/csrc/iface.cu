@@ -257,15 +257,23 @@ ieti_status build_plan(Ctx* c, int es, bool with_phi, StreamPlan* P) {
     }
     cta[grid] = (int)tiles.size();
   }
+  // the subdomains of every CTA's run (tiles are ordered by subdomain)
+  std::vector<int2> ckr(grid, make_int2(0, 0));
+  for (int g = 0; g < grid; ++g)
+    if (cta[g] < cta[g + 1]) ckr[g] = make_int2(tiles[cta[g]].k, tiles[cta[g + 1] - 1].k + 1);
   LTile* dt;
   int* dc;
+  int2* dk;
   ieti_status r;
   if ((r = alloc_dev(c, &dt, tiles.size())) != IETI_OK) return r;
   if ((r = alloc_dev(c, &dc, cta.size())) != IETI_OK) return r;
+  if ((r = alloc_dev(c, &dk, ckr.size())) != IETI_OK) return r;
   IETI_CUDA_TRY(c, cudaMemcpy(dt, tiles.data(), sizeof(LTile) * tiles.size(), cudaMemcpyHostToDevice));
   IETI_CUDA_TRY(c, cudaMemcpy(dc, cta.data(), sizeof(int) * cta.size(), cudaMemcpyHostToDevice));
+  IETI_CUDA_TRY(c, cudaMemcpy(dk, ckr.data(), sizeof(int2) * ckr.size(), cudaMemcpyHostToDevice));
   P->d_tiles = dt;
   P->d_cta = dc;
+  P->d_ckr = dk;
   P->ntiles = (int)tiles.size();
   P->grid = grid;
   P->stage_bytes = stage_bytes;
@@ -379,6 +387,8 @@ ieti_status iface_alloc(Ctx* c) {
     ut += c->sd_host[k].ldI;
   }
   c->utot = std::max<int64_t>(ut, 4);
+  if ((r = alloc_dev(c, &c->d_uoff, c->uoff.size())) != IETI_OK) return r;
+  IETI_CUDA_TRY(c, cudaMemcpy(c->d_uoff, c->uoff.data(), sizeof(int64_t) * c->uoff.size(), cudaMemcpyHostToDevice));
   std::vector<int2> gu(std::max<int64_t>(m, 1));
   for (int64_t l = 0; l < m; ++l) {
     const int k0 = c->topo.dual_pair[l * 4], i0 = c->topo.dual_pair[l * 4 + 1];

@@ -84,6 +84,7 @@ struct StreamPlan {
   int64_t bytes = 0;         // bytes streamed per column group
   void* d_tiles = nullptr;
   int* d_cta = nullptr;      // first tile of every CTA (grid + 1 entries)
+  int2* d_ckr = nullptr;     // subdomains [x, y) that every CTA's tiles touch
 };
 
 struct DeviceBuf {
@@ -154,6 +155,7 @@ struct Ctx {
   double* Phi = nullptr;                 // K_rr^-1 K_rp (n x nP), FP64 storage
   void* Psi = nullptr;                   // L^-1 K_rp (n x nP), factor precision
   void* wyk = nullptr;                   // L^-1 j_r of the last interface right-hand side (factor precision)
+  int64_t* d_uoff = nullptr;             // u-vector offsets of the subdomains (device copy)
   SolveDesc* d_desc_rv = nullptr;        // r-vector sweep ranges: [0, nsub) full, [nsub, 2 nsub) r_I rows
   int min_b0_I = 0;                      // first panel of the r_I range over all subdomains
   double* SPi = nullptr;                 // coarse S_Pi (n_gp x n_gp)

@@ -4,18 +4,22 @@
 // Phi_I^T) tiles and of S tiles exactly as the stand-alone products do, and
 // owns a contiguous slice of the multipliers for the vector work.
 //
-// Per iteration (grid barrier after each phase):
-//   A  t1_k = W_k u_k, q_k = Phi_I^(k)T u_k        (u = D_W p prepared in F)
-//   B  yc = S_Pi^-1 sum C^T q_k (every CTA); q = F p = B t1 + G yc; <p, q>
-//   C  alpha = rz / <p, q>; lam += alpha p; r -= alpha q; <r, r>;
-//      u = D_S r for the preconditioner
-//   D  convergence test; t2_k = S_k u_k
-//   E  z = sum_k B_k D_k t2_k; <r, z>
-//   F  beta = rz_new / rz; p = z + beta p; u = D_W p
-// Every CTA sums the per-CTA partials in the same order, so all CTAs take the
-// same alpha, beta and convergence decisions. The u vectors are written with
-// generic stores and read by bulk copies after the barrier, so the writers
-// fence the async proxy first.
+// Per iteration, four grid barriers:
+//   A  t1_k = W_k u_k, q_k = Phi_I^(k)T u_k          (u = D_W p, written in F)
+//   B  p = z + beta p on the owned slice (deferred from F);
+//      yc = S_Pi^-1 sum C^T q_k (every CTA); q = F p = B t1 + G yc; <p, q>
+//   C  alpha = rz / <p, q>; lam += alpha p; <r', r'> with r' = r - alpha q;
+//      u = D_S r' for the subdomains of the CTA's S run; t2_k = S_k u_k
+//   E  r = r'  on the owned slice (deferred from C); convergence test;
+//      z = sum_k B_k D_k t2_k; <r, z>
+//   F  beta = rz_new / rz; u = D_W (z + beta p) for the subdomains of the
+//      CTA's W run
+// The deferred updates keep r and p unchanged while other CTAs read them.
+// Every CTA that streams tiles of subdomain k writes the whole u_k itself
+// (all of them store identical values) and fences the async proxy before its
+// bulk copies read it, so no barrier separates u from the product. Every CTA
+// sums the per-CTA partials in the same order, so all CTAs take the same
+// alpha, beta and convergence decisions.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -37,6 +41,11 @@ struct PcgStreamArgs {
   StreamCtx CW, CS;              // W (+ Phi_I^T) and S streams
   const int* ctaW;
   const int* ctaS;
+  const int2* ckrW;              // subdomains of every CTA's W and S runs
+  const int2* ckrS;
+  const SubDev* sd;
+  const int64_t* uoff;
+  const int32_t* I_dual;
   double *x, *r, *z, *p, *q;
   double *t1, *t2, *qpart;
   double* part;                  // per-CTA partials [3][grid][CT]
@@ -114,38 +123,28 @@ __device__ inline double ps_sum_part(const double* part, int col, int ct, double
 
 __device__ inline void fence_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
-struct Slice;
-
+// u_k = D_k v at the r_I DOFs of every subdomain k in kr (D = sign, times the
+// rho-scaling if scaled), v = a + s[col] b (b == nullptr: v = a); a column
+// with keep[col] set takes v = b. Each local r_I DOF has one multiplier.
 template <typename T, int CT>
-__device__ inline void write_u(const PcgStreamArgs& A, const Slice& SL, const double* v, bool scaled);
-
-// u = D v at both sides of every owned multiplier (D = sign, times the
-// rho-scaling if scaled)
-template <typename T, int CT>
-__device__ inline void write_u(const PcgStreamArgs& A, const Slice& SL, const double* v, bool scaled) {
+__device__ inline void write_u_run(const PcgStreamArgs& A, int2 kr, const double* a, const double* b,
+                                   const double* s, const int* keep, bool scaled) {
   T* u = (T*)A.CW.uall;
-  for (int64_t q = threadIdx.x; q < SL.nl * A.nrhs; q += blockDim.x) {
-    const int64_t i = q / A.nrhs, col = q % A.nrhs;
-    const int2 o = SL.gu[i];
-    double w0, w1;
-    if (SL.sg) {
-      const double2 sg = SL.sg[i];
-      w0 = sg.x;
-      w1 = sg.y;
-      if (scaled) {
-        const double2 sc = SL.sc[i];
-        w0 *= sc.x;
-        w1 *= sc.y;
-      }
-    } else {
-      const int4 a = SL.gs[i];
-      const int i0 = a.x + a.y, i1 = a.z + a.w;
-      w0 = A.I_sign[i0] * (scaled ? A.I_scale[i0] : 1.0);
-      w1 = A.I_sign[i1] * (scaled ? A.I_scale[i1] : 1.0);
+  for (int k = kr.x; k < kr.y; ++k) {
+    const int64_t iv = A.sd[k].iv;
+    const int nI = A.sd[k].nI;
+    const int64_t uo = A.uoff[k];
+    for (int q = threadIdx.x; q < nI * A.nrhs; q += blockDim.x) {
+      const int i = q % nI, col = q / nI;
+      const int64_t j = iv + i;
+      const int64_t l = A.I_dual[j] + A.m * col;
+      const double w = scaled ? A.I_sign[j] * A.I_scale[j] : A.I_sign[j];
+      double v;
+      if (b == nullptr) v = a[l];
+      else if (keep[col]) v = b[l];
+      else v = a[l] + s[col] * b[l];
+      u[col * A.CW.utot + uo + i] = (T)(w * v);
     }
-    const double x = v[SL.l0 + i + A.m * col];
-    u[col * A.CW.utot + o.x] = (T)(w0 * x);
-    u[col * A.CW.utot + o.y] = (T)(w1 * x);
   }
   fence_async_global();
 }
@@ -158,6 +157,7 @@ __global__ void __launch_bounds__(STREAM_THREADS, 1) k_pcg_stream(PcgStreamArgs 
   __shared__ double qg[PS_MAXGP * CT], yc[PS_MAXGP * CT];
   __shared__ double rz[CT], bb[CT], alpha[CT], beta[CT];
   __shared__ int done[CT];
+  __shared__ int zero_keep[CT];
   __shared__ int its;
   const int tid = threadIdx.x, G = gridDim.x, bid = blockIdx.x;
   const int nrhs = A.nrhs, ngp = A.ngp;
@@ -218,16 +218,20 @@ __global__ void __launch_bounds__(STREAM_THREADS, 1) k_pcg_stream(PcgStreamArgs 
     done[tid] = tid < nrhs ? (A.scal[PS_SC * tid + 7] != 0.0) : 1;
   }
   if (tid == 0) its = (int)A.scal[8];
+  if (tid < CT) zero_keep[tid] = 0;
   uint32_t seq = 0, useq = 0;
   const bool producer = tid >= NCONS;
   int npreW = 0, npreS = 0;   // tiles of the next W / S pass already in flight (producer warp)
   double* pq_part = A.part;
   double* rr_part = A.part + (int64_t)G * CT;
   double* rz_part = A.part + 2 * (int64_t)G * CT;
+  const int2 krW = A.ckrW[bid], krS = A.ckrS[bid];
   // u = D_W p for the first product; the first W tiles are fetched meanwhile
   if (producer) npreW = stream_prefetch<T>(A.CW, A.ctaW[bid], A.ctaW[bid + 1], smem, seq, CT);
-  write_u<T, CT>(A, SL, A.p, false);
-  grid.sync();
+  write_u_run<T, CT>(A, krW, A.p, nullptr, nullptr, nullptr, false);
+  __syncthreads();   // every thread's u stores and fence precede the bulk copies
+  bool pend_p = false;   // p = z + beta p still to be applied to the owned slice
+  int upd[CT];           // columns that this iteration's alpha updates
   for (int iter = 0; iter < A.maxit; ++iter) {
     bool all = true;
     for (int cc = 0; cc < nrhs; ++cc) all &= done[cc] != 0;
@@ -239,7 +243,17 @@ __global__ void __launch_bounds__(STREAM_THREADS, 1) k_pcg_stream(PcgStreamArgs 
     grid.sync();
     // the first S tiles are fetched while the vector phases run
     if (producer) npreS = stream_prefetch<T>(A.CS, A.ctaS[bid], A.ctaS[bid + 1], smem, seq, CT);
-    // ---- B: coarse correction (every CTA), q = F p, partial <p, q>
+    // ---- B: deferred p update; coarse correction (every CTA), q = F p, partial <p, q>
+    if (pend_p) {
+      for (int64_t l = l0 + tid; l < l1; l += blockDim.x)
+#pragma unroll
+        for (int col = 0; col < CT; ++col) {
+          if (col >= nrhs) break;
+          if (!done[col]) A.p[l + m * col] = A.z[l + m * col] + beta[col] * A.p[l + m * col];
+        }
+      pend_p = false;
+      __syncthreads();
+    }
     if (ngp > 0) {
       if (A.cache_coarse) {
         // contributor values in parallel, then ordered sums per coarse DOF
@@ -309,24 +323,26 @@ __global__ void __launch_bounds__(STREAM_THREADS, 1) k_pcg_stream(PcgStreamArgs 
       if (tid == 0) pq_part[(int64_t)bid * CT + cc] = s;
     }
     grid.sync();
-    // ---- C: alpha; lam and r updates; partial <r, r>; u = D_S r
+    // ---- C: alpha; lam update; partial <r', r'>; u = D_S r'; products with S
     for (int cc = 0; cc < nrhs; ++cc) {
       const double pq = ps_sum_part(pq_part, cc, CT, red);
       if (tid == 0) alpha[cc] = (done[cc] || pq == 0.0) ? 0.0 : rz[cc] / pq;
     }
     __syncthreads();
 #pragma unroll
-    for (int cc = 0; cc < CT; ++cc) mine[cc] = 0;
+    for (int cc = 0; cc < CT; ++cc) {
+      mine[cc] = 0;
+      upd[cc] = cc < nrhs && !done[cc];
+    }
     for (int64_t l = l0 + tid; l < l1; l += blockDim.x) {
 #pragma unroll
       for (int col = 0; col < CT; ++col) {
         if (col >= nrhs) break;
-        const int64_t o = l + m * col;   // (same thread mapping as write_u's single column)
+        const int64_t o = l + m * col;
         double rv = A.r[o];
-        if (!done[col]) {
+        if (upd[col]) {
           A.x[o] += alpha[col] * A.p[o];
           rv -= alpha[col] * A.q[o];
-          A.r[o] = rv;
         }
         mine[col] += rv * rv;
       }
@@ -335,9 +351,26 @@ __global__ void __launch_bounds__(STREAM_THREADS, 1) k_pcg_stream(PcgStreamArgs 
       const double s = ps_cta_sum(mine[cc], red);
       if (tid == 0) rr_part[(int64_t)bid * CT + cc] = s;
     }
-    write_u<T, CT>(A, SL, A.r, true);
+    {
+      // r' = r - alpha q (alpha = 0 for finished columns)
+      double nalpha[CT];
+#pragma unroll
+      for (int cc = 0; cc < CT; ++cc) nalpha[cc] = -alpha[cc];
+      write_u_run<T, CT>(A, krS, A.r, A.q, nalpha, zero_keep, true);
+      __syncthreads();   // every thread's u stores and fence precede the bulk copies
+    }
+    stream_tiles<T, CT, ROWS>(A.CS, A.ctaS[bid], A.ctaS[bid + 1], smem, seq, useq, A.t2, nullptr, nrhs, 0, nrhs,
+                              npreS);
+    npreS = 0;
     grid.sync();
-    // ---- D: convergence test, local products with S
+    if (producer) npreW = stream_prefetch<T>(A.CW, A.ctaW[bid], A.ctaW[bid + 1], smem, seq, CT);
+    // ---- E: deferred r update; convergence test; z = preconditioned r, partial <r, z>
+    for (int64_t l = l0 + tid; l < l1; l += blockDim.x)
+#pragma unroll
+      for (int col = 0; col < CT; ++col) {
+        if (col >= nrhs) break;
+        if (upd[col]) A.r[l + m * col] -= alpha[col] * A.q[l + m * col];
+      }
     for (int cc = 0; cc < nrhs; ++cc) {
       const double rr = ps_sum_part(rr_part, cc, CT, red);
       if (tid == 0 && !done[cc]) {
@@ -359,12 +392,6 @@ __global__ void __launch_bounds__(STREAM_THREADS, 1) k_pcg_stream(PcgStreamArgs 
       for (int cc = 0; cc < nrhs; ++cc) fin &= done[cc] != 0;
       if (fin) break;
     }
-    stream_tiles<T, CT, ROWS>(A.CS, A.ctaS[bid], A.ctaS[bid + 1], smem, seq, useq, A.t2, nullptr, nrhs, 0, nrhs,
-                              npreS);
-    npreS = 0;
-    grid.sync();
-    if (producer) npreW = stream_prefetch<T>(A.CW, A.ctaW[bid], A.ctaW[bid + 1], smem, seq, CT);
-    // ---- E: z = preconditioned r, partial <r, z>
 #pragma unroll
     for (int cc = 0; cc < CT; ++cc) mine[cc] = 0;
     for (int64_t i = tid; i < nl; i += blockDim.x) {
@@ -394,7 +421,7 @@ __global__ void __launch_bounds__(STREAM_THREADS, 1) k_pcg_stream(PcgStreamArgs 
       if (tid == 0) rz_part[(int64_t)bid * CT + cc] = s;
     }
     grid.sync();
-    // ---- F: beta, p update, u = D_W p
+    // ---- F: beta; u = D_W (z + beta p) (the owned p follows in B)
     for (int cc = 0; cc < nrhs; ++cc) {
       const double rzn = ps_sum_part(rz_part, cc, CT, red);
       if (tid == 0) {
@@ -410,15 +437,17 @@ __global__ void __launch_bounds__(STREAM_THREADS, 1) k_pcg_stream(PcgStreamArgs 
     }
     __syncthreads();
     if (bid == 0 && tid == 0 && A.hist && its <= A.hist_cap) A.hist[2 * (its - 1) + 1] = beta[0];
+    write_u_run<T, CT>(A, krW, A.z, A.p, beta, done, false);
+    pend_p = true;
+    __syncthreads();   // every thread's u stores and fence precede the bulk copies
+  }
+  if (pend_p) {
     for (int64_t l = l0 + tid; l < l1; l += blockDim.x)
 #pragma unroll
       for (int col = 0; col < CT; ++col) {
         if (col >= nrhs) break;
         if (!done[col]) A.p[l + m * col] = A.z[l + m * col] + beta[col] * A.p[l + m * col];
       }
-    __syncthreads();
-    write_u<T, CT>(A, SL, A.p, false);
-    grid.sync();
   }
   // tiles fetched ahead for a pass that will not run
   if (producer) stream_drain(smem, seq, npreW + npreS, A.CW.stages);
@@ -490,6 +519,11 @@ ieti_status pcg_stream(Ctx* c, double* lam, double* r, double* z, double* p, dou
   A.CS.tiles = (const LTile*)PS.d_tiles;
   A.ctaW = PW.d_cta;
   A.ctaS = PS.d_cta;
+  A.ckrW = PW.d_ckr;
+  A.ckrS = PS.d_ckr;
+  A.sd = c->d_sd;
+  A.uoff = c->d_uoff;
+  A.I_dual = c->d_I_dual;
   A.x = lam;
   A.r = r;
   A.z = z;
