@@ -171,8 +171,10 @@ ieti_status ieti_apply_precond(ieti_ctx* ctx, const double* r_dev, double* z_dev
  * inner solver of FP64 iterative refinement on the assembled system, repeated
  * until the FP64 relative residual of the field is <= tol_field (default 1e-10
  * when <= 0) or 8 refinement steps; each inner PCG then stops at
- * max(tol, 1e-3), since a refinement step with FP32 operators cannot reduce
- * the error by much more than that anyway. lam0_dev: m_r x nrhs initial multipliers or
+ * max(tol, 1e-3) on the first step and max(tol, 3e-3) on the corrections,
+ * since a refinement step with FP32 operators cannot reduce the error by much
+ * more than that anyway. Errors of the single-column sweeps' bounded waits
+ * return CUDA. lam0_dev: m_r x nrhs initial multipliers or
  * NULL for zero. a_dev: nedge x nrhs output field (Dirichlet and tree DOFs are
  * zero). lam_dev: optional m_r x nrhs output of the final multipliers.
  * info: optional host struct. Synchronises the stream. Errors: STATE,

@@ -274,6 +274,7 @@ ieti_status build(Ctx* c, const ieti_problem_desc* desc, bool device) {
   if (!device) return IETI_OK;
   c->no_coop = std::getenv("IETI_NO_COOP") != nullptr;
   c->coop_trsv = !c->no_coop && std::getenv("IETI_COOP_TRSV") != nullptr;
+  c->dep_sweeps = !c->no_coop && std::getenv("IETI_NO_DEP_SWEEP") == nullptr;
   c->syrk_tc = std::getenv("IETI_SYRK_TC") != nullptr;
   {
     int dev = 0, optin = 48 * 1024;
@@ -283,6 +284,7 @@ ieti_status build(Ctx* c, const ieti_problem_desc* desc, bool device) {
     TRY(solve_kernel_attrs(c, optin));
     TRY(factor_kernel_attrs(c));
     TRY(syrk_tc_attrs(c));
+    TRY(dep_sweep_attrs(c));
     if ((size_t)c->max_ldI * sizeof(double) * 2 > (size_t)optin) {
       c->err = "interface block too large for the shared-memory staging of the local products";
       return IETI_ERR_INVALID_ARG;
@@ -379,6 +381,7 @@ ieti_status build(Ctx* c, const ieti_problem_desc* desc, bool device) {
     c->min_b0_I = min_b0 == (1 << 30) ? c->max_nblk : min_b0;
     TRY(upload(c, &c->d_desc_rv, dh));
   }
+  TRY(dep_sweep_alloc(c));
   char* desc_buf;
   TRY(dalloc(c, &desc_buf, 64 * (size_t)c->nsub + 64));
   c->d_descbuf = desc_buf;

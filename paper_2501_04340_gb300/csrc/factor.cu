@@ -866,6 +866,10 @@ ieti_status factor_all(Ctx* c, cudaStream_t st) {
 // sweeps on nrhs-column r-vectors with the range descriptors built at creation
 template <typename T>
 ieti_status rv_solve(Ctx* c, int range, int which, T* B, T* Y, T* X, cudaStream_t st) {
+  if (c->nrhs == 1 && c->dep_sweeps) {
+    const ieti_status r = dep_sweep<T>(c, range, which, B, Y, X, st);
+    if (r != IETI_ERR_STATE) return r;
+  }
   const bool irange = range == RV_IRANGE;
   const SolveDesc* dd = c->d_desc_rv + (irange ? c->nsub : 0);
   return tri_solve<T>(c, c->d_sd, c->nsub, c->max_nblk, c->max_n, c->nrhs, dd, irange ? c->min_b0_I : 0,

@@ -158,6 +158,13 @@ struct Ctx {
   int64_t* d_uoff = nullptr;             // u-vector offsets of the subdomains (device copy)
   SolveDesc* d_desc_rv = nullptr;        // r-vector sweep ranges: [0, nsub) full, [nsub, 2 nsub) r_I rows
   int min_b0_I = 0;                      // first panel of the r_I range over all subdomains
+  // dependency-driven single-column sweeps (sweep_dep.cu)
+  bool dep_sweeps = true;                // IETI_NO_DEP_SWEEP=1: per-panel barrier sweeps instead
+  int2* d_dep_tasks[2][2] = {};          // [range][forward, backward]: (subdomain, block) in run order
+  int dep_ntask[2][2] = {};
+  unsigned long long* d_dep_prog = nullptr;   // per subdomain: epoch << 20 | blocks published
+  unsigned long long dep_epoch = 0;
+  int* d_dep_err = nullptr;              // set when a sweep wait times out
   double* SPi = nullptr;                 // coarse S_Pi (n_gp x n_gp)
   double* SPiInv = nullptr;              // its inverse
   int* d_err = nullptr;                  // device error word (subdomain id + 1 of a bad pivot)
@@ -277,6 +284,12 @@ constexpr int RV_FULL = 0;
 constexpr int RV_IRANGE = 1;
 template <typename T>
 ieti_status rv_solve(Ctx* c, int range, int which, T* B, T* Y, T* X, cudaStream_t s);
+// the same sweeps for one column as dependency-driven block tasks (sweep_dep.cu);
+// IETI_ERR_STATE if the device cannot run them
+ieti_status dep_sweep_attrs(Ctx* c);
+ieti_status dep_sweep_alloc(Ctx* c);
+template <typename T>
+ieti_status dep_sweep(Ctx* c, int range, int which, const T* B, T* Y, T* X, cudaStream_t s);
 // streamed interface products (iface.cu)
 ieti_status iface_alloc(Ctx* c);
 ieti_status iface_prepare(Ctx* c, cudaStream_t s);

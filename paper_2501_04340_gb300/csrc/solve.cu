@@ -916,6 +916,7 @@ ieti_status solve_all(Ctx* c, const double* lam0, double tol, int maxit, double 
   ieti_status r;
   IETI_CUDA_TRY(c, cudaMemsetAsync(a, 0, sizeof(double) * ne * nrhs, st));
   IETI_CUDA_TRY(c, cudaMemsetAsync(c->wlam_acc, 0, sizeof(double) * m * nrhs, st));
+  IETI_CUDA_TRY(c, cudaMemsetAsync(c->d_dep_err, 0, sizeof(int), st));
   // FP64 factors: one pass, refined further only when a field tolerance is given;
   // FP32 factors: always refined (default field tolerance 1e-10)
   const bool refine = fp32 || tol_field > 0;
@@ -942,12 +943,13 @@ ieti_status solve_all(Ctx* c, const double* lam0, double tol, int maxit, double 
     if (warm) IETI_CUDA_TRY(c, cudaMemcpyAsync(lam, lam0, sizeof(double) * m * nrhs, cudaMemcpyDeviceToDevice, st));
     int its = 0;
     double rel = 0, kap = 0;
-    // with FP32 operators a refinement step reduces the error by roughly
-    // kappa(K_rr) u_32 (about 0.07 on the 64-patch cube), so the inner PCG only
-    // has to beat that: an inner tolerance of 1e-3 keeps the number of steps
-    // (7 there) and halves the PCG iterations against 1e-6; the FP64 residual of
-    // the field decides convergence
-    const double tol_in = fp32 ? std::max(tol, 1e-3) : tol;
+    // with FP32 operators a refinement step reduces the field residual by
+    // about 0.03 on the 64-patch cube (kappa(K_rr) u_32), whatever the inner
+    // tolerance below that level, so the inner PCG only has to beat it: 1e-3
+    // on the first step and 3e-3 on the corrections keep the number of steps
+    // (7 there) at the fewest PCG iterations; the FP64 residual of the field
+    // decides convergence
+    const double tol_in = fp32 ? std::max(tol, step == 0 ? 1e-3 : 3e-3) : tol;
     ieti_status pr = pcg(c, b, lam, !warm, tol_in, maxit, fp32, &its, &rel, &kap, st);
     if (pr != IETI_OK && pr != IETI_ERR_NO_CONVERGENCE) return pr;
     if (pr == IETI_ERR_NO_CONVERGENCE && !fp32) conv = false;
@@ -968,8 +970,15 @@ ieti_status solve_all(Ctx* c, const double* lam0, double tol, int maxit, double 
   if (refine && grel > tol_field) conv = false;
   if (lam_out)
     IETI_CUDA_TRY(c, cudaMemcpyAsync(lam_out, c->wlam_acc, sizeof(double) * m * nrhs, cudaMemcpyDeviceToDevice, st));
+  IETI_CUDA_TRY(c, cudaMemcpyAsync(c->h_err + 1, c->d_dep_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   IETI_CUDA_TRY(c, cudaEventRecord(e1, st));
   IETI_CUDA_TRY(c, cudaEventSynchronize(e1));
+  if (c->h_err[1]) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->err = "a triangular-sweep wait timed out";
+    return IETI_ERR_CUDA;
+  }
   float ms = 0;
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);

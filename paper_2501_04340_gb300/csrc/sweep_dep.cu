@@ -1,0 +1,348 @@
+// Single-column triangular sweeps with the blocked Cholesky factors of all
+// subdomains as dependency-driven block tasks: one cooperative launch per
+// sweep and no grid barrier. Forward, block row b of subdomain k:
+//   y_b = Linv_b (b_b - sum_{b0 <= j < b} L_bj y_j)
+// backward, block column b:
+//   x_b = Linv_b^T (y_b - sum_{j > b} L_jb^T x_j)
+// (the local solves K_rr^(k) x = f of Eqs. (8), (9) and of the right-hand
+// side of Eq. (7)). A task is one 64-wide block of one subdomain. The tasks
+// are ordered by b (ascending forward, descending backward) and dealt
+// round-robin to the CTAs; a CTA runs its tasks in that order. A task reads
+// the finished blocks as they are published and publishes its own block by
+// raising the subdomain's progress counter with a release store after writing
+// it; readers poll the counter with acquire loads (bounded, with an error flag
+// on time-out) and read the blocks through L2. Every wait is on a task that
+// comes earlier in the order and all CTAs are resident (cooperative launch),
+// so every wait ends. Progress counters carry an epoch in their upper bits, so
+// they are never reset.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <type_traits>
+#include <vector>
+
+#include "internal.h"
+
+namespace ieti {
+
+namespace {
+
+constexpr int DEP_THREADS = 256;
+constexpr int DEP_EPOCH_SHIFT = 20;            // blocks per subdomain < 2^20
+constexpr long long DEP_SPIN_MAX = 1LL << 22;  // polls of about 0.1 us before giving up
+
+template <typename T>
+using Vec16 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// waits until *p >= need (bounded); on time-out, or once another wait has
+// timed out, records the error and returns so that the launch ends
+__device__ unsigned long long dep_wait(const unsigned long long* p, unsigned long long need, int* err) {
+  unsigned long long v = ld_acquire_u64(p);
+  for (long long it = 0; v < need; ++it) {
+    if (it > DEP_SPIN_MAX || *(volatile int*)err) {
+      atomicExch(err, 1);
+      return need;
+    }
+    __nanosleep(64);
+    v = ld_acquire_u64(p);
+  }
+  return v;
+}
+
+// all threads: the block's stores are done; one thread publishes
+__device__ __forceinline__ void dep_publish(unsigned long long* p, unsigned long long v) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    st_release_u64(p, v);
+  }
+}
+
+// 16 consecutive entries of a published vector, read through L2
+template <typename T>
+__device__ __forceinline__ void load16_cg(const T* src, T (&v)[16]) {
+  constexpr int VL = 16 / sizeof(T);
+  const Vec16<T>* s = reinterpret_cast<const Vec16<T>*>(src);
+#pragma unroll
+  for (int q = 0; q < 16 / VL; ++q) {
+    const Vec16<T> w = __ldcg(s + q);
+    if constexpr (VL == 4) {
+      v[4 * q] = w.x; v[4 * q + 1] = w.y; v[4 * q + 2] = w.z; v[4 * q + 3] = w.w;
+    } else {
+      v[2 * q] = w.x; v[2 * q + 1] = w.y;
+    }
+  }
+}
+
+// Forward task (k, b): thread (i, cs) = (tid % 64, tid / 64) accumulates row
+// b*64+i over the 16 columns cs*16.. of every block j; two blocks per round
+// keep 32 loads of L in flight per thread.
+template <typename T>
+__global__ void __launch_bounds__(DEP_THREADS, 2)
+    k_dep_fwd(const SubDev* sd, const SolveDesc* dsc, const int2* tasks, int ntask, const T* L, const T* Linv,
+              const T* B, T* Y, unsigned long long* prog, unsigned long long base, int* err) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  T* Lis = reinterpret_cast<T*>(dsm);    // Linv_b, column-major 64 x 64
+  T* part = Lis + NB * NB;               // [4][64]
+  T* rhs = part + 4 * NB;                // [64]
+  const int tid = threadIdx.x, i = tid % NB, cs = tid / NB;
+  constexpr int VL = 16 / sizeof(T);
+  for (int t = blockIdx.x; t < ntask; t += gridDim.x) {
+    const int2 tk = tasks[t];
+    const int k = tk.x, b = tk.y;
+    const SubDev s = sd[k];
+    const SolveDesc d = dsc[k];
+    const int64_t n = s.n;
+    const T* Lr = L + s.A + (int64_t)b * NB + i + n * (cs * 16);   // row b*64+i, columns cs*16.. of block 0
+    T* Yk = Y + d.boff - (int64_t)d.b0 * NB;                         // indexed by row of the subdomain
+    __syncthreads();   // the previous task is done with the shared buffers
+    {
+      const Vec16<T>* src = reinterpret_cast<const Vec16<T>*>(Linv + s.linv + (int64_t)b * NB * NB);
+      Vec16<T>* dst = reinterpret_cast<Vec16<T>*>(Lis);
+      for (int q = tid; q < NB * NB / VL; q += DEP_THREADS) dst[q] = src[q];
+    }
+    T acc = 0;
+    unsigned long long seen = 0;
+    int j = d.b0;
+    for (; j + 1 < b; j += 2) {
+      T l0[16], l1[16], y0[16], y1[16];
+      const T* La = Lr + n * ((int64_t)j * NB);
+      const T* Lb2 = La + n * NB;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        l0[c] = La[n * c];
+        l1[c] = Lb2[n * c];
+      }
+      if (seen < base + j + 2) seen = dep_wait(prog + k, base + j + 2, err);
+      load16_cg(Yk + (int64_t)j * NB + cs * 16, y0);
+      load16_cg(Yk + (int64_t)(j + 1) * NB + cs * 16, y1);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) acc += l0[c] * y0[c];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) acc += l1[c] * y1[c];
+    }
+    if (j < b) {
+      T l0[16], y0[16];
+      const T* La = Lr + n * ((int64_t)j * NB);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) l0[c] = La[n * c];
+      if (seen < base + j + 1) seen = dep_wait(prog + k, base + j + 1, err);
+      load16_cg(Yk + (int64_t)j * NB + cs * 16, y0);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) acc += l0[c] * y0[c];
+    }
+    part[cs * NB + i] = acc;
+    __syncthreads();
+    if (tid < NB)
+      rhs[tid] = B[d.boff + (int64_t)(b - d.b0) * NB + tid] -
+                 (part[tid] + part[NB + tid] + part[2 * NB + tid] + part[3 * NB + tid]);
+    __syncthreads();
+    // y_b = Linv_b rhs (zero above the diagonal): part cs sums columns cs*16..
+    T v = 0;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v += Lis[i + NB * (cs * 16 + c)] * rhs[cs * 16 + c];
+    part[cs * NB + i] = v;
+    __syncthreads();
+    if (tid < NB) Yk[(int64_t)b * NB + tid] = part[tid] + part[NB + tid] + part[2 * NB + tid] + part[3 * NB + tid];
+    dep_publish(prog + k, base + (unsigned long long)(b + 1));
+  }
+}
+
+// Backward task (k, b): thread (i, cs) reads row i of every block (j, b) below
+// the diagonal, columns cs*16.., and accumulates the 16 column sums; the sums
+// over i meet in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(DEP_THREADS, 2)
+    k_dep_bwd(const SubDev* sd, const SolveDesc* dsc, const int2* tasks, int ntask, const T* L, const T* Linv,
+              const T* Y, T* X, unsigned long long* prog, unsigned long long base, int* err) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  T* Lis = reinterpret_cast<T*>(dsm);          // Lis[l * 65 + i] = Linv_b[l][i]
+  T* red = Lis + NB * (NB + 1);                // red[i * 65 + c]: partial column sums of row i
+  T* part = red + NB * (NB + 1);               // [4][64]
+  T* rhs = part + 4 * NB;                      // [64]
+  const int tid = threadIdx.x, i = tid % NB, cs = tid / NB;
+  for (int t = blockIdx.x; t < ntask; t += gridDim.x) {
+    const int2 tk = tasks[t];
+    const int k = tk.x, b = tk.y;
+    const SubDev s = sd[k];
+    const SolveDesc d = dsc[k];
+    const int64_t n = s.n;
+    const int nb = s.nblk;
+    const T* Lc = L + s.A + i + n * ((int64_t)b * NB + cs * 16);   // row i of block row 0, columns of block b
+    const T* Yk = Y + d.boff - (int64_t)d.b0 * NB;
+    T* Xk = X + d.boff - (int64_t)d.b0 * NB;
+    __syncthreads();   // the previous task is done with the shared buffers
+    {
+      const T* Lb = Linv + s.linv + (int64_t)b * NB * NB;   // Lb[l + 64 i] = Linv_b[l][i]
+      for (int q = tid; q < NB * NB; q += DEP_THREADS) Lis[(q % NB) * (NB + 1) + q / NB] = Lb[q];
+    }
+    T acc[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc[c] = 0;
+    unsigned long long seen = 0;
+    int j = nb - 1;
+    for (; j - 1 > b; j -= 2) {
+      T l0[16], l1[16];
+      const T* La = Lc + (int64_t)j * NB;
+      const T* Lb2 = La - NB;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        l0[c] = La[n * c];
+        l1[c] = Lb2[n * c];
+      }
+      const unsigned long long need = base + (unsigned long long)(nb - j + 1);
+      if (seen < need) seen = dep_wait(prog + k, need, err);
+      const T x0 = __ldcg(Xk + (int64_t)j * NB + i);
+      const T x1 = __ldcg(Xk + (int64_t)(j - 1) * NB + i);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) acc[c] += l0[c] * x0 + l1[c] * x1;
+    }
+    if (j > b) {
+      T l0[16];
+      const T* La = Lc + (int64_t)j * NB;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) l0[c] = La[n * c];
+      const unsigned long long need = base + (unsigned long long)(nb - j);
+      if (seen < need) seen = dep_wait(prog + k, need, err);
+      const T x0 = __ldcg(Xk + (int64_t)j * NB + i);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) acc[c] += l0[c] * x0;
+    }
+#pragma unroll
+    for (int c = 0; c < 16; ++c) red[i * (NB + 1) + cs * 16 + c] = acc[c];
+    __syncthreads();
+    {
+      // column c = tid % 64 summed over the rows of quarter tid / 64
+      const int c = tid % NB, qr = tid / NB;
+      T v = 0;
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v += red[(qr * 16 + r) * (NB + 1) + c];
+      part[qr * NB + c] = v;
+    }
+    __syncthreads();
+    if (tid < NB)
+      rhs[tid] = Yk[(int64_t)b * NB + tid] - (part[tid] + part[NB + tid] + part[2 * NB + tid] + part[3 * NB + tid]);
+    __syncthreads();
+    // x_b = Linv_b^T rhs: x_i = sum_{l >= i} Linv_b[l][i] rhs_l, part cs sums l = cs*16..
+    T v = 0;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int l = cs * 16 + c;
+      v += Lis[l * (NB + 1) + i] * rhs[l];
+    }
+    part[cs * NB + i] = v;
+    __syncthreads();
+    if (tid < NB) Xk[(int64_t)b * NB + tid] = part[tid] + part[NB + tid] + part[2 * NB + tid] + part[3 * NB + tid];
+    dep_publish(prog + k, base + (unsigned long long)(nb - b));
+  }
+}
+
+template <typename T>
+size_t fwd_smem() { return sizeof(T) * ((size_t)NB * NB + 5 * NB); }
+template <typename T>
+size_t bwd_smem() { return sizeof(T) * (2 * (size_t)NB * (NB + 1) + 5 * NB); }
+
+template <typename T>
+ieti_status launch_dep(Ctx* c, bool fwd, int range, const T* B, const T* Yin, T* Yout, cudaStream_t st) {
+  const int which = fwd ? 0 : 1;
+  const int ntask = c->dep_ntask[range][which];
+  if (ntask == 0) return IETI_OK;
+  int dev = 0, coop = 0;
+  IETI_CUDA_TRY(c, cudaGetDevice(&dev));
+  IETI_CUDA_TRY(c, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop || c->sm_count < 1) return IETI_ERR_STATE;
+  const SolveDesc* dd = c->d_desc_rv + (range == RV_IRANGE ? c->nsub : 0);
+  const int2* tasks = c->d_dep_tasks[range][which];
+  const size_t smem = fwd ? fwd_smem<T>() : bwd_smem<T>();
+  void* kern = fwd ? (void*)k_dep_fwd<T> : (void*)k_dep_bwd<T>;
+  int per_sm = 0;
+  IETI_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, DEP_THREADS, smem));
+  if (per_sm < 1) return IETI_ERR_STATE;
+  const int grid = std::min(ntask, per_sm * c->sm_count);
+  const unsigned long long base = (++c->dep_epoch) << DEP_EPOCH_SHIFT;
+  const T* L = (const T*)c->L;
+  const T* Linv = (const T*)c->Linv;
+  const SubDev* sd = c->d_sd;
+  unsigned long long* prog = c->d_dep_prog;
+  int* err = c->d_dep_err;
+  void* args[] = {(void*)&sd, (void*)&dd, (void*)&tasks, (void*)&ntask, (void*)&L, (void*)&Linv,
+                  (void*)(fwd ? &B : &Yin), (void*)&Yout, (void*)&prog, (void*)&base, (void*)&err};
+  cudaEvent_t p0 = prof_begin(c, st);
+  IETI_CUDA_TRY(c, cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(DEP_THREADS), args, smem, st));
+  prof_end(c, fwd ? PROF_FWD : PROF_BWD, p0, st);
+  IETI_LAUNCH_CHECK(c);
+  return IETI_OK;
+}
+
+}  // namespace
+
+ieti_status dep_sweep_attrs(Ctx* c) {
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_dep_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)fwd_smem<float>()));
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_dep_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)fwd_smem<double>()));
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_dep_bwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)bwd_smem<float>()));
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_dep_bwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)bwd_smem<double>()));
+  return IETI_OK;
+}
+
+// task tables of the r-vector sweeps (whole r range and r_I rows, forward and
+// backward), progress counters and the error flag
+ieti_status dep_sweep_alloc(Ctx* c) {
+  for (int range = 0; range < 2; ++range) {
+    for (int which = 0; which < 2; ++which) {
+      std::vector<int2> tk;
+      for (int b = 0; b < c->max_nblk; ++b)
+        for (int k = 0; k < c->nsub; ++k) {
+          const SubDev& s = c->sd_host[k];
+          const int b0 = range == RV_IRANGE ? s.nVp / NB : 0;
+          if (range == RV_IRANGE && s.nI == 0) continue;
+          const int bb = which == 0 ? b : c->max_nblk - 1 - b;
+          if (bb >= b0 && bb < s.nblk) tk.push_back(make_int2(k, bb));
+        }
+      c->dep_ntask[range][which] = (int)tk.size();
+      int2* d = nullptr;
+      const size_t bytes = sizeof(int2) * std::max<size_t>(tk.size(), 1);
+      IETI_CUDA_TRY(c, cudaMalloc(&d, bytes));
+      c->allocs.push_back({d, bytes});
+      if (!tk.empty()) IETI_CUDA_TRY(c, cudaMemcpy(d, tk.data(), sizeof(int2) * tk.size(), cudaMemcpyHostToDevice));
+      c->d_dep_tasks[range][which] = d;
+    }
+  }
+  unsigned long long* pg = nullptr;
+  IETI_CUDA_TRY(c, cudaMalloc(&pg, sizeof(unsigned long long) * std::max(c->nsub, 1)));
+  c->allocs.push_back({pg, sizeof(unsigned long long) * std::max(c->nsub, 1)});
+  IETI_CUDA_TRY(c, cudaMemset(pg, 0, sizeof(unsigned long long) * std::max(c->nsub, 1)));
+  c->d_dep_prog = pg;
+  int* e = nullptr;
+  IETI_CUDA_TRY(c, cudaMalloc(&e, sizeof(int)));
+  c->allocs.push_back({e, sizeof(int)});
+  IETI_CUDA_TRY(c, cudaMemset(e, 0, sizeof(int)));
+  c->d_dep_err = e;
+  c->dep_epoch = 0;
+  return IETI_OK;
+}
+
+template <typename T>
+ieti_status dep_sweep(Ctx* c, int range, int which, const T* B, T* Y, T* X, cudaStream_t st) {
+  ieti_status r;
+  if ((which & SWEEP_FWD) && (r = launch_dep<T>(c, true, range, B, nullptr, Y, st)) != IETI_OK) return r;
+  if ((which & SWEEP_BWD) && (r = launch_dep<T>(c, false, range, nullptr, Y, X, st)) != IETI_OK) return r;
+  return IETI_OK;
+}
+template ieti_status dep_sweep<float>(Ctx*, int, int, const float*, float*, float*, cudaStream_t);
+template ieti_status dep_sweep<double>(Ctx*, int, int, const double*, double*, double*, cudaStream_t);
+
+}  // namespace ieti
