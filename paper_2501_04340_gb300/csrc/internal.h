@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -158,6 +159,11 @@ struct Ctx {
   int64_t* d_uoff = nullptr;             // u-vector offsets of the subdomains (device copy)
   SolveDesc* d_desc_rv = nullptr;        // r-vector sweep ranges: [0, nsub) full, [nsub, 2 nsub) r_I rows
   int min_b0_I = 0;                      // first panel of the r_I range over all subdomains
+  // nonzero 64 x 64 tiles of K_rr per block row (built once from the assembled K_rr)
+  bool ktile_ready = false;
+  int64_t* d_ktile_row = nullptr;        // per block row (over all subdomains) + 1: start in d_ktile_col
+  int32_t* d_ktile_col = nullptr;        // block columns J with a nonzero tile
+  int* d_ktile_base = nullptr;           // per subdomain: its first block row
   // dependency-driven single-column sweeps (sweep_dep.cu)
   bool dep_sweeps = true;                // IETI_NO_DEP_SWEEP=1: per-panel barrier sweeps instead
   int2* d_dep_tasks[2][2] = {};          // [range][forward, backward]: (subdomain, block) in run order
@@ -317,6 +323,22 @@ ieti_status solve_all(Ctx* c, const double* lam0, double tol, int maxit, double 
                       double* a, double* lam_out, ieti_solve_info* info, cudaStream_t s);
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// device copy of a host vector, owned by the context (freed with it)
+template <typename T>
+ieti_status dev_upload(Ctx* c, T** p, const std::vector<T>& h) {
+  const size_t bytes = std::max<size_t>(h.size(), 1) * sizeof(T);
+  void* q = nullptr;
+  if (cudaMalloc(&q, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    c->err = "cudaMalloc of " + std::to_string(bytes) + " bytes failed";
+    return IETI_ERR_OOM;
+  }
+  c->allocs.push_back({q, bytes});
+  *p = (T*)q;
+  if (!h.empty()) IETI_CUDA_TRY(c, cudaMemcpy(q, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+  return IETI_OK;
+}
 
 // multi-column per-subdomain vectors: subdomain k's block of an nrhs-column
 // vector starts at (offset_k * nrhs), column stride = local size

@@ -518,6 +518,93 @@ __global__ void __launch_bounds__(256) k_residual2(const SubDev* sd, const int64
   }
 }
 
+// nonzero 64 x 64 tiles of K_rr: flags[fo_k + I + nblk J] = 1 when an entry of
+// rows 64 I.., columns 64 J.. is nonzero (one warp per tile)
+__global__ void k_tile_flags(const SubDev* sd, const int64_t* fo, const double* K64, unsigned char* flags) {
+  const int k = blockIdx.y;
+  const SubDev s = sd[k];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int64_t nt = (int64_t)s.nblk * s.nblk;
+  for (int64_t t = (int64_t)blockIdx.x * 8 + warp; t < nt; t += (int64_t)gridDim.x * 8) {
+    const int I = (int)(t % s.nblk), J = (int)(t / s.nblk);
+    const double* base = K64 + s.A + (int64_t)I * NB + (int64_t)s.n * J * NB;
+    bool nz = false;
+    for (int c = 0; c < NB; ++c) {
+      const double2 v = reinterpret_cast<const double2*>(base + (int64_t)s.n * c)[lane];
+      nz |= (v.x != 0.0) || (v.y != 0.0);
+    }
+    nz = __any_sync(0xffffffffu, nz);
+    if (lane == 0) flags[fo[k] + t] = nz ? 1 : 0;
+  }
+}
+
+// k_residual2 over the nonzero tiles of K_rr only: row r of block row I reads
+// the tiles listed for I (K_rr is symmetric, so row r is column r)
+__global__ void __launch_bounds__(256) k_residual3(const SubDev* sd, const int64_t* r_edge, const double* K64,
+                                                   const int64_t* trow, const int32_t* tcol, const int* tb,
+                                                   const double* Kp, const double* Kpp, const double* jr,
+                                                   const double* jp, const double* xr, const double* xp,
+                                                   int64_t nedge, int nrhs, const int32_t* I_dual,
+                                                   const double* I_sign, const double* lam, int64_t m_r,
+                                                   double* rr_out, double* rp_out, double* R) {
+  const int k = blockIdx.y;
+  const SubDev s = sd[k];
+  const int Rn = s.n + s.nP;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int row = blockIdx.x * 8 + warp;
+  if (row >= Rn) return;
+  const int64_t e_row = r_edge[s.dof + row];
+  for (int col = 0; col < nrhs; ++col) {
+    const double2* x2 = reinterpret_cast<const double2*>(xr + RV(s, 0, col, nrhs));
+    double acc0 = 0, acc1 = 0;
+    const double* kpc;
+    int64_t kp_stride;
+    if (row < s.n) {
+      const double2* k2 = reinterpret_cast<const double2*>(K64 + s.A + (int64_t)s.n * row);
+      const int I = row / NB;
+      const int64_t e0 = trow[tb[k] + I], e1 = trow[tb[k] + I + 1];
+#pragma unroll 4
+      for (int64_t e = e0; e < e1; ++e) {
+        const int J = tcol[e];
+        const double2 kv = k2[J * (NB / 2) + lane], xv = x2[J * (NB / 2) + lane];
+        acc0 = fma(kv.x, xv.x, acc0);
+        acc1 = fma(kv.y, xv.y, acc1);
+      }
+      kpc = Kp + s.Kp + row;
+      kp_stride = s.n;
+    } else {
+      const int c = row - s.n;
+      const double2* k2 = reinterpret_cast<const double2*>(Kp + s.Kp + (int64_t)s.n * c);
+#pragma unroll 4
+      for (int j = lane; j < s.n / 2; j += 32) {
+        const double2 kv = k2[j], xv = x2[j];
+        acc0 = fma(kv.x, xv.x, acc0);
+        acc1 = fma(kv.y, xv.y, acc1);
+      }
+      kpc = Kpp + s.Kpp + c;
+      kp_stride = s.nP;
+    }
+    double acc = acc0 + acc1;
+    for (int j = lane; j < s.nP; j += 32) acc += kpc[kp_stride * j] * xp[PV(s, j, col, nrhs)];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      double v;
+      if (row < s.n) {
+        v = (e_row < 0) ? 0.0 : jr[RV(s, row, col, nrhs)] - acc;
+        double vl = v;
+        const int ii = row - s.nVp;
+        if (ii >= 0 && ii < s.nI) vl -= I_sign[s.iv + ii] * lam[I_dual[s.iv + ii] + m_r * col];
+        rr_out[RV(s, row, col, nrhs)] = vl;
+      } else {
+        v = jp[PV(s, row - s.n, col, nrhs)] - acc;
+        rp_out[PV(s, row - s.n, col, nrhs)] = v;
+      }
+      if (R && e_row >= 0) atomicAdd(R + e_row + nedge * col, v);
+    }
+  }
+}
+
 __global__ void k_colnorm2(const double* v, int64_t m, double* out) {
   __shared__ double red[256];
   const int col = blockIdx.x;
@@ -869,18 +956,68 @@ static ieti_status recover(Ctx* c, const double* lam, const double* ycr, double*
                               : recover_t<float>(c, lam, ycr, a, accumulate, st);
 }
 
+// lists of the nonzero tiles of every block row of K_rr (the pattern does
+// not depend on the reluctivities, so it is found once from the assembled K_rr)
+static ieti_status build_ktiles(Ctx* c, cudaStream_t st) {
+  std::vector<int64_t> fo(c->nsub);
+  std::vector<int> tb(c->nsub + 1);
+  int64_t nf = 0;
+  int nb = 0;
+  for (int k = 0; k < c->nsub; ++k) {
+    fo[k] = nf;
+    tb[k] = nb;
+    nf += (int64_t)c->sd_host[k].nblk * c->sd_host[k].nblk;
+    nb += c->sd_host[k].nblk;
+  }
+  tb[c->nsub] = nb;
+  int64_t* d_fo = nullptr;
+  unsigned char* d_flags = nullptr;
+  IETI_CUDA_TRY(c, cudaMalloc(&d_fo, sizeof(int64_t) * c->nsub));
+  IETI_CUDA_TRY(c, cudaMalloc(&d_flags, std::max<int64_t>(nf, 1)));
+  IETI_CUDA_TRY(c, cudaMemcpyAsync(d_fo, fo.data(), sizeof(int64_t) * c->nsub, cudaMemcpyHostToDevice, st));
+  k_tile_flags<<<dim3(256, c->nsub), 256, 0, st>>>(c->d_sd, d_fo, c->K64, d_flags);
+  IETI_LAUNCH_CHECK(c);
+  std::vector<unsigned char> flags(nf);
+  IETI_CUDA_TRY(c, cudaMemcpyAsync(flags.data(), d_flags, nf, cudaMemcpyDeviceToHost, st));
+  IETI_CUDA_TRY(c, cudaStreamSynchronize(st));
+  cudaFree(d_fo);
+  cudaFree(d_flags);
+  // block row I lists the J with tile (J, I) nonzero: row r of block I reads
+  // column r, i.e. entries of rows 64 J.. of column block I
+  std::vector<int64_t> trow(nb + 1, 0);
+  std::vector<int32_t> tcol;
+  for (int k = 0; k < c->nsub; ++k) {
+    const int m = c->sd_host[k].nblk;
+    for (int I = 0; I < m; ++I) {
+      trow[tb[k] + I] = (int64_t)tcol.size();
+      for (int J = 0; J < m; ++J)
+        if (flags[fo[k] + J + (int64_t)m * I]) tcol.push_back(J);
+    }
+  }
+  trow[nb] = (int64_t)tcol.size();
+  if (tcol.empty()) tcol.push_back(0);
+  ieti_status r;
+  if ((r = dev_upload(c, &c->d_ktile_row, trow)) != IETI_OK) return r;
+  if ((r = dev_upload(c, &c->d_ktile_col, tcol)) != IETI_OK) return r;
+  if ((r = dev_upload(c, &c->d_ktile_base, tb)) != IETI_OK) return r;
+  c->ktile_ready = true;
+  return IETI_OK;
+}
+
 // relative FP64 residual ||j - K a|| / ||j|| (max over columns); local residuals to wres_r/wres_p
 static ieti_status residual(Ctx* c, const double* a, double* rel, double* jn2, cudaStream_t st) {
   const int nrhs = c->nrhs;
   const int64_t ne = c->mesh.nedge;
+  ieti_status rk;
+  if (!c->ktile_ready && (rk = build_ktiles(c, st)) != IETI_OK) return rk;
   IETI_CUDA_TRY(c, cudaMemsetAsync(c->wglob, 0, sizeof(double) * ne * nrhs, st));
   dim3 g((unsigned)ceil_div(c->max_n + c->max_nP, 8), c->nsub);
   cudaEvent_t p0 = prof_begin(c, st);
   k_gather_x<<<dim3(64, c->nsub), 256, 0, st>>>(c->d_sd, c->d_r_edge, a, ne, nrhs, c->wr64[2], c->wxp);
   IETI_LAUNCH_CHECK(c);
-  k_residual2<<<g, 256, 0, st>>>(c->d_sd, c->d_r_edge, c->K64, c->Kp64, c->Kpp64, c->jr, c->jp, c->wr64[2],
-                                 c->wxp, ne, nrhs, c->d_I_dual, c->d_I_sign, c->wlam_acc, c->m_r,
-                                 c->wres_r, c->wres_p, c->wglob);
+  k_residual3<<<g, 256, 0, st>>>(c->d_sd, c->d_r_edge, c->K64, c->d_ktile_row, c->d_ktile_col, c->d_ktile_base,
+                                 c->Kp64, c->Kpp64, c->jr, c->jp, c->wr64[2], c->wxp, ne, nrhs, c->d_I_dual,
+                                 c->d_I_sign, c->wlam_acc, c->m_r, c->wres_r, c->wres_p, c->wglob);
   prof_end(c, PROF_RESID, p0, st);
   IETI_LAUNCH_CHECK(c);
   k_colnorm2<<<nrhs, 256, 0, st>>>(c->wglob, ne, c->wnorm);
