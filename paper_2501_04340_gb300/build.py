@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(os.path.dirname(HERE), "_build")
 LIB = os.path.join(HERE, "libieti.so")
-SOURCES = ["model.cpp", "assemble.cu", "factor.cu", "solve.cu", "api.cu", "noalloc.cu", "persist.cu", "mlp.cu", "iface.cu", "pcg_stream.cu", "syrk_tc.cu", "sweep_dep.cu"]
+SOURCES = ["model.cpp", "assemble.cu", "factor.cu", "solve.cu", "api.cu", "noalloc.cu", "persist.cu", "mlp.cu", "iface.cu", "pcg_stream.cu", "syrk_tc.cu", "sweep_dep.cu", "symbolic.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -90,10 +90,12 @@ __global__ void __launch_bounds__(256) k_potrf_diag(const SubDev* sd, T* L, T* L
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_trsm_panel(const SubDev* sd, T* L, const T* Linv, int b) {
-  const int k = blockIdx.y;
+__global__ void __launch_bounds__(256) k_trsm_panel(const SubDev* sd, T* L, const T* Linv, int b,
+                                                    const int2* items) {
+  // items: (subdomain, block row) of the nonzero tiles, else every tile below b
+  const int k = items ? items[blockIdx.x].x : (int)blockIdx.y;
+  const int r = items ? items[blockIdx.x].y : b + 1 + (int)blockIdx.x;
   const SubDev s = sd[k];
-  const int r = b + 1 + blockIdx.x;
   if (r >= s.nblk) return;
   __shared__ T A[NB][NB + 1];
   __shared__ T Li[NB][NB + 1];
@@ -121,18 +123,28 @@ __global__ void __launch_bounds__(256) k_trsm_panel(const SubDev* sd, T* L, cons
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_syrk(const SubDev* sd, T* L, int b) {
-  const int k = blockIdx.y;
+__global__ void __launch_bounds__(256) k_syrk(const SubDev* sd, T* L, int b, const int4* items) {
+  // items: (subdomain, block row, block column) of the tiles to update, else
+  // every tile of the trailing lower triangle
+  int k, r, c;
+  if (items) {
+    const int4 it = items[blockIdx.x];
+    k = it.x;
+    r = it.y;
+    c = it.z;
+  } else {
+    k = blockIdx.y;
+    // triangular decode of the tile index: rr >= cc
+    const int t = blockIdx.x;
+    int rr = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    while (rr * (rr + 1) / 2 > t) --rr;
+    while ((rr + 1) * (rr + 2) / 2 <= t) ++rr;
+    const int cc = t - rr * (rr + 1) / 2;
+    if (rr >= sd[k].nblk - b - 1) return;
+    r = b + 1 + rr;
+    c = b + 1 + cc;
+  }
   const SubDev s = sd[k];
-  const int Tk = s.nblk - b - 1;
-  // triangular decode of the tile index: rr >= cc
-  const int t = blockIdx.x;
-  int rr = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-  while (rr * (rr + 1) / 2 > t) --rr;
-  while ((rr + 1) * (rr + 2) / 2 <= t) ++rr;
-  const int cc = t - rr * (rr + 1) / 2;
-  if (rr >= Tk) return;
-  const int r = b + 1 + rr, c = b + 1 + cc;
   // panels stored transposed (Lr[l][i] = L[r-block row i, panel column l]) with
   // 16-byte aligned rows, so a thread reads its 4 rows / 4 columns as vectors
   constexpr int LDS = NB + 16 / (int)sizeof(T);
@@ -200,15 +212,20 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool vali
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(src), "r"(bytes) : "memory");
 }
 
-__global__ void __launch_bounds__(256, 2) k_syrk2(const SubDev* sd, float* L, int b, int kb, int col_only) {
-  const int k = blockIdx.y;
+__global__ void __launch_bounds__(256, 2) k_syrk2(const SubDev* sd, float* L, int b, int kb, int col_only,
+                                                 const int4* items) {
+  // items: (subdomain, R, C) of the pair tiles to update, else all of them
+  const int k = items ? items[blockIdx.x].x : (int)blockIdx.y;
   const SubDev s = sd[k];
   const int t0 = b + kb;          // first trailing block
   const int Tk = s.nblk - t0;
   if (Tk <= 0) return;
   const int Tt = (Tk + 1) / 2;   // block pairs
   int R, C;
-  if (col_only) {
+  if (items) {
+    R = items[blockIdx.x].y;
+    C = items[blockIdx.x].z;
+  } else if (col_only) {
     R = blockIdx.x;
     C = 0;
   } else {
@@ -392,7 +409,7 @@ __global__ void __launch_bounds__(256) k_tsolve_diag(const SubDev* sd, const Sol
 // forward update of panel b: B[rows below] -= L[rows below, panel b] Y_b
 template <typename T>
 __global__ void __launch_bounds__(256) k_tsolve_fwd(const SubDev* sd, const SolveDesc* dsc, const T* L, T* B,
-                                                    const T* Y, int b) {
+                                                    const T* Y, int b, const unsigned char* lf, const int64_t* lfo) {
   const int k = blockIdx.z;
   const SubDev s = sd[k];
   const SolveDesc d = dsc[k];
@@ -402,6 +419,7 @@ __global__ void __launch_bounds__(256) k_tsolve_fwd(const SubDev* sd, const Solv
   const int row0 = (b - d.b0) * NB, rows = s.n - d.b0 * NB;
   const int r0 = row0 + NB + blockIdx.x * NB;
   if (r0 >= rows) return;
+  if (lf && !lf[lfo[k] + d.b0 + r0 / NB + (int64_t)s.nblk * b]) return;   // zero tile of the factor
   const T* P = L + s.A + (d.b0 * NB + r0) + (int64_t)s.n * (b * NB);
   tile_gemm64<T, true>(P, 1, s.n, min(NB, rows - r0), Y + d.boff + row0 + (int64_t)d.ldb * j0, 1, d.ldb,
                        min(NB, d.ncol - j0), B + d.boff + r0 + (int64_t)d.ldb * j0, d.ldb);
@@ -410,7 +428,7 @@ __global__ void __launch_bounds__(256) k_tsolve_fwd(const SubDev* sd, const Solv
 // backward update of panel b: Y[rows above] -= L[panel b, rows above]^T X_b
 template <typename T>
 __global__ void __launch_bounds__(256) k_tsolve_bwd(const SubDev* sd, const SolveDesc* dsc, const T* L, T* Y,
-                                                    const T* X, int b) {
+                                                    const T* X, int b, const unsigned char* lf, const int64_t* lfo) {
   const int k = blockIdx.z;
   const SubDev s = sd[k];
   const SolveDesc d = dsc[k];
@@ -420,6 +438,7 @@ __global__ void __launch_bounds__(256) k_tsolve_bwd(const SubDev* sd, const Solv
   const int row0 = (b - d.b0) * NB;
   const int a0 = blockIdx.x * NB;
   if (a0 >= row0) return;
+  if (lf && !lf[lfo[k] + b + (int64_t)s.nblk * (d.b0 + a0 / NB)]) return;   // zero tile of the factor
   // P(i, l) = L[b NB + l, d.b0 NB + a0 + i]
   const T* P = L + s.A + (int64_t)b * NB + (int64_t)s.n * (d.b0 * NB + a0);
   tile_gemm64<T, true>(P, s.n, 1, min(NB, row0 - a0), X + d.boff + row0 + (int64_t)d.ldb * j0, 1, d.ldb,
@@ -515,7 +534,8 @@ __global__ void __launch_bounds__(256) k_bwd1(const SubDev* sd, const SolveDesc*
 template <typename T>
 ieti_status tri_solve(Ctx* c, const SubDev* d_sd, int nsub, int max_nblk, int max_rows, int max_ncol,
                       const SolveDesc* d_desc, int min_b0, const T* L, const T* Linv, T* B, T* Y, T* X,
-                      cudaStream_t st, int which = SWEEP_BOTH) {
+                      cudaStream_t st, int which = SWEEP_BOTH, const unsigned char* lf = nullptr,
+                      const int64_t* lfo = nullptr) {
   if (max_ncol <= 0) return IETI_OK;
   if (!c->no_coop) {
     // one persistent launch per sweep (single column, or any width when opted
@@ -536,7 +556,7 @@ ieti_status tri_solve(Ctx* c, const SubDev* d_sd, int nsub, int max_nblk, int ma
     } else {
       k_tsolve_diag<T, false><<<dim3(ctiles, nsub), 256, 0, st>>>(d_sd, d_desc, Linv, B, Y, b);
       IETI_LAUNCH_CHECK(c);
-      k_tsolve_fwd<T><<<dim3(rtiles, ctiles, nsub), 256, 0, st>>>(d_sd, d_desc, L, B, Y, b);
+      k_tsolve_fwd<T><<<dim3(rtiles, ctiles, nsub), 256, 0, st>>>(d_sd, d_desc, L, B, Y, b, lf, lfo);
       IETI_LAUNCH_CHECK(c);
     }
   }
@@ -550,7 +570,7 @@ ieti_status tri_solve(Ctx* c, const SubDev* d_sd, int nsub, int max_nblk, int ma
     } else {
       k_tsolve_diag<T, true><<<dim3(ctiles, nsub), 256, 0, st>>>(d_sd, d_desc, Linv, Y, X, b);
       IETI_LAUNCH_CHECK(c);
-      k_tsolve_bwd<T><<<dim3(rtiles, ctiles, nsub), 256, 0, st>>>(d_sd, d_desc, L, Y, X, b);
+      k_tsolve_bwd<T><<<dim3(rtiles, ctiles, nsub), 256, 0, st>>>(d_sd, d_desc, L, Y, X, b, lf, lfo);
       IETI_LAUNCH_CHECK(c);
     }
   }
@@ -663,7 +683,7 @@ ieti_status factor_kernel_attrs(Ctx* c) {
 
 template <typename T>
 static ieti_status cholesky(Ctx* c, const SubDev* d_sd, const std::vector<SubDev>& sdh, T* L, T* Linv,
-                            T* S, bool snapshot, cudaStream_t st) {
+                            T* S, bool snapshot, cudaStream_t st, const FactorPlan* plan = nullptr) {
   int nsub = (int)sdh.size();
   int max_nblk = 0;
   for (auto& s : sdh) max_nblk = std::max(max_nblk, s.nblk);
@@ -672,56 +692,78 @@ static ieti_status cholesky(Ctx* c, const SubDev* d_sd, const std::vector<SubDev
     for (auto& s : sdh) any |= (s.nVp == b * NB && s.nI > 0);
     return snapshot && any;
   };
-  // diagonal block b and the panel below it
-  auto panel = [&](int b) -> ieti_status {
+  // diagonal block b and the panel below it (the nonzero tiles only with a plan)
+  auto panel = [&](int b, const int2* items, int cnt) -> ieti_status {
     cudaEvent_t p0 = prof_begin(c, st);
     k_potrf_diag<T><<<nsub, 256, 0, st>>>(d_sd, L, Linv, b, c->d_err);
     prof_end(c, PROF_POTRF, p0, st);
     IETI_LAUNCH_CHECK(c);
     const int Tm = max_nblk - b - 1;
-    if (Tm > 0) {
+    if (items ? cnt > 0 : Tm > 0) {
       p0 = prof_begin(c, st);
-      k_trsm_panel<T><<<dim3(Tm, nsub), 256, 0, st>>>(d_sd, L, Linv, b);
+      if (items) k_trsm_panel<T><<<cnt, 256, 0, st>>>(d_sd, L, Linv, b, items);
+      else k_trsm_panel<T><<<dim3(Tm, nsub), 256, 0, st>>>(d_sd, L, Linv, b, nullptr);
       prof_end(c, PROF_TRSM, p0, st);
       IETI_LAUNCH_CHECK(c);
     }
     return IETI_OK;
   };
-  for (int b = 0; b < max_nblk;) {
+  const size_t nsteps = plan ? plan->steps.size() : 0;
+  for (int b = 0, si = 0; plan ? si < (int)nsteps : b < max_nblk; ++si) {
+    FactorStep stp{};
+    if (plan) {
+      stp = plan->steps[si];
+      b = stp.b;
+    } else {
+      // FP32: two panels per trailing update (K = 128 halves the passes over
+      // the trailing matrix), unless the S_rIrI snapshot falls between them
+      stp.b = b;
+      stp.kb = 1;
+      if constexpr (sizeof(T) == 4) stp.kb = (!c->syrk_tc && b + 2 < max_nblk && !snap_at(b + 1)) ? 2 : 1;
+    }
     if (snap_at(b)) {
       k_snapshot<T><<<dim3(256, nsub), 256, 0, st>>>(d_sd, L, S, b);
       IETI_LAUNCH_CHECK(c);
     }
-    // FP32: two panels per trailing update (K = 128 halves the passes over
-    // the trailing matrix), unless the S_rIrI snapshot falls between them
-    int kb = 1;
-    if constexpr (sizeof(T) == 4) kb = (!c->syrk_tc && b + 2 < max_nblk && !snap_at(b + 1)) ? 2 : 1;
+    const int kb = stp.kb;
     ieti_status r;
-    if ((r = panel(b)) != IETI_OK) return r;
+    if ((r = panel(b, plan ? plan->d_trsm + stp.trsm_off[0] : nullptr, stp.trsm_cnt[0])) != IETI_OK) return r;
     if (kb == 2) {
-      // block column b+1 takes panel b's update before its own factorisation
-      const int Tp1 = (max_nblk - b - 1 + 1) / 2;
-      cudaEvent_t p0 = prof_begin(c, st);
-      k_syrk2<<<dim3(Tp1, nsub), 256, S2_SMEM, st>>>(d_sd, (float*)L, b, 1, 1);
-      prof_end(c, PROF_SYRK, p0, st);
-      IETI_LAUNCH_CHECK(c);
-      if ((r = panel(b + 1)) != IETI_OK) return r;
+      if constexpr (sizeof(T) == 4) {
+        // block column b+1 takes panel b's update before its own factorisation
+        cudaEvent_t p0 = prof_begin(c, st);
+        if (plan) {
+          if (stp.col_cnt > 0)
+            k_syrk2<<<stp.col_cnt, 256, S2_SMEM, st>>>(d_sd, (float*)L, b, 1, 1, plan->d_items + stp.col_off);
+        } else {
+          const int Tp1 = (max_nblk - b - 1 + 1) / 2;
+          k_syrk2<<<dim3(Tp1, nsub), 256, S2_SMEM, st>>>(d_sd, (float*)L, b, 1, 1, nullptr);
+        }
+        prof_end(c, PROF_SYRK, p0, st);
+        IETI_LAUNCH_CHECK(c);
+      }
+      if ((r = panel(b + 1, plan ? plan->d_trsm + stp.trsm_off[1] : nullptr, stp.trsm_cnt[1])) != IETI_OK) return r;
     }
     const int Tm = max_nblk - b - kb;
-    if (Tm > 0) {
+    if (plan ? stp.trail_cnt > 0 : Tm > 0) {
       cudaEvent_t p0 = prof_begin(c, st);
+      const int4* items = plan ? plan->d_items + stp.trail_off : nullptr;
       if constexpr (sizeof(T) == 4) {
         if (c->syrk_tc) {
           // opt-in: split TF32 products on the tensor cores (slower than the
-          // CUDA-core kernel at this panel width, see syrk_tc.cu)
+          // CUDA-core kernel at this panel width, see syrk_tc.cu); it updates
+          // every trailing tile, which is exact for the zero ones as well
           ieti_status r2 = syrk_tc(c, d_sd, (float*)L, b, max_nblk, nsub, st);
           if (r2 != IETI_OK) return r2;
+        } else if (plan) {
+          k_syrk2<<<stp.trail_cnt, 256, S2_SMEM, st>>>(d_sd, (float*)L, b, kb, 0, items);
         } else {
           const int Tp = (Tm + 1) / 2;   // block pairs
-          k_syrk2<<<dim3(Tp * (Tp + 1) / 2, nsub), 256, S2_SMEM, st>>>(d_sd, (float*)L, b, kb, 0);
+          k_syrk2<<<dim3(Tp * (Tp + 1) / 2, nsub), 256, S2_SMEM, st>>>(d_sd, (float*)L, b, kb, 0, nullptr);
         }
       } else {
-        k_syrk<T><<<dim3(Tm * (Tm + 1) / 2, nsub), 256, 0, st>>>(d_sd, L, b);
+        if (plan) k_syrk<T><<<stp.trail_cnt, 256, 0, st>>>(d_sd, L, b, items);
+        else k_syrk<T><<<dim3(Tm * (Tm + 1) / 2, nsub), 256, 0, st>>>(d_sd, L, b, nullptr);
       }
       prof_end(c, PROF_SYRK, p0, st);
       IETI_LAUNCH_CHECK(c);
@@ -741,7 +783,10 @@ static ieti_status factor_t(Ctx* c, cudaStream_t st) {
   // factor buffer <- K_rr
   if ((r = convert_copy<T>(c, c->K64, L, c->tot_A, st)) != IETI_OK) return r;
   IETI_CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
-  if ((r = cholesky<T>(c, c->d_sd, c->sd_host, L, Linv, S, true, st)) != IETI_OK) return r;
+  // work lists over the nonzero tiles, found once from the assembled K_rr
+  if (!c->symb_ready && (r = build_symbolic(c, st)) != IETI_OK) return r;
+  const FactorPlan* plan = &c->fplan[sizeof(T) == 4 ? 1 : 0];
+  if ((r = cholesky<T>(c, c->d_sd, c->sd_host, L, Linv, S, true, st, plan)) != IETI_OK) return r;
   IETI_CUDA_TRY(c, cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   IETI_CUDA_TRY(c, cudaStreamSynchronize(st));
   if (*c->h_err) {
@@ -772,7 +817,8 @@ static ieti_status factor_t(Ctx* c, cudaStream_t st) {
     IETI_CUDA_TRY(c, cudaMemcpyAsync(dd, dh.data(), sizeof(SolveDesc) * nsub, cudaMemcpyHostToDevice, st));
     k_identity_rhs<T><<<dim3(256, nsub), 256, 0, st>>>(c->d_sd, dd, B);
     IETI_LAUNCH_CHECK(c);
-    if ((r = tri_solve<T>(c, c->d_sd, nsub, c->max_nblk, max_rows, max_col, dd, min_b0, L, Linv, B, Y, X, st)) != IETI_OK)
+    if ((r = tri_solve<T>(c, c->d_sd, nsub, c->max_nblk, max_rows, max_col, dd, min_b0, L, Linv, B, Y, X, st,
+                          SWEEP_BOTH, c->d_lflags, c->d_tile_off)) != IETI_OK)
       return r;
     k_extract_W<T><<<dim3(256, nsub), 256, 0, st>>>(c->d_sd, dd, X, W);
     IETI_LAUNCH_CHECK(c);
@@ -795,12 +841,12 @@ static ieti_status factor_t(Ctx* c, cudaStream_t st) {
     k_load_Kp<T><<<dim3(256, nsub), 256, 0, st>>>(c->d_sd, dd, c->Kp64, B);
     IETI_LAUNCH_CHECK(c);
     if ((r = tri_solve<T>(c, c->d_sd, nsub, c->max_nblk, c->max_n, c->max_nP, dd, 0, L, Linv, B, Y, X, st,
-                          SWEEP_FWD)) != IETI_OK)
+                          SWEEP_FWD, c->d_lflags, c->d_tile_off)) != IETI_OK)
       return r;
     k_store_Psi<T><<<dim3(256, nsub), 256, 0, st>>>(c->d_sd, dd, Y, (T*)c->Psi);
     IETI_LAUNCH_CHECK(c);
     if ((r = tri_solve<T>(c, c->d_sd, nsub, c->max_nblk, c->max_n, c->max_nP, dd, 0, L, Linv, B, Y, X, st,
-                          SWEEP_BWD)) != IETI_OK)
+                          SWEEP_BWD, c->d_lflags, c->d_tile_off)) != IETI_OK)
       return r;
     k_store_Phi<T><<<dim3(256, nsub), 256, 0, st>>>(c->d_sd, dd, X, c->Phi);
     IETI_LAUNCH_CHECK(c);

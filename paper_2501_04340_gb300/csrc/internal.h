@@ -88,6 +88,25 @@ struct StreamPlan {
   int2* d_ckr = nullptr;     // subdomains [x, y) that every CTA's tiles touch
 };
 
+// one step of the blocked factorisation with its work lists (symbolic.cu)
+struct FactorStep {
+  int b = 0, kb = 1;             // panels b .. b+kb-1
+  bool snap = false;             // S_rIrI snapshot before panel b
+  int64_t trsm_off[2] = {0, 0};  // (subdomain, block row) items of the panel solves of b and b+1
+  int trsm_cnt[2] = {0, 0};
+  int64_t col_off = 0;           // kb == 2: pair rows of block column b+1 updated by panel b
+  int col_cnt = 0;
+  int64_t trail_off = 0;         // trailing-update items
+  int trail_cnt = 0;
+};
+
+struct FactorPlan {
+  bool built = false;
+  std::vector<FactorStep> steps;
+  int4* d_items = nullptr;       // (k, R, C) pair tiles (FP32) or (k, i, j) tiles (FP64)
+  int2* d_trsm = nullptr;        // (k, block row)
+};
+
 struct DeviceBuf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -159,7 +178,20 @@ struct Ctx {
   int64_t* d_uoff = nullptr;             // u-vector offsets of the subdomains (device copy)
   SolveDesc* d_desc_rv = nullptr;        // r-vector sweep ranges: [0, nsub) full, [nsub, 2 nsub) r_I rows
   int min_b0_I = 0;                      // first panel of the r_I range over all subdomains
-  // nonzero 64 x 64 tiles of K_rr per block row (built once from the assembled K_rr)
+  // tile-level symbolic analysis (symbolic.cu), built once from an assembled K_rr
+  std::vector<int64_t> tile_off;         // per subdomain: first of its nblk^2 tile flags
+  std::vector<int> blk_base;             // per subdomain: first of its block rows over all subdomains
+  std::vector<unsigned char> kflags;     // nonzero tiles of K_rr
+  std::vector<unsigned char> lflags;     // nonzero lower tiles of the factor
+  FactorPlan fplan[2];                   // [0] FP64, [1] FP32 work lists
+  bool symb_ready = false;
+  double lfill = 1.0;                    // fraction of the lower tiles that are nonzero
+  int64_t* d_lrow_ptr = nullptr;         // per block row: its nonzero tiles left of the diagonal (ascending)
+  int32_t* d_lrow_col = nullptr;
+  int64_t* d_lcol_ptr = nullptr;         // per block column: its nonzero tiles below the diagonal (descending)
+  int32_t* d_lcol_row = nullptr;
+  unsigned char* d_lflags = nullptr;
+  int64_t* d_tile_off = nullptr;
   bool ktile_ready = false;
   int64_t* d_ktile_row = nullptr;        // per block row (over all subdomains) + 1: start in d_ktile_col
   int32_t* d_ktile_col = nullptr;        // block columns J with a nonzero tile
@@ -290,6 +322,9 @@ constexpr int RV_FULL = 0;
 constexpr int RV_IRANGE = 1;
 template <typename T>
 ieti_status rv_solve(Ctx* c, int range, int which, T* B, T* Y, T* X, cudaStream_t s);
+// tile patterns of K_rr and of the factor, factorisation work lists (symbolic.cu)
+ieti_status build_ktiles(Ctx* c, cudaStream_t s);
+ieti_status build_symbolic(Ctx* c, cudaStream_t s);
 // the same sweeps for one column as dependency-driven block tasks (sweep_dep.cu);
 // IETI_ERR_STATE if the device cannot run them
 ieti_status dep_sweep_attrs(Ctx* c);

@@ -13,6 +13,47 @@
 
 namespace ieti {
 
+namespace {
+
+// Ordering of the interior (r_V) DOFs of a subdomain for the dense blocked
+// factorisation: lexicographic in the control-grid index of the edge, the
+// axis with the longest extent outermost and the shortest innermost, the
+// direction last. Basis functions couple only within p + 1 control indices
+// in every axis, so K_rr^(k) is banded with a bandwidth of a few cross
+// sections of the shortest two axes, and its Cholesky factor fills only the
+// band (about 40 % of the 64 x 64 tiles on a 2 x 2 x 1-patch subdomain, where
+// edge-id order fills them all). The r_I DOFs stay after all r_V DOFs.
+void order_interior(const Mesh& m, std::vector<int64_t>& V) {
+  if (V.size() < 2) return;
+  struct Key {
+    int c[3];
+    int d;
+    int64_t e;
+  };
+  std::vector<Key> key(V.size());
+  int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-1, -1, -1};
+  for (size_t q = 0; q < V.size(); ++q) {
+    Key& K = key[q];
+    m.edge_decode(V[q], K.d, K.c[0], K.c[1], K.c[2]);
+    K.e = V[q];
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], K.c[a]);
+      hi[a] = std::max(hi[a], K.c[a]);
+    }
+  }
+  int ax[3] = {0, 1, 2};
+  std::stable_sort(ax, ax + 3, [&](int a, int b) { return hi[a] - lo[a] > hi[b] - lo[b]; });
+  std::sort(key.begin(), key.end(), [&](const Key& x, const Key& y) {
+    for (int a = 0; a < 3; ++a)
+      if (x.c[ax[a]] != y.c[ax[a]]) return x.c[ax[a]] < y.c[ax[a]];
+    if (x.d != y.d) return x.d < y.d;
+    return x.e < y.e;
+  });
+  for (size_t q = 0; q < V.size(); ++q) V[q] = key[q].e;
+}
+
+}  // namespace
+
 // ---------------------------------------------------------------------------
 // mesh
 // ---------------------------------------------------------------------------
@@ -583,6 +624,7 @@ std::string build_topology(const Mesh& m, const std::vector<int>& sub_of_patch,
       else if (dual_index[e] >= 0) s.I.push_back(e);
       else s.V.push_back(e);
     }
+    order_interior(m, s.V);
     s.nV = (int)s.V.size();
     s.nI = (int)s.I.size();
     s.nP = (int)s.Pr.size();

@@ -518,26 +518,6 @@ __global__ void __launch_bounds__(256) k_residual2(const SubDev* sd, const int64
   }
 }
 
-// nonzero 64 x 64 tiles of K_rr: flags[fo_k + I + nblk J] = 1 when an entry of
-// rows 64 I.., columns 64 J.. is nonzero (one warp per tile)
-__global__ void k_tile_flags(const SubDev* sd, const int64_t* fo, const double* K64, unsigned char* flags) {
-  const int k = blockIdx.y;
-  const SubDev s = sd[k];
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int64_t nt = (int64_t)s.nblk * s.nblk;
-  for (int64_t t = (int64_t)blockIdx.x * 8 + warp; t < nt; t += (int64_t)gridDim.x * 8) {
-    const int I = (int)(t % s.nblk), J = (int)(t / s.nblk);
-    const double* base = K64 + s.A + (int64_t)I * NB + (int64_t)s.n * J * NB;
-    bool nz = false;
-    for (int c = 0; c < NB; ++c) {
-      const double2 v = reinterpret_cast<const double2*>(base + (int64_t)s.n * c)[lane];
-      nz |= (v.x != 0.0) || (v.y != 0.0);
-    }
-    nz = __any_sync(0xffffffffu, nz);
-    if (lane == 0) flags[fo[k] + t] = nz ? 1 : 0;
-  }
-}
-
 // k_residual2 over the nonzero tiles of K_rr only: row r of block row I reads
 // the tiles listed for I (K_rr is symmetric, so row r is column r)
 __global__ void __launch_bounds__(256) k_residual3(const SubDev* sd, const int64_t* r_edge, const double* K64,
@@ -954,54 +934,6 @@ static ieti_status recover(Ctx* c, const double* lam, const double* ycr, double*
                            cudaStream_t st) {
   return c->prec == IETI_FP64 ? recover_t<double>(c, lam, ycr, a, accumulate, st)
                               : recover_t<float>(c, lam, ycr, a, accumulate, st);
-}
-
-// lists of the nonzero tiles of every block row of K_rr (the pattern does
-// not depend on the reluctivities, so it is found once from the assembled K_rr)
-static ieti_status build_ktiles(Ctx* c, cudaStream_t st) {
-  std::vector<int64_t> fo(c->nsub);
-  std::vector<int> tb(c->nsub + 1);
-  int64_t nf = 0;
-  int nb = 0;
-  for (int k = 0; k < c->nsub; ++k) {
-    fo[k] = nf;
-    tb[k] = nb;
-    nf += (int64_t)c->sd_host[k].nblk * c->sd_host[k].nblk;
-    nb += c->sd_host[k].nblk;
-  }
-  tb[c->nsub] = nb;
-  int64_t* d_fo = nullptr;
-  unsigned char* d_flags = nullptr;
-  IETI_CUDA_TRY(c, cudaMalloc(&d_fo, sizeof(int64_t) * c->nsub));
-  IETI_CUDA_TRY(c, cudaMalloc(&d_flags, std::max<int64_t>(nf, 1)));
-  IETI_CUDA_TRY(c, cudaMemcpyAsync(d_fo, fo.data(), sizeof(int64_t) * c->nsub, cudaMemcpyHostToDevice, st));
-  k_tile_flags<<<dim3(256, c->nsub), 256, 0, st>>>(c->d_sd, d_fo, c->K64, d_flags);
-  IETI_LAUNCH_CHECK(c);
-  std::vector<unsigned char> flags(nf);
-  IETI_CUDA_TRY(c, cudaMemcpyAsync(flags.data(), d_flags, nf, cudaMemcpyDeviceToHost, st));
-  IETI_CUDA_TRY(c, cudaStreamSynchronize(st));
-  cudaFree(d_fo);
-  cudaFree(d_flags);
-  // block row I lists the J with tile (J, I) nonzero: row r of block I reads
-  // column r, i.e. entries of rows 64 J.. of column block I
-  std::vector<int64_t> trow(nb + 1, 0);
-  std::vector<int32_t> tcol;
-  for (int k = 0; k < c->nsub; ++k) {
-    const int m = c->sd_host[k].nblk;
-    for (int I = 0; I < m; ++I) {
-      trow[tb[k] + I] = (int64_t)tcol.size();
-      for (int J = 0; J < m; ++J)
-        if (flags[fo[k] + J + (int64_t)m * I]) tcol.push_back(J);
-    }
-  }
-  trow[nb] = (int64_t)tcol.size();
-  if (tcol.empty()) tcol.push_back(0);
-  ieti_status r;
-  if ((r = dev_upload(c, &c->d_ktile_row, trow)) != IETI_OK) return r;
-  if ((r = dev_upload(c, &c->d_ktile_col, tcol)) != IETI_OK) return r;
-  if ((r = dev_upload(c, &c->d_ktile_base, tb)) != IETI_OK) return r;
-  c->ktile_ready = true;
-  return IETI_OK;
 }
 
 // relative FP64 residual ||j - K a|| / ||j|| (max over columns); local residuals to wres_r/wres_p

@@ -5,13 +5,16 @@
 // backward, block column b:
 //   x_b = Linv_b^T (y_b - sum_{j > b} L_jb^T x_j)
 // (the local solves K_rr^(k) x = f of Eqs. (8), (9) and of the right-hand
-// side of Eq. (7)). A task is one 64-wide block of one subdomain. The tasks
+// side of Eq. (7)), over the nonzero tiles of the factor only (symbolic.cu).
+// A task is one 64-wide block of one subdomain. The tasks
 // are ordered by b (ascending forward, descending backward) and dealt
 // round-robin to the CTAs; a CTA runs its tasks in that order. A task reads
 // the finished blocks as they are published and publishes its own block by
 // raising the subdomain's progress counter with a release store after writing
-// it; readers poll the counter with acquire loads (bounded, with an error flag
-// on time-out) and read the blocks through L2. Every wait is on a task that
+// it, once its predecessor in the order has been published (so the counter
+// says that every block up to it is final); readers poll the counter with
+// acquire loads (bounded, with an error flag on time-out) and read the blocks
+// through L2. Every wait is on a task that
 // comes earlier in the order and all CTAs are resident (cooperative launch),
 // so every wait ends. Progress counters carry an epoch in their upper bits, so
 // they are never reset.
@@ -59,10 +62,15 @@ __device__ unsigned long long dep_wait(const unsigned long long* p, unsigned lon
   return v;
 }
 
-// all threads: the block's stores are done; one thread publishes
-__device__ __forceinline__ void dep_publish(unsigned long long* p, unsigned long long v) {
+// all threads: the block's stores are done; one thread waits until the
+// counter reaches prev (the blocks before this one in the order are
+// published: with zero tiles a task may finish before its predecessor, and
+// the counter must mean that every block up to it is final), then publishes
+__device__ __forceinline__ void dep_publish(unsigned long long* p, unsigned long long prev, unsigned long long v,
+                                            int* err) {
   __syncthreads();
   if (threadIdx.x == 0) {
+    dep_wait(p, prev, err);
     __threadfence();
     st_release_u64(p, v);
   }
@@ -90,7 +98,8 @@ __device__ __forceinline__ void load16_cg(const T* src, T (&v)[16]) {
 template <typename T>
 __global__ void __launch_bounds__(DEP_THREADS, 2)
     k_dep_fwd(const SubDev* sd, const SolveDesc* dsc, const int2* tasks, int ntask, const T* L, const T* Linv,
-              const T* B, T* Y, unsigned long long* prog, unsigned long long base, int* err) {
+              const T* B, T* Y, unsigned long long* prog, unsigned long long base, int* err,
+              const int64_t* lptr, const int32_t* lidx, const int* bbase) {
   extern __shared__ __align__(16) unsigned char dsm[];
   T* Lis = reinterpret_cast<T*>(dsm);    // Linv_b, column-major 64 x 64
   T* part = Lis + NB * NB;               // [4][64]
@@ -113,31 +122,36 @@ __global__ void __launch_bounds__(DEP_THREADS, 2)
     }
     T acc = 0;
     unsigned long long seen = 0;
-    int j = d.b0;
-    for (; j + 1 < b; j += 2) {
+    // the nonzero tiles L_bj of block row b (ascending j), from the range start
+    int64_t e = lptr[bbase[k] + b];
+    const int64_t e1 = lptr[bbase[k] + b + 1];
+    while (e < e1 && lidx[e] < d.b0) ++e;
+    for (; e + 1 < e1; e += 2) {
+      const int ja = lidx[e], jb = lidx[e + 1];
       T l0[16], l1[16], y0[16], y1[16];
-      const T* La = Lr + n * ((int64_t)j * NB);
-      const T* Lb2 = La + n * NB;
+      const T* La = Lr + n * ((int64_t)ja * NB);
+      const T* Lb2 = Lr + n * ((int64_t)jb * NB);
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
         l0[c] = La[n * c];
         l1[c] = Lb2[n * c];
       }
-      if (seen < base + j + 2) seen = dep_wait(prog + k, base + j + 2, err);
-      load16_cg(Yk + (int64_t)j * NB + cs * 16, y0);
-      load16_cg(Yk + (int64_t)(j + 1) * NB + cs * 16, y1);
+      if (seen < base + jb + 1) seen = dep_wait(prog + k, base + jb + 1, err);
+      load16_cg(Yk + (int64_t)ja * NB + cs * 16, y0);
+      load16_cg(Yk + (int64_t)jb * NB + cs * 16, y1);
 #pragma unroll
       for (int c = 0; c < 16; ++c) acc += l0[c] * y0[c];
 #pragma unroll
       for (int c = 0; c < 16; ++c) acc += l1[c] * y1[c];
     }
-    if (j < b) {
+    if (e < e1) {
+      const int ja = lidx[e];
       T l0[16], y0[16];
-      const T* La = Lr + n * ((int64_t)j * NB);
+      const T* La = Lr + n * ((int64_t)ja * NB);
 #pragma unroll
       for (int c = 0; c < 16; ++c) l0[c] = La[n * c];
-      if (seen < base + j + 1) seen = dep_wait(prog + k, base + j + 1, err);
-      load16_cg(Yk + (int64_t)j * NB + cs * 16, y0);
+      if (seen < base + ja + 1) seen = dep_wait(prog + k, base + ja + 1, err);
+      load16_cg(Yk + (int64_t)ja * NB + cs * 16, y0);
 #pragma unroll
       for (int c = 0; c < 16; ++c) acc += l0[c] * y0[c];
     }
@@ -154,7 +168,7 @@ __global__ void __launch_bounds__(DEP_THREADS, 2)
     part[cs * NB + i] = v;
     __syncthreads();
     if (tid < NB) Yk[(int64_t)b * NB + tid] = part[tid] + part[NB + tid] + part[2 * NB + tid] + part[3 * NB + tid];
-    dep_publish(prog + k, base + (unsigned long long)(b + 1));
+    dep_publish(prog + k, b > d.b0 ? base + (unsigned long long)b : 0ull, base + (unsigned long long)(b + 1), err);
   }
 }
 
@@ -164,7 +178,8 @@ __global__ void __launch_bounds__(DEP_THREADS, 2)
 template <typename T>
 __global__ void __launch_bounds__(DEP_THREADS, 2)
     k_dep_bwd(const SubDev* sd, const SolveDesc* dsc, const int2* tasks, int ntask, const T* L, const T* Linv,
-              const T* Y, T* X, unsigned long long* prog, unsigned long long base, int* err) {
+              const T* Y, T* X, unsigned long long* prog, unsigned long long base, int* err,
+              const int64_t* lptr, const int32_t* lidx, const int* bbase) {
   extern __shared__ __align__(16) unsigned char dsm[];
   T* Lis = reinterpret_cast<T*>(dsm);          // Lis[l * 65 + i] = Linv_b[l][i]
   T* red = Lis + NB * (NB + 1);                // red[i * 65 + c]: partial column sums of row i
@@ -190,31 +205,35 @@ __global__ void __launch_bounds__(DEP_THREADS, 2)
 #pragma unroll
     for (int c = 0; c < 16; ++c) acc[c] = 0;
     unsigned long long seen = 0;
-    int j = nb - 1;
-    for (; j - 1 > b; j -= 2) {
+    // the nonzero tiles L_jb of block column b (descending j > b)
+    int64_t e = lptr[bbase[k] + b];
+    const int64_t e1 = lptr[bbase[k] + b + 1];
+    for (; e + 1 < e1; e += 2) {
+      const int ja = lidx[e], jb = lidx[e + 1];   // ja > jb
       T l0[16], l1[16];
-      const T* La = Lc + (int64_t)j * NB;
-      const T* Lb2 = La - NB;
+      const T* La = Lc + (int64_t)ja * NB;
+      const T* Lb2 = Lc + (int64_t)jb * NB;
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
         l0[c] = La[n * c];
         l1[c] = Lb2[n * c];
       }
-      const unsigned long long need = base + (unsigned long long)(nb - j + 1);
+      const unsigned long long need = base + (unsigned long long)(nb - jb);
       if (seen < need) seen = dep_wait(prog + k, need, err);
-      const T x0 = __ldcg(Xk + (int64_t)j * NB + i);
-      const T x1 = __ldcg(Xk + (int64_t)(j - 1) * NB + i);
+      const T x0 = __ldcg(Xk + (int64_t)ja * NB + i);
+      const T x1 = __ldcg(Xk + (int64_t)jb * NB + i);
 #pragma unroll
       for (int c = 0; c < 16; ++c) acc[c] += l0[c] * x0 + l1[c] * x1;
     }
-    if (j > b) {
+    if (e < e1) {
+      const int ja = lidx[e];
       T l0[16];
-      const T* La = Lc + (int64_t)j * NB;
+      const T* La = Lc + (int64_t)ja * NB;
 #pragma unroll
       for (int c = 0; c < 16; ++c) l0[c] = La[n * c];
-      const unsigned long long need = base + (unsigned long long)(nb - j);
+      const unsigned long long need = base + (unsigned long long)(nb - ja);
       if (seen < need) seen = dep_wait(prog + k, need, err);
-      const T x0 = __ldcg(Xk + (int64_t)j * NB + i);
+      const T x0 = __ldcg(Xk + (int64_t)ja * NB + i);
 #pragma unroll
       for (int c = 0; c < 16; ++c) acc[c] += l0[c] * x0;
     }
@@ -243,7 +262,8 @@ __global__ void __launch_bounds__(DEP_THREADS, 2)
     part[cs * NB + i] = v;
     __syncthreads();
     if (tid < NB) Xk[(int64_t)b * NB + tid] = part[tid] + part[NB + tid] + part[2 * NB + tid] + part[3 * NB + tid];
-    dep_publish(prog + k, base + (unsigned long long)(nb - b));
+    dep_publish(prog + k, b < nb - 1 ? base + (unsigned long long)(nb - b - 1) : 0ull,
+                base + (unsigned long long)(nb - b), err);
   }
 }
 
@@ -257,6 +277,7 @@ ieti_status launch_dep(Ctx* c, bool fwd, int range, const T* B, const T* Yin, T*
   const int which = fwd ? 0 : 1;
   const int ntask = c->dep_ntask[range][which];
   if (ntask == 0) return IETI_OK;
+  if (!c->symb_ready) return IETI_ERR_STATE;   // tile lists of the factor
   int dev = 0, coop = 0;
   IETI_CUDA_TRY(c, cudaGetDevice(&dev));
   IETI_CUDA_TRY(c, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
@@ -275,8 +296,12 @@ ieti_status launch_dep(Ctx* c, bool fwd, int range, const T* B, const T* Yin, T*
   const SubDev* sd = c->d_sd;
   unsigned long long* prog = c->d_dep_prog;
   int* err = c->d_dep_err;
+  const int64_t* lptr = fwd ? c->d_lrow_ptr : c->d_lcol_ptr;
+  const int32_t* lidx = fwd ? c->d_lrow_col : c->d_lcol_row;
+  const int* bbase = c->d_ktile_base;
   void* args[] = {(void*)&sd, (void*)&dd, (void*)&tasks, (void*)&ntask, (void*)&L, (void*)&Linv,
-                  (void*)(fwd ? &B : &Yin), (void*)&Yout, (void*)&prog, (void*)&base, (void*)&err};
+                  (void*)(fwd ? &B : &Yin), (void*)&Yout, (void*)&prog, (void*)&base, (void*)&err,
+                  (void*)&lptr, (void*)&lidx, (void*)&bbase};
   cudaEvent_t p0 = prof_begin(c, st);
   IETI_CUDA_TRY(c, cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(DEP_THREADS), args, smem, st));
   prof_end(c, fwd ? PROF_FWD : PROF_BWD, p0, st);
