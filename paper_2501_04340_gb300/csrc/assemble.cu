@@ -37,6 +37,8 @@ struct AsmParams {
   const double* nu;
   const double* src;
   const double* gq;
+  double* geo;        // per element and Gauss point: X (3), weight * adj(DF) (9); null: not kept
+  int geo_ready;      // 1: geo holds the values (the geometry of the mesh is fixed)
   const double* gram[3];
   int64_t gram_per[3];
   int gram_nfun[3];
@@ -133,7 +135,7 @@ struct ElemShared {
 };
 
 template <int PD>
-__device__ void elem_setup(const AsmParams& P, int e, ElemShared<PD>& sh, int& q, int& k) {
+__device__ void elem_setup(const AsmParams& P, int e, ElemShared<PD>& sh, int& q, int& k, bool geom = true) {
   constexpr int NQ = PD + 1, NQ3 = NQ * NQ * NQ, NF = ElemShared<PD>::NF;
   const int tid = threadIdx.x;
   q = P.elem[4 * e];
@@ -174,6 +176,7 @@ __device__ void elem_setup(const AsmParams& P, int e, ElemShared<PD>& sh, int& q
     sh.code[f] = P.patch_code[P.patch_code_off[q] + li];
   }
   __syncthreads();
+  if (!geom) return;
   // geometry at the Gauss points
   for (int t = tid; t < NQ3; t += blockDim.x) {
     int x = t % NQ, y = (t / NQ) % NQ, z = t / (NQ * NQ);
@@ -317,22 +320,37 @@ __global__ void __launch_bounds__(256) k_elem_j(AsmParams P) {
   double* G = reinterpret_cast<double*>(smem_raw + sizeof(ElemShared<PD>));   // NQ3 x nrhs x 3
   const int e = blockIdx.x;
   int q, k;
-  elem_setup<PD>(P, e, sh, q, k);
+  // the geometry at the Gauss points does not change between assemblies: it
+  // is computed once and kept (X and the weighted adjugate of DF)
+  const bool cached = P.geo && P.geo_ready;
+  elem_setup<PD>(P, e, sh, q, k, !cached);
   const SubDev s = P.sd[k];
   const int tid = threadIdx.x;
   for (int t = tid; t < NQ3; t += blockDim.x) {
-    const double* F = sh.DF[t];
-    // inverse of DF times det (adjugate)
-    double A[9];
-    A[0] = F[4] * F[8] - F[5] * F[7]; A[1] = F[2] * F[7] - F[1] * F[8]; A[2] = F[1] * F[5] - F[2] * F[4];
-    A[3] = F[5] * F[6] - F[3] * F[8]; A[4] = F[0] * F[8] - F[2] * F[6]; A[5] = F[2] * F[3] - F[0] * F[5];
-    A[6] = F[3] * F[7] - F[4] * F[6]; A[7] = F[1] * F[6] - F[0] * F[7]; A[8] = F[0] * F[4] - F[1] * F[3];
+    double* gk = P.geo ? P.geo + ((int64_t)e * NQ3 + t) * 12 : nullptr;
+    double X[3], A[9];
+    if (cached) {
+      for (int r = 0; r < 3; ++r) X[r] = gk[r];
+      for (int r = 0; r < 9; ++r) A[r] = gk[3 + r];
+    } else {
+      const double* F = sh.DF[t];
+      // inverse of DF times det (adjugate), times the quadrature weight
+      A[0] = F[4] * F[8] - F[5] * F[7]; A[1] = F[2] * F[7] - F[1] * F[8]; A[2] = F[1] * F[5] - F[2] * F[4];
+      A[3] = F[5] * F[6] - F[3] * F[8]; A[4] = F[0] * F[8] - F[2] * F[6]; A[5] = F[2] * F[3] - F[0] * F[5];
+      A[6] = F[3] * F[7] - F[4] * F[6]; A[7] = F[1] * F[6] - F[0] * F[7]; A[8] = F[0] * F[4] - F[1] * F[3];
+      const double w = sh.wt[t];
+      for (int r = 0; r < 9; ++r) A[r] *= w;
+      for (int r = 0; r < 3; ++r) X[r] = sh.X[t][r];
+      if (gk) {
+        for (int r = 0; r < 3; ++r) gk[r] = X[r];
+        for (int r = 0; r < 9; ++r) gk[3 + r] = A[r];
+      }
+    }
     double J[MAX_RHS][3];
-    source_eval(P, q, sh.X[t], J);
-    double w = sh.wt[t];
+    source_eval(P, q, X, J);
     for (int r = 0; r < P.nrhs; ++r)
       for (int a = 0; a < 3; ++a)
-        G[(t * P.nrhs + r) * 3 + a] = w * (A[a * 3 + 0] * J[r][0] + A[a * 3 + 1] * J[r][1] + A[a * 3 + 2] * J[r][2]);
+        G[(t * P.nrhs + r) * 3 + a] = A[a * 3 + 0] * J[r][0] + A[a * 3 + 1] * J[r][1] + A[a * 3 + 2] * J[r][2];
   }
   __syncthreads();
   for (int t = tid; t < NF * P.nrhs; t += blockDim.x) {
@@ -383,14 +401,27 @@ template <typename T>
 __device__ __forceinline__ void kron_entry(const AsmParams& P, T* Lout, int k, const SubDev& s, int i, int j);
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_kron(AsmParams P, T* Lout) {
-  // grid: (row chunks of 256, column groups, subdomain); columns j = blockIdx.y + gridDim.y t
+__global__ void __launch_bounds__(256) k_kron(AsmParams P, T* Lout, int prim_only) {
+  // grid: (row chunks of 256, column groups, subdomain); columns j = blockIdx.y + gridDim.y t,
+  // from the first primal column if prim_only (the K_rp and K_pp blocks)
   const int k = blockIdx.z;
   const SubDev s = P.sd[k];
   const int R = s.n + s.nP;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= R) return;
-  for (int j = blockIdx.y; j < R; j += gridDim.y) kron_entry<T>(P, Lout, k, s, i, j);
+  for (int j = (prim_only ? s.n : 0) + blockIdx.y; j < R; j += gridDim.y) kron_entry<T>(P, Lout, k, s, i, j);
+}
+
+// K_rr entries of the listed nonzero 64 x 64 tiles (k, I, J) only; the other
+// tiles of K_rr are structurally zero and keep the zeros of the first assembly.
+// Thread t: row 64 I + t % 64, columns 64 J + 16 (t / 64) ..
+__global__ void __launch_bounds__(256) k_kron_tiles(AsmParams P, const int4* tiles) {
+  const int4 tl = tiles[blockIdx.x];
+  const int k = tl.x;
+  const SubDev s = P.sd[k];
+  const int i = tl.y * NB + (int)threadIdx.x % NB;
+  const int j0 = tl.z * NB + 16 * ((int)threadIdx.x / NB);
+  for (int j = j0; j < j0 + 16; ++j) kron_entry<double>(P, (double*)nullptr, k, s, i, j);
 }
 
 template <typename T>
@@ -518,6 +549,8 @@ static AsmParams make_params(Ctx* c) {
   P.nu = c->d_nu;
   P.src = c->d_src;
   P.gq = c->d_gq;
+  P.geo = c->d_geo;
+  P.geo_ready = c->geo_ready ? 1 : 0;
   P.K64 = c->K64;
   P.Kp = c->Kp64;
   P.Kpp = c->Kpp64;
@@ -562,9 +595,19 @@ ieti_status assemble_all(Ctx* c, cudaStream_t st) {
   const bool kron = c->affine;
   if (kron) {
     const int64_t R = c->max_n + c->max_nP;
-    dim3 grid((unsigned)ceil_div(R, 256), (unsigned)std::min<int64_t>(R, 65535), (unsigned)c->nsub);
     cudaEvent_t p0 = prof_begin(c, st);
-    k_kron<double><<<grid, 256, 0, st>>>(P, (double*)nullptr);
+    if (c->ktile_ready && c->n_ktiles > 0) {
+      // the nonzero tiles of K_rr (pattern of an earlier assembly), then K_rp and K_pp
+      k_kron_tiles<<<(unsigned)c->n_ktiles, 256, 0, st>>>(P, c->d_ktile_list);
+      IETI_LAUNCH_CHECK(c);
+      if (c->max_nP > 0) {
+        dim3 grid((unsigned)ceil_div(R, 256), (unsigned)c->max_nP, (unsigned)c->nsub);
+        k_kron<double><<<grid, 256, 0, st>>>(P, (double*)nullptr, 1);
+      }
+    } else {
+      dim3 grid((unsigned)ceil_div(R, 256), (unsigned)std::min<int64_t>(R, 65535), (unsigned)c->nsub);
+      k_kron<double><<<grid, 256, 0, st>>>(P, (double*)nullptr, 0);
+    }
     prof_end(c, PROF_ASM_K, p0, st);
     IETI_LAUNCH_CHECK(c);
   } else {
@@ -575,14 +618,51 @@ ieti_status assemble_all(Ctx* c, cudaStream_t st) {
     IETI_LAUNCH_CHECK(c);
   }
   ieti_status r;
+  if (!c->d_geo && !c->geo_failed) {
+    // geometry kept per element and Gauss point (12 doubles each)
+    const int nq3 = (c->mesh.p + 1) * (c->mesh.p + 1) * (c->mesh.p + 1);
+    const size_t bytes = sizeof(double) * 12 * (size_t)nq3 * (size_t)std::max<int64_t>(c->nelem, 1);
+    void* g = nullptr;
+    if (cudaMalloc(&g, bytes) == cudaSuccess) {
+      c->allocs.push_back({g, bytes});
+      c->d_geo = (double*)g;
+      P.geo = c->d_geo;
+    } else {
+      cudaGetLastError();   // not kept: every assembly recomputes the geometry
+      c->geo_failed = true;
+    }
+  }
   switch (c->mesh.p) {
     case 1: r = launch_elem<1>(c, P, !kron, st); break;
     case 2: r = launch_elem<2>(c, P, !kron, st); break;
     case 3: r = launch_elem<3>(c, P, !kron, st); break;
     default: c->err = "degree p must be 1, 2 or 3"; return IETI_ERR_INVALID_ARG;
   }
+  if (r == IETI_OK && c->d_geo) c->geo_ready = true;
   return r;
 }
+
+// dst <- src on the listed 64 x 64 tiles (k, I, J) of the K_rr blocks
+template <typename T>
+__global__ void __launch_bounds__(256) k_convert_tiles(const SubDev* sd, const int4* tiles, const double* src,
+                                                       T* dst) {
+  const int4 tl = tiles[blockIdx.x];
+  const SubDev s = sd[tl.x];
+  const int i = tl.y * NB + (int)threadIdx.x % NB;
+  const int64_t base = s.A + i + (int64_t)s.n * (tl.z * NB + 16 * ((int)threadIdx.x / NB));
+#pragma unroll 4
+  for (int c = 0; c < 16; ++c) dst[base + (int64_t)s.n * c] = (T)src[base + (int64_t)s.n * c];
+}
+
+template <typename T>
+ieti_status convert_tiles(Ctx* c, const int4* tiles, int ntiles, const double* src, T* dst, cudaStream_t st) {
+  if (ntiles <= 0) return IETI_OK;
+  k_convert_tiles<T><<<ntiles, 256, 0, st>>>(c->d_sd, tiles, src, dst);
+  IETI_LAUNCH_CHECK(c);
+  return IETI_OK;
+}
+template ieti_status convert_tiles<float>(Ctx*, const int4*, int, const double*, float*, cudaStream_t);
+template ieti_status convert_tiles<double>(Ctx*, const int4*, int, const double*, double*, cudaStream_t);
 
 // conversion used by the factorisation set-up
 template <typename T>

@@ -18,6 +18,8 @@ namespace ieti {
 
 template <typename T>
 ieti_status convert_copy(Ctx* c, const double* src, T* dst, int64_t n, cudaStream_t st);
+template <typename T>
+ieti_status convert_tiles(Ctx* c, const int4* tiles, int ntiles, const double* src, T* dst, cudaStream_t st);
 
 
 // ---------------------------------------------------------------------------
@@ -40,6 +42,9 @@ __global__ void __launch_bounds__(256) k_potrf_diag(const SubDev* sd, T* L, T* L
   __shared__ int bad;
   if (tid == 0) bad = 0;
   __syncthreads();
+  // thread (row i, column group g) updates a[i][16 g .. 16 g + 15]: the lanes of
+  // a warp share g, so a[l][c] is a broadcast and a[i][l] is conflict-free
+  const int ri = tid % NB, g = tid / NB;
   for (int c = 0; c < NB; ++c) {
     // every thread forms the pivot itself; the threads below it scale column c
     // (a[c][c] itself is written after the barrier, once nobody reads it)
@@ -51,10 +56,14 @@ __global__ void __launch_bounds__(256) k_potrf_diag(const SubDev* sd, T* L, T* L
       if (!(v0 > (T)0)) bad = 1;
       a[c][c] = piv;
     }
-    const int m = NB - 1 - c;
-    for (int t = tid; t < m * m; t += blockDim.x) {
-      int i = c + 1 + t / m, l = c + 1 + t % m;
-      if (l <= i) a[i][l] -= a[i][c] * a[l][c];
+    if (ri > c && 16 * g <= ri && 16 * g + 15 > c) {
+      const T aic = a[ri][c];
+      // unrolled with predicates: the 16 updates are independent
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int l = 16 * g + u;
+        if (l > c && l <= ri) a[ri][l] -= aic * a[l][c];
+      }
     }
     __syncthreads();
   }
@@ -62,21 +71,28 @@ __global__ void __launch_bounds__(256) k_potrf_diag(const SubDev* sd, T* L, T* L
   // inverse of the lower triangular diagonal block: column j by the four
   // threads 4 j .. 4 j + 3 of one warp, each summing every fourth term
   {
+    __shared__ T rd[NB];   // reciprocals of the pivots
+    if (tid < NB) rd[tid] = (T)1 / a[tid][tid];
     const int j = tid / 4, part = tid % 4;
     for (int i = 0; i < j; ++i)
       if (part == 0) inv[i][j] = (T)0;
-    const T djj = (T)1 / a[j][j];
-    if (part == 0) inv[j][j] = djj;
+    __syncthreads();
+    if (part == 0) inv[j][j] = rd[j];
     __syncwarp();
     // the same trip count in every lane (rows i <= j contribute nothing), so the
-    // shuffles stay warp-uniform
+    // shuffles stay warp-uniform; the 16 terms of a lane are independent loads
     for (int i = 1; i < NB; ++i) {
       T acc = 0;
-      if (i > j)
-        for (int l = j + part; l < i; l += 4) acc += a[i][l] * inv[l][j];
+      if (i > j) {
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          const int l = j + part + 4 * t;
+          if (l < i) acc += a[i][l] * inv[l][j];
+        }
+      }
       acc += __shfl_xor_sync(0xffffffffu, acc, 1);
       acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-      if (part == 0 && i > j) inv[i][j] = -acc / a[i][i];
+      if (part == 0 && i > j) inv[i][j] = -acc * rd[i];
       __syncwarp();
     }
   }
@@ -780,11 +796,19 @@ static ieti_status factor_t(Ctx* c, cudaStream_t st) {
   T* S = (T*)c->S;
   T* W = (T*)c->W;
   ieti_status r;
-  // factor buffer <- K_rr
-  if ((r = convert_copy<T>(c, c->K64, L, c->tot_A, st)) != IETI_OK) return r;
-  IETI_CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
   // work lists over the nonzero tiles, found once from the assembled K_rr
   if (!c->symb_ready && (r = build_symbolic(c, st)) != IETI_OK) return r;
+  // factor buffer <- K_rr: in full the first time in this precision (which
+  // zeroes the tiles outside the factor's pattern for good: no step changes
+  // them), then the pattern's tiles only
+  const int pk = sizeof(T) == 4 ? 1 : 0;
+  if (c->l_init_prec != pk) {
+    if ((r = convert_copy<T>(c, c->K64, L, c->tot_A, st)) != IETI_OK) return r;
+    c->l_init_prec = pk;
+  } else if ((r = convert_tiles<T>(c, c->d_ltile_list, c->n_ltiles, c->K64, L, st)) != IETI_OK) {
+    return r;
+  }
+  IETI_CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
   const FactorPlan* plan = &c->fplan[sizeof(T) == 4 ? 1 : 0];
   if ((r = cholesky<T>(c, c->d_sd, c->sd_host, L, Linv, S, true, st, plan)) != IETI_OK) return r;
   IETI_CUDA_TRY(c, cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));

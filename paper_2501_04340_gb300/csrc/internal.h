@@ -135,6 +135,8 @@ struct Ctx {
   std::vector<double> gq_host;           // per patch: nu * L_c^2 / vol (affine path)
   std::vector<int> elem_host;            // per element: q, s0, s1, s2
   int64_t nelem = 0;
+  double* d_geo = nullptr;               // per element and Gauss point: X, weighted adj(DF) (assembly)
+  bool geo_ready = false, geo_failed = false;
 
   // device memory
   std::vector<DeviceBuf> allocs;
@@ -193,6 +195,11 @@ struct Ctx {
   unsigned char* d_lflags = nullptr;
   int64_t* d_tile_off = nullptr;
   bool ktile_ready = false;
+  int4* d_ktile_list = nullptr;          // nonzero tiles (k, I, J) of K_rr, both triangles
+  int n_ktiles = 0;
+  int4* d_ltile_list = nullptr;          // lower tiles (k, I, J) of the factor's pattern
+  int n_ltiles = 0;
+  int l_init_prec = -1;                  // precision whose full conversion zeroed the other tiles of L
   int64_t* d_ktile_row = nullptr;        // per block row (over all subdomains) + 1: start in d_ktile_col
   int32_t* d_ktile_col = nullptr;        // block columns J with a nonzero tile
   int* d_ktile_base = nullptr;           // per subdomain: its first block row

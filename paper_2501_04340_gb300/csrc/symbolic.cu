@@ -84,10 +84,20 @@ ieti_status build_ktiles(Ctx* c, cudaStream_t st) {
   }
   trow[nb] = (int64_t)tcol.size();
   if (tcol.empty()) tcol.push_back(0);
+  std::vector<int4> kt;
+  for (int k = 0; k < nsub; ++k) {
+    const int m = c->sd_host[k].nblk;
+    for (int J = 0; J < m; ++J)
+      for (int I = 0; I < m; ++I)
+        if (c->kflags[c->tile_off[k] + I + (int64_t)m * J]) kt.push_back(make_int4(k, I, J, 0));
+  }
+  c->n_ktiles = (int)kt.size();
+  if (kt.empty()) kt.push_back(make_int4(0, 0, 0, 0));
   ieti_status r;
   if ((r = dev_upload(c, &c->d_ktile_row, trow)) != IETI_OK) return r;
   if ((r = dev_upload(c, &c->d_ktile_col, tcol)) != IETI_OK) return r;
   if ((r = dev_upload(c, &c->d_ktile_base, c->blk_base)) != IETI_OK) return r;
+  if ((r = dev_upload(c, &c->d_ktile_list, kt)) != IETI_OK) return r;
   c->ktile_ready = true;
   return IETI_OK;
 }
@@ -222,6 +232,16 @@ ieti_status build_symbolic(Ctx* c, cudaStream_t st) {
   if ((r = dev_upload(c, &c->d_lcol_ptr, cp)) != IETI_OK) return r;
   if ((r = dev_upload(c, &c->d_lcol_row, cr)) != IETI_OK) return r;
   if ((r = dev_upload(c, &c->d_lflags, F)) != IETI_OK) return r;
+  std::vector<int4> lt;
+  for (int k = 0; k < nsub; ++k) {
+    const int m = c->sd_host[k].nblk;
+    for (int J = 0; J < m; ++J)
+      for (int I = J; I < m; ++I)
+        if (L(k, I, J)) lt.push_back(make_int4(k, I, J, 0));
+  }
+  c->n_ltiles = (int)lt.size();
+  if (lt.empty()) lt.push_back(make_int4(0, 0, 0, 0));
+  if ((r = dev_upload(c, &c->d_ltile_list, lt)) != IETI_OK) return r;
   if ((r = dev_upload(c, &c->d_tile_off, c->tile_off)) != IETI_OK) return r;
   int64_t nz = 0, tot = 0;
   for (int k = 0; k < nsub; ++k) {
