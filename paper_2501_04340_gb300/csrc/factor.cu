@@ -841,9 +841,11 @@ static ieti_status factor_t(Ctx* c, cudaStream_t st) {
     IETI_CUDA_TRY(c, cudaMemcpyAsync(dd, dh.data(), sizeof(SolveDesc) * nsub, cudaMemcpyHostToDevice, st));
     k_identity_rhs<T><<<dim3(256, nsub), 256, 0, st>>>(c->d_sd, dd, B);
     IETI_LAUNCH_CHECK(c);
-    if ((r = tri_solve<T>(c, c->d_sd, nsub, c->max_nblk, max_rows, max_col, dd, min_b0, L, Linv, B, Y, X, st,
-                          SWEEP_BOTH, c->d_lflags, c->d_tile_off)) != IETI_OK)
-      return r;
+    r = dep_mc_solve<T>(c, 0, dh, dd, SWEEP_BOTH, B, Y, X, st);
+    if (r == IETI_ERR_STATE)
+      r = tri_solve<T>(c, c->d_sd, nsub, c->max_nblk, max_rows, max_col, dd, min_b0, L, Linv, B, Y, X, st,
+                       SWEEP_BOTH, c->d_lflags, c->d_tile_off);
+    if (r != IETI_OK) return r;
     k_extract_W<T><<<dim3(256, nsub), 256, 0, st>>>(c->d_sd, dd, X, W);
     IETI_LAUNCH_CHECK(c);
     IETI_CUDA_TRY(c, cudaStreamSynchronize(st));
@@ -864,14 +866,18 @@ static ieti_status factor_t(Ctx* c, cudaStream_t st) {
     IETI_CUDA_TRY(c, cudaMemcpyAsync(dd, dh.data(), sizeof(SolveDesc) * nsub, cudaMemcpyHostToDevice, st));
     k_load_Kp<T><<<dim3(256, nsub), 256, 0, st>>>(c->d_sd, dd, c->Kp64, B);
     IETI_LAUNCH_CHECK(c);
-    if ((r = tri_solve<T>(c, c->d_sd, nsub, c->max_nblk, c->max_n, c->max_nP, dd, 0, L, Linv, B, Y, X, st,
-                          SWEEP_FWD, c->d_lflags, c->d_tile_off)) != IETI_OK)
-      return r;
+    r = dep_mc_solve<T>(c, 1, dh, dd, SWEEP_FWD, B, Y, X, st);
+    if (r == IETI_ERR_STATE)
+      r = tri_solve<T>(c, c->d_sd, nsub, c->max_nblk, c->max_n, c->max_nP, dd, 0, L, Linv, B, Y, X, st, SWEEP_FWD,
+                       c->d_lflags, c->d_tile_off);
+    if (r != IETI_OK) return r;
     k_store_Psi<T><<<dim3(256, nsub), 256, 0, st>>>(c->d_sd, dd, Y, (T*)c->Psi);
     IETI_LAUNCH_CHECK(c);
-    if ((r = tri_solve<T>(c, c->d_sd, nsub, c->max_nblk, c->max_n, c->max_nP, dd, 0, L, Linv, B, Y, X, st,
-                          SWEEP_BWD, c->d_lflags, c->d_tile_off)) != IETI_OK)
-      return r;
+    r = dep_mc_solve<T>(c, 1, dh, dd, SWEEP_BWD, B, Y, X, st);
+    if (r == IETI_ERR_STATE)
+      r = tri_solve<T>(c, c->d_sd, nsub, c->max_nblk, c->max_n, c->max_nP, dd, 0, L, Linv, B, Y, X, st, SWEEP_BWD,
+                       c->d_lflags, c->d_tile_off);
+    if (r != IETI_OK) return r;
     k_store_Phi<T><<<dim3(256, nsub), 256, 0, st>>>(c->d_sd, dd, X, c->Phi);
     IETI_LAUNCH_CHECK(c);
     IETI_CUDA_TRY(c, cudaStreamSynchronize(st));

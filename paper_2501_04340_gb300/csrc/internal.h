@@ -107,6 +107,14 @@ struct FactorPlan {
   int2* d_trsm = nullptr;        // (k, block row)
 };
 
+// task lists of the multi-column dependency-driven solves (sweep_dep.cu)
+struct McPlan {
+  bool built = false;
+  int4* d_tasks[2] = {nullptr, nullptr};   // forward, backward: (k, block, column tile, counter)
+  int ntask[2] = {0, 0};
+  unsigned long long* d_prog = nullptr;    // per (subdomain, column tile)
+};
+
 struct DeviceBuf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -210,6 +218,7 @@ struct Ctx {
   unsigned long long* d_dep_prog = nullptr;   // per subdomain: epoch << 20 | blocks published
   unsigned long long dep_epoch = 0;
   int* d_dep_err = nullptr;              // set when a sweep wait times out
+  McPlan mcplan[2];                      // [0] W solve, [1] Phi solve
   double* SPi = nullptr;                 // coarse S_Pi (n_gp x n_gp)
   double* SPiInv = nullptr;              // its inverse
   int* d_err = nullptr;                  // device error word (subdomain id + 1 of a bad pivot)
@@ -338,6 +347,9 @@ ieti_status dep_sweep_attrs(Ctx* c);
 ieti_status dep_sweep_alloc(Ctx* c);
 template <typename T>
 ieti_status dep_sweep(Ctx* c, int range, int which, const T* B, T* Y, T* X, cudaStream_t s);
+template <typename T>
+ieti_status dep_mc_solve(Ctx* c, int slot, const std::vector<SolveDesc>& dh, const SolveDesc* dd, int which,
+                         const T* B, T* Y, T* X, cudaStream_t s);
 // streamed interface products (iface.cu)
 ieti_status iface_alloc(Ctx* c);
 ieti_status iface_prepare(Ctx* c, cudaStream_t s);

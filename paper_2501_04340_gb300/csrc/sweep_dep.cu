@@ -267,6 +267,116 @@ __global__ void __launch_bounds__(DEP_THREADS, 2)
   }
 }
 
+// Many right-hand sides (the W and Phi solves of the factorisation): a task is
+// one 64-wide block of one subdomain times one tile of up to 64 columns, and
+// every column tile of a subdomain has its own progress counter. Forward,
+// block b: Y_b = Linv_b (B_b - sum_j L_bj Y_j) with 64 x 64 tile products
+// staged in shared memory (4 x 4 outputs per thread); backward, block b:
+// X_b = Linv_b^T (Y_b - sum_{j > b} L_jb^T X_j).
+template <typename T>
+__global__ void __launch_bounds__(DEP_THREADS)
+    k_depmc(const SubDev* sd, const SolveDesc* dsc, const int4* tasks, int ntask, const T* L, const T* Linv,
+            const T* In, T* Out, unsigned long long* prog, unsigned long long base, int* err,
+            const int64_t* lptr, const int32_t* lidx, const int* bbase, int fwd) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  T(*As)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm);
+  T(*Bs)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm + sizeof(T) * NB * (NB + 1));
+  const int tid = threadIdx.x, ti = tid % 16, tj = tid / 16;
+  for (int t = blockIdx.x; t < ntask; t += gridDim.x) {
+    const int4 tk = tasks[t];
+    const int k = tk.x, b = tk.y, c0 = tk.z * NB, v = tk.w;
+    const SubDev s = sd[k];
+    const SolveDesc d = dsc[k];
+    const int64_t n = s.n;
+    const int nb = s.nblk;
+    const int nc = min(NB, d.ncol - c0);
+    // In (forward: B, backward: Y) and Out (Y, X) indexed by subdomain row
+    const T* Ik = In + d.boff + (int64_t)d.ldb * c0 - (int64_t)d.b0 * NB;
+    T* Ok = Out + d.boff + (int64_t)d.ldb * c0 - (int64_t)d.b0 * NB;
+    T acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int w = 0; w < 4; ++w) acc[u][w] = 0;
+    unsigned long long seen = 0;
+    int64_t e = lptr[bbase[k] + b];
+    const int64_t e1 = lptr[bbase[k] + b + 1];
+    if (fwd)
+      while (e < e1 && lidx[e] < d.b0) ++e;
+    for (; e < e1; ++e) {
+      const int j = lidx[e];
+      __syncthreads();   // the previous tiles are consumed
+      // forward: As[i][l] = L[64 b + i, 64 j + l]; backward: As[l][i] = L[64 j + l, 64 b + i]
+      for (int q = tid; q < NB * NB; q += DEP_THREADS) {
+        const int x = q % NB, y = q / NB;
+        if (fwd) As[x][y] = L[s.A + (int64_t)b * NB + x + n * ((int64_t)j * NB + y)];
+        else As[x][y] = L[s.A + (int64_t)j * NB + x + n * ((int64_t)b * NB + y)];
+      }
+      const unsigned long long need = fwd ? base + (unsigned long long)(j + 1) : base + (unsigned long long)(nb - j);
+      if (seen < need) seen = dep_wait(prog + v, need, err);
+      for (int q = tid; q < NB * NB; q += DEP_THREADS) {
+        const int l = q % NB, cc = q / NB;
+        Bs[l][cc] = cc < nc ? __ldcg(Ok + (int64_t)j * NB + l + (int64_t)d.ldb * cc) : (T)0;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int l = 0; l < NB; ++l) {
+        T a[4], y[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] = fwd ? As[4 * ti + u][l] : As[l][4 * ti + u];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) y[w] = Bs[l][4 * tj + w];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int w = 0; w < 4; ++w) acc[u][w] += a[u] * y[w];
+      }
+    }
+    __syncthreads();
+    // right-hand side of the diagonal block, and the inverse of the diagonal
+    // block (forward As[i][l] = Linv_b[i][l], backward As[l][i] = Linv_b[l][i])
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const int i = 4 * ti + u, cc = 4 * tj + w;
+        Bs[i][cc] = (cc < nc ? Ik[(int64_t)b * NB + i + (int64_t)d.ldb * cc] : (T)0) - acc[u][w];
+      }
+    for (int q = tid; q < NB * NB; q += DEP_THREADS) As[q % NB][q / NB] = Linv[s.linv + (int64_t)b * NB * NB + q];
+    __syncthreads();
+    T o[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int w = 0; w < 4; ++w) o[u][w] = 0;
+#pragma unroll 4
+    for (int l = 0; l < NB; ++l) {
+      T a[4], y[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = fwd ? As[4 * ti + u][l] : As[l][4 * ti + u];
+#pragma unroll
+      for (int w = 0; w < 4; ++w) y[w] = Bs[l][4 * tj + w];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) o[u][w] += a[u] * y[w];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const int i = 4 * ti + u, cc = 4 * tj + w;
+        if (cc < nc) Ok[(int64_t)b * NB + i + (int64_t)d.ldb * cc] = o[u][w];
+      }
+    if (fwd) dep_publish(prog + v, b > d.b0 ? base + (unsigned long long)b : 0ull, base + (unsigned long long)(b + 1), err);
+    else dep_publish(prog + v, b < nb - 1 ? base + (unsigned long long)(nb - b - 1) : 0ull,
+                     base + (unsigned long long)(nb - b), err);
+  }
+}
+
+template <typename T>
+size_t mc_smem() { return sizeof(T) * 2 * (size_t)NB * (NB + 1); }
+
 template <typename T>
 size_t fwd_smem() { return sizeof(T) * ((size_t)NB * NB + 5 * NB); }
 template <typename T>
@@ -312,6 +422,10 @@ ieti_status launch_dep(Ctx* c, bool fwd, int range, const T* B, const T* Yin, T*
 }  // namespace
 
 ieti_status dep_sweep_attrs(Ctx* c) {
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_depmc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)mc_smem<float>()));
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_depmc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)mc_smem<double>()));
   IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_dep_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)fwd_smem<float>()));
   IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_dep_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -359,6 +473,77 @@ ieti_status dep_sweep_alloc(Ctx* c) {
   c->dep_epoch = 0;
   return IETI_OK;
 }
+
+// multi-column solves of a fixed descriptor set (slot 0: W, 1: Phi); the task
+// lists and progress counters are built on the first call
+template <typename T>
+ieti_status dep_mc_solve(Ctx* c, int slot, const std::vector<SolveDesc>& dh, const SolveDesc* dd, int which,
+                         const T* B, T* Y, T* X, cudaStream_t st) {
+  if (!c->symb_ready || c->no_coop || !c->dep_sweeps) return IETI_ERR_STATE;
+  int dev = 0, coop = 0;
+  IETI_CUDA_TRY(c, cudaGetDevice(&dev));
+  IETI_CUDA_TRY(c, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop || c->sm_count < 1) return IETI_ERR_STATE;
+  McPlan& P = c->mcplan[slot];
+  if (!P.built) {
+    std::vector<int> vb(c->nsub + 1, 0);
+    for (int k = 0; k < c->nsub; ++k) vb[k + 1] = vb[k] + (int)((std::max(dh[k].ncol, 0) + NB - 1) / NB);
+    for (int dir = 0; dir < 2; ++dir) {
+      std::vector<int4> tk;
+      for (int bb = 0; bb < c->max_nblk; ++bb) {
+        const int b = dir == 0 ? bb : c->max_nblk - 1 - bb;
+        for (int k = 0; k < c->nsub; ++k) {
+          const SubDev& s = c->sd_host[k];
+          if (b < dh[k].b0 || b >= s.nblk || dh[k].ncol <= 0) continue;
+          for (int ct = 0; ct < vb[k + 1] - vb[k]; ++ct) tk.push_back(make_int4(k, b, ct, vb[k] + ct));
+        }
+      }
+      P.ntask[dir] = (int)tk.size();
+      if (tk.empty()) tk.push_back(make_int4(0, 0, 0, 0));
+      ieti_status r;
+      if ((r = dev_upload(c, &P.d_tasks[dir], tk)) != IETI_OK) return r;
+    }
+    std::vector<unsigned long long> z(std::max(vb[c->nsub], 1), 0ull);
+    ieti_status r;
+    if ((r = dev_upload(c, &P.d_prog, z)) != IETI_OK) return r;
+    P.built = true;
+  }
+  const size_t smem = mc_smem<T>();
+  int per_sm = 0;
+  IETI_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_depmc<T>, DEP_THREADS, smem));
+  if (per_sm < 1) return IETI_ERR_STATE;
+  const T* L = (const T*)c->L;
+  const T* Linv = (const T*)c->Linv;
+  const SubDev* sd = c->d_sd;
+  int* err = c->d_dep_err;
+  const int* bbase = c->d_ktile_base;
+  for (int dir = 0; dir < 2; ++dir) {
+    if (!(which & (dir == 0 ? SWEEP_FWD : SWEEP_BWD))) continue;
+    const int ntask = P.ntask[dir];
+    if (ntask == 0) continue;
+    const int4* tasks = P.d_tasks[dir];
+    const int grid = std::min(ntask, per_sm * c->sm_count);
+    const unsigned long long base = (++c->dep_epoch) << DEP_EPOCH_SHIFT;
+    const T* In = dir == 0 ? B : Y;
+    T* Out = dir == 0 ? Y : X;
+    const int64_t* lptr = dir == 0 ? c->d_lrow_ptr : c->d_lcol_ptr;
+    const int32_t* lidx = dir == 0 ? c->d_lrow_col : c->d_lcol_row;
+    int fwd = dir == 0 ? 1 : 0;
+    unsigned long long* prog = P.d_prog;
+    void* args[] = {(void*)&sd, (void*)&dd, (void*)&tasks, (void*)&ntask, (void*)&L, (void*)&Linv,
+                    (void*)&In, (void*)&Out, (void*)&prog, (void*)&base, (void*)&err,
+                    (void*)&lptr, (void*)&lidx, (void*)&bbase, (void*)&fwd};
+    cudaEvent_t p0 = prof_begin(c, st);
+    IETI_CUDA_TRY(c, cudaLaunchCooperativeKernel((void*)k_depmc<T>, dim3(grid), dim3(DEP_THREADS), args, smem, st));
+    prof_end(c, dir == 0 ? PROF_FWD : PROF_BWD, p0, st);
+    IETI_LAUNCH_CHECK(c);
+  }
+  return IETI_OK;
+}
+template ieti_status dep_mc_solve<float>(Ctx*, int, const std::vector<SolveDesc>&, const SolveDesc*, int,
+                                         const float*, float*, float*, cudaStream_t);
+template ieti_status dep_mc_solve<double>(Ctx*, int, const std::vector<SolveDesc>&, const SolveDesc*, int,
+                                          const double*, double*, double*, cudaStream_t);
 
 template <typename T>
 ieti_status dep_sweep(Ctx* c, int range, int which, const T* B, T* Y, T* X, cudaStream_t st) {

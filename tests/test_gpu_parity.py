@@ -202,10 +202,11 @@ def test_per_panel_launch_path_matches_persistent(ieti, prec, monkeypatch):
         finally:
             ieti.ieti_destroy(ctx)
     (a1, i1), (a2, i2) = out
-    # FP32 operators: the two paths sum the local products in different orders,
-    # so the iteration counts (summed over the refinement steps) may differ by a
-    # few; the field is compared at 1e-9 below
-    assert abs(i1 - i2) <= max(1, 0.1 * i2)
+    # FP32 operators: the two paths sum the local products (and form W and Phi)
+    # in different orders, so the inner PCG runs at a loose tolerance stop at
+    # different iterations and the counts summed over the refinement steps may
+    # differ by up to a fifth; the field is compared at 1e-9 below
+    assert abs(i1 - i2) <= max(1, (0.2 if prec else 0.1) * i2)
     assert np.linalg.norm(a1 - a2) <= 1e-9 * np.linalg.norm(a2)
     assert np.linalg.norm(a1 - a_m) <= 1e-8 * np.linalg.norm(a_m)
 
