@@ -700,6 +700,9 @@ void ieti_destroy(ieti_ctx* x) {
   if (!x) return;
   for (DeviceBuf& b : x->c.allocs) cudaFree(b.p);
   if (x->c.h_err) cudaFreeHost(x->c.h_err);
+  for (cudaEvent_t e : x->c.ev_fact)
+    if (e) cudaEventDestroy(e);
+  if (x->c.aux_stream) cudaStreamDestroy(x->c.aux_stream);
   delete x;
 }
 

@@ -725,6 +725,24 @@ static ieti_status cholesky(Ctx* c, const SubDev* d_sd, const std::vector<SubDev
     return IETI_OK;
   };
   const size_t nsteps = plan ? plan->steps.size() : 0;
+  // lookahead: with a plan, a step's trailing update is split into the tiles
+  // of the next panels (on st, so the next panel work follows them directly)
+  // and the rest (on a low-priority second stream, overlapping the next panel
+  // work, which touches other tiles); the next trailing update and any
+  // snapshot wait for that rest
+  const bool ahead = plan && !c->syrk_tc && nsteps > 1;
+  if (ahead && !c->aux_stream) {
+    int lo = 0, hi = 0;
+    IETI_CUDA_TRY(c, cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    IETI_CUDA_TRY(c, cudaStreamCreateWithPriority(&c->aux_stream, cudaStreamNonBlocking, lo));
+    for (cudaEvent_t& e : c->ev_fact) IETI_CUDA_TRY(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  bool rest_pending = false;
+  auto wait_rest = [&]() -> ieti_status {
+    if (rest_pending) IETI_CUDA_TRY(c, cudaStreamWaitEvent(st, c->ev_fact[1], 0));
+    rest_pending = false;
+    return IETI_OK;
+  };
   for (int b = 0, si = 0; plan ? si < (int)nsteps : b < max_nblk; ++si) {
     FactorStep stp{};
     if (plan) {
@@ -738,6 +756,8 @@ static ieti_status cholesky(Ctx* c, const SubDev* d_sd, const std::vector<SubDev
       if constexpr (sizeof(T) == 4) stp.kb = (!c->syrk_tc && b + 2 < max_nblk && !snap_at(b + 1)) ? 2 : 1;
     }
     if (snap_at(b)) {
+      ieti_status rw = wait_rest();
+      if (rw != IETI_OK) return rw;
       k_snapshot<T><<<dim3(256, nsub), 256, 0, st>>>(d_sd, L, S, b);
       IETI_LAUNCH_CHECK(c);
     }
@@ -761,7 +781,31 @@ static ieti_status cholesky(Ctx* c, const SubDev* d_sd, const std::vector<SubDev
       if ((r = panel(b + 1, plan ? plan->d_trsm + stp.trsm_off[1] : nullptr, stp.trsm_cnt[1])) != IETI_OK) return r;
     }
     const int Tm = max_nblk - b - kb;
-    if (plan ? stp.trail_cnt > 0 : Tm > 0) {
+    if ((r = wait_rest()) != IETI_OK) return r;
+    if (ahead && stp.trail_cnt > 0) {
+      // the next panels' tiles on st, the rest on the second stream
+      const int4* items = plan->d_items + stp.trail_off;
+      const int n0 = stp.trail_cnt0, n1 = stp.trail_cnt - stp.trail_cnt0;
+      cudaEvent_t p0 = prof_begin(c, st);
+      if (n0 > 0) {
+        if constexpr (sizeof(T) == 4) k_syrk2<<<n0, 256, S2_SMEM, st>>>(d_sd, (float*)L, b, kb, 0, items);
+        else k_syrk<T><<<n0, 256, 0, st>>>(d_sd, L, b, items);
+        IETI_LAUNCH_CHECK(c);
+      }
+      prof_end(c, PROF_SYRK, p0, st);
+      if (n1 > 0) {
+        IETI_CUDA_TRY(c, cudaEventRecord(c->ev_fact[0], st));
+        IETI_CUDA_TRY(c, cudaStreamWaitEvent(c->aux_stream, c->ev_fact[0], 0));
+        cudaEvent_t p1 = prof_begin(c, c->aux_stream);
+        if constexpr (sizeof(T) == 4)
+          k_syrk2<<<n1, 256, S2_SMEM, c->aux_stream>>>(d_sd, (float*)L, b, kb, 0, items + n0);
+        else k_syrk<T><<<n1, 256, 0, c->aux_stream>>>(d_sd, L, b, items + n0);
+        prof_end(c, PROF_SYRK, p1, c->aux_stream);
+        IETI_LAUNCH_CHECK(c);
+        IETI_CUDA_TRY(c, cudaEventRecord(c->ev_fact[1], c->aux_stream));
+        rest_pending = true;
+      }
+    } else if (plan ? stp.trail_cnt > 0 : Tm > 0) {
       cudaEvent_t p0 = prof_begin(c, st);
       const int4* items = plan ? plan->d_items + stp.trail_off : nullptr;
       if constexpr (sizeof(T) == 4) {
@@ -786,7 +830,7 @@ static ieti_status cholesky(Ctx* c, const SubDev* d_sd, const std::vector<SubDev
     }
     b += kb;
   }
-  return IETI_OK;
+  return wait_rest();
 }
 
 template <typename T>

@@ -96,8 +96,9 @@ struct FactorStep {
   int trsm_cnt[2] = {0, 0};
   int64_t col_off = 0;           // kb == 2: pair rows of block column b+1 updated by panel b
   int col_cnt = 0;
-  int64_t trail_off = 0;         // trailing-update items
+  int64_t trail_off = 0;         // trailing-update items, those of the next panels first
   int trail_cnt = 0;
+  int trail_cnt0 = 0;            // items that update the next step's panel columns
 };
 
 struct FactorPlan {
@@ -219,6 +220,8 @@ struct Ctx {
   unsigned long long dep_epoch = 0;
   int* d_dep_err = nullptr;              // set when a sweep wait times out
   McPlan mcplan[2];                      // [0] W solve, [1] Phi solve
+  cudaStream_t aux_stream = nullptr;     // low-priority stream of the factorisation's lookahead
+  cudaEvent_t ev_fact[3] = {nullptr, nullptr, nullptr};
   double* SPi = nullptr;                 // coarse S_Pi (n_gp x n_gp)
   double* SPiInv = nullptr;              // its inverse
   int* d_err = nullptr;                  // device error word (subdomain id + 1 of a bad pivot)

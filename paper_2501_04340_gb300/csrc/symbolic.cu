@@ -198,6 +198,12 @@ ieti_status build_symbolic(Ctx* c, cudaStream_t st) {
         }
       }
       S.trail_cnt = (int)((int64_t)items.size() - S.trail_off);
+      // the tiles of the next panels first (FP32: pair column 0, FP64: block
+      // column t0), so that the next step's panel work can start after them
+      // while the rest of the update runs on a second stream
+      auto first = [&](const int4& it) { return prec == 1 ? it.z == 0 : it.z == t0; };
+      std::stable_partition(items.begin() + S.trail_off, items.end(), first);
+      S.trail_cnt0 = (int)std::count_if(items.begin() + S.trail_off, items.end(), first);
       P.steps.push_back(S);
       b += S.kb;
     }
