@@ -2,7 +2,7 @@
 
     python -m paper_2501_04340_gb300.run_workload [--patches 4] [--spans 8]
         [--degree 3] [--block 2 2 1] [--precision fp32|fp64] [--tol 1e-8]
-        [--tol-field 1e-9] [--repeat 1]
+        [--tol-field 1e-8] [--repeat 1]
 
 The default is the 64-patch unit cube with 16 subdomains of 2x2x1 patches and
 per-patch reluctivity log-uniform in [1, 1e3] (seed 2). --spans and --patches
@@ -26,7 +26,7 @@ def main():
     ap.add_argument("--block", type=int, nargs=3, default=[2, 2, 1], help="patches per subdomain")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--tol", type=float, default=1e-8)
-    ap.add_argument("--tol-field", type=float, default=1e-9)
+    ap.add_argument("--tol-field", type=float, default=1e-8)
     ap.add_argument("--repeat", type=int, default=1)
     args = ap.parse_args()
 
