@@ -354,19 +354,19 @@ __global__ void k_gather_e(const SubDev* sd, const int32_t* pair, const T* v, in
 // part_k = j_p - K_rp^T v  (p rows of each subdomain)
 __global__ void k_dprime_part(const SubDev* sd, const double* Kp, const double* jp, const double* v, int nrhs,
                               double* part) {
-  const int k = blockIdx.x;
+  // one CTA per (subdomain, primal column c, load column): part = jp - Kp[:, c] . v
+  __shared__ double red[256];
+  const int k = blockIdx.y;
   const SubDev s = sd[k];
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
-  for (int t = warp; t < s.nP * nrhs; t += nw) {
-    int c = t % s.nP, col = t / s.nP;
-    const double* a = Kp + s.Kp + (int64_t)s.n * c;
-    const double* vv = v + RV(s, 0, col, nrhs);
-    double acc = 0;
-    for (int i = lane; i < s.n; i += 32) acc += a[i] * vv[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) part[PV(s, c, col, nrhs)] = jp[PV(s, c, col, nrhs)] - acc;
-  }
+  const int t = blockIdx.x;
+  if (t >= s.nP * nrhs) return;
+  const int c = t % s.nP, col = t / s.nP;
+  const double* a = Kp + s.Kp + (int64_t)s.n * c;
+  const double* vv = v + RV(s, 0, col, nrhs);
+  double acc = 0;
+  for (int i = threadIdx.x; i < s.n; i += blockDim.x) acc += a[i] * vv[i];
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) part[PV(s, c, col, nrhs)] = jp[PV(s, c, col, nrhs)] - acc;
 }
 
 // B <- -B_k^T lam on the r_I rows (zero on their padding), the right-hand side
@@ -585,12 +585,22 @@ __global__ void __launch_bounds__(256) k_residual3(const SubDev* sd, const int64
   }
 }
 
-__global__ void k_colnorm2(const double* v, int64_t m, double* out) {
+// squared column norms in two fixed-order stages: per-CTA partials over a
+// grid of chunks (blockIdx.x), then one CTA per column sums them
+constexpr int NORM_CTAS = 128;
+__global__ void k_colnorm2_part(const double* v, int64_t m, double* part) {
+  __shared__ double red[256];
+  const int col = blockIdx.y;
+  double acc = 0;
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < m; l += (int64_t)gridDim.x * blockDim.x)
+    acc += v[l + m * col] * v[l + m * col];
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x + NORM_CTAS * col] = s;
+}
+__global__ void k_colnorm2_sum(const double* part, double* out) {
   __shared__ double red[256];
   const int col = blockIdx.x;
-  double acc = 0;
-  for (int64_t l = threadIdx.x; l < m; l += blockDim.x) acc += v[l + m * col] * v[l + m * col];
-  double s = block_sum(acc, red);
+  const double s = block_sum(threadIdx.x < NORM_CTAS ? part[threadIdx.x + NORM_CTAS * col] : 0.0, red);
   if (threadIdx.x == 0) out[col] = s;
 }
 
@@ -749,7 +759,8 @@ static ieti_status interface_rhs_t(Ctx* c, const double* jr, const double* jp, d
   IETI_LAUNCH_CHECK(c);
   const bool coarse = c->n_gp > 0;
   if (coarse) {
-    k_dprime_part<<<c->nsub, 256, 0, st>>>(c->d_sd, c->Phi, jp, jr, nrhs, c->wq_part);
+    k_dprime_part<<<dim3((unsigned)std::max(c->max_nP * nrhs, 1), c->nsub), 256, 0, st>>>(c->d_sd, c->Phi, jp, jr,
+                                                                                        nrhs, c->wq_part);
     IETI_LAUNCH_CHECK(c);
     if ((r = coarse_solve(c, c->wq_part, ycr, nrhs, st)) != IETI_OK) return r;
   }
@@ -952,7 +963,9 @@ static ieti_status residual(Ctx* c, const double* a, double* rel, double* jn2, c
                                  c->d_I_sign, c->wlam_acc, c->m_r, c->wres_r, c->wres_p, c->wglob);
   prof_end(c, PROF_RESID, p0, st);
   IETI_LAUNCH_CHECK(c);
-  k_colnorm2<<<nrhs, 256, 0, st>>>(c->wglob, ne, c->wnorm);
+  k_colnorm2_part<<<dim3(NORM_CTAS, nrhs), 256, 0, st>>>(c->wglob, ne, c->wred);
+  IETI_LAUNCH_CHECK(c);
+  k_colnorm2_sum<<<nrhs, 256, 0, st>>>(c->wred, c->wnorm);
   IETI_LAUNCH_CHECK(c);
   std::vector<double> h(nrhs);
   IETI_CUDA_TRY(c, cudaMemcpyAsync(h.data(), c->wnorm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
