@@ -210,11 +210,16 @@ ieti_status alloc_dev(Ctx* c, T** p, size_t count) {
 
 // tile table of one precision: rows of M_k (and of Phi_I^(k)T if with_phi) cut
 // into whole-row tiles of about TILE_TARGET bytes, subdomain by subdomain; CTA
-// j owns the tiles whose byte offsets start in [j B / grid, (j+1) B / grid)
+// j owns the tiles whose cost offsets start in [j C / grid, (j+1) C / grid),
+// the cost being the bytes plus a fixed charge per subdomain entered
 ieti_status build_plan(Ctx* c, int es, bool with_phi, StreamPlan* P) {
   std::vector<LTile> tiles;
-  std::vector<int64_t> start;
-  int64_t bytes = 0;
+  std::vector<int64_t> start;   // balancing cost before each tile
+  int64_t bytes = 0, cost = 0;
+  // a CTA pays for the u vector of every subdomain its run enters (one bulk
+  // copy waited for before the first product): about 1.5 us, the time of
+  // streaming this many bytes at one SM's share of the bandwidth
+  constexpr int64_t U_COST = 48 * 1024;
   int stage_bytes = 0;
   for (int k = 0; k < c->nsub; ++k) {
     const SubDev& s = c->sd_host[k];
@@ -240,8 +245,10 @@ ieti_status build_plan(Ctx* c, int es, bool with_phi, StreamPlan* P) {
         tl.ostride = kind == 0 ? s.nI : s.nP;
         tl.bytes = (int)(tl.nrows * rb);
         tl.uoff = c->uoff[k];
-        start.push_back(bytes);
+        if (kind == 0 && r0 == 0) cost += U_COST;
+        start.push_back(cost);
         bytes += tl.nrows * rb;
+        cost += tl.nrows * rb;
         tiles.push_back(tl);
       }
     }
@@ -251,7 +258,7 @@ ieti_status build_plan(Ctx* c, int es, bool with_phi, StreamPlan* P) {
   {
     int j = 0;
     for (int g = 0; g < grid; ++g) {
-      const int64_t lo = (int64_t)((double)bytes * g / grid);
+      const int64_t lo = (int64_t)((double)cost * g / grid);
       while (j < (int)tiles.size() && start[j] < lo) ++j;
       cta[g] = j;
     }
