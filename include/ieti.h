@@ -191,7 +191,9 @@ ieti_status ieti_query(const ieti_ctx* ctx, ieti_sizes* out);
  *   1 edge weight 1..5 per edge (nedge)
  *   2 primal edge ids (n_gp)
  *   3 dual edge ids (m_r)
- *   4 r_V edge ids of subdomain `sub`
+ *   4 r_V edge ids of subdomain `sub`, in the library's local order:
+ *     lexicographic in the control index of the edge, the axis with the
+ *     longest extent outermost, the direction last (a banded K_rr)
  *   5 r_I edge ids of subdomain `sub`
  *   6 primal edge ids of subdomain `sub`
  *   7 sign (+1/-1) of each r_I DOF of subdomain `sub`

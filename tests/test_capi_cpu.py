@@ -76,3 +76,43 @@ def test_device_entry_points_refuse_host_context():
             ieti.ieti_assemble(ctx)
     finally:
         ieti.ieti_destroy(ctx)
+
+
+def _decode_edges(prob, e):
+    """(direction, i, j, k) of global edge ids: direction blocks one after the
+    other, i fastest; direction d has one edge fewer along d (not periodic)."""
+    N = prob.grid_shape()
+    ext, off = [], [0]
+    for d in range(3):
+        x = list(N)
+        if not (d == 0 and prob.periodic0):
+            x[d] -= 1
+        ext.append(x)
+        off.append(off[-1] + x[0] * x[1] * x[2])
+    d = np.searchsorted(np.array(off[1:]), e, side="right")
+    r = e - np.array(off)[d]
+    e0 = np.array([ext[q][0] for q in d])
+    e1 = np.array([ext[q][1] for q in d])
+    return d, r % e0, (r // e0) % e1, r // (e0 * e1)
+
+
+@pytest.mark.parametrize("make", [lambda: wl.cube64_p3n8_sub16(), lambda: wl.small_cases()[2]])
+def test_interior_dofs_in_banded_order(make):
+    """The r_V DOFs of every subdomain are ordered lexicographically in the
+    control index of their edge (longest axis outermost, shortest innermost),
+    then by direction: the order that keeps K_rr banded for the factor."""
+    prob = make()
+    ctx = ieti.ieti_create_host(prob)
+    try:
+        for k in range(prob.nsub):
+            V = ieti.ieti_get_dofmap(ctx, 4, k)
+            if len(V) < 2:
+                continue
+            d, i, j, kk = _decode_edges(prob, V)
+            c = np.stack([i, j, kk])
+            ext = c.max(axis=1) - c.min(axis=1)
+            ax = sorted(range(3), key=lambda a: -ext[a])   # stable: ties keep axis order
+            key = np.stack([c[ax[0]], c[ax[1]], c[ax[2]], d, V]).T
+            assert all(tuple(key[q]) < tuple(key[q + 1]) for q in range(len(V) - 1)), k
+    finally:
+        ieti.ieti_destroy(ctx)
