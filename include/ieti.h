@@ -139,10 +139,16 @@ ieti_status ieti_set_params(ieti_ctx* ctx, const double* nu_host,
 
 /* Eq. (3), batched over all patches of all subdomains: assembles, per
  * subdomain k, the dense blocks K_rr^(k) (order [r_V, pad, r_I]), K_rp^(k),
- * K_pp^(k) and the loads j_r^(k), j_p^(k) in FP64 on the device. */
+ * K_pp^(k) and the loads j_r^(k), j_p^(k) in FP64 on the device. After the
+ * first factorisation has found the nonzero 64 x 64 tiles of K_rr (a pattern
+ * fixed by the mesh, not by the reluctivities), only those tiles are
+ * generated again; the geometry at the Gauss points is kept from the first
+ * assembly. */
 ieti_status ieti_assemble(ieti_ctx* ctx, void* stream);
 
-/* Sec. 2.1: batched Cholesky of every K_rr^(k) in the chosen precision; the
+/* Sec. 2.1: batched Cholesky of every K_rr^(k) in the chosen precision, over
+ * the nonzero 64 x 64 tiles of a tile-level symbolic factorisation (found on
+ * the first call from the assembled K_rr and kept); the
  * interface Schur complement S_rIrI^(k) of Eq. (10) is taken from the factor
  * after the r_V columns; Phi^(k) = K_rr^-1 K_rp; the coarse matrix
  * S_Pi = -F (F of Eq. (7)) in FP64 and its Cholesky factor; the local
