@@ -459,74 +459,17 @@ __global__ void k_gather_x(const SubDev* sd, const int64_t* r_edge, const double
   }
 }
 
-// residual rows with the gathered field: a dense product over contiguous
-// columns of the symmetric K_rr (16-byte loads, four in flight per lane)
-__global__ void __launch_bounds__(256) k_residual2(const SubDev* sd, const int64_t* r_edge, const double* K64,
-                                                   const double* Kp, const double* Kpp, const double* jr,
-                                                   const double* jp, const double* xr, const double* xp,
-                                                   int64_t nedge, int nrhs, const int32_t* I_dual,
-                                                   const double* I_sign, const double* lam, int64_t m_r,
-                                                   double* rr_out, double* rp_out, double* R) {
-  const int k = blockIdx.y;
-  const SubDev s = sd[k];
-  const int Rn = s.n + s.nP;
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int row = blockIdx.x * 8 + warp;
-  if (row >= Rn) return;
-  const int64_t e_row = r_edge[s.dof + row];
-  for (int col = 0; col < nrhs; ++col) {
-    const double* kc;
-    const double* kpc;
-    int64_t kp_stride;
-    if (row < s.n) {
-      kc = K64 + s.A + (int64_t)s.n * row;         // symmetric: column = row
-      kpc = Kp + s.Kp + row;
-      kp_stride = s.n;
-    } else {
-      const int c = row - s.n;
-      kc = Kp + s.Kp + (int64_t)s.n * c;
-      kpc = Kpp + s.Kpp + c;
-      kp_stride = s.nP;
-    }
-    const double2* k2 = reinterpret_cast<const double2*>(kc);
-    const double2* x2 = reinterpret_cast<const double2*>(xr + RV(s, 0, col, nrhs));
-    double acc0 = 0, acc1 = 0;
-#pragma unroll 4
-    for (int j = lane; j < s.n / 2; j += 32) {
-      const double2 kv = k2[j], xv = x2[j];
-      acc0 = fma(kv.x, xv.x, acc0);
-      acc1 = fma(kv.y, xv.y, acc1);
-    }
-    double acc = acc0 + acc1;
-    for (int j = lane; j < s.nP; j += 32) acc += kpc[kp_stride * j] * xp[PV(s, j, col, nrhs)];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-      double v;
-      if (row < s.n) {
-        v = (e_row < 0) ? 0.0 : jr[RV(s, row, col, nrhs)] - acc;
-        double vl = v;
-        const int ii = row - s.nVp;
-        if (ii >= 0 && ii < s.nI) vl -= I_sign[s.iv + ii] * lam[I_dual[s.iv + ii] + m_r * col];
-        rr_out[RV(s, row, col, nrhs)] = vl;
-      } else {
-        v = jp[PV(s, row - s.n, col, nrhs)] - acc;
-        rp_out[PV(s, row - s.n, col, nrhs)] = v;
-      }
-      if (R && e_row >= 0) atomicAdd(R + e_row + nedge * col, v);
-    }
-  }
-}
-
-// k_residual2 over the nonzero tiles of K_rr only: row r of block row I reads
-// the tiles listed for I (K_rr is symmetric, so row r is column r)
+// residual rows with the gathered field over the nonzero tiles of K_rr only:
+// row r of block row I reads the tiles listed for I (K_rr is symmetric, so row
+// r is column r; 16-byte loads, four in flight per lane)
 __global__ void __launch_bounds__(256) k_residual3(const SubDev* sd, const int64_t* r_edge, const double* K64,
                                                    const int64_t* trow, const int32_t* tcol, const int* tb,
                                                    const double* Kp, const double* Kpp, const double* jr,
                                                    const double* jp, const double* xr, const double* xp,
                                                    int64_t nedge, int nrhs, const int32_t* I_dual,
                                                    const double* I_sign, const double* lam, int64_t m_r,
-                                                   double* rr_out, double* rp_out, double* R) {
+                                                   double* rr_out, double* rp_out, double* R, int zero_x) {
+  // zero_x: the field is zero (the norm of the loads), so the products are skipped
   const int k = blockIdx.y;
   const SubDev s = sd[k];
   const int Rn = s.n + s.nP;
@@ -537,9 +480,11 @@ __global__ void __launch_bounds__(256) k_residual3(const SubDev* sd, const int64
   for (int col = 0; col < nrhs; ++col) {
     const double2* x2 = reinterpret_cast<const double2*>(xr + RV(s, 0, col, nrhs));
     double acc0 = 0, acc1 = 0;
-    const double* kpc;
-    int64_t kp_stride;
-    if (row < s.n) {
+    const double* kpc = nullptr;
+    int64_t kp_stride = 0;
+    if (zero_x) {
+      // no products
+    } else if (row < s.n) {
       const double2* k2 = reinterpret_cast<const double2*>(K64 + s.A + (int64_t)s.n * row);
       const int I = row / NB;
       const int64_t e0 = trow[tb[k] + I], e1 = trow[tb[k] + I + 1];
@@ -565,7 +510,8 @@ __global__ void __launch_bounds__(256) k_residual3(const SubDev* sd, const int64
       kp_stride = s.nP;
     }
     double acc = acc0 + acc1;
-    for (int j = lane; j < s.nP; j += 32) acc += kpc[kp_stride * j] * xp[PV(s, j, col, nrhs)];
+    if (!zero_x)
+      for (int j = lane; j < s.nP; j += 32) acc += kpc[kp_stride * j] * xp[PV(s, j, col, nrhs)];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) {
@@ -948,7 +894,8 @@ static ieti_status recover(Ctx* c, const double* lam, const double* ycr, double*
 }
 
 // relative FP64 residual ||j - K a|| / ||j|| (max over columns); local residuals to wres_r/wres_p
-static ieti_status residual(Ctx* c, const double* a, double* rel, double* jn2, cudaStream_t st) {
+static ieti_status residual(Ctx* c, const double* a, double* rel, double* jn2, cudaStream_t st,
+                           bool zero_field = false) {
   const int nrhs = c->nrhs;
   const int64_t ne = c->mesh.nedge;
   ieti_status rk;
@@ -956,11 +903,14 @@ static ieti_status residual(Ctx* c, const double* a, double* rel, double* jn2, c
   IETI_CUDA_TRY(c, cudaMemsetAsync(c->wglob, 0, sizeof(double) * ne * nrhs, st));
   dim3 g((unsigned)ceil_div(c->max_n + c->max_nP, 8), c->nsub);
   cudaEvent_t p0 = prof_begin(c, st);
-  k_gather_x<<<dim3(64, c->nsub), 256, 0, st>>>(c->d_sd, c->d_r_edge, a, ne, nrhs, c->wr64[2], c->wxp);
-  IETI_LAUNCH_CHECK(c);
+  if (!zero_field) {
+    k_gather_x<<<dim3(64, c->nsub), 256, 0, st>>>(c->d_sd, c->d_r_edge, a, ne, nrhs, c->wr64[2], c->wxp);
+    IETI_LAUNCH_CHECK(c);
+  }
   k_residual3<<<g, 256, 0, st>>>(c->d_sd, c->d_r_edge, c->K64, c->d_ktile_row, c->d_ktile_col, c->d_ktile_base,
                                  c->Kp64, c->Kpp64, c->jr, c->jp, c->wr64[2], c->wxp, ne, nrhs, c->d_I_dual,
-                                 c->d_I_sign, c->wlam_acc, c->m_r, c->wres_r, c->wres_p, c->wglob);
+                                 c->d_I_sign, c->wlam_acc, c->m_r, c->wres_r, c->wres_p, c->wglob,
+                                 zero_field ? 1 : 0);
   prof_end(c, PROF_RESID, p0, st);
   IETI_LAUNCH_CHECK(c);
   k_colnorm2_part<<<dim3(NORM_CTAS, nrhs), 256, 0, st>>>(c->wglob, ne, c->wred);
@@ -1007,7 +957,7 @@ ieti_status solve_all(Ctx* c, const double* lam0, double tol, int maxit, double 
   if (refine) {
     // ||j||^2 of the assembled loads: residual of the zero field
     double dummy;
-    if ((r = residual(c, a, &dummy, nullptr, st)) != IETI_OK) return r;
+    if ((r = residual(c, a, &dummy, nullptr, st, true)) != IETI_OK) return r;
     IETI_CUDA_TRY(c, cudaMemcpy(jn2.data(), c->wnorm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost));
   }
   const int max_steps = refine ? 8 : 1;
