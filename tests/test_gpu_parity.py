@@ -227,3 +227,31 @@ def test_tensor_core_trailing_update_path(ieti, monkeypatch):
         assert np.linalg.norm(a.cpu().numpy().T - a_m) <= 1e-8 * np.linalg.norm(a_m)
     finally:
         ieti.ieti_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_barrier_sweeps_match_dependency_sweeps(ieti, prec, monkeypatch):
+    """The single-column sweeps as barrier-synchronised panel loops (the
+    fallback, IETI_NO_DEP_SWEEP=1) and as dependency-driven block tasks give
+    the same field, and both equal the monolithic oracle solve to 1e-8."""
+    prob, mesh, topo, sysd, a_m = oracle_case("cube12_p2_mixed")
+    out = []
+    for env in (None, "1"):
+        if env:
+            monkeypatch.setenv("IETI_NO_DEP_SWEEP", env)
+        else:
+            monkeypatch.delenv("IETI_NO_DEP_SWEEP", raising=False)
+        ctx = ieti.ieti_create(prob)
+        try:
+            ieti.ieti_assemble(ctx)
+            ieti.ieti_factor(ctx, prec)
+            a = torch.zeros((prob.nrhs, mesh.nedge), dtype=torch.float64, device="cuda")
+            info = ieti.ieti_solve(ctx, a, tol=1e-10, maxit=400, tol_field=1e-12 if prec else 0.0)
+            assert info.converged == 1
+            out.append(a.cpu().numpy().T)
+        finally:
+            ieti.ieti_destroy(ctx)
+    a1, a2 = out
+    assert np.linalg.norm(a1 - a2) <= 1e-9 * np.linalg.norm(a2)
+    for x in out:
+        assert np.linalg.norm(x - a_m) <= 1e-8 * np.linalg.norm(a_m)
