@@ -41,7 +41,14 @@ __global__ void __launch_bounds__(STREAM_THREADS, 1) k_stream(StreamArgs A) {
   const int tb = A.cta[blockIdx.x], te = A.cta[blockIdx.x + 1];
   const int col0 = blockIdx.y * CT;
   uint32_t seq = 0, useq = 0;
-  stream_tiles<T, CT, ROWS>(A.C, tb, te, smem, seq, useq, A.t, A.qpart, A.nrhs, col0, min(CT, A.nrhs - col0));
+  // the first tiles of the blocks do not depend on the u scatter before this
+  // launch: they are in flight while it finishes
+  int npre = 0;
+  if (threadIdx.x >= NCONS) npre = stream_prefetch<T>(A.C, tb, te, smem, seq, CT);
+  griddep_wait();
+  stream_tiles<T, CT, ROWS>(A.C, tb, te, smem, seq, useq, A.t, A.qpart, A.nrhs, col0, min(CT, A.nrhs - col0),
+                            npre);
+  griddep_launch();
 }
 
 // u vectors of all subdomains: for both sides of multiplier l,
@@ -50,6 +57,7 @@ __global__ void __launch_bounds__(STREAM_THREADS, 1) k_stream(StreamArgs A) {
 template <typename T>
 __global__ void k_scatter_u(const int4* gs, const int2* gu, const double* I_sign, const double* I_scale,
                             const double* x, int64_t m, int nrhs, int64_t utot, T* uall) {
+  griddep_launch();   // the streamed product may start fetching its tiles
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m * nrhs;
        q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t l = q % m, col = q / m;
@@ -62,6 +70,9 @@ __global__ void k_scatter_u(const int4* gs, const int2* gu, const double* I_sign
     uall[col * utot + o.x] = (T)(w0 * v);
     uall[col * utot + o.y] = (T)(w1 * v);
   }
+  // the product reads u with bulk copies (async proxy), possibly launched
+  // before this kernel has ended
+  asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
 // y[l] = t_k0[i0] - t_k1[i1] + sum_e G[l, e] yc[g_e] (+ partial <y, dotv>), one
@@ -73,6 +84,7 @@ __global__ void __launch_bounds__(256) k_gather_F3(const int4* gs, const int2* g
                                                    const int64_t* pcsr_off, const int4* pcon, const double* qpart,
                                                    const double* SPiInv, int ldc, const double* yc_in, int ngp,
                                                    int64_t m, int nrhs, double* y, const double* dotv, double* part) {
+  griddep_wait();   // t and the primal partials come from the streamed product
   extern __shared__ double sm[];   // qg[ngp], yc[ngp]
   __shared__ double red[8];
   const int col = blockIdx.y;
@@ -129,6 +141,7 @@ __global__ void __launch_bounds__(256) k_gather_F3(const int4* gs, const int2* g
 __global__ void __launch_bounds__(256) k_gather_P2(const int4* gs, const int2* gn, const double* I_scale,
                                                    const double* t, int64_t m, int nrhs, double* z,
                                                    const double* dotv, double* part) {
+  griddep_wait();   // t comes from the streamed product
   __shared__ double red[8];
   const int col = blockIdx.y;
   double mydot = 0;
@@ -333,8 +346,22 @@ ieti_status launch_stream(Ctx* c, const StreamPlan& P, bool with_phi, const doub
   const size_t smem = stream_hdr(CT) + 2 * u_bytes<T>(c, CT) + (size_t)stages * P.stage_bytes;
   // one column with rows short enough for u in registers: row mode
   const bool rows = CT == 1 && c->max_ldI <= ROW_MAX_ELEMS;
-  if (rows) k_stream<T, CT, true><<<dim3(P.grid, (unsigned)nrhs), STREAM_THREADS, smem, st>>>(A);
-  else k_stream<T, CT, false><<<dim3(P.grid, (unsigned)ceil_div(nrhs, CT)), STREAM_THREADS, smem, st>>>(A);
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(STREAM_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (rows) {
+    cfg.gridDim = dim3(P.grid, (unsigned)nrhs);
+    IETI_CUDA_TRY(c, cudaLaunchKernelEx(&cfg, k_stream<T, CT, true>, A));
+  } else {
+    cfg.gridDim = dim3(P.grid, (unsigned)ceil_div(nrhs, CT));
+    IETI_CUDA_TRY(c, cudaLaunchKernelEx(&cfg, k_stream<T, CT, false>, A));
+  }
   IETI_LAUNCH_CHECK(c);
   return IETI_OK;
 }
@@ -499,9 +526,22 @@ ieti_status iface_gather_F(Ctx* c, const double* t, const double* qpart, const d
   const int ngp = (int)c->n_gp;
   const int ldc = (int)(ceil_div(std::max<int64_t>(c->n_gp, 1), NB) * NB);
   const size_t smem = sizeof(double) * 2 * std::max(ngp, 1);
-  k_gather_F3<<<dim3(blocks, nrhs), 256, smem, st>>>(c->d_gs, c->d_gn, c->d_gell_i, c->d_gell_v, c->gell_E, t,
-                                                    c->d_pcsr_off, c->d_pcon, qpart, c->SPiInv, ldc, yc, ngp,
-                                                    c->m_r, nrhs, y, dotv, part);
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks, nrhs);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const int E = c->gell_E;
+  const int64_t m = c->m_r;
+  IETI_CUDA_TRY(c, cudaLaunchKernelEx(&cfg, k_gather_F3, (const int4*)c->d_gs, (const int2*)c->d_gn,
+                                      (const int32_t*)c->d_gell_i, (const double*)c->d_gell_v, E, t,
+                                      (const int64_t*)c->d_pcsr_off, (const int4*)c->d_pcon, qpart,
+                                      (const double*)c->SPiInv, ldc, yc, ngp, m, nrhs, y, dotv, part));
   prof_end(c, PROF_GATHER, p0, st);
   IETI_LAUNCH_CHECK(c);
   return IETI_OK;
@@ -510,7 +550,18 @@ ieti_status iface_gather_F(Ctx* c, const double* t, const double* qpart, const d
 ieti_status iface_gather_P(Ctx* c, const double* t, int nrhs, double* z, const double* dotv, double* part,
                            int blocks, cudaStream_t st) {
   cudaEvent_t p0 = prof_begin(c, st);
-  k_gather_P2<<<dim3(blocks, nrhs), 256, 0, st>>>(c->d_gs, c->d_gn, c->d_I_scale, t, c->m_r, nrhs, z, dotv, part);
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks, nrhs);
+  cfg.blockDim = dim3(256);
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const int64_t m = c->m_r;
+  IETI_CUDA_TRY(c, cudaLaunchKernelEx(&cfg, k_gather_P2, (const int4*)c->d_gs, (const int2*)c->d_gn,
+                                      (const double*)c->d_I_scale, t, m, nrhs, z, dotv, part));
   prof_end(c, PROF_GATHER, p0, st);
   IETI_LAUNCH_CHECK(c);
   return IETI_OK;

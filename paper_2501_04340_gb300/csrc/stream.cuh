@@ -221,6 +221,13 @@ __device__ int stream_prefetch(const StreamCtx& C, int tb, int te, unsigned char
   return __shfl_sync(0xffffffffu, npre, 0);
 }
 
+// programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start before its predecessor ends; it waits for it here
+// before touching the predecessor's output (a no-op for an ordinary launch)
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// lets the successor launch while this kernel finishes
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Producer warp only: waits (bounded) for tiles issued by stream_prefetch that
 // will not be consumed (the loop ended), so that no copy is in flight when the
 // CTA exits.
