@@ -1,23 +1,24 @@
-// Single-column triangular sweeps with the blocked Cholesky factors of all
-// subdomains as dependency-driven block tasks: one cooperative launch per
-// sweep and no grid barrier. Forward, block row b of subdomain k:
+// Triangular sweeps with the blocked Cholesky factors of all subdomains as
+// dependency-driven block tasks: one cooperative launch per sweep and no grid
+// barrier. Forward, block row b of subdomain k:
 //   y_b = Linv_b (b_b - sum_{b0 <= j < b} L_bj y_j)
 // backward, block column b:
 //   x_b = Linv_b^T (y_b - sum_{j > b} L_jb^T x_j)
 // (the local solves K_rr^(k) x = f of Eqs. (8), (9) and of the right-hand
-// side of Eq. (7)), over the nonzero tiles of the factor only (symbolic.cu).
-// A task is one 64-wide block of one subdomain. The tasks
-// are ordered by b (ascending forward, descending backward) and dealt
-// round-robin to the CTAs; a CTA runs its tasks in that order. A task reads
-// the finished blocks as they are published and publishes its own block by
-// raising the subdomain's progress counter with a release store after writing
-// it, once its predecessor in the order has been published (so the counter
-// says that every block up to it is final); readers poll the counter with
-// acquire loads (bounded, with an error flag on time-out) and read the blocks
-// through L2. Every wait is on a task that
-// comes earlier in the order and all CTAs are resident (cooperative launch),
-// so every wait ends. Progress counters carry an epoch in their upper bits, so
-// they are never reset.
+// side of Eq. (7); with many columns, the W and Phi solves of the
+// factorisation), over the nonzero tiles of the factor only (symbolic.cu).
+// A task is one 64-wide block of one subdomain (times one tile of up to 64
+// columns for many right-hand sides). The tasks are ordered by b (ascending
+// forward, descending backward) and dealt round-robin to the CTAs; a CTA runs
+// its tasks in that order. A task reads the finished blocks as they are
+// published and publishes its own block by raising its progress counter (one
+// per subdomain, or per subdomain and column tile) with a release store after
+// writing it, once its predecessor in the order has been published (so the
+// counter says that every block up to it is final); readers poll the counter
+// with acquire loads (bounded, with an error flag on time-out) and read the
+// blocks through L2. Every wait is on a task that comes earlier in the order
+// and all CTAs are resident (cooperative launch), so every wait ends. Progress
+// counters carry an epoch in their upper bits, so they are never reset.
 #include <cuda_runtime.h>
 
 #include <algorithm>
