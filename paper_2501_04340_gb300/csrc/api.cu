@@ -276,6 +276,7 @@ ieti_status build(Ctx* c, const ieti_problem_desc* desc, bool device) {
   c->coop_trsv = !c->no_coop && std::getenv("IETI_COOP_TRSV") != nullptr;
   c->dep_sweeps = !c->no_coop && std::getenv("IETI_NO_DEP_SWEEP") == nullptr;
   c->syrk_tc = std::getenv("IETI_SYRK_TC") != nullptr;
+  c->autotune = std::getenv("IETI_NO_AUTOTUNE") == nullptr;
   {
     int dev = 0, optin = 48 * 1024;
     IETI_CUDA_TRY(c, cudaGetDevice(&dev));

@@ -225,7 +225,7 @@ ieti_status alloc_dev(Ctx* c, T** p, size_t count) {
 // into whole-row tiles of about TILE_TARGET bytes, subdomain by subdomain; CTA
 // j owns the tiles whose cost offsets start in [j C / grid, (j+1) C / grid),
 // the cost being the bytes plus a fixed charge per subdomain entered
-ieti_status build_plan(Ctx* c, int es, bool with_phi, StreamPlan* P) {
+ieti_status build_plan(Ctx* c, int es, bool with_phi, StreamPlan* P, int rcap = RMAX) {
   std::vector<LTile> tiles;
   std::vector<int64_t> start;   // balancing cost before each tile
   int64_t bytes = 0, cost = 0;
@@ -242,7 +242,7 @@ ieti_status build_plan(Ctx* c, int es, bool with_phi, StreamPlan* P) {
     }
     const int64_t rb = (int64_t)s.ldI * es;
     // whole rows, at most RMAX of them, about TILE_TARGET bytes
-    const int rpt = (int)std::max<int64_t>(1, std::min<int64_t>(RMAX, TILE_TARGET / rb));   // 1 .. RMAX rows
+    const int rpt = (int)std::max<int64_t>(1, std::min<int64_t>(std::min(rcap, RMAX), TILE_TARGET / rb));   // 1 .. rcap rows
     stage_bytes = std::max<int>(stage_bytes, (int)(rpt * rb));
     for (int kind = 0; kind < (with_phi ? 2 : 1); ++kind) {
       const int rows = kind == 0 ? s.nI : s.nP;
@@ -298,6 +298,7 @@ ieti_status build_plan(Ctx* c, int es, bool with_phi, StreamPlan* P) {
   P->grid = grid;
   P->stage_bytes = stage_bytes;
   P->bytes = bytes;
+  P->rows_cap = rcap;
   P->built = true;
   return IETI_OK;
 }
@@ -462,6 +463,56 @@ ieti_status iface_alloc(Ctx* c) {
   return IETI_OK;
 }
 
+// Tile-shape autotuner: for each product (S, and W with the Phi_I^T rows) the
+// rows per tile are chosen among 2, 4 and 8 by timing a few single-column
+// products of this context's blocks with CUDA events (smaller tiles give more
+// pipeline stages in the same shared memory, larger ones fewer copies); runs
+// once per precision, after the blocks of the first factorisation exist
+static ieti_status autotune_plans(Ctx* c, bool fp32, cudaStream_t st) {
+  const int es = fp32 ? 4 : 8;
+  double* x = c->wlam[6];
+  IETI_CUDA_TRY(c, cudaMemsetAsync(x, 0, sizeof(double) * std::max<int64_t>(c->m_r, 1), st));
+  cudaEvent_t e0, e1;
+  IETI_CUDA_TRY(c, cudaEventCreate(&e0));
+  IETI_CUDA_TRY(c, cudaEventCreate(&e1));
+  const bool prof = c->prof.on;
+  c->prof.on = false;
+  ieti_status res = IETI_OK;
+  for (int wp = 0; wp < 2 && res == IETI_OK; ++wp) {
+    const StreamPlan def = c->splan[fp32][wp];
+    StreamPlan best = def;
+    float best_ms = -1.f;
+    for (int rcap : {2, 4, RMAX}) {
+      StreamPlan cand;
+      if (rcap == def.rows_cap) cand = def;
+      else if ((res = build_plan(c, es, wp == 1, &cand, rcap)) != IETI_OK) break;
+      if (cand.incomplete || cand.ntiles == 0) continue;
+      c->splan[fp32][wp] = cand;
+      ieti_status r = IETI_OK;
+      for (int it = 0; it < 3 && r == IETI_OK; ++it)
+        r = iface_local(c, fp32, wp == 1, x, wp == 1 ? nullptr : c->d_I_scale, c->wi[0], c->wq_part, 1, st);
+      if (r != IETI_OK) continue;   // this shape does not fit: not a candidate
+      IETI_CUDA_TRY(c, cudaEventRecord(e0, st));
+      for (int it = 0; it < 10 && r == IETI_OK; ++it)
+        r = iface_local(c, fp32, wp == 1, x, wp == 1 ? nullptr : c->d_I_scale, c->wi[0], c->wq_part, 1, st);
+      IETI_CUDA_TRY(c, cudaEventRecord(e1, st));
+      IETI_CUDA_TRY(c, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      IETI_CUDA_TRY(c, cudaEventElapsedTime(&ms, e0, e1));
+      if (r == IETI_OK && (best_ms < 0.f || ms < best_ms)) {
+        best_ms = ms;
+        best = cand;
+      }
+    }
+    c->splan[fp32][wp] = best;
+  }
+  c->prof.on = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  IETI_CUDA_TRY(c, cudaMemsetAsync(c->uall, 0, sizeof(double) * (size_t)c->utot * MAX_RHS, st));
+  return res;
+}
+
 ieti_status iface_prepare(Ctx* c, cudaStream_t st) {
   const bool fp32 = c->prec == IETI_FP32_IR;
   const int es = fp32 ? 4 : 8;
@@ -480,6 +531,10 @@ ieti_status iface_prepare(Ctx* c, cudaStream_t st) {
     k_build_gell<<<(unsigned)std::min<int64_t>(1024, ceil_div(c->m_r, 256)), 256, 0, st>>>(
         c->d_sd, c->d_pair, c->d_P_glob, c->Phi, c->m_r, c->gell_E, c->d_gell_i, c->d_gell_v);
     IETI_LAUNCH_CHECK(c);
+  }
+  if (c->autotune && !c->tuned[fp32] && c->m_r > 0) {
+    if ((r = autotune_plans(c, fp32, st)) != IETI_OK) return r;
+    c->tuned[fp32] = true;
   }
   return IETI_OK;
 }

@@ -86,6 +86,7 @@ struct StreamPlan {
   void* d_tiles = nullptr;
   int* d_cta = nullptr;      // first tile of every CTA (grid + 1 entries)
   int2* d_ckr = nullptr;     // subdomains [x, y) that every CTA's tiles touch
+  int rows_cap = 0;          // rows per tile at most (chosen by the autotuner)
 };
 
 // one step of the blocked factorisation with its work lists (symbolic.cu)
@@ -220,6 +221,8 @@ struct Ctx {
   unsigned long long dep_epoch = 0;
   int* d_dep_err = nullptr;              // set when a sweep wait times out
   McPlan mcplan[2];                      // [0] W solve, [1] Phi solve
+  bool autotune = true;                  // IETI_NO_AUTOTUNE=1: keep the default tile shapes
+  bool tuned[2] = {false, false};        // [fp32] tile shapes of the streamed products chosen
   cudaStream_t aux_stream = nullptr;     // low-priority stream of the factorisation's lookahead
   cudaEvent_t ev_fact[3] = {nullptr, nullptr, nullptr};
   double* SPi = nullptr;                 // coarse S_Pi (n_gp x n_gp)
