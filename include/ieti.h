@@ -154,7 +154,8 @@ ieti_status ieti_assemble(ieti_ctx* ctx, void* stream);
  * S_Pi = -F (F of Eq. (7)) in FP64 and its Cholesky factor; the local
  * interface operators (K_rr^-1)_II = S_rIrI^-1. Errors: SINGULAR_LOCAL (a
  * non-positive pivot; the subdomain id is in the message), STATE (not
- * assembled). Synchronises the stream. */
+ * assembled), TIMEOUT or CUDA (a bounded device wait of the interface
+ * products or of the W and Phi solves gave up). Synchronises the stream. */
 ieti_status ieti_factor(ieti_ctx* ctx, ieti_precision prec, void* stream);
 
 /* Eq. (7): y = F_DP lam with F_DP = W - G F^-1 G^T = B_r K_rr^-1 B_r^T

@@ -853,6 +853,7 @@ static ieti_status factor_t(Ctx* c, cudaStream_t st) {
     return r;
   }
   IETI_CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
+  IETI_CUDA_TRY(c, cudaMemsetAsync(c->d_dep_err, 0, sizeof(int), st));   // bounded waits of the W and Phi solves
   const FactorPlan* plan = &c->fplan[sizeof(T) == 4 ? 1 : 0];
   if ((r = cholesky<T>(c, c->d_sd, c->sd_host, L, Linv, S, true, st, plan)) != IETI_OK) return r;
   IETI_CUDA_TRY(c, cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -925,6 +926,12 @@ static ieti_status factor_t(Ctx* c, cudaStream_t st) {
     k_store_Phi<T><<<dim3(256, nsub), 256, 0, st>>>(c->d_sd, dd, X, c->Phi);
     IETI_LAUNCH_CHECK(c);
     IETI_CUDA_TRY(c, cudaStreamSynchronize(st));
+  }
+  IETI_CUDA_TRY(c, cudaMemcpyAsync(c->h_err + 1, c->d_dep_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  IETI_CUDA_TRY(c, cudaStreamSynchronize(st));
+  if (c->h_err[1]) {
+    c->err = "a wait of the W or Phi solves timed out";
+    return IETI_ERR_CUDA;
   }
   return IETI_OK;
 }
