@@ -116,3 +116,25 @@ def test_interior_dofs_in_banded_order(make):
             assert all(tuple(key[q]) < tuple(key[q + 1]) for q in range(len(V) - 1)), k
     finally:
         ieti.ieti_destroy(ctx)
+
+
+def test_uneven_partition_of_the_512_patch_cube():
+    """The uneven 64-subdomain partition of the 512-patch cube (the batching
+    workload): sizes within 4..12 patches, every subdomain simply connected
+    (the library's own check accepts it), and the host DOF classes split every
+    subdomain's edges."""
+    prob = wl.cube512_p3_uneven64(nrhs=1)
+    size = np.bincount(prob.sub_of_patch, minlength=64)
+    assert prob.nsub == 64 and size.min() >= 4 and size.max() <= 12 and size.sum() == 512
+    assert size.min() < size.max()   # uneven
+    for k in range(64):
+        assert wl.is_simply_connected_union((8, 8, 8), np.flatnonzero(prob.sub_of_patch == k))
+    ctx = ieti.ieti_create_host(prob)
+    try:
+        q = ieti.ieti_query(ctx)
+        assert q["nsub"] == 64 and q["m_r"] > 0 and q["n_gp"] > 0
+        nI = [len(ieti.ieti_get_dofmap(ctx, 5, k)) for k in range(64)]
+        nV = [len(ieti.ieti_get_dofmap(ctx, 4, k)) for k in range(64)]
+        assert min(nV) > 0 and min(nI) > 0 and max(nI) == q["max_nI"]
+    finally:
+        ieti.ieti_destroy(ctx)
