@@ -347,23 +347,25 @@ def _patch_element_loop(prob, mesh, q, nq=None):
                 yield gids, val, curl, X, DF, wts
 
 
-def assemble_patch(prob, mesh, q):
+def assemble_patch(prob, mesh, q, nq=None):
     """Patch contribution to K_g and j_g (Eq. (3)) as COO triplets and a dense
-    load block: returns (rows, cols, vals, gid_rhs, rhs_vals)."""
+    load block: returns (rows, cols, vals, gid_rhs, rhs_vals). ``nq`` Gauss
+    points per direction per span (default p+1, the reading used throughout)."""
     nu = prob.nu[q]
     R, C, V = [], [], []
     jr_ids, jr_vals = [], []
-    for gids, val, curl, X, DF, wts in _patch_element_loop(prob, mesh, q):
+    for gids, val, curl, X, DF, wts in _patch_element_loop(prob, mesh, q, nq=nq):
         det = np.linalg.det(DF)
-        # curl w = DF curl_hat / det ; int nu curl_i . curl_j = sum_q w nu c_i^T DF^T DF c_j / det
-        M = np.einsum("qra,qrb->qab", DF, DF) * (nu * wts / det)[:, None, None]
+        # dV = |det DF| dxi (a patch map may reverse orientation);
+        # curl w = DF curl_hat / det ; int nu curl_i . curl_j = sum_q w nu c_i^T DF^T DF c_j / |det|
+        M = np.einsum("qra,qrb->qab", DF, DF) * (nu * wts / np.abs(det))[:, None, None]
         Y = np.einsum("qab,jqb->jqa", M, curl)
         nf = curl.shape[0]
         E = curl.reshape(nf, -1) @ Y.reshape(nf, -1).T
-        # j_i = int J . DF^{-T} w_hat det = sum_q w det (DF^{-1} J) . w_hat
+        # j_i = int J . DF^{-T} w_hat |det| = sum_q w |det| (DF^{-1} J) . w_hat
         J = source_values(prob, X, q)                       # (nq3, 3, nrhs)
         DFinv = np.linalg.inv(DF)
-        G = np.einsum("qab,qbr->qar", DFinv, J) * (wts * det)[:, None, None]
+        G = np.einsum("qab,qbr->qar", DFinv, J) * (wts * np.abs(det))[:, None, None]
         je = val.reshape(val.shape[0], -1) @ G.reshape(-1, G.shape[-1])
         R.append(np.repeat(gids, len(gids)))
         C.append(np.tile(gids, len(gids)))
@@ -374,7 +376,7 @@ def assemble_patch(prob, mesh, q):
             np.concatenate(jr_ids), np.concatenate(jr_vals, 0))
 
 
-def assemble_all(prob, mesh=None):
+def assemble_all(prob, mesh=None, nq=None):
     """Per-patch matrices K_patch (global edge indexing, CSR) and loads j_patch
     (dense nedge x nrhs). Subdomain matrices K^(k) (Sec. 2, block-diagonal K) and
     the global K_g are sums of these."""
@@ -382,7 +384,7 @@ def assemble_all(prob, mesh=None):
         mesh = build_mesh(prob)
     Kp, jp = [], []
     for q in range(prob.npatch_total):
-        r, c, v, ji, jv = assemble_patch(prob, mesh, q)
+        r, c, v, ji, jv = assemble_patch(prob, mesh, q, nq=nq)
         Kp.append(sp.csr_matrix((v, (r, c)), shape=(mesh.nedge, mesh.nedge)))
         jj = np.zeros((mesh.nedge, prob.nrhs))
         np.add.at(jj, ji, jv)

@@ -37,7 +37,7 @@ struct AsmParams {
   const double* nu;
   const double* src;
   const double* gq;
-  double* geo;        // per element and Gauss point: X (3), weight * adj(DF) (9); null: not kept
+  double* geo;        // per element and Gauss point: X (3), weight * |det DF| DF^-1 (9); null: not kept
   int geo_ready;      // 1: geo holds the values (the geometry of the mesh is fixed)
   const double* gram[3];
   int64_t gram_per[3];
@@ -236,7 +236,8 @@ __global__ void __launch_bounds__(256) k_elem_K(AsmParams P) {
   const int tid = threadIdx.x;
   for (int t = tid; t < NQ3; t += blockDim.x) {
     const double* F = sh.DF[t];
-    double f = nu * sh.wt[t] / sh.det[t];
+    // dV = |det DF| dxi: a patch map may reverse orientation
+    double f = nu * sh.wt[t] / fabs(sh.det[t]);
     for (int a = 0; a < 3; ++a)
       for (int b = 0; b < 3; ++b) {
         double v = 0;
@@ -334,11 +335,12 @@ __global__ void __launch_bounds__(256) k_elem_j(AsmParams P) {
       for (int r = 0; r < 9; ++r) A[r] = gk[3 + r];
     } else {
       const double* F = sh.DF[t];
-      // inverse of DF times det (adjugate), times the quadrature weight
+      // adjugate of DF (inverse times det)
       A[0] = F[4] * F[8] - F[5] * F[7]; A[1] = F[2] * F[7] - F[1] * F[8]; A[2] = F[1] * F[5] - F[2] * F[4];
       A[3] = F[5] * F[6] - F[3] * F[8]; A[4] = F[0] * F[8] - F[2] * F[6]; A[5] = F[2] * F[3] - F[0] * F[5];
       A[6] = F[3] * F[7] - F[4] * F[6]; A[7] = F[1] * F[6] - F[0] * F[7]; A[8] = F[0] * F[4] - F[1] * F[3];
-      const double w = sh.wt[t];
+      // |det DF| DF^-1 = sign(det) adj(DF), times the quadrature weight
+      const double w = sh.det[t] < 0 ? -sh.wt[t] : sh.wt[t];
       for (int r = 0; r < 9; ++r) A[r] *= w;
       for (int r = 0; r < 3; ++r) X[r] = sh.X[t][r];
       if (gk) {

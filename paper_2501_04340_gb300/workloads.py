@@ -109,6 +109,68 @@ def box_control_net(p: int, nspan: List[List[int]], breaks: List[Sequence[float]
     return np.stack([x, y, z, np.ones_like(x)], axis=-1)
 
 
+def exact_arc_1d(p: int, nspan: int, th0: float, dth: float):
+    """Control points (m x 2) and weights (m) of the circular arc of angle ``dth``
+    starting at angle ``th0`` on the unit circle, in the degree-p spline space
+    with ``nspan`` uniform spans (m = nspan + p).
+
+    The arc is the rational quadratic Bezier curve with end points on the circle
+    and middle weight cos(dth / 2); its homogeneous coordinates (w x, w y, w)
+    are quadratic polynomials of the parameter, so for p >= 2 they lie in the
+    spline space and interpolation at the Greville abscissae reproduces them
+    exactly (degree elevation and knot insertion without changing the curve)."""
+    from scipy.interpolate import BSpline
+
+    if p < 2:
+        raise ValueError("an exact circular arc needs degree p >= 2")
+    h = 0.5 * dth
+    P = np.array([[math.cos(th0), math.sin(th0)],
+                  [math.cos(th0 + h) / math.cos(h), math.sin(th0 + h) / math.cos(h)],
+                  [math.cos(th0 + dth), math.sin(th0 + dth)]])
+    w = np.array([1.0, math.cos(h), 1.0])
+    g = _greville_1d(p, nspan)
+    bern = np.stack([(1 - g) ** 2, 2 * g * (1 - g), g * g], axis=1)        # (m, 3)
+    H = np.concatenate([bern @ (w[:, None] * P), (bern @ w)[:, None]], 1)  # homogeneous
+    t = np.array([0.0] * (p + 1) + [i / nspan for i in range(1, nspan)] + [1.0] * (p + 1))
+    A = BSpline.design_matrix(np.clip(g, 0.0, 1.0 - 1e-15), t, p).toarray()
+    A[-1] = 0.0
+    A[-1, -1] = 1.0                                                         # x = 1 is the last coefficient
+    C = np.linalg.solve(A, H)
+    C[0] = H[0]
+    C[-1] = H[-1]
+    return C[:, :2] / C[:, 2:3], C[:, 2].copy()
+
+
+def annulus_control_net(p: int, nspan: List[List[int]], r_breaks: Sequence[float], z_breaks: Sequence[float],
+                        arc: float, th0: float = 0.0, closed: bool = False) -> np.ndarray:
+    """Control net of a thick cylindrical shell (or a sector of it): direction 0 is
+    the angle (each angular patch an exact arc of ``arc / P0``, glued C^0; with
+    ``closed`` the ring wraps around and direction 0 is periodic), direction 1 the
+    radius (linear between the ``r_breaks``), direction 2 the axis (linear between
+    the ``z_breaks``). Control point (i, j, k) is r_j (q_i, 0) + z_k e_z with
+    weight w_i, where (q_i, w_i) are the angular control points: the map is
+    x = r(xi_1) c(xi_0) + z(xi_2) e_z with c the exact circular arc."""
+    P0 = len(nspan[0])
+    dth = arc / P0
+    qs, ws = [], []
+    for a, s in enumerate(nspan[0]):
+        q, w = exact_arc_1d(p, s, th0 + a * dth, dth)
+        last = a == P0 - 1
+        keep = slice(0 if a == 0 else 1, -1 if (closed and last) else None)
+        qs.append(q[keep])
+        ws.append(w[keep])
+    q = np.concatenate(qs)
+    w = np.concatenate(ws)
+    r = _glued_coords_1d(p, nspan[1], r_breaks)
+    z = _glued_coords_1d(p, nspan[2], z_breaks)
+    ctrl = np.zeros((len(z), len(r), len(q), 4))
+    ctrl[..., 0] = r[None, :, None] * q[None, None, :, 0]
+    ctrl[..., 1] = r[None, :, None] * q[None, None, :, 1]
+    ctrl[..., 2] = z[:, None, None]
+    ctrl[..., 3] = w[None, None, :]
+    return ctrl
+
+
 # ----------------------------------------------------------------------------
 # partitions of the patch dual graph
 # ----------------------------------------------------------------------------
@@ -341,6 +403,67 @@ def cube512_p3_uneven64(seed: int = 3, nrhs: int = 32, span_lo: int = 4, span_hi
     return unit_cube(3, (8, 8, 8), spans, sub_of_patch=sub, nu=np.ones(512),
                      name="cube512_p3_uneven64", source_kind=SOURCE_FOURIER,
                      source_params=sp, nrhs=nrhs)
+
+
+def annulus(p: int, patches: Tuple[int, int, int], spans, r_in: float, r_out: float, length: float,
+            arc: float = 2 * math.pi, sub_of_patch=None, nu=None, name="annulus",
+            source_kind=SOURCE_PATCHWISE, source_params=None, nrhs=1) -> Problem:
+    """Thick cylindrical shell r_in < r < r_out, 0 < z < length, split into
+    P0 angular x P1 radial x P2 axial NURBS patches with exact circular arcs.
+    ``arc`` = 2 pi closes the ring (direction 0 periodic, P0 >= 3); a smaller
+    ``arc`` gives the sector 0 < theta < arc."""
+    if isinstance(spans, int):
+        spans = [[spans] * patches[d] for d in range(3)]
+    closed = abs(arc - 2 * math.pi) < 1e-12
+    ctrl = annulus_control_net(p, spans, np.linspace(r_in, r_out, patches[1] + 1),
+                               np.linspace(0.0, length, patches[2] + 1), arc, closed=closed)
+    npt = int(np.prod(patches))
+    if sub_of_patch is None:
+        sub_of_patch = np.arange(npt, dtype=np.int32)
+    if nu is None:
+        nu = np.ones(npt)
+    if source_params is None:
+        source_params = np.zeros(nrhs * npt * 3)
+    return Problem(name=name, p=p, npatch=tuple(patches), nspan=[list(s) for s in spans],
+                   periodic0=closed, ctrl=ctrl, nu=np.asarray(nu, np.float64),
+                   sub_of_patch=np.asarray(sub_of_patch, np.int32), source_kind=source_kind,
+                   source_params=np.asarray(source_params, np.float64), nrhs=nrhs)
+
+
+NU0 = 1.0 / (4e-7 * math.pi)
+
+
+def machine_annulus(n_ang: int = 36, n_ax: int = 4, spans: int = 6, p: int = 3, nrhs: int = 16, seed: int = 5,
+                    per_sub: int = 3, r_in: float = 0.05, r_out: float = 0.10, length: float = 0.10) -> Problem:
+    """Machine-like ring: n_ang angular x 2 radial x n_ax axial NURBS patches
+    (exact arcs of 360/n_ang degrees), inner ring air nu0 = 1/(4 pi 1e-7), outer
+    ring iron nu0/1000; axial current density in every third angular sector of
+    the inner ring over the whole length (slot s = a // 3 of sector a), load
+    case c: J_z = 1e6 (-1)^s cos(theta_c - 2 pi (s mod 3) / 3) with theta_c
+    drawn uniformly in [0, 2 pi) (seeded). Subdomains: runs of ``per_sub``
+    angular patches of one radial and one axial slab."""
+    P = (n_ang, 2, n_ax)
+    npt = int(np.prod(P))
+    nu = np.empty(npt)
+    sub = np.empty(npt, np.int32)
+    nga = n_ang // per_sub
+    for c in range(n_ax):
+        for b in range(2):
+            for a in range(n_ang):
+                q = a + n_ang * (b + 2 * c)
+                nu[q] = NU0 if b == 0 else NU0 / 1000.0
+                sub[q] = a // per_sub + nga * (b + 2 * c)
+    rng = np.random.default_rng(seed)
+    theta = rng.uniform(0.0, 2 * math.pi, size=nrhs)
+    J = np.zeros((nrhs, npt, 3))
+    for r in range(nrhs):
+        for c in range(n_ax):
+            for a in range(0, n_ang, 3):
+                s = a // 3
+                J[r, a + n_ang * (0 + 2 * c), 2] = 1e6 * (-1) ** s * math.cos(theta[r] - 2 * math.pi * (s % 3) / 3)
+    return annulus(p, P, spans, r_in, r_out, length, sub_of_patch=sub, nu=nu,
+                   name=f"annulus{npt}_p{p}n{spans}_sub{int(sub.max()) + 1}",
+                   source_kind=SOURCE_PATCHWISE, source_params=J.ravel(), nrhs=nrhs)
 
 
 def small_cases():
