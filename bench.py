@@ -129,6 +129,18 @@ def syrk_flops(n_list, nb=64):
     return tot
 
 
+GOLDEN = os.path.join(ROOT, "tests", "golden", WORKLOAD + ".npz")
+
+
+def oracle_field(nedge):
+    """The oracle's FP64 field of the workload (stored by tests/golden/make_golden.py)."""
+    g = np.load(GOLDEN)
+    a = np.zeros((1, int(g["nedge"])))
+    a[0, g["a_idx"]] = g["a_val"][:, 0]
+    assert a.shape[1] == nedge
+    return a
+
+
 def ours(args):
     import torch
     from paper_2501_04340_gb300 import ieti, workloads as wl
@@ -141,15 +153,38 @@ def ours(args):
     q = ieti.ieti_query(ctx)
     nedge, m_r = q["nedge"], q["m_r"]
     tol, tol_field = 1e-8, 1e-8
-
-    # ---- reference field (FP64 factors, tight tolerances; untimed)
-    ieti.ieti_assemble(ctx)
-    ieti.ieti_factor(ctx, ieti.IETI_FP64)
-    a_ref = torch.zeros((prob.nrhs, nedge), dtype=torch.float64, device=dev)
-    ieti.ieti_solve(ctx, a_ref, tol=1e-12, maxit=2000, tol_field=1e-13, allow_no_convergence=True)
+    a_ref = torch.tensor(oracle_field(nedge), dtype=torch.float64, device=dev)
     nref = torch.linalg.norm(a_ref).item()
 
-    # ---- apply_F throughput with FP64 operators (factors of the reference)
+    def rel_err(a):
+        return (torch.linalg.norm(a - a_ref) / nref).item()
+
+    def timed(fn, n):
+        """CUDA-event time (ms) of n calls of fn, and fn's last result."""
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(n):
+            res = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), res
+
+    a = torch.zeros_like(a_ref)
+
+    # ---- plain FP64 arm: assemble + FP64 factor + PCG, at the loosest interface
+    # tolerance whose field meets 1e-8 against the oracle (found untimed)
+    ieti.ieti_assemble(ctx)
+    ieti.ieti_factor(ctx, ieti.IETI_FP64)
+    plain_tol = None
+    for t in (1e-8, 3e-9, 1e-9, 3e-10, 1e-10, 3e-11):
+        ieti.ieti_solve(ctx, a, tol=t, maxit=4000, tol_field=0.0, allow_no_convergence=True)
+        if rel_err(a) <= 1e-8:
+            plain_tol = t
+            break
+    plain_tol = plain_tol or 1e-11
+
+    # ---- apply_F throughput with FP64 operators
     lam = torch.randn((1, m_r), dtype=torch.float64, device=dev)
     y = torch.empty_like(lam)
     flush = torch.empty(int(256e6) // 4, dtype=torch.float32, device=dev)
@@ -158,41 +193,30 @@ def ours(args):
         for _ in range(5):
             ieti.ieti_apply_F(ctx, lam, y, 1)
         torch.cuda.synchronize()
-        tot = 0.0
         if flush_l2:
+            tot = 0.0
             for _ in range(napply // 4):
                 flush.fill_(1.0)
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                ieti.ieti_apply_F(ctx, lam, y, 1)
-                e1.record()
-                torch.cuda.synchronize()
-                tot += e0.elapsed_time(e1)
+                ms, _ = timed(lambda: ieti.ieti_apply_F(ctx, lam, y, 1), 1)
+                tot += ms
             return (napply // 4) / (tot / 1e3)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(napply):
-            ieti.ieti_apply_F(ctx, lam, y, 1)
-        e1.record()
-        torch.cuda.synchronize()
-        return napply / (e0.elapsed_time(e1) / 1e3)
+        ms, _ = timed(lambda: ieti.ieti_apply_F(ctx, lam, y, 1), napply)
+        return napply / (ms / 1e3)
 
     apply64 = apply_rate()
     apply64_cold = apply_rate(flush_l2=True)
 
-    # ---- plain FP64 arm: one full step (assemble + FP64 factor + solve to 1e-8)
-    a = torch.zeros_like(a_ref)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    ieti.ieti_assemble(ctx)
-    ieti.ieti_factor(ctx, ieti.IETI_FP64)
-    info64 = ieti.ieti_solve(ctx, a, tol=tol, maxit=2000, tol_field=0.0, allow_no_convergence=True)
-    e1.record()
-    torch.cuda.synchronize()
-    plain_s = e0.elapsed_time(e1) / 1e3
-    plain_err = (torch.linalg.norm(a - a_ref) / nref).item()
-    plain_solve_s = info64.ms_total / 1e3
+    def plain_step():
+        ieti.ieti_assemble(ctx)
+        ieti.ieti_factor(ctx, ieti.IETI_FP64)
+        return ieti.ieti_solve(ctx, a, tol=plain_tol, maxit=4000, tol_field=0.0, allow_no_convergence=True)
+
+    plain_step()
+    plain_runs = [timed(plain_step, 1) for _ in range(3)]
+    plain_ms = float(np.median([r[0] for r in plain_runs]))
+    info64 = plain_runs[-1][1]
+    plain_err = rel_err(a)
+    plain_solve_s = float(np.median([r[1].ms_total for r in plain_runs])) / 1e3
 
     # ---- chosen form: FP32 factors + FP64 refinement
     def step():
@@ -207,7 +231,9 @@ def ours(args):
     torch.cuda.synchronize()
     barrier(world)
     l0 = ieti.ieti_launch_count(ctx)
-    ieti.ieti_profile(ctx, True)
+    # events only around the persistent PCG launch (one per refinement step):
+    # the dominant kernel's duration, measured inside the timed region
+    ieti.ieti_profile(ctx, classes=["pcg_vec"])
     infos = []
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
@@ -219,12 +245,20 @@ def ours(args):
         torch.cuda.synchronize()
     barrier(world)
     t_ms = allmax(world, e0.elapsed_time(e1))
-    prof = ieti.ieti_profile_read(ctx)
-    ieti.ieti_profile(ctx, False)
+    prof_pcg = ieti.ieti_profile_read(ctx)["pcg_vec"]
     launches = ieti.ieti_launch_count(ctx) - l0
-    chosen_err = (torch.linalg.norm(a - a_ref) / nref).item()
+    chosen_err = rel_err(a)
     ms_per_step = t_ms / args.steps
     value = t_ms / 1e3 / (args.steps * world)      # seconds per solved problem, whole job
+    chosen_solve_s = float(np.median([i.ms_total for i in infos])) / 1e3
+
+    # ---- per-class breakdown: a separate pass with events around every launch group
+    ieti.ieti_profile(ctx, True)
+    nprof = 2
+    for _ in range(nprof):
+        step()
+    prof = ieti.ieti_profile_read(ctx)
+    ieti.ieti_profile(ctx, False)
 
     # ---- end to end through the C ABI with host buffers (parameters in, field out)
     nu_host = torch.tensor(prob.nu, dtype=torch.float64).pin_memory()
@@ -255,37 +289,41 @@ def ours(args):
     bytes_W = sum(n * n for n in sub_nI) * 4 + sum(n * p_ for n, p_ in zip(sub_nI, sub_nP)) * 4
     bytes_S = sum(n * n for n in sub_nI) * 4
     bytes_vec = 2 * m_r * 8
-    roof = None
+    its_total = sum(i.iterations for i in infos)
+    per_it = bytes_W + bytes_S + 12 * bytes_vec
+    hbm = peaks.get("hbm_gbs", 6787.6)
+    pcg_roof = None
+    if prof_pcg[1]:
+        achieved = per_it * its_total / (prof_pcg[0] / 1e3) / 1e9
+        pcg_roof = {"kernel": "k_pcg_stream<float,1,true> (persistent PCG on the streamed products)",
+                    "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                    "frac": round(achieved / hbm, 4), "traffic": None, "bytes_per_iteration": per_it,
+                    "iterations": its_total, "launches": int(prof_pcg[1]),
+                    "avg_launch_ms": round(prof_pcg[0] / prof_pcg[1], 4),
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback"}
     if dom == "syrk_update":
-        flops = syrk_flops(sub_n) * args.steps
+        flops = syrk_flops(sub_n) * nprof
         achieved = flops / (prof[dom][0] / 1e3) / 1e12
         peak = 152 * 128 * 2 * 2.07e9 / 1e12     # FP32 FMA lanes x 2 flops x max SM clock
         roof = {"kernel": "k_syrk2 (128x128 register-blocked trailing update of the FP32 Cholesky)", "bound": "alu",
                 "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
-    elif dom == "pcg_vec":
-        # k_pcg_stream: per iteration one pass over W (+ Phi_I^T rows) and one over S
-        its_total = sum(i.iterations for i in infos)
-        per_it = bytes_W + bytes_S + 12 * bytes_vec
-        achieved = per_it * its_total / (prof[dom][0] / 1e3) / 1e9
-        peak = peaks.get("hbm_gbs", 6787.6)
-        roof = {"kernel": "k_pcg_stream<float,1,true> (persistent PCG on the streamed products)", "bound": "hbm",
-                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": None, "bytes_per_iteration": per_it, "iterations": its_total}
+    elif dom == "pcg_vec" and pcg_roof:
+        roof = pcg_roof
     else:
-        roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"),
-                "unit": "GB/s", "frac": None, "traffic": None}
-    # ieti_apply_F roofline (algorithmic bytes: FP32 W_k and Phi_I^T rows + vectors)
+        roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
+                "traffic": None}
+    # ieti_apply_F roofline (algorithmic bytes: FP32 W_k and Phi_I^T rows + vectors);
+    # W (66 MB) fits in the 129 MB L2, so only the flushed figure is an HBM number
     bytes32 = bytes_W + bytes_vec
-    hbm = peaks.get("hbm_gbs", 6787.6)
     apply_roof = {"bound": "hbm", "bytes_per_apply": bytes32, "peak": hbm, "unit": "GB/s",
-                  "achieved_gbs_l2_warm": round(bytes32 * apply32 / 1e9, 1),
-                  "frac_l2_warm": round(bytes32 * apply32 / 1e9 / hbm, 3),
                   "achieved_gbs_l2_cold": round(bytes32 * apply32_cold / 1e9, 1),
                   "frac_l2_cold": round(bytes32 * apply32_cold / 1e9 / hbm, 3),
+                  "l2_resident_gbs": round(bytes32 * apply32 / 1e9, 1),
                   "note": "whole call (u scatter + streamed product + gather with the coarse solve); "
-                          "cold = 256 MB buffer written before each apply"}
+                          "cold = 256 MB buffer written before each apply; l2_resident = back-to-back applies "
+                          "with the operator in L2 (not an HBM figure)"}
 
     out = {
         "metric": METRIC, "value": round(value, 5), "unit": "s", "higher_is_better": False,
@@ -298,16 +336,20 @@ def ours(args):
                    "l2": "each step writes > 10 GB (assembly of the dense blocks): inputs larger than L2",
                    "parallelism": f"replicas x{world}"},
         "chosen": {"pcg_iterations": infos[-1].iterations, "refinement_steps": infos[-1].refinement_steps,
-                   "field_residual": infos[-1].global_relres, "rel_err_vs_fp64_ref": chosen_err,
-                   "kappa": round(infos[-1].kappa, 2)},
-        "plain_fp64": {"s": round(plain_s, 4), "solve_only_s": round(plain_solve_s, 4),
-                       "pcg_iterations": info64.iterations, "rel_err_vs_fp64_ref": plain_err},
-        "chosen_vs_plain_speedup": round(plain_s / (ms_per_step / 1e3), 3),
-        "apply_F_per_s": {"fp32_ops_l2_warm": round(apply32, 1), "fp32_ops_l2_cold": round(apply32_cold, 1),
-                          "fp64_ops_l2_warm": round(apply64, 1), "fp64_ops_l2_cold": round(apply64_cold, 1)},
+                   "refinement_steps_all": [i.refinement_steps for i in infos],
+                   "field_residual": infos[-1].global_relres, "rel_err_vs_oracle": chosen_err,
+                   "solve_only_s": round(chosen_solve_s, 4), "kappa": round(infos[-1].kappa, 2)},
+        "plain_fp64": {"s": round(plain_ms / 1e3, 4), "solve_only_s": round(plain_solve_s, 4),
+                       "tol_interface": plain_tol, "pcg_iterations": info64.iterations,
+                       "rel_err_vs_oracle": plain_err},
+        "chosen_vs_plain_speedup": round(plain_ms / ms_per_step, 3),
+        "chosen_vs_plain_solve_only_speedup": round(plain_solve_s / chosen_solve_s, 3),
+        "apply_F_per_s": {"fp32_ops_l2_cold": round(apply32_cold, 1), "fp32_ops_l2_resident": round(apply32, 1),
+                          "fp64_ops_l2_cold": round(apply64_cold, 1), "fp64_ops_l2_resident": round(apply64, 1)},
         "apply_F_roofline": apply_roof,
-        "kernel_ms": {k: round(v[0] / args.steps, 3) for k, v in prof.items() if v[1]},
+        "kernel_ms": {k: round(v[0] / nprof, 3) for k, v in prof.items() if v[1]},
         "roofline": roof,
+        "pcg_roofline": pcg_roof,
         "e2e": {"value": round(e2e_s, 5), "unit": "s", "h2d_bytes_per_step": int(prob.nu.nbytes),
                 "d2h_bytes_per_step": int(a_host.numel() * 8)},
         "gpu_launches": int(launches),
@@ -411,7 +453,7 @@ def cpu_sample(pcg_iters):
     t_sol = (time.perf_counter() - t0) / 10
     nsub = prob.nsub
     est = (t_topo + nsub * t_asm + 2 * nsub * t_fac + (pcg_iters * 2 + 2) * nsub * t_sol)
-    return {"value": round(est, 2), "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+    return {"value": round(est, 2), "unit": "s", "cores": os.cpu_count(), "kind": "oracle", "extrapolated": True,
             "sample": (f"subdomain 0 of {nsub}: assembly of its {len(pats)} patches {t_asm:.2f} s, SuperLU "
                        f"of K_rr ({Krr.shape[0]} rows) {t_fac:.2f} s, local solve {t_sol * 1e3:.1f} ms; "
                        f"extrapolated to {nsub} subdomains x (assembly + 2 factorisations) + "

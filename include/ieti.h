@@ -87,7 +87,10 @@ typedef struct {
   int n_source_params;
   int nrhs;                    /* load cases, 1 .. 64 */
   int affine;                  /* 1 if every patch map is an axis-aligned affine
-                                  map (enables the Kronecker assembly path) */
+                                  map (enables the Kronecker assembly path; the
+                                  library checks it: weights 1 and control points
+                                  at the scaled Greville abscissae, else
+                                  IETI_ERR_INVALID_ARG); 0 for any other map */
 } ieti_problem_desc;
 
 typedef struct ieti_ctx ieti_ctx;
@@ -154,8 +157,8 @@ ieti_status ieti_assemble(ieti_ctx* ctx, void* stream);
  * S_Pi = -F (F of Eq. (7)) in FP64 and its Cholesky factor; the local
  * interface operators (K_rr^-1)_II = S_rIrI^-1. Errors: SINGULAR_LOCAL (a
  * non-positive pivot; the subdomain id is in the message), STATE (not
- * assembled), TIMEOUT or CUDA (a bounded device wait of the interface
- * products or of the W and Phi solves gave up). Synchronises the stream. */
+ * assembled), TIMEOUT (a bounded device wait of the interface products or of
+ * the W and Phi solves gave up), CUDA. Synchronises the stream. */
 ieti_status ieti_factor(ieti_ctx* ctx, ieti_precision prec, void* stream);
 
 /* Eq. (7): y = F_DP lam with F_DP = W - G F^-1 G^T = B_r K_rr^-1 B_r^T
@@ -180,15 +183,47 @@ ieti_status ieti_apply_precond(ieti_ctx* ctx, const double* r_dev, double* z_dev
  * when <= 0) or 8 refinement steps; each inner PCG then stops at
  * max(tol, 1e-3) on the first step and max(tol, 3e-3) on the corrections,
  * since a refinement step with FP32 operators cannot reduce the error by much
- * more than that anyway. Errors of the single-column sweeps' bounded waits
- * return CUDA. lam0_dev: m_r x nrhs initial multipliers or
- * NULL for zero. a_dev: nedge x nrhs output field (Dirichlet and tree DOFs are
+ * more than that anyway. lam0_dev: m_r x nrhs initial multipliers or
+ * NULL for zero (INVALID_ARG if it holds NaN or infinite values). a_dev: nedge x nrhs output field (Dirichlet and tree DOFs are
  * zero). lam_dev: optional m_r x nrhs output of the final multipliers.
  * info: optional host struct. Synchronises the stream. Errors: STATE,
- * NO_CONVERGENCE (info still filled, a_dev holds the last iterate). */
+ * INVALID_ARG, NO_CONVERGENCE (info still filled, a_dev holds the last
+ * iterate), TIMEOUT (a bounded wait of the triangular sweeps or of the
+ * streamed products gave up; the context stays usable). */
 ieti_status ieti_solve(ieti_ctx* ctx, const double* lam0_dev, double tol, int maxit,
                        double tol_field, double* a_dev, double* lam_dev,
                        ieti_solve_info* info, void* stream);
+
+/* Reference fields of ieti_eval_B. */
+typedef enum {
+  IETI_BREF_NONE = 0,   /* no reference: only the norms of B */
+  IETI_BREF_SINE = 1    /* B_ref = s curl(sin pi y sin pi z, sin pi x sin pi z, sin pi x sin pi y)
+                           = s pi (sin pi x (cos pi y - cos pi z), sin pi y (cos pi z - cos pi x),
+                           sin pi z (cos pi x - cos pi y)), one amplitude s per load case: the
+                           exact flux of IETI_SOURCE_SINE with amplitude s when nu = 1 */
+} ieti_bref_kind;
+
+/* Sec. 3: the magnetic flux density B = curl a and the error
+ * eps_B = sqrt(sum_k ||B_ref - B||^2_L2(Omega^(k))) of fields a, evaluated on
+ * the device at the p+1 Gauss points per direction per knot span of every
+ * element (the assembly's rule), with the covariant Piola map
+ * B = DF curl_hat(a) / det DF and the measure |det DF| dxi.
+ *   a_dev        nedge x nrhs FP64 device array in the global edge numbering;
+ *                every entry is used (Dirichlet and tree edges included), so
+ *                any field of the discrete space can be evaluated
+ *   nrhs         1 .. 64 columns
+ *   ref_kind     ieti_bref_kind; ref_amp_host: nrhs amplitudes (host), used
+ *                unless ref_kind is IETI_BREF_NONE
+ *   nB2_host     npatch x nrhs (patch fastest): ||B||^2_L2 over each patch
+ *   err2_host    npatch x nrhs: ||B_ref - B||^2_L2 over each patch, or NULL
+ *                (sum over the patches of subdomain k: the k-th term of eps_B^2)
+ *   B_dev        optional (NULL): B at the Gauss points, nelem x (p+1)^3 x 3
+ *                per column (elements patch by patch, spans with direction 0
+ *                fastest; Gauss points x fastest; then the 3 components)
+ * Synchronises the stream. Errors: STATE (host-only context), INVALID_ARG. */
+ieti_status ieti_eval_B(ieti_ctx* ctx, const double* a_dev, int nrhs, int ref_kind,
+                        const double* ref_amp_host, double* nB2_host, double* err2_host,
+                        double* B_dev, void* stream);
 
 /* Sizes of the problem and of the device data. */
 ieti_status ieti_query(const ieti_ctx* ctx, ieti_sizes* out);
@@ -227,8 +262,27 @@ ieti_status ieti_interface_rhs(ieti_ctx* ctx, double* b_dev, void* stream);
 /* Number of kernel launches this context has issued so far. */
 int64_t ieti_launch_count(const ieti_ctx* ctx);
 
+/* Testing aids for the failure paths (the paper has no counterpart; faults
+ * are injected from the host, no device code is made to fault):
+ *   IETI_DEBUG_WAIT_POLLS   poll limit of the progress-counter waits of the
+ *                           dependency-driven triangular sweeps (value >= 0
+ *                           polls of about 0.1 us; < 0 restores the default
+ *                           2^22). A wait that runs out sets the context's
+ *                           error flag and lets the launch finish; the call
+ *                           then returns IETI_ERR_TIMEOUT.
+ *   IETI_DEBUG_PIVOT_FAULT  subdomain whose K_rr gets a negative first diagonal
+ *                           entry in the factor buffer at every following
+ *                           ieti_factor, which then returns
+ *                           IETI_ERR_SINGULAR_LOCAL naming that subdomain
+ *                           (value < 0 switches it off).
+ * Errors: INVALID_ARG (unknown setting, subdomain out of range), STATE. */
+enum { IETI_DEBUG_WAIT_POLLS = 1, IETI_DEBUG_PIVOT_FAULT = 2 };
+ieti_status ieti_debug_set(ieti_ctx* ctx, int what, int64_t value);
+
 /* Per-kernel-class device timing with CUDA events recorded around each launch
- * group on the launching stream (enable = 1) or off (0); resets the totals.
+ * group on the launching stream (enable = 1), around the groups of some
+ * classes only (enable > 1: class c is timed if bit c + 1 of enable is set),
+ * or off (0); resets the totals.
  * Classes, in order: 0 assembly of K, 1 assembly of j, 2 diagonal-block
  * Cholesky, 3 panel triangular solve, 4 trailing symmetric update, 5 forward
  * substitution sweeps, 6 backward substitution sweeps, 7 local products with
@@ -258,17 +312,20 @@ const char* ieti_last_error(const ieti_ctx* ctx);
  * Computes y = sum_k B_k^T diag(w_k) M_k diag(w_k) B_k x, i.e. for each
  * subdomain k: u = w_k .* x[dual_k]; t = M_k u; y[dual_k] += w_k .* t.
  *   nsub        number of subdomains, 1..4096
- *   nI_host     host array: interface block size nI_k of each subdomain
+ *   nI_host     host array: interface block size nI_k >= 0 of each subdomain
+ *               (read during the call only)
  *   M_dev       device FP64: the symmetric blocks M_k, each nI_k x nI_k
  *               column-major, concatenated in subdomain order
  *   dual_dev    device int32: multiplier index (0 .. m-1) of every local
- *               interface DOF, concatenated in subdomain order
+ *               interface DOF, concatenated in subdomain order; an index
+ *               outside [0, m) is a caller error and its entry is skipped
  *   weight_dev  device FP64: weight w of every local interface DOF (same order)
  *   m, nrhs     multipliers and columns; x_dev, y_dev are m x nrhs FP64
  *               column-major, not aliased; y_dev is overwritten
- * With M_k = S_rIrI^(k) and w_k = sign * rho-scaling weight this is the
- * Dirichlet preconditioner of Eq. (10); with M_k = S_rIrI^(k)-1 and w_k = sign
- * it is the local part of the F-apply.
+ * Two uses: with M_k the interface Schur complement S_rIrI^(k) and w_k the
+ * sign of each multiplier times its scaling weight this is the Dirichlet
+ * preconditioner; with M_k = (K_rr^(k)^-1)_II (the inverse of S_rIrI^(k)) and
+ * w_k the signs it is the local part of the F-apply, B_r K_rr^-1 B_r^T x.
  * Limits and errors: sum_k nI_k * nrhs must not exceed 4,177,920 (the scratch
  * minus the descriptor area); larger requests return IETI_ERR_INVALID_ARG with a
  * message on stderr, as do bad arguments. IETI_ERR_CUDA on a CUDA error.

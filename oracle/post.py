@@ -20,12 +20,13 @@ def sine_B(X, amp=1.0):
                                 np.sin(pi * z) * (np.cos(pi * x) - np.cos(pi * y))], -1)
 
 
-def flux_l2(prob, mesh, a, B_exact=None, nq=None, rhs=0):
+def flux_l2(prob, mesh, a, B_exact=None, nq=None, rhs=0, patches=None):
     """Returns (||B_num||_L2, ||B_exact - B_num||_L2) for load case ``rhs``;
-    B_num = DF curl_hat(a) / det DF at the quadrature points."""
+    B_num = DF curl_hat(a) / det DF at the quadrature points. ``patches``
+    restricts both norms to those patches (default: the whole domain)."""
     nb2 = 0.0
     err2 = 0.0
-    for q in range(prob.npatch_total):
+    for q in (range(prob.npatch_total) if patches is None else patches):
         for gids, val, curl, X, DF, wts in dz._patch_element_loop(prob, mesh, q, nq=nq):
             det = np.linalg.det(DF)
             ch = np.einsum("iqa,i->qa", curl, a[gids, rhs])

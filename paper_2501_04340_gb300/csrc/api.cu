@@ -62,6 +62,54 @@ void compute_scaling(Ctx* c, std::vector<double>& scale) {
   }
 }
 
+// true if every patch map is an axis-aligned affine map: unit weights and
+// control point (i, j, k) of each patch at (x0 + L0 g_i, y0 + L1 g_j, z0 + L2 g_k)
+// with g the Greville abscissae of the patch's knot vectors (the only control
+// nets of an open uniform knot vector that give such a map)
+bool nets_are_boxes(const Mesh& m, const std::vector<double>& ctrl, std::string& why) {
+  if (m.per0) {
+    why = "a periodic direction cannot be an affine box";
+    return false;
+  }
+  const int p = m.p;
+  for (int q = 0; q < m.npatch(); ++q) {
+    int a[3];
+    m.patch_abc(q, a);
+    std::vector<double> g[3];
+    int lo[3], cnt[3];
+    for (int d = 0; d < 3; ++d) {
+      const int n = m.nspan[d][a[d]];
+      lo[d] = m.start[d][a[d]];
+      cnt[d] = n + p;
+      for (int i = 0; i < n + p; ++i) {
+        double acc = 0;
+        for (int l = i + 1; l <= i + p; ++l) acc += (l <= p) ? 0.0 : (l >= n + p ? 1.0 : (double)(l - p) / n);
+        g[d].push_back(acc / p);
+      }
+    }
+    auto X = [&](int i, int j, int k, int r) {
+      return ctrl[(((size_t)(lo[2] + k) * m.N[1] + (lo[1] + j)) * m.N[0] + (lo[0] + i)) * 4 + r];
+    };
+    double x0[3] = {X(0, 0, 0, 0), X(0, 0, 0, 1), X(0, 0, 0, 2)};
+    double L[3] = {X(cnt[0] - 1, 0, 0, 0) - x0[0], X(0, cnt[1] - 1, 0, 1) - x0[1], X(0, 0, cnt[2] - 1, 2) - x0[2]};
+    const double tol = 1e-12 * std::max({std::fabs(L[0]), std::fabs(L[1]), std::fabs(L[2]), std::fabs(x0[0]),
+                                         std::fabs(x0[1]), std::fabs(x0[2])});
+    for (int k = 0; k < cnt[2]; ++k)
+      for (int j = 0; j < cnt[1]; ++j)
+        for (int i = 0; i < cnt[0]; ++i) {
+          const double want[3] = {x0[0] + L[0] * g[0][i], x0[1] + L[1] * g[1][j], x0[2] + L[2] * g[2][k]};
+          bool ok = X(i, j, k, 3) == 1.0;
+          for (int r = 0; r < 3; ++r) ok = ok && std::fabs(X(i, j, k, r) - want[r]) <= tol;
+          if (!ok) {
+            why = "patch " + std::to_string(q) + " is not an axis-aligned affine box (control point (" +
+                  std::to_string(i) + "," + std::to_string(j) + "," + std::to_string(k) + "))";
+            return false;
+          }
+        }
+  }
+  return true;
+}
+
 void compute_gq(Ctx* c) {
   // per patch nu * L_c^2 / (L0 L1 L2) from the control net (axis-aligned affine maps)
   const Mesh& m = c->mesh;
@@ -122,6 +170,14 @@ ieti_status build(Ctx* c, const ieti_problem_desc* desc, bool device) {
       return IETI_ERR_INVALID_ARG;
     }
   c->ctrl.assign(desc->ctrl_host, desc->ctrl_host + (size_t)m.nnode * 4);
+  if (c->affine) {
+    // the Kronecker assembly is exact only for boxes: check the claim
+    std::string why;
+    if (!nets_are_boxes(m, c->ctrl, why)) {
+      c->err = "affine = 1 but " + why;
+      return IETI_ERR_INVALID_ARG;
+    }
+  }
   c->src.assign(desc->source_params_host, desc->source_params_host + desc->n_source_params);
   if (c->src.empty()) c->src.push_back(0.0);
   for (int q = 0; q < np; ++q)
@@ -272,9 +328,6 @@ ieti_status build(Ctx* c, const ieti_problem_desc* desc, bool device) {
 
   c->host_only = !device;
   if (!device) return IETI_OK;
-  c->no_coop = std::getenv("IETI_NO_COOP") != nullptr;
-  c->coop_trsv = !c->no_coop && std::getenv("IETI_COOP_TRSV") != nullptr;
-  c->dep_sweeps = !c->no_coop && std::getenv("IETI_NO_DEP_SWEEP") == nullptr;
   c->syrk_tc = std::getenv("IETI_SYRK_TC") != nullptr;
   c->autotune = std::getenv("IETI_NO_AUTOTUNE") == nullptr;
   {
@@ -282,6 +335,7 @@ ieti_status build(Ctx* c, const ieti_problem_desc* desc, bool device) {
     IETI_CUDA_TRY(c, cudaGetDevice(&dev));
     IETI_CUDA_TRY(c, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     TRY(assemble_kernel_attrs(c, optin));
+    TRY(flux_kernel_attrs(c, optin));
     TRY(solve_kernel_attrs(c, optin));
     TRY(factor_kernel_attrs(c));
     TRY(syrk_tc_attrs(c));
@@ -304,6 +358,13 @@ ieti_status build(Ctx* c, const ieti_problem_desc* desc, bool device) {
   TRY(upload(c, &c->d_patch_code_off, pc_off));
   TRY(upload(c, &c->d_sub_of_patch, c->sub_of_patch));
   TRY(upload(c, &c->d_elem, c->elem_host));
+  {
+    std::vector<int64_t> eoff(np + 1, 0);
+    for (int q = 0; q < np; ++q) eoff[q + 1] = eoff[q] + m.nelem(q);
+    TRY(upload(c, &c->d_patch_eoff, eoff));
+    TRY(dalloc(c, &c->d_flux_out, (size_t)2 * np * MAX_RHS));
+    TRY(dalloc(c, &c->d_flux_amp, MAX_RHS));
+  }
   for (int d = 0; d < 3; ++d) {
     TRY(upload(c, &c->d_tabN[d], c->tab.N[d]));
     TRY(upload(c, &c->d_tabdN[d], c->tab.dN[d]));
@@ -543,6 +604,40 @@ ieti_status ieti_interface_rhs(ieti_ctx* x, double* b, void* stream) {
   return interface_rhs(c, c->jr, c->jp, b, c->wc[1], c->nrhs, (cudaStream_t)stream);
 }
 
+ieti_status ieti_eval_B(ieti_ctx* x, const double* a, int nrhs, int ref_kind, const double* amp, double* nB2,
+                        double* err2, double* Bq, void* stream) {
+  if (!x) return IETI_ERR_INVALID_ARG;
+  Ctx* c = &x->c;
+  if (c->host_only) {
+    c->err = "context was created without a device";
+    return IETI_ERR_STATE;
+  }
+  if (!a || !nB2 || nrhs < 1 || nrhs > MAX_RHS || ref_kind < IETI_BREF_NONE || ref_kind > IETI_BREF_SINE ||
+      (ref_kind != IETI_BREF_NONE && !amp)) {
+    c->err = "ieti_eval_B: bad arguments";
+    return IETI_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t need = c->nelem * nrhs * 2;
+  if (need > c->flux_part_cap) {
+    double* p = nullptr;
+    TRY(dalloc(c, &p, need));
+    c->d_flux_part = p;
+    c->flux_part_cap = need;
+  }
+  std::vector<double> amp_h(MAX_RHS, 0.0);
+  if (ref_kind != IETI_BREF_NONE) std::copy(amp, amp + nrhs, amp_h.begin());
+  IETI_CUDA_TRY(c, cudaMemcpyAsync(c->d_flux_amp, amp_h.data(), sizeof(double) * MAX_RHS, cudaMemcpyHostToDevice, st));
+  TRY(eval_flux(c, a, nrhs, ref_kind, c->d_flux_amp, c->d_flux_part, c->d_flux_out, Bq, st));
+  const int np = c->mesh.npatch();
+  std::vector<double> out((size_t)2 * np * nrhs);
+  IETI_CUDA_TRY(c, cudaMemcpyAsync(out.data(), c->d_flux_out, sizeof(double) * out.size(), cudaMemcpyDeviceToHost, st));
+  IETI_CUDA_TRY(c, cudaStreamSynchronize(st));
+  std::copy(out.begin(), out.begin() + (size_t)np * nrhs, nB2);
+  if (err2) std::copy(out.begin() + (size_t)np * nrhs, out.end(), err2);
+  return IETI_OK;
+}
+
 ieti_status ieti_query(const ieti_ctx* x, ieti_sizes* o) {
   if (!x || !o) return IETI_ERR_INVALID_ARG;
   const Ctx* c = &x->c;
@@ -674,11 +769,35 @@ ieti_status ieti_get_coarse(ieti_ctx* x, double* out, int64_t cap) {
 
 int64_t ieti_launch_count(const ieti_ctx* x) { return x ? x->c.launches : 0; }
 
+ieti_status ieti_debug_set(ieti_ctx* x, int what, int64_t value) {
+  if (!x) return IETI_ERR_INVALID_ARG;
+  Ctx* c = &x->c;
+  if (c->host_only) {
+    c->err = "context was created without a device";
+    return IETI_ERR_STATE;
+  }
+  switch (what) {
+    case IETI_DEBUG_WAIT_POLLS:
+      return dep_set_poll_limit(c, value < 0 ? (1LL << 22) : (long long)value);
+    case IETI_DEBUG_PIVOT_FAULT:
+      if (value >= c->nsub) {
+        c->err = "ieti_debug_set: subdomain out of range";
+        return IETI_ERR_INVALID_ARG;
+      }
+      c->fault_pivot_sub = value < 0 ? -1 : (int)value;
+      return IETI_OK;
+    default:
+      c->err = "ieti_debug_set: unknown setting";
+      return IETI_ERR_INVALID_ARG;
+  }
+}
+
 ieti_status ieti_profile(ieti_ctx* x, int enable) {
   if (!x) return IETI_ERR_INVALID_ARG;
   Ctx* c = &x->c;
   prof_collect(c);
   c->prof.on = enable != 0;
+  c->prof.mask = enable > 1 ? (unsigned)(((unsigned)enable >> 1) & ((1u << PROF_NCAT) - 1)) : ~0u;
   for (int i = 0; i < PROF_NCAT; ++i) {
     c->prof.ms[i] = 0;
     c->prof.calls[i] = 0;

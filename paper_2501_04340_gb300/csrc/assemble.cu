@@ -51,6 +51,8 @@ struct AsmParams {
   double* Kpp;
   double* jr;
   double* jp;
+  int64_t eoff[3];    // first edge id of each direction (global numbering)
+  int64_t eext[3][3]; // index extents of each direction's edge block
 };
 
 // ---------------------------------------------------------------------------
@@ -558,6 +560,10 @@ static AsmParams make_params(Ctx* c) {
   P.Kpp = c->Kpp64;
   P.jr = c->jr;
   P.jp = c->jp;
+  for (int d = 0; d < 3; ++d) {
+    P.eoff[d] = c->mesh.off[d];
+    for (int e = 0; e < 3; ++e) P.eext[d][e] = c->mesh.ext[d][e];
+  }
   return P;
 }
 
@@ -642,6 +648,184 @@ ieti_status assemble_all(Ctx* c, cudaStream_t st) {
   }
   if (r == IETI_OK && c->d_geo) c->geo_ready = true;
   return r;
+}
+
+// ---------------------------------------------------------------------------
+// B = curl a at the Gauss points and its L2 norms (Sec. 3 error norm)
+// ---------------------------------------------------------------------------
+
+constexpr int FLUX_CG = 8;   // load cases per pass of the flux kernel
+
+struct FluxArgs {
+  const double* a;       // nedge x nrhs, global edge numbering
+  int64_t nedge;
+  int nrhs;
+  int ref_kind;          // ieti_bref_kind
+  const double* amp;     // nrhs amplitudes of the reference field
+  double* part;          // per element and load case: |B|^2 and |B_ref - B|^2 integrals
+  double* Bq;            // optional: B at the Gauss points (nelem x NQ3 x 3 per load case)
+};
+
+// reference flux density curl(amp (sin pi y sin pi z, sin pi x sin pi z, sin pi x sin pi y))
+__device__ inline void sine_flux(const double X[3], double amp, double B[3]) {
+  const double pi = 3.14159265358979323846;
+  const double sx = sin(pi * X[0]), sy = sin(pi * X[1]), sz = sin(pi * X[2]);
+  const double cx = cos(pi * X[0]), cy = cos(pi * X[1]), cz = cos(pi * X[2]);
+  B[0] = amp * pi * sx * (cy - cz);
+  B[1] = amp * pi * sy * (cz - cx);
+  B[2] = amp * pi * sz * (cx - cy);
+}
+
+// one CTA per element: the field's coefficients of the element functions, the
+// reference curls of those functions at the Gauss points (two nonzero
+// components each), B = DF curl_hat / det DF, and the element integrals
+// sum_q w |det DF| |B|^2 (and |B_ref - B|^2) per load case
+template <int PD>
+__global__ void __launch_bounds__(256) k_elem_B(AsmParams P, FluxArgs F) {
+  constexpr int NQ = PD + 1, NQ3 = NQ * NQ * NQ, NF = ElemShared<PD>::NF;
+  constexpr int NFD = PD * (PD + 1) * (PD + 1);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ElemShared<PD>& sh = *reinterpret_cast<ElemShared<PD>*>(smem_raw);
+  double* C = reinterpret_cast<double*>(smem_raw + sizeof(ElemShared<PD>));   // NF x NQ3 x 2
+  double* coef = C + (size_t)NF * NQ3 * 2;                                     // NF x FLUX_CG
+  double* acc = coef + (size_t)NF * FLUX_CG;                                   // NQ3 x FLUX_CG x 2
+  __shared__ int64_t gid[NF];
+  const int e = blockIdx.x;
+  int q, k;
+  elem_setup<PD>(P, e, sh, q, k);
+  const int tid = threadIdx.x;
+  int a3[3];
+  patch_abc_d(P, q, a3);
+  int st[3] = {P.start[0][a3[0]], P.start[1][a3[1]], P.start[2][a3[2]]};
+  int s[3] = {P.elem[4 * e + 1], P.elem[4 * e + 2], P.elem[4 * e + 3]};
+  for (int f = tid; f < NF; f += blockDim.x) {
+    const int d = f / NFD, r = f % NFD;
+    int ext[3] = {PD + 1, PD + 1, PD + 1};
+    ext[d] = PD;
+    int64_t ix[3] = {st[0] + s[0] + r % ext[0], st[1] + s[1] + (r / ext[0]) % ext[1],
+                     st[2] + s[2] + r / (ext[0] * ext[1])};
+    if (P.per0) ix[0] %= P.N0;
+    gid[f] = P.eoff[d] + ix[0] + P.eext[d][0] * (ix[1] + P.eext[d][1] * ix[2]);
+  }
+  for (int t = tid; t < NF * NQ3; t += blockDim.x) {
+    int f = t / NQ3, qq = t % NQ3;
+    int x = qq % NQ, y = (qq / NQ) % NQ, z = qq / (NQ * NQ);
+    int d = f / NFD, r = f % NFD;
+    int ext[3] = {PD + 1, PD + 1, PD + 1};
+    ext[d] = PD;
+    int la = r % ext[0], lb = (r / ext[0]) % ext[1], lc = r / (ext[0] * ext[1]);
+    double c0, c1;
+    if (d == 0) {        // components 1, 2
+      c0 = sh.D[0][la][x] * sh.N[1][lb][y] * sh.dN[2][lc][z];
+      c1 = -sh.D[0][la][x] * sh.dN[1][lb][y] * sh.N[2][lc][z];
+    } else if (d == 1) { // components 0, 2
+      c0 = -sh.N[0][la][x] * sh.D[1][lb][y] * sh.dN[2][lc][z];
+      c1 = sh.dN[0][la][x] * sh.D[1][lb][y] * sh.N[2][lc][z];
+    } else {             // components 0, 1
+      c0 = sh.N[0][la][x] * sh.dN[1][lb][y] * sh.D[2][lc][z];
+      c1 = -sh.dN[0][la][x] * sh.N[1][lb][y] * sh.D[2][lc][z];
+    }
+    C[(f * NQ3 + qq) * 2 + 0] = c0;
+    C[(f * NQ3 + qq) * 2 + 1] = c1;
+  }
+  __syncthreads();
+  for (int c0 = 0; c0 < F.nrhs; c0 += FLUX_CG) {
+    const int ng = min(FLUX_CG, F.nrhs - c0);
+    for (int t = tid; t < NF * ng; t += blockDim.x) {
+      const int f = t % NF, col = t / NF;
+      coef[f * FLUX_CG + col] = F.a[gid[f] + F.nedge * (c0 + col)];
+    }
+    __syncthreads();
+    for (int t = tid; t < NQ3 * ng; t += blockDim.x) {
+      const int qq = t % NQ3, col = t / NQ3;
+      double ch[3] = {0, 0, 0};
+      for (int f = 0; f < NF; ++f) {
+        const int d = f / NFD;
+        const double v = coef[f * FLUX_CG + col];
+        const double* cf = C + (f * NQ3 + qq) * 2;
+        ch[d == 0 ? 1 : 0] += v * cf[0];
+        ch[d == 2 ? 1 : 2] += v * cf[1];
+      }
+      const double* Df = sh.DF[qq];
+      const double det = sh.det[qq];
+      double B[3];
+      for (int r = 0; r < 3; ++r) B[r] = (Df[r * 3 + 0] * ch[0] + Df[r * 3 + 1] * ch[1] + Df[r * 3 + 2] * ch[2]) / det;
+      const double w = sh.wt[qq] * fabs(det);
+      acc[(qq * FLUX_CG + col) * 2 + 0] = w * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+      double e2 = 0;
+      if (F.ref_kind == IETI_BREF_SINE) {
+        double R[3];
+        sine_flux(sh.X[qq], F.amp[c0 + col], R);
+        e2 = w * ((R[0] - B[0]) * (R[0] - B[0]) + (R[1] - B[1]) * (R[1] - B[1]) + (R[2] - B[2]) * (R[2] - B[2]));
+      }
+      acc[(qq * FLUX_CG + col) * 2 + 1] = e2;
+      if (F.Bq) {
+        double* o = F.Bq + (((int64_t)e * NQ3 + qq) * 3) + (int64_t)gridDim.x * NQ3 * 3 * (c0 + col);
+        o[0] = B[0]; o[1] = B[1]; o[2] = B[2];
+      }
+    }
+    __syncthreads();
+    // element sums in a fixed order
+    if (tid < 2 * ng) {
+      const int col = tid / 2, which = tid % 2;
+      double v = 0;
+      for (int qq = 0; qq < NQ3; ++qq) v += acc[(qq * FLUX_CG + col) * 2 + which];
+      F.part[((int64_t)e * F.nrhs + c0 + col) * 2 + which] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// per patch and load case: sums of the element integrals of its elements
+// (contiguous, [eoff[q], eoff[q+1])) in element order
+__global__ void k_flux_patch(const double* part, const int64_t* eoff, int npatch, int nrhs, double* out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npatch * nrhs * 2) return;
+  const int which = t % 2, col = (t / 2) % nrhs, q = t / (2 * nrhs);
+  double v = 0;
+  for (int64_t e = eoff[q]; e < eoff[q + 1]; ++e) v += part[(e * nrhs + col) * 2 + which];
+  out[((int64_t)which * nrhs + col) * npatch + q] = v;
+}
+
+template <int PD>
+static size_t flux_smem() {
+  constexpr int NQ3 = (PD + 1) * (PD + 1) * (PD + 1), NF = ElemShared<PD>::NF;
+  return sizeof(ElemShared<PD>) + sizeof(double) * ((size_t)NF * NQ3 * 2 + (size_t)NF * FLUX_CG + NQ3 * FLUX_CG * 2);
+}
+
+ieti_status flux_kernel_attrs(Ctx* c, int smem_max) {
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_elem_B<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_elem_B<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_elem_B<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  return IETI_OK;
+}
+
+// B = curl a for nrhs fields; out = [npatch x nrhs] squared norms, then the
+// squared errors against the reference field (device, 2 npatch nrhs values)
+ieti_status eval_flux(Ctx* c, const double* a, int nrhs, int ref_kind, const double* amp_dev, double* part,
+                      double* out, double* Bq, cudaStream_t st) {
+  AsmParams P = make_params(c);
+  FluxArgs F;
+  F.a = a;
+  F.nedge = c->mesh.nedge;
+  F.nrhs = nrhs;
+  F.ref_kind = ref_kind;
+  F.amp = amp_dev;
+  F.part = part;
+  F.Bq = Bq;
+  const unsigned ne = (unsigned)c->nelem;
+  switch (c->mesh.p) {
+    case 1: k_elem_B<1><<<ne, 256, flux_smem<1>(), st>>>(P, F); break;
+    case 2: k_elem_B<2><<<ne, 256, flux_smem<2>(), st>>>(P, F); break;
+    case 3: k_elem_B<3><<<ne, 256, flux_smem<3>(), st>>>(P, F); break;
+    default: c->err = "degree p must be 1, 2 or 3"; return IETI_ERR_INVALID_ARG;
+  }
+  IETI_LAUNCH_CHECK(c);
+  const int npatch = c->mesh.npatch();
+  const int nt = npatch * nrhs * 2;
+  k_flux_patch<<<(nt + 255) / 256, 256, 0, st>>>(part, c->d_patch_eoff, npatch, nrhs, out);
+  IETI_LAUNCH_CHECK(c);
+  return IETI_OK;
 }
 
 // dst <- src on the listed 64 x 64 tiles (k, I, J) of the K_rr blocks

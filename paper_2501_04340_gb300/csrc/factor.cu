@@ -553,13 +553,6 @@ ieti_status tri_solve(Ctx* c, const SubDev* d_sd, int nsub, int max_nblk, int ma
                       cudaStream_t st, int which = SWEEP_BOTH, const unsigned char* lf = nullptr,
                       const int64_t* lfo = nullptr) {
   if (max_ncol <= 0) return IETI_OK;
-  if (!c->no_coop) {
-    // one persistent launch per sweep (single column, or any width when opted
-    // in); the per-panel launches below serve devices without cooperative launch
-    ieti_status r =
-        tri_solve_coop<T>(c, d_sd, nsub, max_nblk, min_b0, max_ncol, d_desc, L, Linv, B, Y, X, which, st);
-    if (r != IETI_ERR_STATE) return r;
-  }
   const bool one = max_ncol == 1;   // single right-hand side: one-column kernels
   const unsigned ctiles = (unsigned)ceil_div(max_ncol, NB);
   const unsigned rtiles = (unsigned)std::max<int64_t>(1, ceil_div(max_rows, NB));
@@ -852,6 +845,12 @@ static ieti_status factor_t(Ctx* c, cudaStream_t st) {
   } else if ((r = convert_tiles<T>(c, c->d_ltile_list, c->n_ltiles, c->K64, L, st)) != IETI_OK) {
     return r;
   }
+  if (c->fault_pivot_sub >= 0 && c->fault_pivot_sub < c->nsub) {
+    // testing aid: a negative first diagonal entry, found by the pivot check below
+    const T v = (T)-1;
+    IETI_CUDA_TRY(c, cudaMemcpyAsync(L + c->sd_host[c->fault_pivot_sub].A, &v, sizeof(T), cudaMemcpyHostToDevice, st));
+    IETI_CUDA_TRY(c, cudaStreamSynchronize(st));
+  }
   IETI_CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
   IETI_CUDA_TRY(c, cudaMemsetAsync(c->d_dep_err, 0, sizeof(int), st));   // bounded waits of the W and Phi solves
   const FactorPlan* plan = &c->fplan[sizeof(T) == 4 ? 1 : 0];
@@ -931,7 +930,7 @@ static ieti_status factor_t(Ctx* c, cudaStream_t st) {
   IETI_CUDA_TRY(c, cudaStreamSynchronize(st));
   if (c->h_err[1]) {
     c->err = "a wait of the W or Phi solves timed out";
-    return IETI_ERR_CUDA;
+    return IETI_ERR_TIMEOUT;
   }
   return IETI_OK;
 }
@@ -993,7 +992,7 @@ ieti_status factor_all(Ctx* c, cudaStream_t st) {
 // sweeps on nrhs-column r-vectors with the range descriptors built at creation
 template <typename T>
 ieti_status rv_solve(Ctx* c, int range, int which, T* B, T* Y, T* X, cudaStream_t st) {
-  if (c->nrhs == 1 && c->dep_sweeps) {
+  if (c->nrhs == 1) {
     const ieti_status r = dep_sweep<T>(c, range, which, B, Y, X, st);
     if (r != IETI_ERR_STATE) return r;
   }

@@ -43,6 +43,7 @@ enum ProfCat {
 
 struct Prof {
   bool on = false;
+  unsigned mask = ~0u;     // classes timed (bit c: class c); launch groups of unnamed class only with all bits
   std::vector<cudaEvent_t> pool;
   size_t used = 0;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
@@ -64,13 +65,6 @@ struct Ctx;
 constexpr int SWEEP_FWD = 1;    // L Y = B (B is overwritten)
 constexpr int SWEEP_BWD = 2;    // L^T X = Y (Y is overwritten)
 constexpr int SWEEP_BOTH = 3;
-// persistent (cooperative) triangular solves L Y = B, L^T X = Y over all
-// subdomains, one launch per sweep; returns IETI_ERR_STATE if the device cannot run it
-template <typename T>
-ieti_status tri_solve_coop(Ctx* c, const SubDev* d_sd, int nsub, int max_nblk, int min_b0, int max_ncol,
-                           const SolveDesc* d_desc, const T* L, const T* Linv, T* B, T* Y, T* X, int which,
-                           cudaStream_t st);
-
 // local DOF: direction d and global control-grid index (i, j, k) of its edge;
 // d = -1 for padding
 struct DofDev {
@@ -145,8 +139,13 @@ struct Ctx {
   std::vector<double> gq_host;           // per patch: nu * L_c^2 / vol (affine path)
   std::vector<int> elem_host;            // per element: q, s0, s1, s2
   int64_t nelem = 0;
-  double* d_geo = nullptr;               // per element and Gauss point: X, weighted adj(DF) (assembly)
+  double* d_geo = nullptr;               // per element and Gauss point: X, weight |det DF| DF^-1 (assembly)
   bool geo_ready = false, geo_failed = false;
+  int64_t* d_patch_eoff = nullptr;       // per patch: its first element (npatch + 1 entries)
+  double* d_flux_part = nullptr;         // flux evaluation: per element and load case, 2 integrals
+  int64_t flux_part_cap = 0;
+  double* d_flux_out = nullptr;          // per patch and load case: 2 squared norms
+  double* d_flux_amp = nullptr;          // reference amplitudes (MAX_RHS)
 
   // device memory
   std::vector<DeviceBuf> allocs;
@@ -214,12 +213,12 @@ struct Ctx {
   int32_t* d_ktile_col = nullptr;        // block columns J with a nonzero tile
   int* d_ktile_base = nullptr;           // per subdomain: its first block row
   // dependency-driven single-column sweeps (sweep_dep.cu)
-  bool dep_sweeps = true;                // IETI_NO_DEP_SWEEP=1: per-panel barrier sweeps instead
   int2* d_dep_tasks[2][2] = {};          // [range][forward, backward]: (subdomain, block) in run order
   int dep_ntask[2][2] = {};
   unsigned long long* d_dep_prog = nullptr;   // per subdomain: epoch << 20 | blocks published
   unsigned long long dep_epoch = 0;
-  int* d_dep_err = nullptr;              // set when a sweep wait times out
+  int* d_dep_err = nullptr;              // set when a sweep wait times out; the poll limit at byte 8
+  int fault_pivot_sub = -1;              // testing aid: subdomain whose next factorisation gets a negative pivot
   McPlan mcplan[2];                      // [0] W solve, [1] Phi solve
   bool autotune = true;                  // IETI_NO_AUTOTUNE=1: keep the default tile shapes
   bool tuned[2] = {false, false};        // [fp32] tile shapes of the streamed products chosen
@@ -276,8 +275,6 @@ struct Ctx {
   bool syrk_tc = false;                  // IETI_SYRK_TC=1: FP32 trailing update with split TF32 tensor-core products
 
   bool assembled = false, factored = false, host_only = false;
-  bool no_coop = false;                  // IETI_NO_COOP=1: per-phase launches instead of the persistent PCG
-  bool coop_trsv = false;                // IETI_COOP_TRSV=1: persistent substitution sweeps (slower on GB300)
   ieti_precision prec = IETI_FP64;
 };
 
@@ -302,9 +299,11 @@ struct Ctx {
     }                                                                              \
   } while (0)
 
-// profiling marks (no-ops unless enabled)
-inline cudaEvent_t prof_begin(Ctx* c, cudaStream_t st) {
+// profiling marks (no-ops unless enabled); `cat` names the class at the start
+// of the group where only some classes are timed
+inline cudaEvent_t prof_begin(Ctx* c, cudaStream_t st, int cat = -1) {
   if (!c->prof.on) return nullptr;
+  if (cat >= 0 ? !(c->prof.mask & (1u << cat)) : c->prof.mask != ~0u) return nullptr;
   if (c->prof.used + 2 > c->prof.pool.size()) {
     for (int i = 0; i < 256; ++i) {
       cudaEvent_t e;
@@ -327,6 +326,11 @@ void prof_collect(Ctx* c);
 
 // assembly
 ieti_status assemble_all(Ctx* c, cudaStream_t s);
+// B = curl a at the Gauss points of every element and its squared L2 norms per
+// patch (out: npatch x nrhs norms, then npatch x nrhs errors to the reference)
+ieti_status flux_kernel_attrs(Ctx* c, int smem_max);
+ieti_status eval_flux(Ctx* c, const double* a, int nrhs, int ref_kind, const double* amp_dev, double* part,
+                      double* out, double* Bq, cudaStream_t st);
 ieti_status assemble_kernel_attrs(Ctx* c, int smem_max);
 ieti_status solve_kernel_attrs(Ctx* c, int smem_max);
 // factorisation
@@ -351,6 +355,8 @@ ieti_status build_symbolic(Ctx* c, cudaStream_t s);
 // IETI_ERR_STATE if the device cannot run them
 ieti_status dep_sweep_attrs(Ctx* c);
 ieti_status dep_sweep_alloc(Ctx* c);
+// poll limit of the dependency waits (a testing aid; default 2^22 polls)
+ieti_status dep_set_poll_limit(Ctx* c, long long polls);
 template <typename T>
 ieti_status dep_sweep(Ctx* c, int range, int which, const T* B, T* Y, T* X, cudaStream_t s);
 template <typename T>

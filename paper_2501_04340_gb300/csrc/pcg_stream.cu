@@ -482,7 +482,7 @@ ieti_status launch_pcg_stream(Ctx* c, PcgStreamArgs A, int stages_max, size_t ub
   IETI_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, STREAM_THREADS, smem));
   if (per_sm < 1 || PW.grid > per_sm * c->sm_count) return IETI_ERR_STATE;
   void* args[] = {(void*)&A};
-  cudaEvent_t p0 = prof_begin(c, st);
+  cudaEvent_t p0 = prof_begin(c, st, PROF_PCG);
   IETI_CUDA_TRY(c, cudaLaunchCooperativeKernel((void*)kern, dim3(PW.grid), dim3(STREAM_THREADS), args, smem, st));
   prof_end(c, PROF_PCG, p0, st);
   IETI_LAUNCH_CHECK(c);

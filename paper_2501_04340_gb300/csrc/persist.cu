@@ -1,13 +1,6 @@
-// Persistent (cooperative) kernels: one launch runs a whole sequence of
-// dependent steps over all subdomains, with a grid-wide barrier between steps
-// instead of a kernel boundary.
-//
-// k_trsv_coop: forward substitution L Y = B and backward substitution
-// L^T X = Y with the blocked Cholesky factors of all subdomains. Step b of the
-// forward sweep solves the 64 x 64 diagonal block (through its stored inverse)
-// and updates the rows below it; step b of the backward sweep solves block b
-// and updates the rows above it. Work items (subdomain, column tile, row or
-// column chunk) of a step are spread over the co-resident grid.
+// Persistent (cooperative) PCG with per-item local products: the PCG loop when
+// the streamed products do not apply (for example a coarse space too large
+// for the per-CTA caches of the streamed form).
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -19,353 +12,6 @@
 namespace cg = cooperative_groups;
 
 namespace ieti {
-
-constexpr int CO_RC = 256;   // rows below the panel per forward work item
-constexpr int CO_BC = 256;   // rows above the panel per backward work item
-
-template <typename T, int CT>
-__device__ void fwd_item(const SubDev& s, const SolveDesc& d, int b, int ct, int ch, const T* L, const T* Linv,
-                         T* B, T* Y, T (*Li)[NB + 1], T (*vb)[CT], T (*sol)[CT]) {
-  const int tid = threadIdx.x;
-  const int c0 = ct * CT;
-  const int nc = min(CT, d.ncol - c0);
-  const int row0 = (b - d.b0) * NB;
-  const int rows = s.n - d.b0 * NB;
-  T* Bk = B + d.boff;
-  __syncthreads();   // shared buffers of the previous item are free
-  const T* Lb = Linv + s.linv + (int64_t)b * NB * NB;
-  for (int t = tid; t < NB * NB; t += blockDim.x) Li[t % NB][t / NB] = Lb[t];
-  for (int t = tid; t < NB * CT; t += blockDim.x) {
-    int i = t % NB, cc = t / NB;
-    vb[i][cc] = (cc < nc) ? Bk[row0 + i + (int64_t)d.ldb * (c0 + cc)] : (T)0;
-  }
-  __syncthreads();
-  for (int t = tid; t < NB * CT; t += blockDim.x) {
-    int i = t % NB, cc = t / NB;
-    T acc = 0;
-    for (int l = 0; l <= i; ++l) acc += Li[i][l] * vb[l][cc];
-    sol[i][cc] = acc;
-  }
-  __syncthreads();
-  if (ch == 0) {
-    T* Yk = Y + d.boff;
-    for (int t = tid; t < NB * nc; t += blockDim.x) {
-      int i = t % NB, cc = t / NB;
-      Yk[row0 + i + (int64_t)d.ldb * (c0 + cc)] = sol[i][cc];
-    }
-  }
-  const int rend = min(rows, row0 + NB + (ch + 1) * CO_RC);
-  for (int r = row0 + NB + ch * CO_RC + tid; r < rend; r += blockDim.x) {
-    T acc[CT];
-#pragma unroll
-    for (int cc = 0; cc < CT; ++cc) acc[cc] = 0;
-    const T* Lcol = L + s.A + (d.b0 * NB + r) + (int64_t)s.n * (b * NB);
-#pragma unroll 8
-    for (int l = 0; l < NB; ++l) {
-      T lv = Lcol[(int64_t)s.n * l];
-#pragma unroll
-      for (int cc = 0; cc < CT; ++cc) acc[cc] += lv * sol[l][cc];
-    }
-    for (int cc = 0; cc < nc; ++cc) Bk[r + (int64_t)d.ldb * (c0 + cc)] -= acc[cc];
-  }
-}
-
-template <typename T, int CT>
-__device__ void bwd_item(const SubDev& s, const SolveDesc& d, int b, int ct, int ch, const T* L, const T* Linv,
-                         T* Y, T* X, T (*Li)[NB + 1], T (*vb)[CT], T (*sol)[CT]) {
-  const int tid = threadIdx.x;
-  const int c0 = ct * CT;
-  const int nc = min(CT, d.ncol - c0);
-  const int row0 = (b - d.b0) * NB;
-  T* Yk = Y + d.boff;
-  __syncthreads();
-  const T* Lb = Linv + s.linv + (int64_t)b * NB * NB;
-  for (int t = tid; t < NB * NB; t += blockDim.x) Li[t % NB][t / NB] = Lb[t];
-  for (int t = tid; t < NB * CT; t += blockDim.x) {
-    int i = t % NB, cc = t / NB;
-    vb[i][cc] = (cc < nc) ? Yk[row0 + i + (int64_t)d.ldb * (c0 + cc)] : (T)0;
-  }
-  __syncthreads();
-  for (int t = tid; t < NB * CT; t += blockDim.x) {
-    int i = t % NB, cc = t / NB;
-    T acc = 0;
-    for (int l = i; l < NB; ++l) acc += Li[l][i] * vb[l][cc];
-    sol[i][cc] = acc;
-  }
-  __syncthreads();
-  if (ch == 0) {
-    T* Xk = X + d.boff;
-    for (int t = tid; t < NB * nc; t += blockDim.x) {
-      int i = t % NB, cc = t / NB;
-      Xk[row0 + i + (int64_t)d.ldb * (c0 + cc)] = sol[i][cc];
-    }
-  }
-  const int warp = tid / 32, lane = tid % 32;
-  const int cend = min((ch + 1) * CO_BC, row0);
-  for (int ccol = ch * CO_BC + warp; ccol < cend; ccol += 8) {
-    const T* Lc = L + s.A + (int64_t)b * NB + (int64_t)s.n * (d.b0 * NB + ccol);
-    T l0 = Lc[lane], l1 = Lc[lane + 32];
-    for (int cc = 0; cc < nc; ++cc) {
-      T v = l0 * sol[lane][cc] + l1 * sol[lane + 32][cc];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) Yk[ccol + (int64_t)d.ldb * (c0 + cc)] -= v;
-    }
-  }
-}
-
-template <typename T, int CT>
-__global__ void __launch_bounds__(256) k_trsv_coop(const SubDev* sd, const SolveDesc* dsc, int nsub, int max_nblk,
-                                                   int min_b0, const T* L, const T* Linv, T* B, T* Y, T* X) {
-  cg::grid_group grid = cg::this_grid();
-  __shared__ T Li[NB][NB + 1];
-  __shared__ T vb[NB][CT];
-  __shared__ T sol[NB][CT];
-  for (int b = min_b0; b < max_nblk; ++b) {
-    int item = blockIdx.x, base = 0;
-    for (int k = 0; k < nsub; ++k) {
-      const SubDev s = sd[k];
-      const SolveDesc d = dsc[k];
-      if (b < d.b0 || b >= s.nblk || d.ncol <= 0) continue;
-      const int below = (s.n - d.b0 * NB) - (b - d.b0) * NB - NB;
-      const int nch = below > 0 ? (below + CO_RC - 1) / CO_RC : 1;
-      const int cnt = nch * ((d.ncol + CT - 1) / CT);
-      for (; item < base + cnt; item += gridDim.x) {
-        const int loc = item - base;
-        fwd_item<T, CT>(s, d, b, loc / nch, loc % nch, L, Linv, B, Y, Li, vb, sol);
-      }
-      base += cnt;
-    }
-    grid.sync();
-  }
-  for (int b = max_nblk - 1; b >= min_b0; --b) {
-    int item = blockIdx.x, base = 0;
-    for (int k = 0; k < nsub; ++k) {
-      const SubDev s = sd[k];
-      const SolveDesc d = dsc[k];
-      if (b < d.b0 || b >= s.nblk || d.ncol <= 0) continue;
-      const int above = (b - d.b0) * NB;
-      const int nch = above > 0 ? (above + CO_BC - 1) / CO_BC : 1;
-      const int cnt = nch * ((d.ncol + CT - 1) / CT);
-      for (; item < base + cnt; item += gridDim.x) {
-        const int loc = item - base;
-        bwd_item<T, CT>(s, d, b, loc / nch, loc % nch, L, Linv, Y, X, Li, vb, sol);
-      }
-      base += cnt;
-    }
-    grid.sync();
-  }
-}
-
-template <typename T, int CT>
-static ieti_status launch_coop(Ctx* c, const SubDev* d_sd, int nsub, int max_nblk, int min_b0,
-                               const SolveDesc* d_desc, const T* L, const T* Linv, T* B, T* Y, T* X,
-                               cudaStream_t st) {
-  static int grid_cache[2] = {0, 0};
-  int& gsz = grid_cache[sizeof(T) == 8 ? 1 : 0];
-  (void)gsz;
-  int dev = 0, sms = 0, per_sm = 0, coop = 0;
-  IETI_CUDA_TRY(c, cudaGetDevice(&dev));
-  IETI_CUDA_TRY(c, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-  if (!coop) return IETI_ERR_STATE;
-  IETI_CUDA_TRY(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  IETI_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trsv_coop<T, CT>, 256, 0));
-  if (per_sm < 1) return IETI_ERR_STATE;
-  dim3 grid(sms * per_sm);
-  void* args[] = {(void*)&d_sd, (void*)&d_desc, (void*)&nsub, (void*)&max_nblk, (void*)&min_b0,
-                  (void*)&L, (void*)&Linv, (void*)&B, (void*)&Y, (void*)&X};
-  cudaEvent_t p0 = prof_begin(c, st);
-  IETI_CUDA_TRY(c, cudaLaunchCooperativeKernel((void*)k_trsv_coop<T, CT>, grid, dim3(256), args, 0, st));
-  prof_end(c, PROF_FWD, p0, st);
-  IETI_LAUNCH_CHECK(c);
-  return IETI_OK;
-}
-
-// ---------------------------------------------------------------------------
-// Single-column sweeps as one persistent launch each: the panel loop runs
-// inside the kernel with a grid barrier per panel. Every CTA that owns work in
-// a subdomain forms that panel's 64-entry solution itself (from the stored
-// inverse of the diagonal block), so one barrier per panel suffices. A thread
-// issues all 64 loads of its row (forward) or column (backward) before the
-// panel's solution is needed.
-// ---------------------------------------------------------------------------
-
-constexpr int SW_ROWS = 256;   // rows (forward) or columns (backward) per work item
-
-template <typename T>
-__global__ void __launch_bounds__(256, 1) k_sweep1_fwd(const SubDev* sd, const SolveDesc* dsc, int nsub,
-                                                       int max_nblk, int min_b0, const T* L, const T* Linv, T* B,
-                                                       T* Y) {
-  cg::grid_group grid = cg::this_grid();
-  __shared__ T bb[NB], y[NB];
-  const int tid = threadIdx.x;
-  for (int b = min_b0; b < max_nblk; ++b) {
-    int item = blockIdx.x, base = 0;
-    int yk = -1;   // subdomain whose panel solution y currently holds
-    for (int k = 0; k < nsub; ++k) {
-      const SubDev s = sd[k];
-      const SolveDesc d = dsc[k];
-      if (b < d.b0 || b >= s.nblk || d.ncol <= 0) continue;
-      const int rows = s.n - d.b0 * NB, row0 = (b - d.b0) * NB;
-      const int below = rows - row0 - NB;
-      const int cnt = below > 0 ? (below + SW_ROWS - 1) / SW_ROWS : 1;
-      for (; item < base + cnt; item += gridDim.x) {
-        const int ch = item - base;
-        T* Bk = B + d.boff;
-        const int r = row0 + NB + ch * SW_ROWS + tid;
-        const bool valid = r < rows;
-        T lv[NB];
-        const T* Lrow = L + s.A + (d.b0 * NB + r) + (int64_t)s.n * (b * NB);
-#pragma unroll
-        for (int l = 0; l < NB; ++l) lv[l] = valid ? Lrow[(int64_t)s.n * l] : (T)0;
-        if (yk != k) {
-          // y_b = Linv_b b_b, once per subdomain and panel in this CTA
-          const T* Lb = Linv + s.linv + (int64_t)b * NB * NB;
-          const int i = tid / 4, part = tid % 4;
-          T li[16];
-#pragma unroll
-          for (int q = 0; q < 16; ++q) li[q] = Lb[i + NB * (part * 16 + q)];   // zero above the diagonal
-          __syncthreads();   // the previous item is done with bb and y
-          if (tid < NB) bb[tid] = Bk[row0 + tid];
-          __syncthreads();
-          T acc = 0;
-#pragma unroll
-          for (int q = 0; q < 16; ++q) acc += li[q] * bb[part * 16 + q];
-          acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-          acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-          if (part == 0) {
-            y[i] = acc;
-            if (ch == 0) Y[d.boff + row0 + i] = acc;
-          }
-          __syncthreads();
-          yk = k;
-        } else if (ch == 0 && tid < NB) {
-          Y[d.boff + row0 + tid] = y[tid];
-        }
-        if (valid) {
-          T u = 0;
-#pragma unroll
-          for (int l = 0; l < NB; ++l) u += lv[l] * y[l];
-          Bk[r] -= u;
-        }
-      }
-      base += cnt;
-    }
-    grid.sync();
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_sweep1_bwd(const SubDev* sd, const SolveDesc* dsc, int nsub,
-                                                       int max_nblk, int min_b0, const T* L, const T* Linv, T* Y,
-                                                       T* X) {
-  cg::grid_group grid = cg::this_grid();
-  using V2 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-  constexpr int VL = 16 / sizeof(T);
-  __shared__ T yb[NB], x[NB];
-  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  for (int b = max_nblk - 1; b >= min_b0; --b) {
-    int item = blockIdx.x, base = 0;
-    int xk = -1;   // subdomain whose panel solution x currently holds
-    for (int k = 0; k < nsub; ++k) {
-      const SubDev s = sd[k];
-      const SolveDesc d = dsc[k];
-      if (b < d.b0 || b >= s.nblk || d.ncol <= 0) continue;
-      const int row0 = (b - d.b0) * NB;
-      const int cnt = row0 > 0 ? (row0 + SW_ROWS - 1) / SW_ROWS : 1;
-      for (; item < base + cnt; item += gridDim.x) {
-        const int ch = item - base;
-        T* Yk = Y + d.boff;
-        // this thread's column: the 64 entries of row block b, contiguous
-        const int ccol = ch * SW_ROWS + tid;
-        const bool valid = ccol < row0;
-        V2 lv[NB / VL];
-        const V2* Lc = reinterpret_cast<const V2*>(L + s.A + (d.b0 * NB + row0) + (int64_t)s.n * (d.b0 * NB + ccol));
-#pragma unroll
-        for (int q = 0; q < NB / VL; ++q) {
-          if (valid) lv[q] = Lc[q];
-          else if constexpr (VL == 4) lv[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-          else lv[q] = make_double2(0.0, 0.0);
-        }
-        if (xk != k) {
-          // x_i = sum_{l >= i} Linv[l][i] y_l: warp w computes x_i for i = w, w + 8, ...
-          const T* Lb = Linv + s.linv + (int64_t)b * NB * NB;
-          __syncthreads();   // the previous item is done with yb and x
-          if (tid < NB) yb[tid] = Yk[row0 + tid];
-          __syncthreads();
-          for (int i = warp; i < NB; i += 8) {
-            T v = (lane >= i ? Lb[lane + NB * i] * yb[lane] : (T)0) +
-                  (lane + 32 >= i ? Lb[lane + 32 + NB * i] * yb[lane + 32] : (T)0);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) x[i] = v;
-          }
-          __syncthreads();
-          xk = k;
-        }
-        if (ch == 0 && tid < NB) X[d.boff + row0 + tid] = x[tid];
-        if (valid) {
-          T u = 0;
-#pragma unroll
-          for (int q = 0; q < NB / VL; ++q) {
-            if constexpr (VL == 4) {
-              u += lv[q].x * x[4 * q] + lv[q].y * x[4 * q + 1] + lv[q].z * x[4 * q + 2] + lv[q].w * x[4 * q + 3];
-            } else {
-              u += lv[q].x * x[2 * q] + lv[q].y * x[2 * q + 1];
-            }
-          }
-          Yk[ccol] -= u;
-        }
-      }
-      base += cnt;
-    }
-    grid.sync();
-  }
-}
-
-template <typename T>
-static ieti_status launch_sweep1(Ctx* c, const SubDev* d_sd, int nsub, int max_nblk, int min_b0,
-                                 const SolveDesc* d_desc, const T* L, const T* Linv, T* B, T* Y, T* X,
-                                 int which, cudaStream_t st) {
-  int dev = 0, sms = 0, pf = 0, pb = 0, coop = 0;
-  IETI_CUDA_TRY(c, cudaGetDevice(&dev));
-  IETI_CUDA_TRY(c, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-  if (!coop) return IETI_ERR_STATE;
-  IETI_CUDA_TRY(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  IETI_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pf, k_sweep1_fwd<T>, 256, 0));
-  IETI_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pb, k_sweep1_bwd<T>, 256, 0));
-  const int per_sm = std::min(std::min(pf, pb), 4);
-  if (per_sm < 1) return IETI_ERR_STATE;
-  const dim3 grid(sms * per_sm);
-  if (which & SWEEP_FWD) {
-    void* fa[] = {(void*)&d_sd, (void*)&d_desc, (void*)&nsub, (void*)&max_nblk, (void*)&min_b0,
-                  (void*)&L, (void*)&Linv, (void*)&B, (void*)&Y};
-    cudaEvent_t p0 = prof_begin(c, st);
-    IETI_CUDA_TRY(c, cudaLaunchCooperativeKernel((void*)k_sweep1_fwd<T>, grid, dim3(256), fa, 0, st));
-    prof_end(c, PROF_FWD, p0, st);
-    IETI_LAUNCH_CHECK(c);
-  }
-  if (which & SWEEP_BWD) {
-    void* ba[] = {(void*)&d_sd, (void*)&d_desc, (void*)&nsub, (void*)&max_nblk, (void*)&min_b0,
-                  (void*)&L, (void*)&Linv, (void*)&Y, (void*)&X};
-    cudaEvent_t p0 = prof_begin(c, st);
-    IETI_CUDA_TRY(c, cudaLaunchCooperativeKernel((void*)k_sweep1_bwd<T>, grid, dim3(256), ba, 0, st));
-    prof_end(c, PROF_BWD, p0, st);
-    IETI_LAUNCH_CHECK(c);
-  }
-  return IETI_OK;
-}
-
-template <typename T>
-ieti_status tri_solve_coop(Ctx* c, const SubDev* d_sd, int nsub, int max_nblk, int min_b0, int max_ncol,
-                           const SolveDesc* d_desc, const T* L, const T* Linv, T* B, T* Y, T* X, int which,
-                           cudaStream_t st) {
-  if (max_ncol <= 0) return IETI_OK;
-  if (max_ncol == 1) return launch_sweep1<T>(c, d_sd, nsub, max_nblk, min_b0, d_desc, L, Linv, B, Y, X, which, st);
-  // multi-column: per-panel launches unless opted in (the opt-in kernel runs both sweeps)
-  if (!c->coop_trsv || which != SWEEP_BOTH) return IETI_ERR_STATE;
-  return launch_coop<T, 8>(c, d_sd, nsub, max_nblk, min_b0, d_desc, L, Linv, B, Y, X, st);
-}
 
 // ---------------------------------------------------------------------------
 // k_pcg_coop: the PCG iteration on F_DP lam = b with the Dirichlet
@@ -703,7 +349,7 @@ static ieti_status launch_pcg(Ctx* c, PcgArgs A, cudaStream_t st) {
   if (per_sm < 1) return IETI_ERR_STATE;
   const int grid = std::min(sms * per_sm, PCG_COOP_MAX_GRID);
   void* args[] = {(void*)&A};
-  cudaEvent_t p0 = prof_begin(c, st);
+  cudaEvent_t p0 = prof_begin(c, st, PROF_PCG);
   IETI_CUDA_TRY(c, cudaLaunchCooperativeKernel((void*)k_pcg_coop<T, CT>, dim3(grid), dim3(256), args, smem, st));
   prof_end(c, PROF_PCG, p0, st);
   IETI_LAUNCH_CHECK(c);
@@ -756,10 +402,5 @@ ieti_status pcg_coop(Ctx* c, double* lam, double* r, double* z, double* p, doubl
   return fp32 ? launch_pcg<float, 8>(c, A, st) : launch_pcg<double, 8>(c, A, st);
 }
 
-template ieti_status tri_solve_coop<float>(Ctx*, const SubDev*, int, int, int, int, const SolveDesc*, const float*,
-                                           const float*, float*, float*, float*, int, cudaStream_t);
-template ieti_status tri_solve_coop<double>(Ctx*, const SubDev*, int, int, int, int, const SolveDesc*,
-                                            const double*, const double*, double*, double*, double*, int,
-                                            cudaStream_t);
 
 }  // namespace ieti

@@ -309,6 +309,12 @@ __global__ void k_sub(double* r, const double* b, const double* y, int64_t n) {
     r[l] = b[l] - y[l];
 }
 
+// flag = 1 if any of the n values is NaN or infinite
+__global__ void k_flag_nonfinite(const double* x, int64_t n, int* flag) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite(x[i])) *flag = 1;
+}
+
 __global__ void k_add(double* a, const double* b, int64_t n) {
   for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x)
     a[l] += b[l];
@@ -762,7 +768,7 @@ static ieti_status pcg(Ctx* c, const double* b, double* lam, bool zero_start, do
   k_update_p<<<vg, 256, 0, st>>>(p, z, scal, m, 1);
   IETI_LAUNCH_CHECK(c);
   bool persistent = false;
-  if (!c->no_coop && nrhs <= 8) {
+  if (nrhs <= 8) {
     // the whole iteration loop in one cooperative launch: on the streamed
     // products if they apply, else with per-item local products
     ieti_status pr = pcg_stream(c, lam, r, z, p, q, tol2, maxit, fp32, st);
@@ -946,6 +952,21 @@ ieti_status solve_all(Ctx* c, const double* lam0, double tol, int maxit, double 
   IETI_CUDA_TRY(c, cudaEventCreate(&e1));
   IETI_CUDA_TRY(c, cudaEventRecord(e0, st));
   ieti_status r;
+  if (lam0) {
+    // an initial guess with NaN or infinite entries is refused before any work
+    IETI_CUDA_TRY(c, cudaMemsetAsync(c->wflag, 0, sizeof(int), st));
+    k_flag_nonfinite<<<304, 256, 0, st>>>(lam0, m * nrhs, c->wflag);
+    IETI_LAUNCH_CHECK(c);
+    int bad = 0;
+    IETI_CUDA_TRY(c, cudaMemcpyAsync(&bad, c->wflag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    IETI_CUDA_TRY(c, cudaStreamSynchronize(st));
+    if (bad) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      c->err = "the initial multipliers lam0 contain NaN or infinite values";
+      return IETI_ERR_INVALID_ARG;
+    }
+  }
   IETI_CUDA_TRY(c, cudaMemsetAsync(a, 0, sizeof(double) * ne * nrhs, st));
   IETI_CUDA_TRY(c, cudaMemsetAsync(c->wlam_acc, 0, sizeof(double) * m * nrhs, st));
   IETI_CUDA_TRY(c, cudaMemsetAsync(c->d_dep_err, 0, sizeof(int), st));
@@ -1009,7 +1030,7 @@ ieti_status solve_all(Ctx* c, const double* lam0, double tol, int maxit, double 
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->err = "a triangular-sweep wait timed out";
-    return IETI_ERR_CUDA;
+    return IETI_ERR_TIMEOUT;
   }
   float ms = 0;
   cudaEventElapsedTime(&ms, e0, e1);

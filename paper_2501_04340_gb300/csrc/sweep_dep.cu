@@ -33,7 +33,7 @@ namespace {
 
 constexpr int DEP_THREADS = 256;
 constexpr int DEP_EPOCH_SHIFT = 20;            // blocks per subdomain < 2^20
-constexpr long long DEP_SPIN_MAX = 1LL << 22;  // polls of about 0.1 us before giving up
+constexpr long long DEP_SPIN_MAX = 1LL << 22;  // default poll limit (polls of about 0.1 us)
 
 template <typename T>
 using Vec16 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
@@ -49,11 +49,13 @@ __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned l
 }
 
 // waits until *p >= need (bounded); on time-out, or once another wait has
-// timed out, records the error and returns so that the launch ends
+// timed out, records the error and returns so that the launch ends. err[0] is
+// the error flag; the poll limit is the 64-bit value at err + 2 (set by the host)
 __device__ unsigned long long dep_wait(const unsigned long long* p, unsigned long long need, int* err) {
   unsigned long long v = ld_acquire_u64(p);
+  const long long lim = v < need ? *reinterpret_cast<const volatile long long*>(err + 2) : 0;
   for (long long it = 0; v < need; ++it) {
-    if (it > DEP_SPIN_MAX || *(volatile int*)err) {
+    if (it >= lim || *(volatile int*)err) {
       atomicExch(err, 1);
       return need;
     }
@@ -438,6 +440,19 @@ ieti_status dep_sweep_attrs(Ctx* c) {
   return IETI_OK;
 }
 
+#define TRY_DEP(x)                   \
+  do {                               \
+    ieti_status r__ = (x);           \
+    if (r__ != IETI_OK) return r__;  \
+  } while (0)
+
+// poll limit of the dependency waits (polls of about 0.1 us each)
+ieti_status dep_set_poll_limit(Ctx* c, long long polls) {
+  const long long v = std::max(0LL, polls);
+  IETI_CUDA_TRY(c, cudaMemcpy(reinterpret_cast<char*>(c->d_dep_err) + 8, &v, sizeof(v), cudaMemcpyHostToDevice));
+  return IETI_OK;
+}
+
 // task tables of the r-vector sweeps (whole r range and r_I rows, forward and
 // backward), progress counters and the error flag
 ieti_status dep_sweep_alloc(Ctx* c) {
@@ -466,11 +481,13 @@ ieti_status dep_sweep_alloc(Ctx* c) {
   c->allocs.push_back({pg, sizeof(unsigned long long) * std::max(c->nsub, 1)});
   IETI_CUDA_TRY(c, cudaMemset(pg, 0, sizeof(unsigned long long) * std::max(c->nsub, 1)));
   c->d_dep_prog = pg;
+  // error flag (int) at offset 0, poll limit of the waits (int64) at offset 8
   int* e = nullptr;
-  IETI_CUDA_TRY(c, cudaMalloc(&e, sizeof(int)));
-  c->allocs.push_back({e, sizeof(int)});
-  IETI_CUDA_TRY(c, cudaMemset(e, 0, sizeof(int)));
+  IETI_CUDA_TRY(c, cudaMalloc(&e, 16));
+  c->allocs.push_back({e, 16});
+  IETI_CUDA_TRY(c, cudaMemset(e, 0, 16));
   c->d_dep_err = e;
+  TRY_DEP(dep_set_poll_limit(c, DEP_SPIN_MAX));
   c->dep_epoch = 0;
   return IETI_OK;
 }
@@ -480,7 +497,7 @@ ieti_status dep_sweep_alloc(Ctx* c) {
 template <typename T>
 ieti_status dep_mc_solve(Ctx* c, int slot, const std::vector<SolveDesc>& dh, const SolveDesc* dd, int which,
                          const T* B, T* Y, T* X, cudaStream_t st) {
-  if (!c->symb_ready || c->no_coop || !c->dep_sweeps) return IETI_ERR_STATE;
+  if (!c->symb_ready) return IETI_ERR_STATE;
   int dev = 0, coop = 0;
   IETI_CUDA_TRY(c, cudaGetDevice(&dev));
   IETI_CUDA_TRY(c, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));

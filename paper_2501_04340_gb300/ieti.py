@@ -64,6 +64,8 @@ _sig = {
     "ieti_apply_precond": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp]),
     "ieti_solve": (C.c_int, [_vp, _vp, C.c_double, C.c_int, C.c_double, _vp, _vp,
                              C.POINTER(ieti_solve_info), _vp]),
+    "ieti_eval_B": (C.c_int, [_vp, _vp, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                              C.POINTER(C.c_double), _vp, _vp]),
     "ieti_query": (C.c_int, [_vp, C.POINTER(ieti_sizes)]),
     "ieti_get_dofmap": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(C.c_int64), C.c_int64,
                                   C.POINTER(C.c_int64)]),
@@ -72,6 +74,7 @@ _sig = {
     "ieti_get_coarse": (C.c_int, [_vp, C.POINTER(C.c_double), C.c_int64]),
     "ieti_interface_rhs": (C.c_int, [_vp, _vp, _vp]),
     "ieti_launch_count": (C.c_int64, [_vp]),
+    "ieti_debug_set": (C.c_int, [_vp, C.c_int, C.c_int64]),
     "ieti_profile": (C.c_int, [_vp, C.c_int]),
     "ieti_profile_read": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]),
     "ieti_interface_product_noalloc": (C.c_int, [C.c_int, C.POINTER(C.c_int), _vp, _vp, _vp, C.c_int64, _vp,
@@ -146,7 +149,7 @@ class _Desc:
         d.source_params_host = self.src.ctypes.data_as(C.POINTER(C.c_double))
         d.n_source_params = len(self.src)
         d.nrhs = prob.nrhs
-        d.affine = 1 if getattr(prob, "affine", not prob.periodic0 and np.all(prob.ctrl[..., 3] == 1.0)) else 0
+        d.affine = 1 if prob.affine else 0
         self.desc = d
 
 
@@ -206,6 +209,26 @@ def ieti_interface_rhs(ctx, b, stream=None):
     _check(ctx, _lib.ieti_interface_rhs(ctx, _dptr(b), _stream(stream)))
 
 
+IETI_BREF_NONE = 0
+IETI_BREF_SINE = 1
+
+
+def ieti_eval_B(ctx, a, npatch, nrhs=None, ref_kind=IETI_BREF_NONE, ref_amp=None, B=None, stream=None):
+    """a: (nrhs, nedge) float64 CUDA tensor. Returns (nB2, err2) as (nrhs, npatch)
+    host arrays of squared L2 norms per patch (err2 is None without a reference);
+    B: optional CUDA tensor for the flux at the Gauss points."""
+    nr = a.shape[0] if nrhs is None else int(nrhs)
+    nB2 = np.zeros(nr * npatch, np.float64)
+    err2 = np.zeros(nr * npatch, np.float64) if ref_kind != IETI_BREF_NONE else None
+    amp = None if ref_amp is None else np.ascontiguousarray(ref_amp, np.float64)
+    _check(ctx, _lib.ieti_eval_B(ctx, _dptr(a), nr, int(ref_kind),
+                                 None if amp is None else amp.ctypes.data_as(C.POINTER(C.c_double)),
+                                 nB2.ctypes.data_as(C.POINTER(C.c_double)),
+                                 None if err2 is None else err2.ctypes.data_as(C.POINTER(C.c_double)),
+                                 _dptr(B), _stream(stream)))
+    return nB2.reshape(nr, npatch), (None if err2 is None else err2.reshape(nr, npatch))
+
+
 def ieti_query(ctx):
     s = ieti_sizes()
     _check(ctx, _lib.ieti_query(ctx, C.byref(s)))
@@ -240,12 +263,25 @@ def ieti_launch_count(ctx):
     return int(_lib.ieti_launch_count(ctx))
 
 
+IETI_DEBUG_WAIT_POLLS = 1
+IETI_DEBUG_PIVOT_FAULT = 2
+
+
+def ieti_debug_set(ctx, what, value):
+    _check(ctx, _lib.ieti_debug_set(ctx, int(what), int(value)))
+
+
 PROFILE_CLASSES = ["assemble_K", "assemble_j", "potrf_diag", "trsm_panel", "syrk_update", "trsv_fwd",
                    "trsv_bwd", "local_W", "local_S", "gather", "coarse", "pcg_vec", "residual", "other"]
 
 
-def ieti_profile(ctx, enable=True):
-    _check(ctx, _lib.ieti_profile(ctx, 1 if enable else 0))
+def ieti_profile(ctx, enable=True, classes=None):
+    """enable: time every class; classes: names of PROFILE_CLASSES to time alone."""
+    if classes is not None:
+        mode = sum(2 << PROFILE_CLASSES.index(n) for n in classes)
+    else:
+        mode = 1 if enable else 0
+    _check(ctx, _lib.ieti_profile(ctx, mode))
 
 
 def ieti_profile_read(ctx):

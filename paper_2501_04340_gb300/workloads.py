@@ -53,6 +53,7 @@ class Problem:
     source_kind: int
     source_params: np.ndarray   # float64, layout per kind (module docstring)
     nrhs: int
+    affine: bool = False        # every patch map is an axis-aligned affine map (a box)
 
     @property
     def npatch_total(self) -> int:
@@ -372,7 +373,7 @@ def unit_cube(p: int, patches: Tuple[int, int, int], spans, sub_of_patch=None, n
     return Problem(name=name, p=p, npatch=tuple(patches), nspan=[list(s) for s in spans],
                    periodic0=False, ctrl=ctrl, nu=np.asarray(nu, np.float64),
                    sub_of_patch=np.asarray(sub_of_patch, np.int32), source_kind=source_kind,
-                   source_params=np.asarray(source_params, np.float64), nrhs=nrhs)
+                   source_params=np.asarray(source_params, np.float64), nrhs=nrhs, affine=True)
 
 
 def cube8_p2n4(spans: int = 4, p: int = 2) -> Problem:

@@ -23,7 +23,9 @@ def test_library_exports_every_declared_symbol():
 CASES = [lambda: wl.cube8_p2n4(), lambda: wl.small_cases()[1], lambda: wl.small_cases()[2],
          lambda: wl.small_cases()[3], lambda: wl.cube64_p3n8_sub16(),
          lambda: wl.unit_cube(2, (4, 4, 2), [[1, 2, 1, 3], [2, 1, 1, 2], [2, 1]],
-                              sub_of_patch=wl.block_partition((4, 4, 2), (2, 2, 1)))]
+                              sub_of_patch=wl.block_partition((4, 4, 2), (2, 2, 1))),
+         lambda: wl.machine_annulus(n_ang=12, n_ax=1, spans=2, nrhs=2),
+         lambda: wl.machine_annulus(nrhs=1)]
 
 
 @pytest.mark.parametrize("make", CASES)
@@ -138,3 +140,21 @@ def test_uneven_partition_of_the_512_patch_cube():
         assert min(nV) > 0 and min(nI) > 0 and max(nI) == q["max_nI"]
     finally:
         ieti.ieti_destroy(ctx)
+
+
+def test_affine_flag_is_checked():
+    """The Kronecker assembly is exact only for axis-aligned boxes: a claim of
+    affine maps on any other control net is rejected, whatever the weights."""
+    box = wl.unit_cube(2, (2, 1, 1), [[2, 3], [2], [1]])
+    ieti.ieti_destroy(ieti.ieti_create_host(box))
+    bent = wl.unit_cube(2, (2, 1, 1), [[2, 3], [2], [1]])
+    bent.ctrl[1, 1, 2, 0] += 0.01          # one interior control point moved: unit weights, not a box
+    with pytest.raises(ieti.IetiError, match="INVALID_ARG.*affine"):
+        ieti.ieti_create_host(bent)
+    bent.affine = False
+    ieti.ieti_destroy(ieti.ieti_create_host(bent))
+    ring = wl.machine_annulus(n_ang=12, n_ax=1, spans=2, nrhs=1)
+    assert not ring.affine
+    ring.affine = True
+    with pytest.raises(ieti.IetiError, match="INVALID_ARG"):
+        ieti.ieti_create_host(ring)

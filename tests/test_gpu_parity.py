@@ -33,11 +33,32 @@ def _ragged():
                         nu=[1.0, 30.0, 2.0, 500.0], nrhs=2, source_params=[1.0, -2.0])
 
 
+def _cube32_p3n3_sub8():
+    """16 panels per subdomain, nu jumps up to 1e3, 8 subdomains of 2 x 2 x 1 patches."""
+    rng = np.random.default_rng(4)
+    return wl.unit_cube(3, (4, 4, 2), 3, sub_of_patch=wl.block_partition((4, 4, 2), (2, 2, 1)),
+                        nu=10.0 ** rng.uniform(0, 3, 32), name="cube32_p3n3_sub8", nrhs=2,
+                        source_params=[1.0, -0.5])
+
+
+def _cube18_p3_mixed():
+    """Mixed spans 3/4 per slab, uneven subdomains of 1 to 4 patches (up to 23 panels), nu jumps."""
+    rng = np.random.default_rng(6)
+    P = (3, 3, 2)
+    sub = np.array([min(a, 1) + 2 * (b // 2) + 4 * c for c in range(2) for b in range(3) for a in range(3)])
+    return wl.unit_cube(3, P, [[3, 4, 3], [4, 3, 4], [3, 4]], sub_of_patch=np.unique(sub, return_inverse=True)[1],
+                        nu=10.0 ** rng.uniform(0, 3, 18), name="cube18_p3_mixed", nrhs=1)
+
+
 CASES = {
     "cube8_p2n4": lambda: wl.cube8_p2n4(),
     "cube8_p1n2": lambda: wl.small_cases()[1],
     "cube12_p2_mixed": lambda: wl.small_cases()[3],
     "ragged_p3": _ragged,
+    "cube32_p3n3_sub8": _cube32_p3n3_sub8,
+    "cube18_p3_mixed": _cube18_p3_mixed,
+    # curved, periodic: the NURBS ring (exact 30-degree arcs), air / iron nu jump 1e3, slot currents
+    "ring24_p3n2": lambda: wl.machine_annulus(n_ang=12, n_ax=1, spans=2, nrhs=2),
 }
 
 _cache = {}
@@ -63,7 +84,13 @@ def rel(a, b):
 def test_assembly_blocks(ieti, name, affine):
     prob, mesh, topo, sysd, _ = oracle_case(name)
     prob = prob.with_params()
-    prob.affine = affine
+    if affine and not prob.affine:
+        # the Kronecker path is only for boxes: the library refuses the claim
+        prob.affine = True
+        with pytest.raises(ieti.IetiError, match="INVALID_ARG"):
+            ieti.ieti_create(prob)
+        return
+    prob.affine = bool(affine)
     ctx = ieti.ieti_create(prob)
     try:
         ieti.ieti_assemble(ctx)
@@ -182,33 +209,26 @@ def test_warm_start_with_exact_multipliers_needs_no_iteration(ieti):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_per_panel_launch_path_matches_persistent(ieti, prec, monkeypatch):
-    """The per-panel / per-phase launch path (devices without cooperative launch)
-    gives the same field and iteration count as the persistent kernels."""
+def test_many_load_cases_match_the_oracle(ieti, prec):
+    """Ten load cases at once take the per-phase PCG loop (more than eight
+    columns) and the barrier-synchronised multi-column sweeps; by linearity of
+    Eq. (3) in the source, column c equals amplitude_c times the oracle field of
+    the unit amplitude, to 1e-8."""
     prob, mesh, topo, sysd, a_m = oracle_case("cube12_p2_mixed")
-    out = []
-    for env in (None, "1"):
-        if env:
-            monkeypatch.setenv("IETI_NO_COOP", env)
-        else:
-            monkeypatch.delenv("IETI_NO_COOP", raising=False)
-        ctx = ieti.ieti_create(prob)
-        try:
-            ieti.ieti_assemble(ctx)
-            ieti.ieti_factor(ctx, prec)
-            a = torch.zeros((prob.nrhs, mesh.nedge), dtype=torch.float64, device="cuda")
-            info = ieti.ieti_solve(ctx, a, tol=1e-10, maxit=400, tol_field=1e-12 if prec else 0.0)
-            out.append((a.cpu().numpy().T, info.iterations))
-        finally:
-            ieti.ieti_destroy(ctx)
-    (a1, i1), (a2, i2) = out
-    # FP32 operators: the two paths sum the local products (and form W and Phi)
-    # in different orders, so the inner PCG runs at a loose tolerance stop at
-    # different iterations and the counts summed over the refinement steps may
-    # differ by up to a fifth; the field is compared at 1e-9 below
-    assert abs(i1 - i2) <= max(1, (0.2 if prec else 0.1) * i2)
-    assert np.linalg.norm(a1 - a2) <= 1e-9 * np.linalg.norm(a2)
-    assert np.linalg.norm(a1 - a_m) <= 1e-8 * np.linalg.norm(a_m)
+    amps = np.linspace(-2.0, 3.0, 10)
+    probn = prob.with_params(source_params=amps, nrhs=10)
+    ctx = ieti.ieti_create(probn)
+    try:
+        ieti.ieti_assemble(ctx)
+        ieti.ieti_factor(ctx, prec)
+        a = torch.zeros((10, mesh.nedge), dtype=torch.float64, device="cuda")
+        info = ieti.ieti_solve(ctx, a, tol=1e-11, maxit=400, tol_field=1e-12 if prec else 0.0)
+        assert info.converged == 1
+        ag = a.cpu().numpy().T
+        ref = a_m[:, :1] * amps[None, :]
+        assert np.linalg.norm(ag - ref) <= 1e-8 * np.linalg.norm(ref)
+    finally:
+        ieti.ieti_destroy(ctx)
 
 
 def test_tensor_core_trailing_update_path(ieti, monkeypatch):
@@ -227,31 +247,3 @@ def test_tensor_core_trailing_update_path(ieti, monkeypatch):
         assert np.linalg.norm(a.cpu().numpy().T - a_m) <= 1e-8 * np.linalg.norm(a_m)
     finally:
         ieti.ieti_destroy(ctx)
-
-
-@pytest.mark.parametrize("prec", [0, 1])
-def test_barrier_sweeps_match_dependency_sweeps(ieti, prec, monkeypatch):
-    """The single-column sweeps as barrier-synchronised panel loops (the
-    fallback, IETI_NO_DEP_SWEEP=1) and as dependency-driven block tasks give
-    the same field, and both equal the monolithic oracle solve to 1e-8."""
-    prob, mesh, topo, sysd, a_m = oracle_case("cube12_p2_mixed")
-    out = []
-    for env in (None, "1"):
-        if env:
-            monkeypatch.setenv("IETI_NO_DEP_SWEEP", env)
-        else:
-            monkeypatch.delenv("IETI_NO_DEP_SWEEP", raising=False)
-        ctx = ieti.ieti_create(prob)
-        try:
-            ieti.ieti_assemble(ctx)
-            ieti.ieti_factor(ctx, prec)
-            a = torch.zeros((prob.nrhs, mesh.nedge), dtype=torch.float64, device="cuda")
-            info = ieti.ieti_solve(ctx, a, tol=1e-10, maxit=400, tol_field=1e-12 if prec else 0.0)
-            assert info.converged == 1
-            out.append(a.cpu().numpy().T)
-        finally:
-            ieti.ieti_destroy(ctx)
-    a1, a2 = out
-    assert np.linalg.norm(a1 - a2) <= 1e-9 * np.linalg.norm(a2)
-    for x in out:
-        assert np.linalg.norm(x - a_m) <= 1e-8 * np.linalg.norm(a_m)

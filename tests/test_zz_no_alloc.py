@@ -53,6 +53,50 @@ def test_noalloc_product_matches_preconditioner_twice():
         ieti.ieti_destroy(ctx)
 
 
+def test_noalloc_product_gives_the_local_F_apply():
+    """With M_k = (K_rr^-1)_II and the signs as weights the product is
+    B_r K_rr^-1 B_r^T x (the oracle's W of Eq. (7)), including a subdomain
+    block of size zero in the list; two calls in a row."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2501_04340_gb300 import ieti
+
+    prob = wl.small_cases()[3]
+    sysd = fd.build_system(prob)
+    ctx = ieti.ieti_create(prob)
+    try:
+        ieti.ieti_assemble(ctx)
+        ieti.ieti_factor(ctx, ieti.IETI_FP64)
+        dual_edges = ieti.ieti_get_dofmap(ctx, 3)
+        m = len(dual_edges)
+        nI, blocks, dual, weight = [], [], [], []
+        for k in range(sysd.topo.nsub):
+            W = ieti.ieti_get_block(ctx, 6, k)
+            I_edges = ieti.ieti_get_dofmap(ctx, 5, k)
+            nI.append(len(I_edges))
+            blocks.append(W.T.ravel())
+            dual.append(np.searchsorted(dual_edges, I_edges))
+            weight.append(ieti.ieti_get_dofmap(ctx, 7, k).astype(np.float64))
+            if k == 1:
+                nI.append(0)                         # an empty block between two others
+        M = torch.tensor(np.concatenate(blocks), dtype=torch.float64, device="cuda")
+        dual_t = torch.tensor(np.concatenate(dual), dtype=torch.int32, device="cuda")
+        w_t = torch.tensor(np.concatenate(weight), dtype=torch.float64, device="cuda")
+        rng = np.random.default_rng(12)
+        for call in range(2):
+            nrhs = 2 + call
+            xh = rng.standard_normal((m, nrhs))
+            x = torch.tensor(xh.T.copy(), dtype=torch.float64, device="cuda")
+            y = torch.full_like(x, float("nan"))
+            ieti.ieti_interface_product_noalloc(nI, M, dual_t, w_t, x, y, m, nrhs)
+            torch.cuda.synchronize()
+            ref = fd.apply_W(sysd, xh)
+            err = np.abs(y.cpu().numpy().T - ref).max() / np.abs(ref).max()
+            assert err < 1e-9, (call, err)
+    finally:
+        ieti.ieti_destroy(ctx)
+
+
 def test_noalloc_product_rejects_oversize_request():
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
