@@ -116,6 +116,8 @@ typedef struct {
   double kappa;                /* Lanczos estimate of kappa(M^-1 F) (first load case) */
   int converged;               /* 1 if every load case met the tolerance */
   double ms_total;             /* device time of the call */
+  int fp64_fallback;           /* 1 if the FP32 factors were replaced by FP64 factors
+                                  during the call (refinement stalled) */
 } ieti_solve_info;
 
 /* Builds the mesh, the 1D basis tables at the Gauss points (p+1 per span), the
@@ -155,8 +157,11 @@ ieti_status ieti_assemble(ieti_ctx* ctx, void* stream);
  * interface Schur complement S_rIrI^(k) of Eq. (10) is taken from the factor
  * after the r_V columns; Phi^(k) = K_rr^-1 K_rp; the coarse matrix
  * S_Pi = -F (F of Eq. (7)) in FP64 and its Cholesky factor; the local
- * interface operators (K_rr^-1)_II = S_rIrI^-1. Errors: SINGULAR_LOCAL (a
- * non-positive pivot; the subdomain id is in the message), STATE (not
+ * interface operators (K_rr^-1)_II = S_rIrI^-1. Under IETI_FP32_IR a
+ * non-positive FP32 pivot (a local block too ill-conditioned for single
+ * precision) makes the call factor in FP64 instead; the context then holds
+ * FP64 factors as after IETI_FP64. Errors: SINGULAR_LOCAL (a non-positive
+ * pivot in FP64; the subdomain id is in the message), STATE (not
  * assembled), TIMEOUT (a bounded device wait of the interface products or of
  * the W and Phi solves gave up), CUDA. Synchronises the stream. */
 ieti_status ieti_factor(ieti_ctx* ctx, ieti_precision prec, void* stream);
@@ -180,7 +185,11 @@ ieti_status ieti_apply_precond(ieti_ctx* ctx, const double* r_dev, double* z_dev
  * a_r = K_rr^-1 (j_r - K_rp a_p - B_r^T lam). Under IETI_FP32_IR this is the
  * inner solver of FP64 iterative refinement on the assembled system, repeated
  * until the FP64 relative residual of the field is <= tol_field (default 1e-10
- * when <= 0) or 8 refinement steps; each inner PCG then stops at
+ * when <= 0) or 16 refinement steps; if one of the first two correction
+ * steps cuts the field residual by less than a factor 4 although its inner
+ * PCG converged (FP32 factors outside their regime, kappa(K_rr) u_32 not
+ * small), the context switches to FP64 factors for the remaining steps
+ * (info->fp64_fallback). Each inner PCG stops at
  * max(tol, 1e-3) on the first step and max(tol, 3e-3) on the corrections,
  * since a refinement step with FP32 operators cannot reduce the error by much
  * more than that anyway. lam0_dev: m_r x nrhs initial multipliers or

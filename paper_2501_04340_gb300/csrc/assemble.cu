@@ -793,11 +793,26 @@ static size_t flux_smem() {
   return sizeof(ElemShared<PD>) + sizeof(double) * ((size_t)NF * NQ3 * 2 + (size_t)NF * FLUX_CG + NQ3 * FLUX_CG * 2);
 }
 
-ieti_status flux_kernel_attrs(Ctx* c, int smem_max) {
-  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_elem_B<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
-  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_elem_B<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
-  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_elem_B<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+// the dynamic shared memory of the flux kernels is exactly flux_smem (their
+// static shared memory comes on top, within the opt-in limit)
+template <int PD>
+static ieti_status flux_attr(Ctx* c, int smem_max) {
+  cudaFuncAttributes fa;
+  IETI_CUDA_TRY(c, cudaFuncGetAttributes(&fa, k_elem_B<PD>));
+  if (flux_smem<PD>() + fa.sharedSizeBytes > (size_t)smem_max) {
+    c->err = "shared memory of the flux kernel exceeds the device limit";
+    return IETI_ERR_INVALID_ARG;
+  }
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_elem_B<PD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)flux_smem<PD>()));
   return IETI_OK;
+}
+
+ieti_status flux_kernel_attrs(Ctx* c, int smem_max) {
+  ieti_status r;
+  if ((r = flux_attr<1>(c, smem_max)) != IETI_OK) return r;
+  if ((r = flux_attr<2>(c, smem_max)) != IETI_OK) return r;
+  return flux_attr<3>(c, smem_max);
 }
 
 // B = curl a for nrhs fields; out = [npatch x nrhs] squared norms, then the

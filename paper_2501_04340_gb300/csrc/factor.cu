@@ -858,6 +858,10 @@ static ieti_status factor_t(Ctx* c, cudaStream_t st) {
   IETI_CUDA_TRY(c, cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   IETI_CUDA_TRY(c, cudaStreamSynchronize(st));
   if (*c->h_err) {
+    // the failed factorisation may have written non-finite values into tiles
+    // outside the pattern (products with overflowed entries): the next one
+    // starts from a full copy of K_rr
+    c->l_init_prec = -1;
     c->err = "non-positive pivot in the factorisation of subdomain " + std::to_string(*c->h_err - 1);
     return IETI_ERR_SINGULAR_LOCAL;
   }
@@ -983,6 +987,13 @@ static ieti_status coarse_factor(Ctx* c, cudaStream_t st) {
 
 ieti_status factor_all(Ctx* c, cudaStream_t st) {
   ieti_status r = (c->prec == IETI_FP64) ? factor_t<double>(c, st) : factor_t<float>(c, st);
+  if (r == IETI_ERR_SINGULAR_LOCAL && c->prec == IETI_FP32_IR && c->fault_pivot_sub < 0) {
+    // a non-positive pivot in FP32 (a local block too ill-conditioned for
+    // single precision): the factors are redone in FP64
+    c->prec = IETI_FP64;
+    c->fp64_fallbacks++;
+    r = factor_t<double>(c, st);
+  }
   if (r != IETI_OK) return r;
   if ((r = coarse_factor(c, st)) != IETI_OK) return r;
   if ((r = iface_prepare(c, st)) != IETI_OK) return r;

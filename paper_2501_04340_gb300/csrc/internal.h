@@ -219,6 +219,7 @@ struct Ctx {
   unsigned long long dep_epoch = 0;
   int* d_dep_err = nullptr;              // set when a sweep wait times out; the poll limit at byte 8
   int fault_pivot_sub = -1;              // testing aid: subdomain whose next factorisation gets a negative pivot
+  int fp64_fallbacks = 0;                // FP32 factorisations redone in FP64 (non-positive FP32 pivot)
   McPlan mcplan[2];                      // [0] W solve, [1] Phi solve
   bool autotune = true;                  // IETI_NO_AUTOTUNE=1: keep the default tile shapes
   bool tuned[2] = {false, false};        // [fp32] tile shapes of the streamed products chosen

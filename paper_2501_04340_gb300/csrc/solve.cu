@@ -21,6 +21,12 @@
 
 namespace ieti {
 
+// FP64 refinement of the assembled system under FP32 factors: at most this many
+// steps, and a step must cut the field residual at least by this factor, else
+// the factors are redone in FP64
+constexpr int MAX_REFINE_STEPS = 16;
+constexpr double FALLBACK_CONTRACTION = 0.25;
+
 constexpr int LOC_CT = 8;      // RHS columns per CTA in the local products
 constexpr int LOC_ROWS = 32;   // rows of W per CTA (4 per warp)
 constexpr int RED_BLOCKS = 304;
@@ -946,7 +952,7 @@ ieti_status solve_all(Ctx* c, const double* lam0, double tol, int maxit, double 
                       double* lam_out, ieti_solve_info* info, cudaStream_t st) {
   const int nrhs = c->nrhs;
   const int64_t ne = c->mesh.nedge, m = c->m_r;
-  const bool fp32 = c->prec == IETI_FP32_IR;
+  bool fp32 = c->prec == IETI_FP32_IR;
   cudaEvent_t e0, e1;
   IETI_CUDA_TRY(c, cudaEventCreate(&e0));
   IETI_CUDA_TRY(c, cudaEventCreate(&e1));
@@ -981,16 +987,18 @@ ieti_status solve_all(Ctx* c, const double* lam0, double tol, int maxit, double 
     if ((r = residual(c, a, &dummy, nullptr, st, true)) != IETI_OK) return r;
     IETI_CUDA_TRY(c, cudaMemcpy(jn2.data(), c->wnorm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost));
   }
-  const int max_steps = refine ? 8 : 1;
+  const int max_steps = refine ? MAX_REFINE_STEPS : 1;
   int total_it = 0, steps = 0;
   double relres = 0, grel = -1, kappa = 0;
-  bool conv = true;
+  bool conv = true, fallback = false;
+  bool fresh = true;          // this step solves for the loads themselves (no field yet)
+  double grel_prev = 1.0;   // field residual after the previous step
   double* b = c->wlam[4];
   double* lam = c->wlam[5];
   double* ycr = c->wc[1];
   for (int step = 0; step < max_steps; ++step) {
-    const double* jr = (step == 0) ? c->jr : c->wres_r;
-    const double* jp = (step == 0) ? c->jp : c->wres_p;
+    const double* jr = fresh ? c->jr : c->wres_r;
+    const double* jp = fresh ? c->jp : c->wres_p;
     if ((r = interface_rhs(c, jr, jp, b, ycr, nrhs, st)) != IETI_OK) return r;
     bool warm = (step == 0 && lam0 != nullptr);
     if (warm) IETI_CUDA_TRY(c, cudaMemcpyAsync(lam, lam0, sizeof(double) * m * nrhs, cudaMemcpyDeviceToDevice, st));
@@ -1000,9 +1008,9 @@ ieti_status solve_all(Ctx* c, const double* lam0, double tol, int maxit, double 
     // about 0.03 on the 64-patch cube (kappa(K_rr) u_32), whatever the inner
     // tolerance below that level, so the inner PCG only has to beat it: 1e-3
     // on the first step and 3e-3 on the corrections keep the number of steps
-    // (7 there) at the fewest PCG iterations; the FP64 residual of the field
+    // (6-7 there) at the fewest PCG iterations; the FP64 residual of the field
     // decides convergence
-    const double tol_in = fp32 ? std::max(tol, step == 0 ? 1e-3 : 3e-3) : tol;
+    const double tol_in = fp32 ? std::max(tol, fresh ? 1e-3 : 3e-3) : tol;
     ieti_status pr = pcg(c, b, lam, !warm, tol_in, maxit, fp32, &its, &rel, &kap, st);
     if (pr != IETI_OK && pr != IETI_ERR_NO_CONVERGENCE) return pr;
     if (pr == IETI_ERR_NO_CONVERGENCE && !fp32) conv = false;
@@ -1011,14 +1019,42 @@ ieti_status solve_all(Ctx* c, const double* lam0, double tol, int maxit, double 
     if (step == 0) kappa = kap;
     k_add<<<1216, 256, 0, st>>>(c->wlam_acc, lam, m * nrhs);
     IETI_LAUNCH_CHECK(c);
-    if ((r = recover(c, lam, ycr, a, step > 0 ? 1 : 0, st)) != IETI_OK) return r;
+    if ((r = recover(c, lam, ycr, a, fresh ? 0 : 1, st)) != IETI_OK) return r;
     steps = step + 1;
+    fresh = false;
     if (refine) {
       if ((r = residual(c, a, &grel, jn2.data(), st)) != IETI_OK) return r;
     }
     if (std::getenv("IETI_TRACE"))
       std::fprintf(stderr, "[ieti] step %d: pcg its %d relres %.3e field residual %.3e\n", step, its, rel, grel);
     if (!refine || grel <= tol_field) break;
+    // a timed-out sweep wait leaves garbage: stop and report it (below)
+    IETI_CUDA_TRY(c, cudaMemcpy(c->h_err + 1, c->d_dep_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (c->h_err[1]) break;
+    // FP32 factors outside their regime (kappa(K_rr) u_32 not small) show in
+    // the first corrections: one of the first two correction steps whose inner
+    // PCG converged but which does not cut the field residual by
+    // FALLBACK_CONTRACTION, or any step that gives a non-finite residual,
+    // switches the context to FP64 factors for the remaining steps (restarting
+    // from the loads if the field is not finite). Later stalls come from the
+    // rounding floor of the FP64 residual, which FP64 factors do not lower.
+    const bool stalled = step > 0 && step <= 2 && pr == IETI_OK && grel > FALLBACK_CONTRACTION * grel_prev;
+    if (fp32 && (stalled || !std::isfinite(grel))) {
+      c->prec = IETI_FP64;
+      if ((r = factor_all(c, st)) != IETI_OK) {
+        c->factored = false;
+        return r;
+      }
+      fp32 = false;
+      fallback = true;
+      if (!std::isfinite(grel)) {
+        IETI_CUDA_TRY(c, cudaMemsetAsync(a, 0, sizeof(double) * ne * nrhs, st));
+        IETI_CUDA_TRY(c, cudaMemsetAsync(c->wlam_acc, 0, sizeof(double) * m * nrhs, st));
+        fresh = true;
+        grel = 1.0;
+      }
+    }
+    grel_prev = grel;
   }
   if (refine && grel > tol_field) conv = false;
   if (lam_out)
@@ -1044,6 +1080,7 @@ ieti_status solve_all(Ctx* c, const double* lam0, double tol, int maxit, double 
     info->kappa = kappa;
     info->converged = conv ? 1 : 0;
     info->ms_total = ms;
+    info->fp64_fallback = fallback ? 1 : 0;
   }
   if (!conv) {
     c->err = "PCG or refinement did not reach the tolerance";

@@ -50,7 +50,7 @@ class ieti_sizes(C.Structure):
 class ieti_solve_info(C.Structure):
     _fields_ = [("iterations", C.c_int), ("refinement_steps", C.c_int), ("relres", C.c_double),
                 ("global_relres", C.c_double), ("kappa", C.c_double), ("converged", C.c_int),
-                ("ms_total", C.c_double)]
+                ("ms_total", C.c_double), ("fp64_fallback", C.c_int)]
 
 
 _vp = C.c_void_p

@@ -61,7 +61,8 @@ def test_iteration_cap_gives_no_convergence_with_info(ieti, case, prec):
         if prec == 0:
             assert info.iterations == 3 and info.refinement_steps == 1
         else:
-            assert info.refinement_steps == 8 and info.iterations <= 8 * 3
+            assert info.refinement_steps == 16 and info.iterations <= 16 * 3
+            assert info.fp64_fallback == 0     # the inner PCG was capped: not a precision failure
             assert info.global_relres > 1e-12
         _solve_ok(ieti, ctx, prob, mesh, a_ref, prec)
     finally:

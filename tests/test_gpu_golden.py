@@ -55,14 +55,16 @@ def ctx_by_prec(ieti):
         ieti.ieti_destroy(c)
 
 
-@pytest.mark.parametrize("prec,tol,tol_field", [(0, 1e-11, 0.0), (1, 1e-8, 1e-8), (1, 1e-11, 1e-12), (0, 1e-9, 0.0)])
+@pytest.mark.parametrize("prec,tol,tol_field", [(0, 1e-11, 0.0), (1, 1e-8, 1e-8), (1, 1e-10, 1e-10), (0, 1e-10, 0.0)])
 def test_field_and_flux_match_the_oracle(ieti, gold, ctx_by_prec, prec, tol, tol_field):
+    """The FP32 factors of this workload are inside their regime: the
+    refinement never falls back to FP64 here."""
     a_ref, nB_ref = gold
     prob, ctxs = ctx_by_prec
     ctx = ctxs[prec]
     a = torch.zeros((1, len(a_ref)), dtype=torch.float64, device="cuda")
     info = ieti.ieti_solve(ctx, a, tol=tol, maxit=2000, tol_field=tol_field)
-    assert info.converged == 1
+    assert info.converged == 1 and info.fp64_fallback == 0
     ag = a.cpu().numpy()[0]
     err_a = np.linalg.norm(ag - a_ref) / np.linalg.norm(a_ref)
     assert err_a <= 1e-8, err_a

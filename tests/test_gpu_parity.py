@@ -6,7 +6,11 @@ Tolerances (relative, max-norm unless stated):
   * assembly (FP64 on both sides, different summation order): 1e-12;
   * FP64 factorisation products (S_rIrI, its inverse, S_Pi, F_DP, M_D^-1): 1e-9
     (condition numbers of the local blocks are below 1e4 here);
-  * FP32 operators: 2e-3 (FP32 factor, kappa(K_rr) ~ 1e3 times u_32 ~ 6e-8);
+  * FP32 operators: max(2e-3, kappa_max u_32), with kappa_max the largest
+    condition number of the local blocks K_rr^(k) (dense eigenvalues in the
+    oracle) and u_32 = 2^-24: the first-order error of an inverse from an FP32
+    Cholesky factor; a case with kappa_max u_32 >= 1 is outside the FP32
+    regime and only its solve is checked (the refinement falls back to FP64);
   * the field a and the flux B = curl a against the monolithic oracle solve:
     1e-8 in the 2-norm, for both precisions (FP32 through FP64 refinement).
 """
@@ -75,6 +79,20 @@ def oracle_case(name):
     return _cache[name]
 
 
+_kappa = {}
+
+
+def fp32_tol(name):
+    """Tolerance of the FP32 operator checks (module docstring); None if the
+    case is outside the FP32 regime."""
+    if name not in _kappa:
+        sysd = oracle_case(name)[3]
+        _kappa[name] = max(np.linalg.cond(s.Krr.toarray()) for s in sysd.subs)
+        print(f"{name}: max kappa(K_rr) = {_kappa[name]:.3e}")
+    ku = _kappa[name] * 2.0 ** -24
+    return None if ku >= 1.0 else max(2e-3, ku)
+
+
 def rel(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
@@ -121,8 +139,11 @@ def _factored(ieti, name, prec):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 2e-3)])
-def test_schur_blocks_and_coarse(ieti, name, prec, tol):
+@pytest.mark.parametrize("prec", [0, 1])
+def test_schur_blocks_and_coarse(ieti, name, prec):
+    tol = 1e-9 if prec == 0 else fp32_tol(name)
+    if tol is None:
+        pytest.skip("kappa(K_rr) u_32 >= 1: FP32 factors outside their regime")
     ctx, prob, mesh, topo, sysd, _ = _factored(ieti, name, prec)
     try:
         op = fd.InterfaceOperator(sysd)
@@ -140,8 +161,11 @@ def test_schur_blocks_and_coarse(ieti, name, prec, tol):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 2e-3)])
-def test_apply_F_and_preconditioner(ieti, name, prec, tol):
+@pytest.mark.parametrize("prec", [0, 1])
+def test_apply_F_and_preconditioner(ieti, name, prec):
+    tol = 1e-9 if prec == 0 else fp32_tol(name)
+    if tol is None:
+        pytest.skip("kappa(K_rr) u_32 >= 1: FP32 factors outside their regime")
     ctx, prob, mesh, topo, sysd, _ = _factored(ieti, name, prec)
     try:
         op = fd.InterfaceOperator(sysd)
@@ -175,6 +199,8 @@ def test_solve_matches_monolithic_field_and_flux(ieti, name, prec):
         lam = torch.zeros((prob.nrhs, sysd.m_r), dtype=torch.float64, device="cuda")
         info = ieti.ieti_solve(ctx, a, tol=1e-11, maxit=400, tol_field=1e-12, lam_out=lam)
         assert info.converged == 1
+        if prec == 1 and fp32_tol(name) is None:
+            assert info.fp64_fallback == 1      # outside the FP32 regime: finished with FP64 factors
         ag = a.cpu().numpy().T
         assert np.linalg.norm(ag - a_m) <= 1e-8 * np.linalg.norm(a_m)
         for r in range(prob.nrhs):
