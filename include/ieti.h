@@ -284,8 +284,12 @@ int64_t ieti_launch_count(const ieti_ctx* ctx);
  *                           ieti_factor, which then returns
  *                           IETI_ERR_SINGULAR_LOCAL naming that subdomain
  *                           (value < 0 switches it off).
+ *   IETI_DEBUG_FP64_FALLBACK value != 0: the next FP32 refinement treats its
+ *                           first correction step as stalled and switches to
+ *                           FP64 factors (the path taken when FP32 factors are
+ *                           outside their regime).
  * Errors: INVALID_ARG (unknown setting, subdomain out of range), STATE. */
-enum { IETI_DEBUG_WAIT_POLLS = 1, IETI_DEBUG_PIVOT_FAULT = 2 };
+enum { IETI_DEBUG_WAIT_POLLS = 1, IETI_DEBUG_PIVOT_FAULT = 2, IETI_DEBUG_FP64_FALLBACK = 3 };
 ieti_status ieti_debug_set(ieti_ctx* ctx, int what, int64_t value);
 
 /* Per-kernel-class device timing with CUDA events recorded around each launch

@@ -786,6 +786,9 @@ ieti_status ieti_debug_set(ieti_ctx* x, int what, int64_t value) {
       }
       c->fault_pivot_sub = value < 0 ? -1 : (int)value;
       return IETI_OK;
+    case IETI_DEBUG_FP64_FALLBACK:
+      c->force_fallback = value != 0;
+      return IETI_OK;
     default:
       c->err = "ieti_debug_set: unknown setting";
       return IETI_ERR_INVALID_ARG;

@@ -986,6 +986,7 @@ static ieti_status coarse_factor(Ctx* c, cudaStream_t st) {
 }
 
 ieti_status factor_all(Ctx* c, cudaStream_t st) {
+  IETI_CUDA_TRY(c, cudaMemsetAsync(c->d_stream_err, 0, sizeof(int), st));
   ieti_status r = (c->prec == IETI_FP64) ? factor_t<double>(c, st) : factor_t<float>(c, st);
   if (r == IETI_ERR_SINGULAR_LOCAL && c->prec == IETI_FP32_IR && c->fault_pivot_sub < 0) {
     // a non-positive pivot in FP32 (a local block too ill-conditioned for

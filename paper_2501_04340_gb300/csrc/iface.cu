@@ -340,6 +340,7 @@ ieti_status launch_stream(Ctx* c, const StreamPlan& P, bool with_phi, const doub
   A.C.stages = stages;
   A.C.stage_bytes = P.stage_bytes;
   A.C.err = c->d_stream_err;
+  A.C.l2_hint = 0;
   A.cta = P.d_cta;
   A.t = t;
   A.qpart = qpart;
@@ -414,6 +415,20 @@ ieti_status iface_alloc(Ctx* c) {
     E = std::max(E, s0.nP + s1.nP);
   }
   c->gell_E = E;
+  {
+    // per local interface DOF: its multiplier and the other side's (iv, i, nI)
+    std::vector<int4> jt(std::max<int64_t>(c->tot_iv, 1), make_int4(0, 0, 0, 0));
+    for (int64_t l = 0; l < m; ++l) {
+      const int k0 = c->topo.dual_pair[l * 4], i0 = c->topo.dual_pair[l * 4 + 1];
+      const int k1 = c->topo.dual_pair[l * 4 + 2], i1 = c->topo.dual_pair[l * 4 + 3];
+      const SubDev &s0 = c->sd_host[k0], &s1 = c->sd_host[k1];
+      jt[s0.iv + i0] = make_int4((int)l, (int)s1.iv, i1, s1.nI);
+      jt[s1.iv + i1] = make_int4((int)l, (int)s0.iv, i0, s0.nI);
+    }
+    ieti_status r2;
+    if ((r2 = alloc_dev(c, &c->d_jt, jt.size())) != IETI_OK) return r2;
+    IETI_CUDA_TRY(c, cudaMemcpy(c->d_jt, jt.data(), sizeof(int4) * jt.size(), cudaMemcpyHostToDevice));
+  }
   // prepared u vectors: subdomain k's block at uoff_k (ldI_k entries), MAX_RHS columns
   c->uoff.assign(c->nsub, 0);
   int64_t ut = 0;

@@ -220,6 +220,7 @@ struct Ctx {
   int* d_dep_err = nullptr;              // set when a sweep wait times out; the poll limit at byte 8
   int fault_pivot_sub = -1;              // testing aid: subdomain whose next factorisation gets a negative pivot
   int fp64_fallbacks = 0;                // FP32 factorisations redone in FP64 (non-positive FP32 pivot)
+  bool force_fallback = false;           // testing aid: the next FP32 refinement treats its first correction as stalled
   McPlan mcplan[2];                      // [0] W solve, [1] Phi solve
   bool autotune = true;                  // IETI_NO_AUTOTUNE=1: keep the default tile shapes
   bool tuned[2] = {false, false};        // [fp32] tile shapes of the streamed products chosen
@@ -262,6 +263,7 @@ struct Ctx {
   int4* d_gs = nullptr;                  // per multiplier: iv and i of both sides
   int2* d_gn = nullptr;                  // per multiplier: nI of both sides
   int2* d_gu = nullptr;                  // per multiplier: positions of both sides in the u vectors
+  int4* d_jt = nullptr;                  // per local interface DOF: multiplier, other side's iv, i, nI
   std::vector<int64_t> uoff;             // per subdomain: offset of u_k (ldI_k entries)
   int64_t utot = 0;                      // column stride of the u vectors
   void* uall = nullptr;                  // prepared u vectors (factor precision, MAX_RHS columns)

@@ -4,22 +4,31 @@
 // Phi_I^T) tiles and of S tiles exactly as the stand-alone products do, and
 // owns a contiguous slice of the multipliers for the vector work.
 //
-// Per iteration, four grid barriers:
-//   A  t1_k = W_k u_k, q_k = Phi_I^(k)T u_k          (u = D_W p, written in F)
-//   B  p = z + beta p on the owned slice (deferred from F);
-//      yc = S_Pi^-1 sum C^T q_k (every CTA); q = F p = B t1 + G yc; <p, q>
-//   C  alpha = rz / <p, q>; lam += alpha p; <r', r'> with r' = r - alpha q;
-//      u = D_S r' for the subdomains of the CTA's S run; t2_k = S_k u_k
-//   E  r = r'  on the owned slice (deferred from C); convergence test;
-//      z = sum_k B_k D_k t2_k; <r, z>
-//   F  beta = rz_new / rz; u = D_W (z + beta p) for the subdomains of the
-//      CTA's W run
-// The deferred updates keep r and p unchanged while other CTAs read them.
-// Every CTA that streams tiles of subdomain k writes the whole u_k itself
-// (all of them store identical values) and fences the async proxy before its
-// bulk copies read it, so no barrier separates u from the product. Every CTA
-// sums the per-CTA partials in the same order, so all CTAs take the same
-// alpha, beta and convergence decisions.
+// Both inner products of an iteration are sums over the rows the products
+// produce: <p, B t1> = sum_k u_k . t1_k with u_k = D_W,k B_k^T p, and
+// <r', z'> = sum_k u_k . t2_k with u_k = D_S,k B_k^T r' (D diagonal), so the
+// streaming passes form them on the fly and no reduction phase follows a
+// gather. r and p are double-buffered, so a CTA never reads a value another
+// CTA rewrites in the same phase, and the owner of a multiplier writes the
+// entries of the next u vectors at both of its sides. Per iteration, four
+// grid barriers, two of them after balanced vector phases:
+//   P1  t1_k = W_k u_k, q_k = Phi_I^(k)T u_k (u = D_W p) and the CTA's share
+//       of <p, B t1>                                                   | barrier
+//   P2  every CTA: yc = S_Pi^-1 sum C^T q_k, <p, F p> = sum of the shares
+//       + (G^T p) . yc, alpha. Owned slice: q = B t1 + G yc, lam += alpha p,
+//       r' = r - alpha q into the other r buffer, u = D_S r' at both sides,
+//       share of <r', r'>                                              | barrier
+//   P3  t2_k = S_k u_k and the CTA's share of <r', z'>                 | barrier
+//   P4  every CTA: convergence test on <r', r'>, beta = <r', z'> / <r, z>.
+//       Owned slice: z' = sum_k B_k D_k t2_k, p' = z' + beta p into the other
+//       p buffer, u = D_W p' at both sides                             | barrier
+// Every CTA sums the per-CTA shares in the same order, so all CTAs take the
+// same alpha, beta and convergence decisions. The loads of a vector phase are
+// issued in one round before its block reductions, since the data were
+// written by other SMs and every round trip costs an L2 latency. The W tiles
+// are fetched with the L2 evict-last priority and the S tiles with
+// evict-first, so that W stays in L2 from one iteration to the next when W and
+// S together exceed it.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -46,9 +55,9 @@ struct PcgStreamArgs {
   const SubDev* sd;
   const int64_t* uoff;
   const int32_t* I_dual;
-  double *x, *r, *z, *p, *q;
+  double *x, *r, *z, *p, *q;     // lam, r, p, and the second r (q) and p (z) buffers
   double *t1, *t2, *qpart;
-  double* part;                  // per-CTA partials [3][grid][CT]
+  double* part;                  // per-CTA shares [3][grid][CT]: <p, B t1>, <r', r'>, <r', z'>
   double* scal;
   double* hist;
   int hist_cap;
@@ -101,26 +110,6 @@ __host__ __device__ inline size_t coarse_bytes(int ngp, int64_t ncontrib) {
          (size_t)ncontrib * 16;
 }
 
-// CTA sum in a fixed order (all STREAM_THREADS threads; every thread gets it)
-__device__ inline double ps_cta_sum(double v, double* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double s = 0;
-  for (int w = 0; w < STREAM_THREADS / 32; ++w) s += red[w];
-  return s;
-}
-
-// sum of one column's per-CTA partials, thread-strided then a fixed tree
-__device__ inline double ps_sum_part(const double* part, int col, int ct, double* red) {
-  double v = 0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) v += part[(int64_t)i * ct + col];
-  return ps_cta_sum(v, red);
-}
-
 __device__ inline void fence_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
 // u_k = D_k v at the r_I DOFs of every subdomain k in kr (D = sign, times the
@@ -149,15 +138,353 @@ __device__ inline void write_u_run(const PcgStreamArgs& A, int2 kr, const double
   fence_async_global();
 }
 
+// Vector phases run on the consumer warps alone (named barrier 2), so that the
+// producer warp can issue the bulk copies of the next pass meanwhile.
+__device__ __forceinline__ void cons_sync() { asm volatile("bar.sync 2, 256;" ::: "memory"); }
+
+// Block sum over the consumer warps of one value per thread, in the warps
+// [0, nw) that hold nonzero values; red: [8] doubles. The total is in
+// red[8] afterwards (visible after the next cons_sync). GB300's FP64 pipe is
+// narrow: the partial sums are formed once, not in every thread.
+__device__ __forceinline__ void cons_sum_begin(double v, int nw, double* red) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (warp < nw) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp] = v;
+  }
+}
+__device__ __forceinline__ double cons_sum_end(int nw, const double* red) {
+  double s = 0;
+  for (int w = 0; w < nw; ++w) s += red[w];
+  return s;
+}
+
+// z' = s0 t2(side 0) - s1 t2(side 1) of the multiplier, as one expression
+__device__ __forceinline__ double zgather(double s0, double ta, double s1, double tb) {
+  return fma(s0, ta, -(s1 * tb));
+}
+
+// state of the vector phases of one CTA: the shared-memory caches and
+// scalars of the kernel
+template <int CT>
+struct PhaseCtx {
+  Slice SL;
+  int64_t l0, nl, estride, m;
+  int E, ngp, nrhs, G, bid, nwG, nwL;
+  double* c_spi;
+  double* c_cv;
+  const int32_t* c_co;
+  const int4* c_pc;
+  double *qg, *yc, *redA, *redB, *rz, *bb, *alpha_s, *beta_s;
+  int* done;
+  int* its;
+  double *pW, *pR, *pZ;
+};
+
+// The vector phases are out-of-line functions of the consumer warps: compiled
+// inside the register-capped kernel body, the same straight-line code
+// scheduled far worse (P4 took 6.8 us per iteration inline against 2 us as a
+// separate body).
+template <typename T, int CT>
+__device__ __noinline__ void pcg_phase2(const PcgStreamArgs& A, const PhaseCtx<CT>& X, double* rc, double* rn,
+                                        double* pc) {
+  const int tid = threadIdx.x;
+  const Slice& SL = X.SL;
+  const int64_t l0 = X.l0, nl = X.nl, estride = X.estride, m = X.m;
+  const int E = X.E, ngp = X.ngp, nrhs = X.nrhs, G = X.G, bid = X.bid, nwG = X.nwG, nwL = X.nwL;
+  double* c_spi = X.c_spi;
+  double* c_cv = X.c_cv;
+  const int32_t* c_co = X.c_co;
+  const int4* c_pc = X.c_pc;
+  double* qg = X.qg;
+  double* yc = X.yc;
+  double* redA = X.redA;
+  double* redB = X.redB;
+  double* rz = X.rz;
+  double* bb = X.bb;
+  double* alpha_s = X.alpha_s;
+  double* beta_s = X.beta_s;
+  int* done = X.done;
+  int* its = X.its;
+  double* pW = X.pW;
+  double* pR = X.pR;
+  double* pZ = X.pZ;
+  (void)bb; (void)its; (void)pZ; (void)pW; (void)pR; (void)beta_s; (void)c_spi; (void)c_cv; (void)c_co; (void)c_pc;
+  // ---- P2 (consumers): one round of loads (the shares of <p, B t1>, the
+  // primal partials of the coarse DOFs, the owned entries of t1, lam, p,
+  // r); the coarse correction and alpha (one thread per column); the owned
+  // updates and the u = D_S r' entries of both sides of every owned
+  // multiplier
+  double sv[CT];
+#pragma unroll
+  for (int cc = 0; cc < CT; ++cc) sv[cc] = (cc < nrhs && tid < G) ? pW[(int64_t)tid * CT + cc] : 0.0;
+  const bool own0 = tid < nl;
+  double ta[CT], tb[CT], xo[CT], po[CT], ro[CT];
+  if (own0) {
+    const int4 a0 = SL.gs[tid];
+    const int2 n0 = SL.gn[tid];
+#pragma unroll
+    for (int col = 0; col < CT; ++col) {
+      if (col >= nrhs) break;
+      const int64_t o = l0 + tid + m * col;
+      ta[col] = A.t1[(int64_t)a0.x * nrhs + a0.y + (int64_t)n0.x * col];
+      tb[col] = A.t1[(int64_t)a0.z * nrhs + a0.w + (int64_t)n0.y * col];
+      xo[col] = A.x[o];
+      po[col] = pc[o];
+      ro[col] = rc[o];
+    }
+  }
+  if (ngp > 0 && A.cache_coarse && nrhs == 1) {
+    // contributor values of G^T p in parallel (one round with the loads above)
+    for (int64_t e = tid; e < A.ncontrib; e += NCONS) {
+      const int4 pc4 = c_pc[e];
+      c_cv[e] = A.qpart[(int64_t)pc4.x + pc4.y];
+    }
+  }
+#pragma unroll
+  for (int cc = 0; cc < CT; ++cc)
+    if (cc < nrhs) cons_sum_begin(sv[cc], nwG, redA + 8 * cc);
+  cons_sync();
+  if (ngp > 0) {
+    if (A.cache_coarse && nrhs == 1) {
+      for (int g = tid; g < ngp; g += NCONS) {
+        double acc = 0;
+        for (int e = c_co[g]; e < c_co[g + 1]; ++e) acc += c_cv[e];
+        qg[g] = acc;
+      }
+    } else {
+      for (int t = tid; t < ngp * nrhs; t += NCONS) {
+        const int g = t % ngp, col = t / ngp;
+        double acc = 0;
+        for (int64_t e = A.pcsr_off[g]; e < A.pcsr_off[g + 1]; ++e) {
+          const int4 pc4 = A.cache_coarse ? c_pc[e] : A.pcon[e];
+          acc += A.qpart[(int64_t)pc4.x * nrhs + pc4.y + (int64_t)pc4.z * col];
+        }
+        qg[t] = acc;
+      }
+    }
+    cons_sync();
+    for (int t = tid; t < ngp * nrhs; t += NCONS) {
+      const int g = t % ngp, col = t / ngp;
+      const double* sp = A.cache_coarse ? c_spi + (size_t)ngp * g : A.SPiInv + (int64_t)A.ldc * g;
+      double acc = 0;
+      for (int h = 0; h < ngp; ++h) acc += sp[h] * qg[h + ngp * col];
+      yc[t] = acc;
+    }
+    cons_sync();
+  }
+  if (tid < nrhs) {
+    // alpha of column tid: <p, F p> = sum of the shares + (G^T p) . S_Pi^-1 (G^T p)
+    double cq = 0;
+    for (int g = 0; g < ngp; ++g) cq += qg[g + ngp * tid] * yc[g + ngp * tid];
+    const double pq = cons_sum_end(nwG, redA + 8 * tid) + cq;
+    alpha_s[tid] = (done[tid] || pq == 0.0) ? 0.0 : rz[tid] / pq;
+  }
+  cons_sync();
+  double rrp[CT];
+#pragma unroll
+  for (int cc = 0; cc < CT; ++cc) rrp[cc] = 0.0;
+  T* u = (T*)A.CW.uall;
+  for (int64_t i = tid; i < nl; i += NCONS) {
+    const bool first = i == tid;
+    const int64_t l = l0 + i;
+    const int4 a = SL.gs[i];
+    const int2 nn = SL.gn[i];
+    const int2 gu = SL.gu[i];
+    double w0, w1;   // D_S at both sides: sign times rho-scaling
+    if (SL.sg) {
+      const double2 sg = SL.sg[i], sc = SL.sc[i];
+      w0 = sg.x * sc.x;
+      w1 = sg.y * sc.y;
+    } else {
+      w0 = A.I_sign[a.x + a.y] * A.I_scale[a.x + a.y];
+      w1 = A.I_sign[a.z + a.w] * A.I_scale[a.z + a.w];
+    }
+#pragma unroll
+    for (int col = 0; col < CT; ++col) {
+      if (col >= nrhs) break;
+      const int64_t o = l + m * col;
+      const double al = alpha_s[col];
+      double v = (first ? ta[col] : A.t1[(int64_t)a.x * nrhs + a.y + (int64_t)nn.x * col]) -
+                 (first ? tb[col] : A.t1[(int64_t)a.z * nrhs + a.w + (int64_t)nn.y * col]);
+      if (ngp > 0) {
+#pragma unroll 8
+        for (int e = 0; e < E; ++e) v += SL.gv[e * estride + i] * yc[SL.gi[e * estride + i] + ngp * col];
+      }
+      A.x[o] = fma(al, first ? po[col] : pc[o], first ? xo[col] : A.x[o]);
+      const double rv = fma(-al, v, first ? ro[col] : rc[o]);
+      rn[o] = rv;
+      rrp[col] += rv * rv;
+      u[col * A.CW.utot + gu.x] = (T)(w0 * rv);
+      u[col * A.CW.utot + gu.y] = (T)(w1 * rv);
+    }
+  }
+  fence_async_global();   // the S pass reads u with bulk copies after the barrier
+#pragma unroll
+  for (int cc = 0; cc < CT; ++cc)
+    if (cc < nrhs) cons_sum_begin(rrp[cc], nwL, redB + 8 * cc);
+  cons_sync();
+  if (tid < nrhs) {
+    // a CTA whose bulk-copy wait timed out poisons its share, so that every
+    // CTA sees the same non-finite <r', r'> and leaves the loop with it
+    const double share = cons_sum_end(nwL, redB + 8 * tid);
+    pR[(int64_t)bid * CT + tid] = *(volatile int*)A.err ? __longlong_as_double(0x7ff8000000000000ll) : share;
+  }
+}
+
+template <typename T, int CT>
+__device__ __noinline__ void pcg_phase4(const PcgStreamArgs& A, const PhaseCtx<CT>& X, double* pc, double* pn) {
+  const int tid = threadIdx.x;
+  const Slice& SL = X.SL;
+  const int64_t l0 = X.l0, nl = X.nl, estride = X.estride, m = X.m;
+  const int E = X.E, ngp = X.ngp, nrhs = X.nrhs, G = X.G, bid = X.bid, nwG = X.nwG, nwL = X.nwL;
+  double* c_spi = X.c_spi;
+  double* c_cv = X.c_cv;
+  const int32_t* c_co = X.c_co;
+  const int4* c_pc = X.c_pc;
+  double* qg = X.qg;
+  double* yc = X.yc;
+  double* redA = X.redA;
+  double* redB = X.redB;
+  double* rz = X.rz;
+  double* bb = X.bb;
+  double* alpha_s = X.alpha_s;
+  double* beta_s = X.beta_s;
+  int* done = X.done;
+  int* its = X.its;
+  double* pW = X.pW;
+  double* pR = X.pR;
+  double* pZ = X.pZ;
+  (void)bb; (void)its; (void)pZ; (void)pW; (void)pR; (void)beta_s; (void)c_spi; (void)c_cv; (void)c_co; (void)c_pc;
+  // ---- P4 (consumers): one round of loads (the shares of <r', r'> and
+  // <r', z'>, the owned entries of t2 and p); convergence test and beta
+  // (one thread per column); owned p' and the u = D_W p' entries
+  double sr[CT], sz[CT];
+#pragma unroll
+  for (int cc = 0; cc < CT; ++cc) {
+    sr[cc] = (cc < nrhs && tid < G) ? pR[(int64_t)tid * CT + cc] : 0.0;
+    sz[cc] = (cc < nrhs && tid < G) ? pZ[(int64_t)tid * CT + cc] : 0.0;
+  }
+  const bool own0 = tid < nl;
+  double zt[CT], po[CT];
+  if (own0) {
+    const int4 a0 = SL.gs[tid];
+    const int2 n0 = SL.gn[tid];
+    double s0, s1;
+    if (SL.sc) {
+      const double2 sc = SL.sc[tid];
+      s0 = sc.x;
+      s1 = sc.y;
+    } else {
+      s0 = A.I_scale[a0.x + a0.y];
+      s1 = A.I_scale[a0.z + a0.w];
+    }
+#pragma unroll
+    for (int col = 0; col < CT; ++col) {
+      if (col >= nrhs) break;
+      const int64_t o = l0 + tid + m * col;
+      zt[col] = zgather(s0, A.t2[(int64_t)a0.x * nrhs + a0.y + (int64_t)n0.x * col], s1,
+                        A.t2[(int64_t)a0.z * nrhs + a0.w + (int64_t)n0.y * col]);
+      po[col] = pc[o];
+    }
+  }
+#pragma unroll
+  for (int cc = 0; cc < CT; ++cc)
+    if (cc < nrhs) {
+      cons_sum_begin(sr[cc], nwG, redA + 8 * cc);
+      cons_sum_begin(sz[cc], nwG, redB + 8 * cc);
+    }
+  cons_sync();
+  if (tid < nrhs) {
+    const int cc = tid;
+    const double rr = cons_sum_end(nwG, redA + 8 * cc), rzn = cons_sum_end(nwG, redB + 8 * cc);
+    const bool was = done[cc] != 0;
+    // a non-finite residual (a timed-out wait somewhere, see P2) ends the loop
+    const bool now = was || rr <= A.tol2 * bb[cc] || !isfinite(rr);
+    const double b = (now || rz[cc] == 0.0) ? 0.0 : rzn / rz[cc];
+    beta_s[cc] = b;
+    if (!was) {
+      if (bid == 0) {
+        A.scal[PS_SC * cc + 2] = rr;
+        A.scal[PS_SC * cc + 4] = alpha_s[cc];
+        A.scal[PS_SC * cc + 8] += 1.0;
+      }
+      done[cc] = now ? 1 : 0;
+      if (!now) {
+        rz[cc] = rzn;
+        if (bid == 0) {
+          A.scal[PS_SC * cc + 0] = rzn;
+          A.scal[PS_SC * cc + 5] = b;
+        }
+      }
+    }
+    if (cc == 0) {
+      ++*its;
+      if (bid == 0 && A.hist && *its <= A.hist_cap) {
+        A.hist[2 * (*its - 1)] = alpha_s[0];
+        A.hist[2 * (*its - 1) + 1] = b;
+      }
+    }
+  }
+  cons_sync();
+  T* u = (T*)A.CW.uall;
+  for (int64_t i = tid; i < nl; i += NCONS) {
+    const bool first = i == tid;
+    const int64_t l = l0 + i;
+    const int2 gu = SL.gu[i];
+    double w0, w1;   // D_W at both sides: the signs
+    if (SL.sg) {
+      const double2 sg = SL.sg[i];
+      w0 = sg.x;
+      w1 = sg.y;
+    } else {
+      const int4 a = SL.gs[i];
+      w0 = A.I_sign[a.x + a.y];
+      w1 = A.I_sign[a.z + a.w];
+    }
+    double zr[CT];
+    if (!first) {
+      const int4 a = SL.gs[i];
+      const int2 nn = SL.gn[i];
+      double s0, s1;
+      if (SL.sc) {
+        const double2 sc = SL.sc[i];
+        s0 = sc.x;
+        s1 = sc.y;
+      } else {
+        s0 = A.I_scale[a.x + a.y];
+        s1 = A.I_scale[a.z + a.w];
+      }
+#pragma unroll
+      for (int col = 0; col < CT; ++col) {
+        if (col >= nrhs) break;
+        zr[col] = zgather(s0, A.t2[(int64_t)a.x * nrhs + a.y + (int64_t)nn.x * col], s1,
+                          A.t2[(int64_t)a.z * nrhs + a.w + (int64_t)nn.y * col]);
+      }
+    }
+#pragma unroll
+    for (int col = 0; col < CT; ++col) {
+      if (col >= nrhs) break;
+      const int64_t o = l + m * col;
+      const double pv = fma(beta_s[col], first ? po[col] : pc[o], first ? zt[col] : zr[col]);
+      pn[o] = pv;
+      u[col * A.CW.utot + gu.x] = (T)(w0 * pv);
+      u[col * A.CW.utot + gu.y] = (T)(w1 * pv);
+    }
+  }
+  fence_async_global();   // the W pass reads u with bulk copies after the barrier
+}
+
 template <typename T, int CT, bool ROWS>
 __global__ void __launch_bounds__(STREAM_THREADS, 1) k_pcg_stream(PcgStreamArgs A) {
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ double red[STREAM_THREADS / 32];
+  __shared__ double dred[8 * CT];
+  __shared__ double redA[8 * CT], redB[8 * CT];
   __shared__ double qg[PS_MAXGP * CT], yc[PS_MAXGP * CT];
-  __shared__ double rz[CT], bb[CT], alpha[CT], beta[CT];
+  __shared__ double rz[CT], bb[CT], alpha_s[CT], beta_s[CT];
   __shared__ int done[CT];
-  __shared__ int zero_keep[CT];
   __shared__ int its;
   const int tid = threadIdx.x, G = gridDim.x, bid = blockIdx.x;
   const int nrhs = A.nrhs, ngp = A.ngp;
@@ -218,236 +545,84 @@ __global__ void __launch_bounds__(STREAM_THREADS, 1) k_pcg_stream(PcgStreamArgs 
     done[tid] = tid < nrhs ? (A.scal[PS_SC * tid + 7] != 0.0) : 1;
   }
   if (tid == 0) its = (int)A.scal[8];
-  if (tid < CT) zero_keep[tid] = 0;
   uint32_t seq = 0, useq = 0;
   const bool producer = tid >= NCONS;
   int npreW = 0, npreS = 0;   // tiles of the next W / S pass already in flight (producer warp)
-  double* pq_part = A.part;
-  double* rr_part = A.part + (int64_t)G * CT;
-  double* rz_part = A.part + 2 * (int64_t)G * CT;
-  const int2 krW = A.ckrW[bid], krS = A.ckrS[bid];
+  double* pW = A.part;                          // shares of <p, B t1>
+  double* pR = A.part + (int64_t)G * CT;        // shares of <r', r'>
+  double* pZ = A.part + 2 * (int64_t)G * CT;    // shares of <r', z'>
+  double* rb[2] = {A.r, A.q};
+  double* pb[2] = {A.p, A.z};
+  int cur = 0;
+  const int2 krW = A.ckrW[bid];
   // u = D_W p for the first product; the first W tiles are fetched meanwhile
   if (producer) npreW = stream_prefetch<T>(A.CW, A.ctaW[bid], A.ctaW[bid + 1], smem, seq, CT);
-  write_u_run<T, CT>(A, krW, A.p, nullptr, nullptr, nullptr, false);
+  write_u_run<T, CT>(A, krW, pb[0], nullptr, nullptr, nullptr, false);
   __syncthreads();   // every thread's u stores and fence precede the bulk copies
-  bool pend_p = false;   // p = z + beta p still to be applied to the owned slice
-  int upd[CT];           // columns that this iteration's alpha updates
+  const int nwG = (G + 31) / 32;                       // warps holding per-CTA shares
+  const int nwL = (int)((std::min<int64_t>(nl, NCONS) + 31) / 32);   // warps holding owned entries
+  PhaseCtx<CT> X;
+  X.SL = SL;
+  X.l0 = l0;
+  X.nl = nl;
+  X.estride = estride;
+  X.m = m;
+  X.E = E;
+  X.ngp = ngp;
+  X.nrhs = nrhs;
+  X.G = G;
+  X.bid = bid;
+  X.nwG = nwG;
+  X.nwL = nwL;
+  X.c_spi = c_spi;
+  X.c_cv = c_cv;
+  X.c_co = c_co;
+  X.c_pc = c_pc;
+  X.qg = qg;
+  X.yc = yc;
+  X.redA = redA;
+  X.redB = redB;
+  X.rz = rz;
+  X.bb = bb;
+  X.alpha_s = alpha_s;
+  X.beta_s = beta_s;
+  X.done = done;
+  X.its = &its;
+  X.pW = pW;
+  X.pR = pR;
+  X.pZ = pZ;
   for (int iter = 0; iter < A.maxit; ++iter) {
     bool all = true;
     for (int cc = 0; cc < nrhs; ++cc) all &= done[cc] != 0;
-    if (all || *(volatile int*)A.err) break;
-    // ---- A: local products with W and the primal partials
-    stream_tiles<T, CT, ROWS>(A.CW, A.ctaW[bid], A.ctaW[bid + 1], smem, seq, useq, A.t1, A.qpart, nrhs, 0, nrhs,
-                              npreW);
+    if (all) break;
+    double* rc = rb[cur];
+    double* rn = rb[cur ^ 1];
+    double* pc = pb[cur];
+    double* pn = pb[cur ^ 1];
+    // ---- P1: local products with W, the primal partials, share of <p, B t1>
+    stream_tiles<T, CT, ROWS, true>(A.CW, A.ctaW[bid], A.ctaW[bid + 1], smem, seq, useq, A.t1, A.qpart, nrhs, 0,
+                                    nrhs, npreW, pW + (int64_t)bid * CT, dred);
     npreW = 0;
     grid.sync();
-    // the first S tiles are fetched while the vector phases run
-    if (producer) npreS = stream_prefetch<T>(A.CS, A.ctaS[bid], A.ctaS[bid + 1], smem, seq, CT);
-    // ---- B: deferred p update; coarse correction (every CTA), q = F p, partial <p, q>
-    if (pend_p) {
-      for (int64_t l = l0 + tid; l < l1; l += blockDim.x)
-#pragma unroll
-        for (int col = 0; col < CT; ++col) {
-          if (col >= nrhs) break;
-          if (!done[col]) A.p[l + m * col] = A.z[l + m * col] + beta[col] * A.p[l + m * col];
-        }
-      pend_p = false;
-      __syncthreads();
-    }
-    if (ngp > 0) {
-      if (A.cache_coarse) {
-        // contributor values in parallel, then ordered sums per coarse DOF
-        for (int col = 0; col < nrhs; ++col) {
-          for (int64_t e = tid; e < A.ncontrib; e += blockDim.x) {
-            const int4 pc = c_pc[e];
-            c_cv[e] = A.qpart[(int64_t)pc.x * nrhs + pc.y + (int64_t)pc.z * col];
-          }
-          __syncthreads();
-          for (int g = tid; g < ngp; g += blockDim.x) {
-            double acc = 0;
-            for (int e = c_co[g]; e < c_co[g + 1]; ++e) acc += c_cv[e];
-            qg[g + ngp * col] = acc;
-          }
-          __syncthreads();
-        }
-        for (int t = tid; t < ngp * nrhs; t += blockDim.x) {
-          const int g = t % ngp, col = t / ngp;
-          const double* sp = c_spi + (size_t)ngp * g;
-          double acc = 0;
-          for (int h = 0; h < ngp; ++h) acc += sp[h] * qg[h + ngp * col];
-          yc[t] = acc;
-        }
-      } else {
-        for (int t = tid; t < ngp * nrhs; t += blockDim.x) {
-          const int g = t % ngp, col = t / ngp;
-          double acc = 0;
-          for (int64_t e = A.pcsr_off[g]; e < A.pcsr_off[g + 1]; ++e) {
-            const int4 pc = A.pcon[e];
-            acc += A.qpart[(int64_t)pc.x * nrhs + pc.y + (int64_t)pc.z * col];
-          }
-          qg[t] = acc;
-        }
-        __syncthreads();
-        for (int t = tid; t < ngp * nrhs; t += blockDim.x) {
-          const int g = t % ngp, col = t / ngp;
-          const double* cg_ = A.SPiInv + (int64_t)A.ldc * g;
-          double acc = 0;
-          for (int h = 0; h < ngp; ++h) acc += cg_[h] * qg[h + ngp * col];
-          yc[t] = acc;
-        }
-      }
-      __syncthreads();
-    }
-    double mine[CT];
-#pragma unroll
-    for (int cc = 0; cc < CT; ++cc) mine[cc] = 0;
-    for (int64_t i = tid; i < nl; i += blockDim.x) {
-      const int64_t l = l0 + i;
-      const int4 a = SL.gs[i];
-      const int2 nn = SL.gn[i];
-#pragma unroll
-      for (int col = 0; col < CT; ++col) {
-        if (col >= nrhs) break;
-        double v = A.t1[(int64_t)a.x * nrhs + a.y + (int64_t)nn.x * col] -
-                   A.t1[(int64_t)a.z * nrhs + a.w + (int64_t)nn.y * col];
-        if (ngp > 0) {
-#pragma unroll 8
-          for (int e = 0; e < E; ++e) v += SL.gv[e * estride + i] * yc[SL.gi[e * estride + i] + ngp * col];
-        }
-        A.q[l + m * col] = v;
-        mine[col] += v * A.p[l + m * col];
-      }
-    }
-    for (int cc = 0; cc < nrhs; ++cc) {
-      const double s = ps_cta_sum(mine[cc], red);
-      if (tid == 0) pq_part[(int64_t)bid * CT + cc] = s;
+    if (producer) {
+      // the first S tiles are fetched while the consumers run the vector phase
+      npreS = stream_prefetch<T>(A.CS, A.ctaS[bid], A.ctaS[bid + 1], smem, seq, CT);
+    } else {
+      pcg_phase2<T, CT>(A, X, rc, rn, pc);
     }
     grid.sync();
-    // ---- C: alpha; lam update; partial <r', r'>; u = D_S r'; products with S
-    for (int cc = 0; cc < nrhs; ++cc) {
-      const double pq = ps_sum_part(pq_part, cc, CT, red);
-      if (tid == 0) alpha[cc] = (done[cc] || pq == 0.0) ? 0.0 : rz[cc] / pq;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int cc = 0; cc < CT; ++cc) {
-      mine[cc] = 0;
-      upd[cc] = cc < nrhs && !done[cc];
-    }
-    for (int64_t l = l0 + tid; l < l1; l += blockDim.x) {
-#pragma unroll
-      for (int col = 0; col < CT; ++col) {
-        if (col >= nrhs) break;
-        const int64_t o = l + m * col;
-        double rv = A.r[o];
-        if (upd[col]) {
-          A.x[o] += alpha[col] * A.p[o];
-          rv -= alpha[col] * A.q[o];
-        }
-        mine[col] += rv * rv;
-      }
-    }
-    for (int cc = 0; cc < nrhs; ++cc) {
-      const double s = ps_cta_sum(mine[cc], red);
-      if (tid == 0) rr_part[(int64_t)bid * CT + cc] = s;
-    }
-    {
-      // r' = r - alpha q (alpha = 0 for finished columns)
-      double nalpha[CT];
-#pragma unroll
-      for (int cc = 0; cc < CT; ++cc) nalpha[cc] = -alpha[cc];
-      write_u_run<T, CT>(A, krS, A.r, A.q, nalpha, zero_keep, true);
-      __syncthreads();   // every thread's u stores and fence precede the bulk copies
-    }
-    stream_tiles<T, CT, ROWS>(A.CS, A.ctaS[bid], A.ctaS[bid + 1], smem, seq, useq, A.t2, nullptr, nrhs, 0, nrhs,
-                              npreS);
+    // ---- P3: local products with S, share of <r', z'>
+    stream_tiles<T, CT, ROWS, true>(A.CS, A.ctaS[bid], A.ctaS[bid + 1], smem, seq, useq, A.t2, nullptr, nrhs, 0,
+                                    nrhs, npreS, pZ + (int64_t)bid * CT, dred);
     npreS = 0;
     grid.sync();
-    if (producer) npreW = stream_prefetch<T>(A.CW, A.ctaW[bid], A.ctaW[bid + 1], smem, seq, CT);
-    // ---- E: deferred r update; convergence test; z = preconditioned r, partial <r, z>
-    for (int64_t l = l0 + tid; l < l1; l += blockDim.x)
-#pragma unroll
-      for (int col = 0; col < CT; ++col) {
-        if (col >= nrhs) break;
-        if (upd[col]) A.r[l + m * col] -= alpha[col] * A.q[l + m * col];
-      }
-    for (int cc = 0; cc < nrhs; ++cc) {
-      const double rr = ps_sum_part(rr_part, cc, CT, red);
-      if (tid == 0 && !done[cc]) {
-        if (bid == 0) {
-          A.scal[PS_SC * cc + 2] = rr;
-          A.scal[PS_SC * cc + 4] = alpha[cc];
-          A.scal[PS_SC * cc + 8] += 1.0;
-        }
-        if (rr <= A.tol2 * bb[cc]) done[cc] = 1;
-      }
+    if (producer) {
+      npreW = stream_prefetch<T>(A.CW, A.ctaW[bid], A.ctaW[bid + 1], smem, seq, CT);
+    } else {
+      pcg_phase4<T, CT>(A, X, pc, pn);
     }
-    if (tid == 0) {
-      ++its;
-      if (bid == 0 && A.hist && its <= A.hist_cap) A.hist[2 * (its - 1)] = alpha[0];
-    }
-    __syncthreads();
-    {
-      bool fin = true;
-      for (int cc = 0; cc < nrhs; ++cc) fin &= done[cc] != 0;
-      if (fin) break;
-    }
-#pragma unroll
-    for (int cc = 0; cc < CT; ++cc) mine[cc] = 0;
-    for (int64_t i = tid; i < nl; i += blockDim.x) {
-      const int64_t l = l0 + i;
-      const int4 a = SL.gs[i];
-      const int2 nn = SL.gn[i];
-      double s0, s1;
-      if (SL.sc) {
-        const double2 sc = SL.sc[i];
-        s0 = sc.x;
-        s1 = sc.y;
-      } else {
-        s0 = A.I_scale[a.x + a.y];
-        s1 = A.I_scale[a.z + a.w];
-      }
-#pragma unroll
-      for (int col = 0; col < CT; ++col) {
-        if (col >= nrhs) break;
-        const double v = s0 * A.t2[(int64_t)a.x * nrhs + a.y + (int64_t)nn.x * col] -
-                         s1 * A.t2[(int64_t)a.z * nrhs + a.w + (int64_t)nn.y * col];
-        A.z[l + m * col] = v;
-        mine[col] += v * A.r[l + m * col];
-      }
-    }
-    for (int cc = 0; cc < nrhs; ++cc) {
-      const double s = ps_cta_sum(mine[cc], red);
-      if (tid == 0) rz_part[(int64_t)bid * CT + cc] = s;
-    }
-    grid.sync();
-    // ---- F: beta; u = D_W (z + beta p) (the owned p follows in B)
-    for (int cc = 0; cc < nrhs; ++cc) {
-      const double rzn = ps_sum_part(rz_part, cc, CT, red);
-      if (tid == 0) {
-        beta[cc] = (done[cc] || rz[cc] == 0.0) ? 0.0 : rzn / rz[cc];
-        if (!done[cc]) {
-          rz[cc] = rzn;
-          if (bid == 0) {
-            A.scal[PS_SC * cc + 0] = rzn;
-            A.scal[PS_SC * cc + 5] = beta[cc];
-          }
-        }
-      }
-    }
-    __syncthreads();
-    if (bid == 0 && tid == 0 && A.hist && its <= A.hist_cap) A.hist[2 * (its - 1) + 1] = beta[0];
-    write_u_run<T, CT>(A, krW, A.z, A.p, beta, done, false);
-    pend_p = true;
-    __syncthreads();   // every thread's u stores and fence precede the bulk copies
-  }
-  if (pend_p) {
-    for (int64_t l = l0 + tid; l < l1; l += blockDim.x)
-#pragma unroll
-      for (int col = 0; col < CT; ++col) {
-        if (col >= nrhs) break;
-        if (!done[col]) A.p[l + m * col] = A.z[l + m * col] + beta[col] * A.p[l + m * col];
-      }
+    grid.sync();   // every CTA's u entries (and the done flags) before the next W pass
+    cur ^= 1;
   }
   // tiles fetched ahead for a pass that will not run
   if (producer) stream_drain(smem, seq, npreW + npreS, A.CW.stages);
@@ -514,7 +689,9 @@ ieti_status pcg_stream(Ctx* c, double* lam, double* r, double* z, double* p, dou
   A.CW.utot = c->utot;
   A.CW.u_ld = c->max_ldI;
   A.CW.err = c->d_stream_err;
+  A.CW.l2_hint = 1;   // W stays in L2 across iterations
   A.CS = A.CW;
+  A.CS.l2_hint = 2;   // S streams through
   A.CS.M = c->S;
   A.CS.tiles = (const LTile*)PS.d_tiles;
   A.ctaW = PW.d_cta;

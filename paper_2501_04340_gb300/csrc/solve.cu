@@ -26,6 +26,7 @@ namespace ieti {
 // the factors are redone in FP64
 constexpr int MAX_REFINE_STEPS = 16;
 constexpr double FALLBACK_CONTRACTION = 0.25;
+constexpr int FALLBACK_MIN_ITS = 50;
 
 constexpr int LOC_CT = 8;      // RHS columns per CTA in the local products
 constexpr int LOC_ROWS = 32;   // rows of W per CTA (4 per warp)
@@ -976,6 +977,7 @@ ieti_status solve_all(Ctx* c, const double* lam0, double tol, int maxit, double 
   IETI_CUDA_TRY(c, cudaMemsetAsync(a, 0, sizeof(double) * ne * nrhs, st));
   IETI_CUDA_TRY(c, cudaMemsetAsync(c->wlam_acc, 0, sizeof(double) * m * nrhs, st));
   IETI_CUDA_TRY(c, cudaMemsetAsync(c->d_dep_err, 0, sizeof(int), st));
+  IETI_CUDA_TRY(c, cudaMemsetAsync(c->d_stream_err, 0, sizeof(int), st));
   // FP64 factors: one pass, refined further only when a field tolerance is given;
   // FP32 factors: always refined (default field tolerance 1e-10)
   const bool refine = fp32 || tol_field > 0;
@@ -1033,12 +1035,16 @@ ieti_status solve_all(Ctx* c, const double* lam0, double tol, int maxit, double 
     if (c->h_err[1]) break;
     // FP32 factors outside their regime (kappa(K_rr) u_32 not small) show in
     // the first corrections: one of the first two correction steps whose inner
-    // PCG converged but which does not cut the field residual by
+    // PCG converged (or ran at least FALLBACK_MIN_ITS iterations, so that an
+    // iteration cap of the caller is not mistaken for it) but which does not cut the field residual by
     // FALLBACK_CONTRACTION, or any step that gives a non-finite residual,
     // switches the context to FP64 factors for the remaining steps (restarting
     // from the loads if the field is not finite). Later stalls come from the
     // rounding floor of the FP64 residual, which FP64 factors do not lower.
-    const bool stalled = step > 0 && step <= 2 && pr == IETI_OK && grel > FALLBACK_CONTRACTION * grel_prev;
+    const bool stalled = (step > 0 && step <= 2 && (pr == IETI_OK || its >= FALLBACK_MIN_ITS) &&
+                          grel > FALLBACK_CONTRACTION * grel_prev) ||
+                         (fp32 && step == 1 && c->force_fallback);
+    if (step == 1) c->force_fallback = false;
     if (fp32 && (stalled || !std::isfinite(grel))) {
       c->prec = IETI_FP64;
       if ((r = factor_all(c, st)) != IETI_OK) {
@@ -1060,12 +1066,13 @@ ieti_status solve_all(Ctx* c, const double* lam0, double tol, int maxit, double 
   if (lam_out)
     IETI_CUDA_TRY(c, cudaMemcpyAsync(lam_out, c->wlam_acc, sizeof(double) * m * nrhs, cudaMemcpyDeviceToDevice, st));
   IETI_CUDA_TRY(c, cudaMemcpyAsync(c->h_err + 1, c->d_dep_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  IETI_CUDA_TRY(c, cudaMemcpyAsync(c->h_err + 2, c->d_stream_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   IETI_CUDA_TRY(c, cudaEventRecord(e1, st));
   IETI_CUDA_TRY(c, cudaEventSynchronize(e1));
-  if (c->h_err[1]) {
+  if (c->h_err[1] || c->h_err[2]) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    c->err = "a triangular-sweep wait timed out";
+    c->err = c->h_err[1] ? "a triangular-sweep wait timed out" : "a bulk-copy wait of the interface products timed out";
     return IETI_ERR_TIMEOUT;
   }
   float ms = 0;

@@ -73,6 +73,31 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                : "memory");
 }
 
+// the same copy with an L2 eviction priority (a policy from l2_policy)
+__device__ __forceinline__ void bulk_load_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                               uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          saddr(dst)),
+      "l"(src), "r"(bytes), "r"(saddr(bar)), "l"(policy)
+      : "memory");
+}
+
+// L2 policies: 1 = keep (evict last), 2 = stream through (evict first)
+__device__ __forceinline__ uint64_t l2_policy(int hint) {
+  uint64_t pol = 0;
+  if (hint == 1) asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  else if (hint == 2) asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+// a tile copy with the stream's L2 priority
+__device__ __forceinline__ void tile_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar, int hint,
+                                          uint64_t policy) {
+  if (hint) bulk_load_hint(dst, src, bytes, bar, policy);
+  else bulk_load(dst, src, bytes, bar);
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -106,6 +131,7 @@ struct StreamCtx {
   int64_t utot;        // column stride of uall (elements)
   int u_ld, stages, stage_bytes;
   int* err;            // device error word (set on a timed-out wait)
+  int l2_hint;         // L2 priority of the tile copies: 0 normal, 1 evict last, 2 evict first
 };
 
 __device__ __forceinline__ void consumer_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
@@ -189,7 +215,7 @@ __device__ __forceinline__ void stream_init_bars(unsigned char* smem, int stages
 // stages they used (the caller places a barrier in between). Returns the
 // number of tiles issued (0 after a timed-out wait, which sets the abort flag).
 template <typename T>
-__device__ int stream_prefetch(const StreamCtx& C, int tb, int te, unsigned char* smem, uint32_t seq, int ct) {
+__device__ __noinline__ int stream_prefetch(const StreamCtx& C, int tb, int te, unsigned char* smem, uint32_t seq, int ct) {
   const int n = te - tb;
   if (n <= 0) return 0;
   StreamBars B(smem);
@@ -202,6 +228,7 @@ __device__ int stream_prefetch(const StreamCtx& C, int tb, int te, unsigned char
   __syncwarp();
   int npre = 0;
   if (lane == 0) {
+    const uint64_t pol = l2_policy(C.l2_hint);
     const int want = min(n, (int)S);
     for (int j = 0; j < want && !*B.abort_flag; ++j) {
       const LTile tl = win[j];
@@ -214,7 +241,7 @@ __device__ int stream_prefetch(const StreamCtx& C, int tb, int te, unsigned char
       }
       const T* src = (tl.kind ? (const T*)C.PhiT : (const T*)C.M) + tl.src;
       mbar_expect_tx(&B.full[st], (uint32_t)tl.bytes);
-      bulk_load(stage_base + (size_t)st * C.stage_bytes, src, (uint32_t)tl.bytes, &B.full[st]);
+      tile_load(stage_base + (size_t)st * C.stage_bytes, src, (uint32_t)tl.bytes, &B.full[st], C.l2_hint, pol);
       npre = j + 1;
     }
   }
@@ -259,14 +286,28 @@ __device__ inline void stream_drain(unsigned char* smem, uint32_t seq, int npre,
 // the partial products of all rows (at most RMAX) for all CT columns. The
 // partials are summed by a halving exchange within each warp and a fixed-order
 // sum over the 8 warps.
-template <typename T, int CT, bool ROWS = false>
-__device__ void stream_tiles(const StreamCtx& C, int tb, int te, unsigned char* smem, uint32_t& seq,
+//
+// With DOT, the consumers also form sum_k u_k . t_k over the rows of M_k that
+// this range produces, per column (the CTA's share of an inner product such
+// as <p, B W B^T p>), and consumer thread 0 writes it to dot_out[col]
+// (dred: 8 CT doubles of shared scratch; zero for an empty range).
+// Kept out of line: the persistent PCG kernel calls it for both passes, and
+// two inlined copies of the streaming loop left one of them with a far worse
+// register allocation (the FP64 W pass ran at half the speed of the S pass).
+template <typename T, int CT, bool ROWS = false, bool DOT = false>
+__device__ __noinline__ void stream_tiles(const StreamCtx& C, int tb, int te, unsigned char* smem, uint32_t& seq,
                              uint32_t& useq, double* t, double* qpart, int nrhs, int col0, int nc,
-                             int npre = 0) {
+                             int npre = 0, double* dot_out = nullptr, double* dred = nullptr) {
   constexpr int VEC = 16 / sizeof(T);
   constexpr int V = RMAX * CT;
   const int n = te - tb;
-  if (n <= 0) return;
+  if (n <= 0) {
+    if (DOT && threadIdx.x < nc) dot_out[threadIdx.x] = 0.0;
+    return;
+  }
+  double dacc[CT];
+#pragma unroll
+  for (int cc = 0; cc < CT; ++cc) dacc[cc] = 0.0;
   StreamBars B(smem);
   LTile* win = reinterpret_cast<LTile*>(smem + BAR_BYTES);      // [2][WIN]
   double* red = reinterpret_cast<double*>(smem + BAR_BYTES + WIN_BYTES);   // [2][8 warps][V]
@@ -278,12 +319,16 @@ __device__ void stream_tiles(const StreamCtx& C, int tb, int te, unsigned char* 
 
   uint32_t uq_end;   // useq after this range (the same in every thread unless aborted)
   if (warp == NCONS / 32) {
+    // u may have been written by other CTAs (generic proxy) before a grid
+    // barrier: order the bulk copies (async proxy) after that view
+    asm volatile("fence.proxy.async.global;" ::: "memory");
     // ---- producer warp: every WIN tiles all lanes copy the next WIN
     // descriptors into a shared window (the consumers read them there once the
     // tile has landed); lane 0 waits for free buffers and issues the copies
     uint32_t uq = useq;
     int issued = 0, pk = -1;
     bool stop = false;
+    const uint64_t pol = lane == 0 ? l2_policy(C.l2_hint) : 0;
     for (int j = 0; j < n && !stop; ++j) {
       if (j % WIN == 0 && !(j == 0 && npre > 0)) {   // window 0 is filled by stream_prefetch
         const int jj = j + lane;
@@ -321,7 +366,8 @@ __device__ void stream_tiles(const StreamCtx& C, int tb, int te, unsigned char* 
           } else {
             const T* src = (tl.kind ? (const T*)C.PhiT : (const T*)C.M) + tl.src;
             mbar_expect_tx(&B.full[st], (uint32_t)tl.bytes);
-            bulk_load(stage_base + (size_t)st * C.stage_bytes, src, (uint32_t)tl.bytes, &B.full[st]);
+            tile_load(stage_base + (size_t)st * C.stage_bytes, src, (uint32_t)tl.bytes, &B.full[st], C.l2_hint,
+                      pol);
             issued = j + 1;
           }
         }
@@ -381,6 +427,11 @@ __device__ void stream_tiles(const StreamCtx& C, int tb, int te, unsigned char* 
       const T* buf = reinterpret_cast<const T*>(stage_base + (size_t)st * C.stage_bytes);
       for (int r = warp; ok && r < tl.nrows; r += NCONS / 32) {
         const V4* row = reinterpret_cast<const V4*>(buf + (size_t)r * tl.ldI);
+        // u at this row for the inner product, from the prepared vectors in
+        // global memory (this CTA wrote them before the pass: an L1 or L2 hit),
+        // loaded before the row's products so that its latency overlaps them
+        T ue = 0;
+        if (DOT && tl.kind == 0 && lane == 0) ue = ((const T*)C.uall)[(int64_t)col0 * C.utot + tl.uoff + tl.row0 + r];
         T a0 = 0, a1 = 0;   // two chains of fused multiply-adds
 #pragma unroll
         for (int q = 0; q < UREG; ++q) {
@@ -405,6 +456,9 @@ __device__ void stream_tiles(const StreamCtx& C, int tb, int te, unsigned char* 
         if (lane == 0 && nc > 0) {
           double* out = tl.kind == 0 ? t : qpart;
           out[tl.obase * nrhs + tl.row0 + r + (int64_t)tl.ostride * col0] = (double)acc;
+        }
+        if constexpr (DOT) {
+          if (tl.kind == 0 && lane == 0) dacc[0] += (double)acc * (double)ue;
         }
       }
       __syncwarp();
@@ -494,11 +548,38 @@ __device__ void stream_tiles(const StreamCtx& C, int tb, int te, unsigned char* 
           for (int w = 0; w < 8; ++w) sum += rd[w * V + v];
           double* out = tl.kind == 0 ? t : qpart;
           out[tl.obase * nrhs + tl.row0 + r + (int64_t)tl.ostride * (col0 + cc)] = sum;
+          if constexpr (DOT) {
+            if (tl.kind == 0) {
+              const double pr = sum * (double)u[(size_t)cc * C.u_ld + tl.row0 + r];
+#pragma unroll
+              for (int c2 = 0; c2 < CT; ++c2)
+                if (c2 == cc) dacc[c2] += pr;
+            }
+          }
         }
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&B.uempty[(uq - 1) & 1u]);   // done with the last u
     uq_end = uq;
+  }
+  if constexpr (DOT) {
+    // the CTA's share per column: warp sums, then the 8 consumer warps in order
+    if (warp < NCONS / 32) {
+#pragma unroll
+      for (int cc = 0; cc < CT; ++cc) {
+        double v = dacc[cc];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) dred[warp * CT + cc] = v;
+      }
+      consumer_bar();
+      if (tid < nc) {
+        double s = 0;
+#pragma unroll
+        for (int w = 0; w < NCONS / 32; ++w) s += dred[w * CT + tid];
+        dot_out[tid] = s;
+      }
+    }
   }
   seq += (uint32_t)n;
   useq = uq_end;

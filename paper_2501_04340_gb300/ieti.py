@@ -265,6 +265,7 @@ def ieti_launch_count(ctx):
 
 IETI_DEBUG_WAIT_POLLS = 1
 IETI_DEBUG_PIVOT_FAULT = 2
+IETI_DEBUG_FP64_FALLBACK = 3
 
 
 def ieti_debug_set(ctx, what, value):
