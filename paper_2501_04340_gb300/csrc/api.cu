@@ -417,6 +417,7 @@ ieti_status build(Ctx* c, const ieti_problem_desc* desc, bool device) {
   for (int i = 0; i < 2; ++i) TRY(dalloc(c, &c->wc[i], std::max<int64_t>(c->n_gp, 1) * MAX_RHS));
   for (int i = 0; i < 8; ++i) TRY(dalloc(c, &c->wlam[i], std::max<int64_t>(c->m_r, 1) * nr));
   TRY(dalloc(c, &c->wlam_acc, std::max<int64_t>(c->m_r, 1) * nr));
+  TRY(dalloc(c, &c->wvf, 5 * std::max<int64_t>(c->m_r, 1) * nr));
   TRY(dalloc(c, &c->wscal, 16 * MAX_RHS));
   TRY(dalloc(c, &c->wred, 512 * MAX_RHS));
   TRY(dalloc(c, &c->wflag, 64));

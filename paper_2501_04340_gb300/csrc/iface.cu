@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "internal.h"
@@ -25,6 +27,8 @@
 namespace ieti {
 
 namespace {
+
+constexpr int ROW_TARGET_DEFAULT = 32 * 1024;   // bytes per row-mode tile before autotuning
 
 struct StreamArgs {
   StreamCtx C;
@@ -225,7 +229,12 @@ ieti_status alloc_dev(Ctx* c, T** p, size_t count) {
 // into whole-row tiles of about TILE_TARGET bytes, subdomain by subdomain; CTA
 // j owns the tiles whose cost offsets start in [j C / grid, (j+1) C / grid),
 // the cost being the bytes plus a fixed charge per subdomain entered
-ieti_status build_plan(Ctx* c, int es, bool with_phi, StreamPlan* P, int rcap = RMAX) {
+// Row mode (row_target > 0, one column): a warp reduces whole rows, so a tile
+// may hold more than RMAX rows; tiles of about row_target bytes keep the same
+// bytes in flight in every stage whatever the row length of the subdomain
+// (with a fixed row count, CTAs on subdomains with short rows streamed fewer
+// bytes per round trip and finished last).
+ieti_status build_plan(Ctx* c, int es, bool with_phi, StreamPlan* P, int rcap = RMAX, int row_target = 0) {
   std::vector<LTile> tiles;
   std::vector<int64_t> start;   // balancing cost before each tile
   int64_t bytes = 0, cost = 0;
@@ -242,7 +251,9 @@ ieti_status build_plan(Ctx* c, int es, bool with_phi, StreamPlan* P, int rcap = 
     }
     const int64_t rb = (int64_t)s.ldI * es;
     // whole rows, at most RMAX of them, about TILE_TARGET bytes
-    const int rpt = (int)std::max<int64_t>(1, std::min<int64_t>(std::min(rcap, RMAX), TILE_TARGET / rb));   // 1 .. rcap rows
+    const int rpt = row_target > 0
+                        ? (int)std::max<int64_t>(1, std::min<int64_t>(RROW_MAX, row_target / rb))
+                        : (int)std::max<int64_t>(1, std::min<int64_t>(std::min(rcap, RMAX), TILE_TARGET / rb));
     stage_bytes = std::max<int>(stage_bytes, (int)(rpt * rb));
     for (int kind = 0; kind < (with_phi ? 2 : 1); ++kind) {
       const int rows = kind == 0 ? s.nI : s.nP;
@@ -298,7 +309,8 @@ ieti_status build_plan(Ctx* c, int es, bool with_phi, StreamPlan* P, int rcap = 
   P->grid = grid;
   P->stage_bytes = stage_bytes;
   P->bytes = bytes;
-  P->rows_cap = rcap;
+  P->rows_cap = row_target > 0 ? RROW_MAX : rcap;
+  P->row_target = row_target;
   P->built = true;
   return IETI_OK;
 }
@@ -486,14 +498,18 @@ ieti_status iface_alloc(Ctx* c) {
 static ieti_status autotune_plans(Ctx* c, bool fp32, cudaStream_t st) {
   const int es = fp32 ? 4 : 8;
   double* x = c->wlam[6];
-  IETI_CUDA_TRY(c, cudaMemsetAsync(x, 0, sizeof(double) * std::max<int64_t>(c->m_r, 1), st));
+  // the multi-column plans are timed on all columns (a single column runs on
+  // the row-mode plans when they exist)
+  const int tn = c->nrhs;
+  IETI_CUDA_TRY(c, cudaMemsetAsync(x, 0, sizeof(double) * std::max<int64_t>(c->m_r, 1) * tn, st));
+  const bool trace = std::getenv("IETI_TRACE") != nullptr;
   cudaEvent_t e0, e1;
   IETI_CUDA_TRY(c, cudaEventCreate(&e0));
   IETI_CUDA_TRY(c, cudaEventCreate(&e1));
   const bool prof = c->prof.on;
   c->prof.on = false;
   ieti_status res = IETI_OK;
-  for (int wp = 0; wp < 2 && res == IETI_OK; ++wp) {
+  for (int wp = 0; wp < 2 && res == IETI_OK && !(tn == 1 && c->rplan[fp32][wp].built); ++wp) {
     const StreamPlan def = c->splan[fp32][wp];
     StreamPlan best = def;
     float best_ms = -1.f;
@@ -505,8 +521,38 @@ static ieti_status autotune_plans(Ctx* c, bool fp32, cudaStream_t st) {
       c->splan[fp32][wp] = cand;
       ieti_status r = IETI_OK;
       for (int it = 0; it < 3 && r == IETI_OK; ++it)
-        r = iface_local(c, fp32, wp == 1, x, wp == 1 ? nullptr : c->d_I_scale, c->wi[0], c->wq_part, 1, st);
+        r = iface_local(c, fp32, wp == 1, x, wp == 1 ? nullptr : c->d_I_scale, c->wi[0], c->wq_part, tn, st);
       if (r != IETI_OK) continue;   // this shape does not fit: not a candidate
+      IETI_CUDA_TRY(c, cudaEventRecord(e0, st));
+      for (int it = 0; it < 10 && r == IETI_OK; ++it)
+        r = iface_local(c, fp32, wp == 1, x, wp == 1 ? nullptr : c->d_I_scale, c->wi[0], c->wq_part, tn, st);
+      IETI_CUDA_TRY(c, cudaEventRecord(e1, st));
+      IETI_CUDA_TRY(c, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      IETI_CUDA_TRY(c, cudaEventElapsedTime(&ms, e0, e1));
+      if (trace) std::fprintf(stderr, "[ieti] plan fp32=%d phi=%d rows<=%d: %.1f us\n", (int)fp32, wp, rcap, 100.f * ms);
+      if (r == IETI_OK && (best_ms < 0.f || ms < best_ms)) {
+        best_ms = ms;
+        best = cand;
+      }
+    }
+    c->splan[fp32][wp] = best;
+  }
+  // row-mode plans: the bytes per tile
+  for (int wp = 0; wp < 2 && res == IETI_OK && c->rplan[fp32][0].built; ++wp) {
+    const StreamPlan def = c->rplan[fp32][wp];
+    StreamPlan best = def;
+    float best_ms = -1.f;
+    for (int target : {16 * 1024, 24 * 1024, 32 * 1024, 48 * 1024}) {
+      StreamPlan cand;
+      if (target == def.row_target) cand = def;
+      else if ((res = build_plan(c, es, wp == 1, &cand, RMAX, target)) != IETI_OK) break;
+      if (cand.incomplete || cand.ntiles == 0) continue;
+      c->rplan[fp32][wp] = cand;
+      ieti_status r = IETI_OK;
+      for (int it = 0; it < 3 && r == IETI_OK; ++it)
+        r = iface_local(c, fp32, wp == 1, x, wp == 1 ? nullptr : c->d_I_scale, c->wi[0], c->wq_part, 1, st);
+      if (r != IETI_OK) continue;
       IETI_CUDA_TRY(c, cudaEventRecord(e0, st));
       for (int it = 0; it < 10 && r == IETI_OK; ++it)
         r = iface_local(c, fp32, wp == 1, x, wp == 1 ? nullptr : c->d_I_scale, c->wi[0], c->wq_part, 1, st);
@@ -514,12 +560,15 @@ static ieti_status autotune_plans(Ctx* c, bool fp32, cudaStream_t st) {
       IETI_CUDA_TRY(c, cudaEventSynchronize(e1));
       float ms = 0.f;
       IETI_CUDA_TRY(c, cudaEventElapsedTime(&ms, e0, e1));
+      if (trace)
+        std::fprintf(stderr, "[ieti] row plan fp32=%d phi=%d %d KB tiles: %.1f us\n", (int)fp32, wp, target / 1024,
+                     100.f * ms);
       if (r == IETI_OK && (best_ms < 0.f || ms < best_ms)) {
         best_ms = ms;
         best = cand;
       }
     }
-    c->splan[fp32][wp] = best;
+    c->rplan[fp32][wp] = best;
   }
   c->prof.on = prof;
   cudaEventDestroy(e0);
@@ -534,6 +583,11 @@ ieti_status iface_prepare(Ctx* c, cudaStream_t st) {
   ieti_status r;
   for (int wp = 0; wp < 2; ++wp)
     if (!c->splan[fp32][wp].built && (r = build_plan(c, es, wp == 1, &c->splan[fp32][wp])) != IETI_OK) return r;
+  if (c->max_ldI <= ROW_MAX_ELEMS)
+    for (int wp = 0; wp < 2; ++wp)
+      if (!c->rplan[fp32][wp].built &&
+          (r = build_plan(c, es, wp == 1, &c->rplan[fp32][wp], RMAX, ROW_TARGET_DEFAULT)) != IETI_OK)
+        return r;
   // the u vectors are read in the factor precision: clear them (their padding
   // entries must be zero in that view)
   IETI_CUDA_TRY(c, cudaMemsetAsync(c->uall, 0, sizeof(double) * (size_t)c->utot * MAX_RHS, st));
@@ -558,7 +612,9 @@ ieti_status iface_prepare(Ctx* c, cudaStream_t st) {
 // with_phi); IETI_ERR_STATE if the streamed form does not fit this context
 ieti_status iface_local(Ctx* c, bool fp32, bool with_phi, const double* x, const double* scale, double* t,
                         double* qpart, int nrhs, cudaStream_t st) {
-  const StreamPlan& P = c->splan[fp32][with_phi];
+  // one column in row mode: the plan with tiles of equal bytes
+  const bool rowp = nrhs == 1 && c->rplan[fp32][with_phi].built;
+  const StreamPlan& P = rowp ? c->rplan[fp32][with_phi] : c->splan[fp32][with_phi];
   if (!P.built || P.ntiles == 0 || P.incomplete) return IETI_ERR_STATE;
   const int want = nrhs == 1 ? 1 : nrhs == 2 ? 2 : nrhs <= 4 ? 4 : 8;
   int ct = 0, stages = 0;

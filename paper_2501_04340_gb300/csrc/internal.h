@@ -81,6 +81,7 @@ struct StreamPlan {
   int* d_cta = nullptr;      // first tile of every CTA (grid + 1 entries)
   int2* d_ckr = nullptr;     // subdomains [x, y) that every CTA's tiles touch
   int rows_cap = 0;          // rows per tile at most (chosen by the autotuner)
+  int row_target = 0;        // row-mode plan: tiles of whole rows of about this many bytes (0: rows_cap rows)
 };
 
 // one step of the blocked factorisation with its work lists (symbolic.cu)
@@ -239,6 +240,7 @@ struct Ctx {
   double* wq_part = nullptr;             // per subdomain primal partials
   double* wc[2] = {nullptr, nullptr};    // coarse vectors
   double* wlam[8] = {};                  // PCG vectors (m_r x nrhs)
+  float* wvf = nullptr;                  // FP32 PCG vectors of the streamed form (5 x m_r x nrhs)
   double* wscal = nullptr;               // PCG scalars
   double* wred = nullptr;                // reduction partials
   int* wflag = nullptr;
@@ -257,6 +259,7 @@ struct Ctx {
   // streamed interface products (iface.cu)
   int sm_count = 0, smem_optin = 0;
   StreamPlan splan[2][2];                // [FP32 operators][with the Phi_I^T rows]
+  StreamPlan rplan[2][2];                // the same for single-column row mode: tiles of equal bytes
   void* PhiT = nullptr;                  // rows of Phi_I^(k)T in the factor precision (nP x ldI)
   std::vector<int64_t> phio;             // their offsets
   int64_t* d_phio = nullptr;

@@ -29,10 +29,20 @@
 // are fetched with the L2 evict-last priority and the S tiles with
 // evict-first, so that W stays in L2 from one iteration to the next when W and
 // S together exceed it.
+//
+// The vectors and scalars of the loop are kept in the operators' precision V:
+// FP64 with FP64 operators, FP32 with FP32 operators (the inner solve of the
+// refinement, which stops at a relative residual of 1e-3 or above). GB300
+// issues an FP64 fused multiply-add at 2 per clock per SM with a dependent
+// latency of 64 clocks, so FP64 chains in the latency-bound vector phases cost
+// far more than the FP32 ones. The FP32 vectors are normalised per column by
+// ||b|| so that no value leaves the FP32 range; the shared scalars written for
+// the host are scaled back.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.h"
 #include "stream.cuh"
@@ -55,7 +65,7 @@ struct PcgStreamArgs {
   const SubDev* sd;
   const int64_t* uoff;
   const int32_t* I_dual;
-  double *x, *r, *z, *p, *q;     // lam, r, p, and the second r (q) and p (z) buffers
+  void *x, *r, *z, *p, *q;       // lam, r, p, and the second r (q) and p (z) buffers (V)
   double *t1, *t2, *qpart;
   double* part;                  // per-CTA shares [3][grid][CT]: <p, B t1>, <r', r'>, <r', z'>
   double* scal;
@@ -78,6 +88,7 @@ struct PcgStreamArgs {
   double tol2;
   int* err;
   int64_t ncontrib;              // contributors of all coarse DOFs (pcsr entries)
+  int vscaled;                   // 1: the vectors are divided by ||b|| per column (FP32 vectors)
   size_t cache_off;              // dynamic shared memory offset of the per-CTA caches
   int cache_slice;               // 1: the slice metadata is cached in shared memory
   int cache_coarse;              // 1: S_Pi^-1 and the contributor lists are cached
@@ -90,23 +101,29 @@ struct PcgStreamArgs {
 //   sides) | sc double2[nl] (rho-scaling of both sides) | gv double[E nl] |
 //   gi int32[E nl] | then, if cached, S_Pi^-1 (ngp x ngp) | contributor values
 //   double[ncontrib] | contributor offsets int32[ngp + 1] | contributors int4
+template <typename V>
+using Vec2 = typename std::conditional<sizeof(V) == 4, float2, double2>::type;
+
+template <typename V>
 struct Slice {
   int64_t l0, nl;
   const int4* gs;
   const int2* gn;
   const int2* gu;
-  const double2* sg;
-  const double2* sc;
-  const double* gv;
+  const Vec2<V>* sg;
+  const Vec2<V>* sc;
+  const V* gv;                   // cached coarse map, else nullptr and gv64 (FP64, in global memory)
+  const double* gv64;
   const int32_t* gi;
 };
 
-__host__ __device__ inline size_t slice_bytes(int64_t nl, int E) {
-  return (size_t)nl * (16 + 8 + 8 + 16 + 16) + (size_t)nl * E * (8 + 4);
+// vs: bytes of V
+__host__ __device__ inline size_t slice_bytes(int64_t nl, int E, int vs) {
+  return (size_t)nl * (16 + 8 + 8 + 4 * vs) + (size_t)nl * E * (vs + 4);
 }
 __host__ __device__ inline size_t round16(size_t b) { return (b + 15) / 16 * 16; }
-__host__ __device__ inline size_t coarse_bytes(int ngp, int64_t ncontrib) {
-  return round16((size_t)ngp * ngp * 8) + round16((size_t)ncontrib * 8) + round16((size_t)(ngp + 1) * 4) +
+__host__ __device__ inline size_t coarse_bytes(int ngp, int64_t ncontrib, int vs) {
+  return round16((size_t)ngp * ngp * vs) + round16((size_t)ncontrib * vs) + round16((size_t)(ngp + 1) * 4) +
          (size_t)ncontrib * 16;
 }
 
@@ -115,9 +132,9 @@ __device__ inline void fence_async_global() { asm volatile("fence.proxy.async.gl
 // u_k = D_k v at the r_I DOFs of every subdomain k in kr (D = sign, times the
 // rho-scaling if scaled), v = a + s[col] b (b == nullptr: v = a); a column
 // with keep[col] set takes v = b. Each local r_I DOF has one multiplier.
-template <typename T, int CT>
-__device__ inline void write_u_run(const PcgStreamArgs& A, int2 kr, const double* a, const double* b,
-                                   const double* s, const int* keep, bool scaled) {
+template <typename T, int CT, typename V>
+__device__ inline void write_u_run(const PcgStreamArgs& A, int2 kr, const V* a, const V* b,
+                                   const V* s, const int* keep, bool scaled) {
   T* u = (T*)A.CW.uall;
   for (int k = kr.x; k < kr.y; ++k) {
     const int64_t iv = A.sd[k].iv;
@@ -127,8 +144,8 @@ __device__ inline void write_u_run(const PcgStreamArgs& A, int2 kr, const double
       const int i = q % nI, col = q / nI;
       const int64_t j = iv + i;
       const int64_t l = A.I_dual[j] + A.m * col;
-      const double w = scaled ? A.I_sign[j] * A.I_scale[j] : A.I_sign[j];
-      double v;
+      const V w = (V)(scaled ? A.I_sign[j] * A.I_scale[j] : A.I_sign[j]);
+      V v;
       if (b == nullptr) v = a[l];
       else if (keep[col]) v = b[l];
       else v = a[l] + s[col] * b[l];
@@ -143,10 +160,11 @@ __device__ inline void write_u_run(const PcgStreamArgs& A, int2 kr, const double
 __device__ __forceinline__ void cons_sync() { asm volatile("bar.sync 2, 256;" ::: "memory"); }
 
 // Block sum over the consumer warps of one value per thread, in the warps
-// [0, nw) that hold nonzero values; red: [8] doubles. The total is in
-// red[8] afterwards (visible after the next cons_sync). GB300's FP64 pipe is
-// narrow: the partial sums are formed once, not in every thread.
-__device__ __forceinline__ void cons_sum_begin(double v, int nw, double* red) {
+// [0, nw) that hold nonzero values; red: [8] values; cons_sum_end (after the
+// next cons_sync) adds the warp sums. The partial sums are formed once, not in
+// every thread.
+template <typename V>
+__device__ __forceinline__ void cons_sum_begin(V v, int nw, V* red) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   if (warp < nw) {
 #pragma unroll
@@ -154,32 +172,35 @@ __device__ __forceinline__ void cons_sum_begin(double v, int nw, double* red) {
     if (lane == 0) red[warp] = v;
   }
 }
-__device__ __forceinline__ double cons_sum_end(int nw, const double* red) {
-  double s = 0;
+template <typename V>
+__device__ __forceinline__ V cons_sum_end(int nw, const V* red) {
+  V s = 0;
   for (int w = 0; w < nw; ++w) s += red[w];
   return s;
 }
 
 // z' = s0 t2(side 0) - s1 t2(side 1) of the multiplier, as one expression
-__device__ __forceinline__ double zgather(double s0, double ta, double s1, double tb) {
+template <typename V>
+__device__ __forceinline__ V zgather(V s0, V ta, V s1, V tb) {
   return fma(s0, ta, -(s1 * tb));
 }
 
 // state of the vector phases of one CTA: the shared-memory caches and
 // scalars of the kernel
-template <int CT>
+template <typename V, int CT>
 struct PhaseCtx {
-  Slice SL;
+  Slice<V> SL;
   int64_t l0, nl, estride, m;
   int E, ngp, nrhs, G, bid, nwG, nwL;
-  double* c_spi;
-  double* c_cv;
+  V* c_spi;
+  V* c_cv;
   const int32_t* c_co;
   const int4* c_pc;
-  double *qg, *yc, *redA, *redB, *rz, *bb, *alpha_s, *beta_s;
+  V *qg, *yc, *redA, *redB, *rz, *bb, *alpha_s, *beta_s;
+  double* s2;                    // ||b||^2 per column when the vectors are normalised, else 1
   int* done;
   int* its;
-  double *pW, *pR, *pZ;
+  double *pW, *pR, *pZ;          // per-CTA shares (FP64 in memory)
 };
 
 // The vector phases are out-of-line functions of the consumer warps: compiled
@@ -187,40 +208,23 @@ struct PhaseCtx {
 // scheduled far worse (P4 took 6.8 us per iteration inline against 2 us as a
 // separate body).
 template <typename T, int CT>
-__device__ __noinline__ void pcg_phase2(const PcgStreamArgs& A, const PhaseCtx<CT>& X, double* rc, double* rn,
-                                        double* pc) {
+__device__ __noinline__ void pcg_phase2(const PcgStreamArgs& A, const PhaseCtx<T, CT>& X, T* rc, T* rn, T* pc) {
+  using V = T;
   const int tid = threadIdx.x;
-  const Slice& SL = X.SL;
+  const Slice<V>& SL = X.SL;
   const int64_t l0 = X.l0, nl = X.nl, estride = X.estride, m = X.m;
   const int E = X.E, ngp = X.ngp, nrhs = X.nrhs, G = X.G, bid = X.bid, nwG = X.nwG, nwL = X.nwL;
-  double* c_spi = X.c_spi;
-  double* c_cv = X.c_cv;
-  const int32_t* c_co = X.c_co;
-  const int4* c_pc = X.c_pc;
-  double* qg = X.qg;
-  double* yc = X.yc;
-  double* redA = X.redA;
-  double* redB = X.redB;
-  double* rz = X.rz;
-  double* bb = X.bb;
-  double* alpha_s = X.alpha_s;
-  double* beta_s = X.beta_s;
-  int* done = X.done;
-  int* its = X.its;
-  double* pW = X.pW;
-  double* pR = X.pR;
-  double* pZ = X.pZ;
-  (void)bb; (void)its; (void)pZ; (void)pW; (void)pR; (void)beta_s; (void)c_spi; (void)c_cv; (void)c_co; (void)c_pc;
+  V* xv = static_cast<V*>(A.x);
   // ---- P2 (consumers): one round of loads (the shares of <p, B t1>, the
   // primal partials of the coarse DOFs, the owned entries of t1, lam, p,
   // r); the coarse correction and alpha (one thread per column); the owned
   // updates and the u = D_S r' entries of both sides of every owned
   // multiplier
-  double sv[CT];
+  V sv[CT];
 #pragma unroll
-  for (int cc = 0; cc < CT; ++cc) sv[cc] = (cc < nrhs && tid < G) ? pW[(int64_t)tid * CT + cc] : 0.0;
+  for (int cc = 0; cc < CT; ++cc) sv[cc] = (cc < nrhs && tid < G) ? (V)X.pW[(int64_t)tid * CT + cc] : (V)0;
   const bool own0 = tid < nl;
-  double ta[CT], tb[CT], xo[CT], po[CT], ro[CT];
+  V ta[CT], tb[CT], xo[CT], po[CT], ro[CT];
   if (own0) {
     const int4 a0 = SL.gs[tid];
     const int2 n0 = SL.gn[tid];
@@ -228,9 +232,9 @@ __device__ __noinline__ void pcg_phase2(const PcgStreamArgs& A, const PhaseCtx<C
     for (int col = 0; col < CT; ++col) {
       if (col >= nrhs) break;
       const int64_t o = l0 + tid + m * col;
-      ta[col] = A.t1[(int64_t)a0.x * nrhs + a0.y + (int64_t)n0.x * col];
-      tb[col] = A.t1[(int64_t)a0.z * nrhs + a0.w + (int64_t)n0.y * col];
-      xo[col] = A.x[o];
+      ta[col] = (V)A.t1[(int64_t)a0.x * nrhs + a0.y + (int64_t)n0.x * col];
+      tb[col] = (V)A.t1[(int64_t)a0.z * nrhs + a0.w + (int64_t)n0.y * col];
+      xo[col] = xv[o];
       po[col] = pc[o];
       ro[col] = rc[o];
     }
@@ -238,28 +242,30 @@ __device__ __noinline__ void pcg_phase2(const PcgStreamArgs& A, const PhaseCtx<C
   if (ngp > 0 && A.cache_coarse && nrhs == 1) {
     // contributor values of G^T p in parallel (one round with the loads above)
     for (int64_t e = tid; e < A.ncontrib; e += NCONS) {
-      const int4 pc4 = c_pc[e];
-      c_cv[e] = A.qpart[(int64_t)pc4.x + pc4.y];
+      const int4 pc4 = X.c_pc[e];
+      X.c_cv[e] = (V)A.qpart[(int64_t)pc4.x + pc4.y];
     }
   }
 #pragma unroll
   for (int cc = 0; cc < CT; ++cc)
-    if (cc < nrhs) cons_sum_begin(sv[cc], nwG, redA + 8 * cc);
+    if (cc < nrhs) cons_sum_begin(sv[cc], nwG, X.redA + 8 * cc);
   cons_sync();
+  V* qg = X.qg;
+  V* yc = X.yc;
   if (ngp > 0) {
     if (A.cache_coarse && nrhs == 1) {
       for (int g = tid; g < ngp; g += NCONS) {
-        double acc = 0;
-        for (int e = c_co[g]; e < c_co[g + 1]; ++e) acc += c_cv[e];
+        V acc = 0;
+        for (int e = X.c_co[g]; e < X.c_co[g + 1]; ++e) acc += X.c_cv[e];
         qg[g] = acc;
       }
     } else {
       for (int t = tid; t < ngp * nrhs; t += NCONS) {
         const int g = t % ngp, col = t / ngp;
-        double acc = 0;
+        V acc = 0;
         for (int64_t e = A.pcsr_off[g]; e < A.pcsr_off[g + 1]; ++e) {
-          const int4 pc4 = A.cache_coarse ? c_pc[e] : A.pcon[e];
-          acc += A.qpart[(int64_t)pc4.x * nrhs + pc4.y + (int64_t)pc4.z * col];
+          const int4 pc4 = A.cache_coarse ? X.c_pc[e] : A.pcon[e];
+          acc += (V)A.qpart[(int64_t)pc4.x * nrhs + pc4.y + (int64_t)pc4.z * col];
         }
         qg[t] = acc;
       }
@@ -267,24 +273,29 @@ __device__ __noinline__ void pcg_phase2(const PcgStreamArgs& A, const PhaseCtx<C
     cons_sync();
     for (int t = tid; t < ngp * nrhs; t += NCONS) {
       const int g = t % ngp, col = t / ngp;
-      const double* sp = A.cache_coarse ? c_spi + (size_t)ngp * g : A.SPiInv + (int64_t)A.ldc * g;
-      double acc = 0;
-      for (int h = 0; h < ngp; ++h) acc += sp[h] * qg[h + ngp * col];
+      V acc = 0;
+      if (A.cache_coarse) {
+        const V* sp = X.c_spi + (size_t)ngp * g;
+        for (int h = 0; h < ngp; ++h) acc += sp[h] * qg[h + ngp * col];
+      } else {
+        const double* sp = A.SPiInv + (int64_t)A.ldc * g;
+        for (int h = 0; h < ngp; ++h) acc += (V)sp[h] * qg[h + ngp * col];
+      }
       yc[t] = acc;
     }
     cons_sync();
   }
   if (tid < nrhs) {
     // alpha of column tid: <p, F p> = sum of the shares + (G^T p) . S_Pi^-1 (G^T p)
-    double cq = 0;
+    V cq = 0;
     for (int g = 0; g < ngp; ++g) cq += qg[g + ngp * tid] * yc[g + ngp * tid];
-    const double pq = cons_sum_end(nwG, redA + 8 * tid) + cq;
-    alpha_s[tid] = (done[tid] || pq == 0.0) ? 0.0 : rz[tid] / pq;
+    const V pq = cons_sum_end(nwG, X.redA + 8 * tid) + cq;
+    X.alpha_s[tid] = (X.done[tid] || pq == (V)0) ? (V)0 : X.rz[tid] / pq;
   }
   cons_sync();
-  double rrp[CT];
+  V rrp[CT];
 #pragma unroll
-  for (int cc = 0; cc < CT; ++cc) rrp[cc] = 0.0;
+  for (int cc = 0; cc < CT; ++cc) rrp[cc] = 0;
   T* u = (T*)A.CW.uall;
   for (int64_t i = tid; i < nl; i += NCONS) {
     const bool first = i == tid;
@@ -292,28 +303,32 @@ __device__ __noinline__ void pcg_phase2(const PcgStreamArgs& A, const PhaseCtx<C
     const int4 a = SL.gs[i];
     const int2 nn = SL.gn[i];
     const int2 gu = SL.gu[i];
-    double w0, w1;   // D_S at both sides: sign times rho-scaling
+    V w0, w1;   // D_S at both sides: sign times rho-scaling
     if (SL.sg) {
-      const double2 sg = SL.sg[i], sc = SL.sc[i];
+      const Vec2<V> sg = SL.sg[i], sc = SL.sc[i];
       w0 = sg.x * sc.x;
       w1 = sg.y * sc.y;
     } else {
-      w0 = A.I_sign[a.x + a.y] * A.I_scale[a.x + a.y];
-      w1 = A.I_sign[a.z + a.w] * A.I_scale[a.z + a.w];
+      w0 = (V)(A.I_sign[a.x + a.y] * A.I_scale[a.x + a.y]);
+      w1 = (V)(A.I_sign[a.z + a.w] * A.I_scale[a.z + a.w]);
     }
 #pragma unroll
     for (int col = 0; col < CT; ++col) {
       if (col >= nrhs) break;
       const int64_t o = l + m * col;
-      const double al = alpha_s[col];
-      double v = (first ? ta[col] : A.t1[(int64_t)a.x * nrhs + a.y + (int64_t)nn.x * col]) -
-                 (first ? tb[col] : A.t1[(int64_t)a.z * nrhs + a.w + (int64_t)nn.y * col]);
+      const V al = X.alpha_s[col];
+      V v = (first ? ta[col] : (V)A.t1[(int64_t)a.x * nrhs + a.y + (int64_t)nn.x * col]) -
+            (first ? tb[col] : (V)A.t1[(int64_t)a.z * nrhs + a.w + (int64_t)nn.y * col]);
       if (ngp > 0) {
+        if (SL.gv) {
 #pragma unroll 8
-        for (int e = 0; e < E; ++e) v += SL.gv[e * estride + i] * yc[SL.gi[e * estride + i] + ngp * col];
+          for (int e = 0; e < E; ++e) v += SL.gv[e * estride + i] * yc[SL.gi[e * estride + i] + ngp * col];
+        } else {
+          for (int e = 0; e < E; ++e) v += (V)SL.gv64[e * estride + i] * yc[SL.gi[e * estride + i] + ngp * col];
+        }
       }
-      A.x[o] = fma(al, first ? po[col] : pc[o], first ? xo[col] : A.x[o]);
-      const double rv = fma(-al, v, first ? ro[col] : rc[o]);
+      xv[o] = fma(al, first ? po[col] : pc[o], first ? xo[col] : xv[o]);
+      const V rv = fma(-al, v, first ? ro[col] : rc[o]);
       rn[o] = rv;
       rrp[col] += rv * rv;
       u[col * A.CW.utot + gu.x] = (T)(w0 * rv);
@@ -323,107 +338,90 @@ __device__ __noinline__ void pcg_phase2(const PcgStreamArgs& A, const PhaseCtx<C
   fence_async_global();   // the S pass reads u with bulk copies after the barrier
 #pragma unroll
   for (int cc = 0; cc < CT; ++cc)
-    if (cc < nrhs) cons_sum_begin(rrp[cc], nwL, redB + 8 * cc);
+    if (cc < nrhs) cons_sum_begin(rrp[cc], nwL, X.redB + 8 * cc);
   cons_sync();
   if (tid < nrhs) {
     // a CTA whose bulk-copy wait timed out poisons its share, so that every
     // CTA sees the same non-finite <r', r'> and leaves the loop with it
-    const double share = cons_sum_end(nwL, redB + 8 * tid);
-    pR[(int64_t)bid * CT + tid] = *(volatile int*)A.err ? __longlong_as_double(0x7ff8000000000000ll) : share;
+    const double share = (double)cons_sum_end(nwL, X.redB + 8 * tid);
+    X.pR[(int64_t)bid * CT + tid] = *(volatile int*)A.err ? __longlong_as_double(0x7ff8000000000000ll) : share;
   }
 }
 
 template <typename T, int CT>
-__device__ __noinline__ void pcg_phase4(const PcgStreamArgs& A, const PhaseCtx<CT>& X, double* pc, double* pn) {
+__device__ __noinline__ void pcg_phase4(const PcgStreamArgs& A, const PhaseCtx<T, CT>& X, T* pc, T* pn) {
+  using V = T;
   const int tid = threadIdx.x;
-  const Slice& SL = X.SL;
-  const int64_t l0 = X.l0, nl = X.nl, estride = X.estride, m = X.m;
-  const int E = X.E, ngp = X.ngp, nrhs = X.nrhs, G = X.G, bid = X.bid, nwG = X.nwG, nwL = X.nwL;
-  double* c_spi = X.c_spi;
-  double* c_cv = X.c_cv;
-  const int32_t* c_co = X.c_co;
-  const int4* c_pc = X.c_pc;
-  double* qg = X.qg;
-  double* yc = X.yc;
-  double* redA = X.redA;
-  double* redB = X.redB;
-  double* rz = X.rz;
-  double* bb = X.bb;
-  double* alpha_s = X.alpha_s;
-  double* beta_s = X.beta_s;
-  int* done = X.done;
-  int* its = X.its;
-  double* pW = X.pW;
-  double* pR = X.pR;
-  double* pZ = X.pZ;
-  (void)bb; (void)its; (void)pZ; (void)pW; (void)pR; (void)beta_s; (void)c_spi; (void)c_cv; (void)c_co; (void)c_pc;
+  const Slice<V>& SL = X.SL;
+  const int64_t l0 = X.l0, nl = X.nl, m = X.m;
+  const int nrhs = X.nrhs, G = X.G, bid = X.bid, nwG = X.nwG;
   // ---- P4 (consumers): one round of loads (the shares of <r', r'> and
   // <r', z'>, the owned entries of t2 and p); convergence test and beta
   // (one thread per column); owned p' and the u = D_W p' entries
-  double sr[CT], sz[CT];
+  V sr[CT], sz[CT];
 #pragma unroll
   for (int cc = 0; cc < CT; ++cc) {
-    sr[cc] = (cc < nrhs && tid < G) ? pR[(int64_t)tid * CT + cc] : 0.0;
-    sz[cc] = (cc < nrhs && tid < G) ? pZ[(int64_t)tid * CT + cc] : 0.0;
+    sr[cc] = (cc < nrhs && tid < G) ? (V)X.pR[(int64_t)tid * CT + cc] : (V)0;
+    sz[cc] = (cc < nrhs && tid < G) ? (V)X.pZ[(int64_t)tid * CT + cc] : (V)0;
   }
   const bool own0 = tid < nl;
-  double zt[CT], po[CT];
+  V zt[CT], po[CT];
   if (own0) {
     const int4 a0 = SL.gs[tid];
     const int2 n0 = SL.gn[tid];
-    double s0, s1;
+    V s0, s1;
     if (SL.sc) {
-      const double2 sc = SL.sc[tid];
+      const Vec2<V> sc = SL.sc[tid];
       s0 = sc.x;
       s1 = sc.y;
     } else {
-      s0 = A.I_scale[a0.x + a0.y];
-      s1 = A.I_scale[a0.z + a0.w];
+      s0 = (V)A.I_scale[a0.x + a0.y];
+      s1 = (V)A.I_scale[a0.z + a0.w];
     }
 #pragma unroll
     for (int col = 0; col < CT; ++col) {
       if (col >= nrhs) break;
       const int64_t o = l0 + tid + m * col;
-      zt[col] = zgather(s0, A.t2[(int64_t)a0.x * nrhs + a0.y + (int64_t)n0.x * col], s1,
-                        A.t2[(int64_t)a0.z * nrhs + a0.w + (int64_t)n0.y * col]);
+      zt[col] = zgather(s0, (V)A.t2[(int64_t)a0.x * nrhs + a0.y + (int64_t)n0.x * col], s1,
+                        (V)A.t2[(int64_t)a0.z * nrhs + a0.w + (int64_t)n0.y * col]);
       po[col] = pc[o];
     }
   }
 #pragma unroll
   for (int cc = 0; cc < CT; ++cc)
     if (cc < nrhs) {
-      cons_sum_begin(sr[cc], nwG, redA + 8 * cc);
-      cons_sum_begin(sz[cc], nwG, redB + 8 * cc);
+      cons_sum_begin(sr[cc], nwG, X.redA + 8 * cc);
+      cons_sum_begin(sz[cc], nwG, X.redB + 8 * cc);
     }
   cons_sync();
   if (tid < nrhs) {
     const int cc = tid;
-    const double rr = cons_sum_end(nwG, redA + 8 * cc), rzn = cons_sum_end(nwG, redB + 8 * cc);
-    const bool was = done[cc] != 0;
+    const V rr = cons_sum_end(nwG, X.redA + 8 * cc), rzn = cons_sum_end(nwG, X.redB + 8 * cc);
+    const bool was = X.done[cc] != 0;
     // a non-finite residual (a timed-out wait somewhere, see P2) ends the loop
-    const bool now = was || rr <= A.tol2 * bb[cc] || !isfinite(rr);
-    const double b = (now || rz[cc] == 0.0) ? 0.0 : rzn / rz[cc];
-    beta_s[cc] = b;
+    const bool now = was || (double)rr <= A.tol2 * (double)X.bb[cc] || !isfinite(rr);
+    const V b = (now || X.rz[cc] == (V)0) ? (V)0 : rzn / X.rz[cc];
+    X.beta_s[cc] = b;
     if (!was) {
       if (bid == 0) {
-        A.scal[PS_SC * cc + 2] = rr;
-        A.scal[PS_SC * cc + 4] = alpha_s[cc];
+        A.scal[PS_SC * cc + 2] = (double)rr * X.s2[cc];
+        A.scal[PS_SC * cc + 4] = (double)X.alpha_s[cc];
         A.scal[PS_SC * cc + 8] += 1.0;
       }
-      done[cc] = now ? 1 : 0;
+      X.done[cc] = now ? 1 : 0;
       if (!now) {
-        rz[cc] = rzn;
+        X.rz[cc] = rzn;
         if (bid == 0) {
-          A.scal[PS_SC * cc + 0] = rzn;
-          A.scal[PS_SC * cc + 5] = b;
+          A.scal[PS_SC * cc + 0] = (double)rzn * X.s2[cc];
+          A.scal[PS_SC * cc + 5] = (double)b;
         }
       }
     }
     if (cc == 0) {
-      ++*its;
-      if (bid == 0 && A.hist && *its <= A.hist_cap) {
-        A.hist[2 * (*its - 1)] = alpha_s[0];
-        A.hist[2 * (*its - 1) + 1] = b;
+      ++*X.its;
+      if (bid == 0 && A.hist && *X.its <= A.hist_cap) {
+        A.hist[2 * (*X.its - 1)] = (double)X.alpha_s[0];
+        A.hist[2 * (*X.its - 1) + 1] = (double)b;
       }
     }
   }
@@ -433,41 +431,41 @@ __device__ __noinline__ void pcg_phase4(const PcgStreamArgs& A, const PhaseCtx<C
     const bool first = i == tid;
     const int64_t l = l0 + i;
     const int2 gu = SL.gu[i];
-    double w0, w1;   // D_W at both sides: the signs
+    V w0, w1;   // D_W at both sides: the signs
     if (SL.sg) {
-      const double2 sg = SL.sg[i];
+      const Vec2<V> sg = SL.sg[i];
       w0 = sg.x;
       w1 = sg.y;
     } else {
       const int4 a = SL.gs[i];
-      w0 = A.I_sign[a.x + a.y];
-      w1 = A.I_sign[a.z + a.w];
+      w0 = (V)A.I_sign[a.x + a.y];
+      w1 = (V)A.I_sign[a.z + a.w];
     }
-    double zr[CT];
+    V zr[CT];
     if (!first) {
       const int4 a = SL.gs[i];
       const int2 nn = SL.gn[i];
-      double s0, s1;
+      V s0, s1;
       if (SL.sc) {
-        const double2 sc = SL.sc[i];
+        const Vec2<V> sc = SL.sc[i];
         s0 = sc.x;
         s1 = sc.y;
       } else {
-        s0 = A.I_scale[a.x + a.y];
-        s1 = A.I_scale[a.z + a.w];
+        s0 = (V)A.I_scale[a.x + a.y];
+        s1 = (V)A.I_scale[a.z + a.w];
       }
 #pragma unroll
       for (int col = 0; col < CT; ++col) {
         if (col >= nrhs) break;
-        zr[col] = zgather(s0, A.t2[(int64_t)a.x * nrhs + a.y + (int64_t)nn.x * col], s1,
-                          A.t2[(int64_t)a.z * nrhs + a.w + (int64_t)nn.y * col]);
+        zr[col] = zgather(s0, (V)A.t2[(int64_t)a.x * nrhs + a.y + (int64_t)nn.x * col], s1,
+                          (V)A.t2[(int64_t)a.z * nrhs + a.w + (int64_t)nn.y * col]);
       }
     }
 #pragma unroll
     for (int col = 0; col < CT; ++col) {
       if (col >= nrhs) break;
       const int64_t o = l + m * col;
-      const double pv = fma(beta_s[col], first ? po[col] : pc[o], first ? zt[col] : zr[col]);
+      const V pv = fma(X.beta_s[col], first ? po[col] : pc[o], first ? zt[col] : zr[col]);
       pn[o] = pv;
       u[col * A.CW.utot + gu.x] = (T)(w0 * pv);
       u[col * A.CW.utot + gu.y] = (T)(w1 * pv);
@@ -478,12 +476,14 @@ __device__ __noinline__ void pcg_phase4(const PcgStreamArgs& A, const PhaseCtx<C
 
 template <typename T, int CT, bool ROWS>
 __global__ void __launch_bounds__(STREAM_THREADS, 1) k_pcg_stream(PcgStreamArgs A) {
+  using V = T;   // vectors and scalars in the operators' precision
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ double dred[8 * CT];
-  __shared__ double redA[8 * CT], redB[8 * CT];
-  __shared__ double qg[PS_MAXGP * CT], yc[PS_MAXGP * CT];
-  __shared__ double rz[CT], bb[CT], alpha_s[CT], beta_s[CT];
+  __shared__ V redA[8 * CT], redB[8 * CT];
+  __shared__ V qg[PS_MAXGP * CT], yc[PS_MAXGP * CT];
+  __shared__ V rz[CT], bb[CT], alpha_s[CT], beta_s[CT];
+  __shared__ double s2[CT];
   __shared__ int done[CT];
   __shared__ int its;
   const int tid = threadIdx.x, G = gridDim.x, bid = blockIdx.x;
@@ -498,15 +498,16 @@ __global__ void __launch_bounds__(STREAM_THREADS, 1) k_pcg_stream(PcgStreamArgs 
   int4* c_gs = reinterpret_cast<int4*>(cbase);
   int2* c_gn = reinterpret_cast<int2*>(c_gs + nl);
   int2* c_gu = c_gn + nl;
-  double2* c_sg = reinterpret_cast<double2*>(c_gu + nl);
-  double2* c_sc = c_sg + nl;
-  double* c_gv = reinterpret_cast<double*>(c_sc + nl);
+  Vec2<V>* c_sg = reinterpret_cast<Vec2<V>*>(c_gu + nl);
+  Vec2<V>* c_sc = c_sg + nl;
+  V* c_gv = reinterpret_cast<V*>(c_sc + nl);
   int32_t* c_gi = reinterpret_cast<int32_t*>(c_gv + (size_t)E * nl);
   unsigned char* cend = A.cache_slice ? reinterpret_cast<unsigned char*>(c_gi + (size_t)E * nl) : cbase;
   cend = reinterpret_cast<unsigned char*>(((uintptr_t)cend + 15) / 16 * 16);
-  double* c_spi = reinterpret_cast<double*>(cend);   // each coarse buffer starts on 16 bytes
-  double* c_cv = reinterpret_cast<double*>(cend + round16((size_t)ngp * ngp * 8));
-  int32_t* c_co = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(c_cv) + round16((size_t)A.ncontrib * 8));
+  V* c_spi = reinterpret_cast<V*>(cend);   // each coarse buffer starts on 16 bytes
+  V* c_cv = reinterpret_cast<V*>(cend + round16((size_t)ngp * ngp * sizeof(V)));
+  int32_t* c_co =
+      reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(c_cv) + round16((size_t)A.ncontrib * sizeof(V)));
   int4* c_pc = reinterpret_cast<int4*>(reinterpret_cast<unsigned char*>(c_co) + round16((size_t)(ngp + 1) * 4));
   if (A.cache_slice) {
     for (int64_t i = tid; i < nl; i += blockDim.x) {
@@ -515,33 +516,37 @@ __global__ void __launch_bounds__(STREAM_THREADS, 1) k_pcg_stream(PcgStreamArgs 
       c_gs[i] = a;
       c_gn[i] = A.gn[l];
       c_gu[i] = A.gu[l];
-      c_sg[i] = make_double2(A.I_sign[a.x + a.y], A.I_sign[a.z + a.w]);
-      c_sc[i] = make_double2(A.I_scale[a.x + a.y], A.I_scale[a.z + a.w]);
+      c_sg[i] = {(V)A.I_sign[a.x + a.y], (V)A.I_sign[a.z + a.w]};
+      c_sc[i] = {(V)A.I_scale[a.x + a.y], (V)A.I_scale[a.z + a.w]};
       for (int e = 0; e < E; ++e) {
-        c_gv[(size_t)e * nl + i] = A.gv[e * m + l];
+        c_gv[(size_t)e * nl + i] = (V)A.gv[e * m + l];
         c_gi[(size_t)e * nl + i] = A.gi[e * m + l];
       }
     }
   }
   if (A.cache_coarse) {
-    for (int t = tid; t < ngp * ngp; t += blockDim.x) c_spi[t] = A.SPiInv[(int64_t)A.ldc * (t / ngp) + t % ngp];
+    for (int t = tid; t < ngp * ngp; t += blockDim.x) c_spi[t] = (V)A.SPiInv[(int64_t)A.ldc * (t / ngp) + t % ngp];
     for (int g = tid; g <= ngp; g += blockDim.x) c_co[g] = (int32_t)A.pcsr_off[g];
     for (int64_t e = tid; e < A.ncontrib; e += blockDim.x) c_pc[e] = A.pcon[e];
   }
-  Slice SL;
+  Slice<V> SL;
   SL.l0 = l0;
   SL.nl = nl;
   if (A.cache_slice) {
-    SL.gs = c_gs; SL.gn = c_gn; SL.gu = c_gu; SL.sg = c_sg; SL.sc = c_sc; SL.gv = c_gv; SL.gi = c_gi;
+    SL.gs = c_gs; SL.gn = c_gn; SL.gu = c_gu; SL.sg = c_sg; SL.sc = c_sc; SL.gv = c_gv; SL.gv64 = nullptr;
+    SL.gi = c_gi;
   } else {
     SL.gs = A.gs + l0; SL.gn = A.gn + l0; SL.gu = A.gu + l0; SL.sg = nullptr; SL.sc = nullptr;
-    SL.gv = A.gv + l0; SL.gi = A.gi + l0;
+    SL.gv = nullptr; SL.gv64 = A.gv + l0; SL.gi = A.gi + l0;
   }
   const int64_t estride = A.cache_slice ? nl : m;
   __syncthreads();
   if (tid < CT) {
-    rz[tid] = tid < nrhs ? A.scal[PS_SC * tid + 0] : 0.0;
-    bb[tid] = tid < nrhs ? A.scal[PS_SC * tid + 3] : 1.0;
+    // normalised vectors: <r, z> and ||b||^2 in units of ||b||^2
+    const double b2 = tid < nrhs ? A.scal[PS_SC * tid + 3] : 1.0;
+    s2[tid] = (A.vscaled && b2 > 0.0) ? b2 : 1.0;
+    rz[tid] = tid < nrhs ? (V)(A.scal[PS_SC * tid + 0] / s2[tid]) : (V)0;
+    bb[tid] = (V)(b2 / s2[tid]);
     done[tid] = tid < nrhs ? (A.scal[PS_SC * tid + 7] != 0.0) : 1;
   }
   if (tid == 0) its = (int)A.scal[8];
@@ -551,17 +556,17 @@ __global__ void __launch_bounds__(STREAM_THREADS, 1) k_pcg_stream(PcgStreamArgs 
   double* pW = A.part;                          // shares of <p, B t1>
   double* pR = A.part + (int64_t)G * CT;        // shares of <r', r'>
   double* pZ = A.part + 2 * (int64_t)G * CT;    // shares of <r', z'>
-  double* rb[2] = {A.r, A.q};
-  double* pb[2] = {A.p, A.z};
+  V* rb[2] = {static_cast<V*>(A.r), static_cast<V*>(A.q)};
+  V* pb[2] = {static_cast<V*>(A.p), static_cast<V*>(A.z)};
   int cur = 0;
   const int2 krW = A.ckrW[bid];
   // u = D_W p for the first product; the first W tiles are fetched meanwhile
   if (producer) npreW = stream_prefetch<T>(A.CW, A.ctaW[bid], A.ctaW[bid + 1], smem, seq, CT);
-  write_u_run<T, CT>(A, krW, pb[0], nullptr, nullptr, nullptr, false);
+  write_u_run<T, CT, V>(A, krW, pb[0], nullptr, nullptr, nullptr, false);
   __syncthreads();   // every thread's u stores and fence precede the bulk copies
   const int nwG = (G + 31) / 32;                       // warps holding per-CTA shares
   const int nwL = (int)((std::min<int64_t>(nl, NCONS) + 31) / 32);   // warps holding owned entries
-  PhaseCtx<CT> X;
+  PhaseCtx<V, CT> X;
   X.SL = SL;
   X.l0 = l0;
   X.nl = nl;
@@ -586,6 +591,7 @@ __global__ void __launch_bounds__(STREAM_THREADS, 1) k_pcg_stream(PcgStreamArgs 
   X.bb = bb;
   X.alpha_s = alpha_s;
   X.beta_s = beta_s;
+  X.s2 = s2;
   X.done = done;
   X.its = &its;
   X.pW = pW;
@@ -595,10 +601,10 @@ __global__ void __launch_bounds__(STREAM_THREADS, 1) k_pcg_stream(PcgStreamArgs 
     bool all = true;
     for (int cc = 0; cc < nrhs; ++cc) all &= done[cc] != 0;
     if (all) break;
-    double* rc = rb[cur];
-    double* rn = rb[cur ^ 1];
-    double* pc = pb[cur];
-    double* pn = pb[cur ^ 1];
+    V* rc = rb[cur];
+    V* rn = rb[cur ^ 1];
+    V* pc = pb[cur];
+    V* pn = pb[cur ^ 1];
     // ---- P1: local products with W, the primal partials, share of <p, B t1>
     stream_tiles<T, CT, ROWS, true>(A.CW, A.ctaW[bid], A.ctaW[bid + 1], smem, seq, useq, A.t1, A.qpart, nrhs, 0,
                                     nrhs, npreW, pW + (int64_t)bid * CT, dred);
@@ -629,21 +635,45 @@ __global__ void __launch_bounds__(STREAM_THREADS, 1) k_pcg_stream(PcgStreamArgs 
   if (bid == 0 && tid < nrhs) A.scal[PS_SC * tid + 7] = done[tid] ? 1.0 : 0.0;
 }
 
+// FP32 copies of lam, r and p, each column divided by ||b|| (||b||^2 is
+// scalar 3 of the column), and the way back for lam
+__global__ void k_vec_to_f32(const double* lam, const double* r, const double* p, const double* scal, int64_t m,
+                             float* xf, float* rf, float* pf) {
+  const int col = blockIdx.y;
+  const double b2 = scal[PS_SC * col + 3];
+  const double is = b2 > 0.0 ? 1.0 / sqrt(b2) : 1.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = i + m * col;
+    xf[o] = (float)(lam[o] * is);
+    rf[o] = (float)(r[o] * is);
+    pf[o] = (float)(p[o] * is);
+  }
+}
+__global__ void k_vec_from_f32(const float* xf, const double* scal, int64_t m, double* lam) {
+  const int col = blockIdx.y;
+  const double b2 = scal[PS_SC * col + 3];
+  const double sc = b2 > 0.0 ? sqrt(b2) : 1.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = i + m * col;
+    lam[o] = (double)xf[o] * sc;
+  }
+}
+
 template <typename T, int CT, bool ROWS>
 ieti_status launch_pcg_stream(Ctx* c, PcgStreamArgs A, int stages_max, size_t ubytes, cudaStream_t st) {
   auto kern = k_pcg_stream<T, CT, ROWS>;
   cudaFuncAttributes fa;
   IETI_CUDA_TRY(c, cudaFuncGetAttributes(&fa, kern));
-  const StreamPlan& PW = c->splan[sizeof(T) == 4][1];
-  const StreamPlan& PS = c->splan[sizeof(T) == 4][0];
+  const StreamPlan& PW = ROWS ? c->rplan[sizeof(T) == 4][1] : c->splan[sizeof(T) == 4][1];
+  const StreamPlan& PS = ROWS ? c->rplan[sizeof(T) == 4][0] : c->splan[sizeof(T) == 4][0];
   const int stage_bytes = std::max(PW.stage_bytes, PS.stage_bytes);
   // caches: the slice metadata if it takes at most 40 KB, the coarse data if
   // n_gp <= 64
   const int64_t nlmax = ceil_div(A.m, PW.grid) + 1;
-  A.cache_slice = slice_bytes(nlmax, A.E) <= 40 * 1024;
+  A.cache_slice = slice_bytes(nlmax, A.E, sizeof(T)) <= 40 * 1024;
   A.cache_coarse = A.ngp > 0 && A.ngp <= 64;
-  const size_t cache = (A.cache_slice ? (slice_bytes(nlmax, A.E) + 15) / 16 * 16 : 0) +
-                       (A.cache_coarse ? coarse_bytes(A.ngp, A.ncontrib) : 0);
+  const size_t cache = (A.cache_slice ? (slice_bytes(nlmax, A.E, sizeof(T)) + 15) / 16 * 16 : 0) +
+                       (A.cache_coarse ? coarse_bytes(A.ngp, A.ncontrib, sizeof(T)) : 0);
   const long long avail = (long long)c->smem_optin - (long long)fa.sharedSizeBytes - stream_hdr(CT) -
                           2 * (long long)ubytes - (long long)cache - 128;
   const int stages = (int)std::min<long long>(stages_max, avail / std::max(stage_bytes, 1));
@@ -672,8 +702,9 @@ ieti_status launch_pcg_stream(Ctx* c, PcgStreamArgs A, int stages_max, size_t ub
 ieti_status pcg_stream(Ctx* c, double* lam, double* r, double* z, double* p, double* q, double tol2, int maxit,
                        bool fp32, cudaStream_t st) {
   const int nrhs = c->nrhs;
-  const StreamPlan& PW = c->splan[fp32][1];
-  const StreamPlan& PS = c->splan[fp32][0];
+  const bool rows = nrhs == 1 && c->max_ldI <= ROW_MAX_ELEMS && c->rplan[fp32][0].built && c->rplan[fp32][1].built;
+  const StreamPlan& PW = rows ? c->rplan[fp32][1] : c->splan[fp32][1];
+  const StreamPlan& PS = rows ? c->rplan[fp32][0] : c->splan[fp32][0];
   if (nrhs > 8 || c->n_gp > PS_MAXGP || !PW.built || !PS.built || PW.incomplete || PW.ntiles == 0 ||
       PS.ntiles == 0 || PW.grid != PS.grid)
     return IETI_ERR_STATE;
@@ -701,11 +732,23 @@ ieti_status pcg_stream(Ctx* c, double* lam, double* r, double* z, double* p, dou
   A.sd = c->d_sd;
   A.uoff = c->d_uoff;
   A.I_dual = c->d_I_dual;
-  A.x = lam;
-  A.r = r;
-  A.z = z;
-  A.p = p;
-  A.q = q;
+  const int64_t mn = c->m_r * nrhs;
+  float* xf = c->wvf;   // FP32 vectors: lam, r, second r, p, second p
+  if (fp32) {
+    A.x = xf;
+    A.r = xf + mn;
+    A.q = xf + 2 * mn;
+    A.p = xf + 3 * mn;
+    A.z = xf + 4 * mn;
+    A.vscaled = 1;
+  } else {
+    A.x = lam;
+    A.r = r;
+    A.z = z;
+    A.p = p;
+    A.q = q;
+    A.vscaled = 0;
+  }
   A.t1 = c->wi[0];
   A.t2 = c->wi[1];
   A.qpart = c->wq_part;
@@ -732,17 +775,29 @@ ieti_status pcg_stream(Ctx* c, double* lam, double* r, double* z, double* p, dou
   A.tol2 = tol2;
   A.err = c->d_stream_err;
   A.ncontrib = c->pcon_count;
-  const bool rows = nrhs == 1 && c->max_ldI <= ROW_MAX_ELEMS;
   const size_t ub1 = ((size_t)c->max_ldI * (fp32 ? 4 : 8) + 127) / 128 * 128;
+  const dim3 vg((unsigned)std::min<int64_t>(ceil_div(c->m_r, 256), 1024), nrhs);
+  if (fp32) {
+    k_vec_to_f32<<<vg, 256, 0, st>>>(lam, r, p, c->wscal, c->m_r, xf, xf + mn, xf + 3 * mn);
+    IETI_LAUNCH_CHECK(c);
+  }
+  ieti_status res;
   if (nrhs == 1) {
     if (fp32)
-      return rows ? launch_pcg_stream<float, 1, true>(c, A, MAX_STAGES, ub1, st)
-                  : launch_pcg_stream<float, 1, false>(c, A, MAX_STAGES, ub1, st);
-    return rows ? launch_pcg_stream<double, 1, true>(c, A, MAX_STAGES, ub1, st)
-                : launch_pcg_stream<double, 1, false>(c, A, MAX_STAGES, ub1, st);
+      res = rows ? launch_pcg_stream<float, 1, true>(c, A, MAX_STAGES, ub1, st)
+                 : launch_pcg_stream<float, 1, false>(c, A, MAX_STAGES, ub1, st);
+    else
+      res = rows ? launch_pcg_stream<double, 1, true>(c, A, MAX_STAGES, ub1, st)
+                 : launch_pcg_stream<double, 1, false>(c, A, MAX_STAGES, ub1, st);
+  } else {
+    res = fp32 ? launch_pcg_stream<float, 8, false>(c, A, MAX_STAGES, ub1 * 8, st)
+               : launch_pcg_stream<double, 8, false>(c, A, MAX_STAGES, ub1 * 8, st);
   }
-  return fp32 ? launch_pcg_stream<float, 8, false>(c, A, MAX_STAGES, ub1 * 8, st)
-              : launch_pcg_stream<double, 8, false>(c, A, MAX_STAGES, ub1 * 8, st);
+  if (res == IETI_OK && fp32) {
+    k_vec_from_f32<<<vg, 256, 0, st>>>(xf, c->wscal, c->m_r, lam);
+    IETI_LAUNCH_CHECK(c);
+  }
+  return res;
 }
 
 }  // namespace ieti

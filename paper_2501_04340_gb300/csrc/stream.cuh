@@ -13,7 +13,8 @@
 namespace ieti {
 
 constexpr int TILE_TARGET = 64 * 1024;   // bytes per tile at most (whole rows, at most RMAX)
-constexpr int RMAX = 8;                  // rows per tile at most
+constexpr int RMAX = 8;                  // rows per tile at most (multi-column mode)
+constexpr int RROW_MAX = 64;             // rows per tile at most (single-column row mode)
 constexpr int MAX_STAGES = 12;
 constexpr int NCONS = 256;               // consumer threads (8 warps); one producer warp follows
 constexpr int STREAM_THREADS = NCONS + 32;
@@ -384,13 +385,26 @@ __device__ __noinline__ void stream_tiles(const StreamCtx& C, int tb, int te, un
     uq_end = __shfl_sync(0xffffffffu, uq, 0);
   } else if constexpr (ROWS) {
     // ---- consumers, row mode (one column, rows of at most ROW_MAX_ELEMS):
-    // every lane keeps its 16-byte chunks lane, lane + 32, ... of u in
-    // registers and each warp reduces whole rows, so no cross-warp step is
-    // needed
+    // each warp reduces whole rows against the 16-byte chunks lane,
+    // lane + 32, ... of u, so no cross-warp step is needed. Warp w takes the
+    // rows w, w + 8, ... of the CTA's run, whatever the tile boundaries, and
+    // issues the shared loads of a group of chunks before their
+    // multiply-adds. The u buffer stays in shared memory until the run leaves
+    // the subdomain: the inner product reads u at the row from there.
     constexpr int UREG = ROW_MAX_ELEMS / (32 * VEC);
+    constexpr int QG = 8;                // chunks per load group
+    constexpr int NW = NCONS / 32;
+    // FP32: u in registers (64 of them); FP64: u would take 128 registers of
+    // the 168 a thread has here, so its chunks are read from shared memory
+    // with the rows
+    constexpr bool UREGS = VEC == 4;
+    static_assert(UREG % QG == 0, "load groups");
     using V4 = typename std::conditional<VEC == 4, float4, double2>::type;
-    V4 ur[UREG];
+    V4 ur[UREGS ? UREG : 1];
+    T dtacc = 0;             // lane 0: this warp's share of the inner product
+    const T* us = nullptr;   // the subdomain's u in shared memory
     int curk = -1;
+    int rdone = 0;           // rows of this range before the current tile
     uint32_t uq = useq;
     for (int j = 0; j < n; ++j) {
       const uint32_t sq = seq + (uint32_t)j;
@@ -405,6 +419,10 @@ __device__ __noinline__ void stream_tiles(const StreamCtx& C, int tb, int te, un
       const LTile tl = win[((j / WIN) & 1) * WIN + j % WIN];
       const int nv = tl.ldI / VEC;
       if (tl.k != curk) {
+        if (curk >= 0) {
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&B.uempty[(uq - 1) & 1u]);   // done with the previous u
+        }
         const uint32_t ub = uq & 1u;
         bool uok = ok && mbar_wait(&B.ufull[ub], (uq >> 1) & 1u);
         if (ok && !uok) {
@@ -412,41 +430,53 @@ __device__ __noinline__ void stream_tiles(const StreamCtx& C, int tb, int te, un
           *B.abort_flag = 1;
         }
         ok = __all_sync(0xffffffffu, uok);
-        const V4* u4 = reinterpret_cast<const V4*>(ubase + ub * ubytes);
+        us = reinterpret_cast<const T*>(ubase + ub * ubytes);
+        if constexpr (UREGS) {
+          const V4* u4 = reinterpret_cast<const V4*>(us);
 #pragma unroll
-        for (int q = 0; q < UREG; ++q) {
-          if (32 * q >= nv) break;
-          const int jv = lane + 32 * q;
-          if (jv < nv) ur[q] = u4[jv];
+          for (int q = 0; q < UREG; ++q) {
+            const int jv = lane + 32 * q;
+            if (jv < nv) ur[q] = u4[jv];
+          }
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&B.uempty[ub]);   // u now lives in registers
         ++uq;
         curk = tl.k;
       }
       const T* buf = reinterpret_cast<const T*>(stage_base + (size_t)st * C.stage_bytes);
-      for (int r = warp; ok && r < tl.nrows; r += NCONS / 32) {
+      const int rfirst = (warp - rdone % NW + NW) % NW;
+      rdone += tl.nrows;
+      for (int r = rfirst; ok && r < tl.nrows; r += NW) {
         const V4* row = reinterpret_cast<const V4*>(buf + (size_t)r * tl.ldI);
-        // u at this row for the inner product, from the prepared vectors in
-        // global memory (this CTA wrote them before the pass: an L1 or L2 hit),
-        // loaded before the row's products so that its latency overlaps them
-        T ue = 0;
-        if (DOT && tl.kind == 0 && lane == 0) ue = ((const T*)C.uall)[(int64_t)col0 * C.utot + tl.uoff + tl.row0 + r];
+        const T ue = (DOT && tl.kind == 0 && lane == 0) ? us[tl.row0 + r] : (T)0;
         T a0 = 0, a1 = 0;   // two chains of fused multiply-adds
 #pragma unroll
-        for (int q = 0; q < UREG; ++q) {
-          if (32 * q >= nv) break;
-          const int jv = lane + 32 * q;
-          if (jv < nv) {
-            const V4 m = row[jv];
-            if constexpr (VEC == 4) {
-              a0 = fma(m.x, ur[q].x, a0);
-              a1 = fma(m.y, ur[q].y, a1);
-              a0 = fma(m.z, ur[q].z, a0);
-              a1 = fma(m.w, ur[q].w, a1);
-            } else {
-              a0 = fma(m.x, ur[q].x, a0);
-              a1 = fma(m.y, ur[q].y, a1);
+        for (int g = 0; g < UREG; g += QG) {
+          if (32 * g >= nv) break;   // the same in every lane
+          V4 m[QG], xs[UREGS ? 1 : QG];
+#pragma unroll
+          for (int q = 0; q < QG; ++q) {
+            const int jv = lane + 32 * (g + q);
+            if (jv < nv) {
+              m[q] = row[jv];
+              if constexpr (!UREGS) xs[UREGS ? 0 : q] = reinterpret_cast<const V4*>(us)[jv];
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < QG; ++q) {
+            const int jv = lane + 32 * (g + q);
+            if (jv < nv) {
+              V4 x;
+              if constexpr (UREGS) x = ur[g + q];
+              else x = xs[UREGS ? 0 : q];
+              if constexpr (VEC == 4) {
+                a0 = fma(m[q].x, x.x, a0);
+                a1 = fma(m[q].y, x.y, a1);
+                a0 = fma(m[q].z, x.z, a0);
+                a1 = fma(m[q].w, x.w, a1);
+              } else {
+                a0 = fma(m[q].x, x.x, a0);
+                a1 = fma(m[q].y, x.y, a1);
+              }
             }
           }
         }
@@ -457,13 +487,15 @@ __device__ __noinline__ void stream_tiles(const StreamCtx& C, int tb, int te, un
           double* out = tl.kind == 0 ? t : qpart;
           out[tl.obase * nrhs + tl.row0 + r + (int64_t)tl.ostride * col0] = (double)acc;
         }
-        if constexpr (DOT) {
-          if (tl.kind == 0 && lane == 0) dacc[0] += (double)acc * (double)ue;
-        }
+        // in the operator's precision: GB300's FP64 pipe is narrow
+        if constexpr (DOT) dtacc += acc * ue;
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&B.empty[st]);   // this warp has read the stage
     }
+    __syncwarp();
+    if (curk >= 0 && lane == 0) mbar_arrive(&B.uempty[(uq - 1) & 1u]);   // done with the last u
+    if constexpr (DOT) dacc[0] = (double)dtacc;
     uq_end = uq;
   } else {
     // ---- consumers: wait for the tile, then read its descriptor from the

@@ -68,13 +68,15 @@ __device__ unsigned long long dep_wait(const unsigned long long* p, unsigned lon
 // all threads: the block's stores are done; one thread waits until the
 // counter reaches prev (the blocks before this one in the order are
 // published: with zero tiles a task may finish before its predecessor, and
-// the counter must mean that every block up to it is final), then publishes
+// the counter must mean that every block up to it is final), then publishes.
+// seen: the counter value thread 0 has already observed (no second poll when
+// it covers prev). The release store orders the stores of the whole CTA,
+// which the barrier has made visible to thread 0, before the new counter.
 __device__ __forceinline__ void dep_publish(unsigned long long* p, unsigned long long prev, unsigned long long v,
-                                            int* err) {
+                                            int* err, unsigned long long seen = 0) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    dep_wait(p, prev, err);
-    __threadfence();
+    if (seen < prev) dep_wait(p, prev, err);
     st_release_u64(p, v);
   }
 }
@@ -123,6 +125,8 @@ __global__ void __launch_bounds__(DEP_THREADS, 2)
       Vec16<T>* dst = reinterpret_cast<Vec16<T>*>(Lis);
       for (int q = tid; q < NB * NB / VL; q += DEP_THREADS) dst[q] = src[q];
     }
+    // the right-hand side of the block, loaded before the waits
+    const T bv = tid < NB ? B[d.boff + (int64_t)(b - d.b0) * NB + tid] : (T)0;
     T acc = 0;
     unsigned long long seen = 0;
     // the nonzero tiles L_bj of block row b (ascending j), from the range start
@@ -160,9 +164,7 @@ __global__ void __launch_bounds__(DEP_THREADS, 2)
     }
     part[cs * NB + i] = acc;
     __syncthreads();
-    if (tid < NB)
-      rhs[tid] = B[d.boff + (int64_t)(b - d.b0) * NB + tid] -
-                 (part[tid] + part[NB + tid] + part[2 * NB + tid] + part[3 * NB + tid]);
+    if (tid < NB) rhs[tid] = bv - (part[tid] + part[NB + tid] + part[2 * NB + tid] + part[3 * NB + tid]);
     __syncthreads();
     // y_b = Linv_b rhs (zero above the diagonal): part cs sums columns cs*16..
     T v = 0;
@@ -171,7 +173,8 @@ __global__ void __launch_bounds__(DEP_THREADS, 2)
     part[cs * NB + i] = v;
     __syncthreads();
     if (tid < NB) Yk[(int64_t)b * NB + tid] = part[tid] + part[NB + tid] + part[2 * NB + tid] + part[3 * NB + tid];
-    dep_publish(prog + k, b > d.b0 ? base + (unsigned long long)b : 0ull, base + (unsigned long long)(b + 1), err);
+    dep_publish(prog + k, b > d.b0 ? base + (unsigned long long)b : 0ull, base + (unsigned long long)(b + 1), err,
+                seen);
   }
 }
 
@@ -204,6 +207,8 @@ __global__ void __launch_bounds__(DEP_THREADS, 2)
       const T* Lb = Linv + s.linv + (int64_t)b * NB * NB;   // Lb[l + 64 i] = Linv_b[l][i]
       for (int q = tid; q < NB * NB; q += DEP_THREADS) Lis[(q % NB) * (NB + 1) + q / NB] = Lb[q];
     }
+    // the right-hand side of the block (written by the forward sweep), loaded before the waits
+    const T yv = tid < NB ? Yk[(int64_t)b * NB + tid] : (T)0;
     T acc[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) acc[c] = 0;
@@ -252,8 +257,7 @@ __global__ void __launch_bounds__(DEP_THREADS, 2)
       part[qr * NB + c] = v;
     }
     __syncthreads();
-    if (tid < NB)
-      rhs[tid] = Yk[(int64_t)b * NB + tid] - (part[tid] + part[NB + tid] + part[2 * NB + tid] + part[3 * NB + tid]);
+    if (tid < NB) rhs[tid] = yv - (part[tid] + part[NB + tid] + part[2 * NB + tid] + part[3 * NB + tid]);
     __syncthreads();
     // x_b = Linv_b^T rhs: x_i = sum_{l >= i} Linv_b[l][i] rhs_l, part cs sums l = cs*16..
     T v = 0;
@@ -266,7 +270,7 @@ __global__ void __launch_bounds__(DEP_THREADS, 2)
     __syncthreads();
     if (tid < NB) Xk[(int64_t)b * NB + tid] = part[tid] + part[NB + tid] + part[2 * NB + tid] + part[3 * NB + tid];
     dep_publish(prog + k, b < nb - 1 ? base + (unsigned long long)(nb - b - 1) : 0ull,
-                base + (unsigned long long)(nb - b), err);
+                base + (unsigned long long)(nb - b), err, seen);
   }
 }
 
@@ -371,9 +375,12 @@ __global__ void __launch_bounds__(DEP_THREADS)
         const int i = 4 * ti + u, cc = 4 * tj + w;
         if (cc < nc) Ok[(int64_t)b * NB + i + (int64_t)d.ldb * cc] = o[u][w];
       }
-    if (fwd) dep_publish(prog + v, b > d.b0 ? base + (unsigned long long)b : 0ull, base + (unsigned long long)(b + 1), err);
-    else dep_publish(prog + v, b < nb - 1 ? base + (unsigned long long)(nb - b - 1) : 0ull,
-                     base + (unsigned long long)(nb - b), err);
+    if (fwd)
+      dep_publish(prog + v, b > d.b0 ? base + (unsigned long long)b : 0ull, base + (unsigned long long)(b + 1), err,
+                  seen);
+    else
+      dep_publish(prog + v, b < nb - 1 ? base + (unsigned long long)(nb - b - 1) : 0ull,
+                  base + (unsigned long long)(nb - b), err, seen);
   }
 }
 
