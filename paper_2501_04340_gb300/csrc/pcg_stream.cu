@@ -159,6 +159,14 @@ __device__ inline void write_u_run(const PcgStreamArgs& A, int2 kr, const V* a, 
 // producer warp can issue the bulk copies of the next pass meanwhile.
 __device__ __forceinline__ void cons_sync() { asm volatile("bar.sync 2, 256;" ::: "memory"); }
 
+// The producer warp starts the bulk copies of the next pass only once the
+// consumers hold the loads of their vector phase (named barrier 3): issued at
+// the start of the phase, the copies of all SMs held those L2 loads up by
+// about 2 us. (Whatever part of the phase runs under the copies slows down by
+// about as much; the copies ahead still pay for themselves at the pass start.)
+__device__ __forceinline__ void gate_open() { asm volatile("bar.arrive 3, 288;" ::: "memory"); }
+__device__ __forceinline__ void gate_wait() { asm volatile("bar.sync 3, 288;" ::: "memory"); }
+
 // Block sum over the consumer warps of one value per thread, in the warps
 // [0, nw) that hold nonzero values; red: [8] values; cons_sum_end (after the
 // next cons_sync) adds the warp sums. The partial sums are formed once, not in
@@ -200,6 +208,7 @@ struct PhaseCtx {
   double* s2;                    // ||b||^2 per column when the vectors are normalised, else 1
   int* done;
   int* its;
+  int* itc;                      // iterations per column
   double *pW, *pR, *pZ;          // per-CTA shares (FP64 in memory)
 };
 
@@ -250,47 +259,56 @@ __device__ __noinline__ void pcg_phase2(const PcgStreamArgs& A, const PhaseCtx<T
   for (int cc = 0; cc < CT; ++cc)
     if (cc < nrhs) cons_sum_begin(sv[cc], nwG, X.redA + 8 * cc);
   cons_sync();
+  gate_open();
   V* qg = X.qg;
   V* yc = X.yc;
+  const int warp = tid / 32, lane = tid % 32;
+  constexpr int NWC = NCONS / 32;
+  // the coarse step and the scalars are spread over warps and lanes with
+  // shuffle sums: serial chains of shared loads are slow while the bulk copies
+  // of the next pass write shared memory
   if (ngp > 0) {
-    if (A.cache_coarse && nrhs == 1) {
-      for (int g = tid; g < ngp; g += NCONS) {
-        V acc = 0;
-        for (int e = X.c_co[g]; e < X.c_co[g + 1]; ++e) acc += X.c_cv[e];
-        qg[g] = acc;
-      }
-    } else {
-      for (int t = tid; t < ngp * nrhs; t += NCONS) {
-        const int g = t % ngp, col = t / ngp;
-        V acc = 0;
-        for (int64_t e = A.pcsr_off[g]; e < A.pcsr_off[g + 1]; ++e) {
+    // qg = G^T p from the contributors: one warp per coarse DOF and column
+    for (int t = warp; t < ngp * nrhs; t += NWC) {
+      const int g = t % ngp, col = t / ngp;
+      V acc = 0;
+      if (A.cache_coarse && nrhs == 1) {
+        for (int e = X.c_co[g] + lane; e < X.c_co[g + 1]; e += 32) acc += X.c_cv[e];
+      } else {
+        for (int64_t e = A.pcsr_off[g] + lane; e < A.pcsr_off[g + 1]; e += 32) {
           const int4 pc4 = A.cache_coarse ? X.c_pc[e] : A.pcon[e];
           acc += (V)A.qpart[(int64_t)pc4.x * nrhs + pc4.y + (int64_t)pc4.z * col];
         }
-        qg[t] = acc;
       }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) qg[t] = acc;
     }
     cons_sync();
-    for (int t = tid; t < ngp * nrhs; t += NCONS) {
+    // yc = S_Pi^-1 qg: one warp per row and column
+    for (int t = warp; t < ngp * nrhs; t += NWC) {
       const int g = t % ngp, col = t / ngp;
       V acc = 0;
       if (A.cache_coarse) {
         const V* sp = X.c_spi + (size_t)ngp * g;
-        for (int h = 0; h < ngp; ++h) acc += sp[h] * qg[h + ngp * col];
+        for (int h = lane; h < ngp; h += 32) acc += sp[h] * qg[h + ngp * col];
       } else {
         const double* sp = A.SPiInv + (int64_t)A.ldc * g;
-        for (int h = 0; h < ngp; ++h) acc += (V)sp[h] * qg[h + ngp * col];
+        for (int h = lane; h < ngp; h += 32) acc += (V)sp[h] * qg[h + ngp * col];
       }
-      yc[t] = acc;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) yc[t] = acc;
     }
     cons_sync();
   }
-  if (tid < nrhs) {
-    // alpha of column tid: <p, F p> = sum of the shares + (G^T p) . S_Pi^-1 (G^T p)
-    V cq = 0;
-    for (int g = 0; g < ngp; ++g) cq += qg[g + ngp * tid] * yc[g + ngp * tid];
-    const V pq = cons_sum_end(nwG, X.redA + 8 * tid) + cq;
-    X.alpha_s[tid] = (X.done[tid] || pq == (V)0) ? (V)0 : X.rz[tid] / pq;
+  // alpha of column cc (warp cc): <p, F p> = sum of the shares + (G^T p) . S_Pi^-1 (G^T p)
+  for (int cc = warp; cc < nrhs; cc += NWC) {
+    V v = lane < nwG ? X.redA[8 * cc + lane] : (V)0;
+    for (int g = lane; g < ngp; g += 32) v += qg[g + ngp * cc] * yc[g + ngp * cc];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) X.alpha_s[cc] = (X.done[cc] || v == (V)0) ? (V)0 : X.rz[cc] / v;
   }
   cons_sync();
   V rrp[CT];
@@ -394,19 +412,28 @@ __device__ __noinline__ void pcg_phase4(const PcgStreamArgs& A, const PhaseCtx<T
       cons_sum_begin(sz[cc], nwG, X.redB + 8 * cc);
     }
   cons_sync();
-  if (tid < nrhs) {
-    const int cc = tid;
-    const V rr = cons_sum_end(nwG, X.redA + 8 * cc), rzn = cons_sum_end(nwG, X.redB + 8 * cc);
+  gate_open();
+  const int warp = tid / 32, lane = tid % 32;
+  for (int cc = warp; cc < nrhs; cc += NCONS / 32) {
+    // column cc on warp cc: the warp sums of the shares, then lane 0
+    V rr = lane < nwG ? X.redA[8 * cc + lane] : (V)0, rzn = lane < nwG ? X.redB[8 * cc + lane] : (V)0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      rr += __shfl_xor_sync(0xffffffffu, rr, o);
+      rzn += __shfl_xor_sync(0xffffffffu, rzn, o);
+    }
+    if (lane != 0) continue;
     const bool was = X.done[cc] != 0;
     // a non-finite residual (a timed-out wait somewhere, see P2) ends the loop
     const bool now = was || (double)rr <= A.tol2 * (double)X.bb[cc] || !isfinite(rr);
     const V b = (now || X.rz[cc] == (V)0) ? (V)0 : rzn / X.rz[cc];
     X.beta_s[cc] = b;
     if (!was) {
-      if (bid == 0) {
+      ++X.itc[cc];
+      if (bid == 0) {   // stores only: a read here would hold CTA 0 up by an L2 round trip
         A.scal[PS_SC * cc + 2] = (double)rr * X.s2[cc];
         A.scal[PS_SC * cc + 4] = (double)X.alpha_s[cc];
-        A.scal[PS_SC * cc + 8] += 1.0;
+        A.scal[PS_SC * cc + 8] = (double)X.itc[cc];
       }
       X.done[cc] = now ? 1 : 0;
       if (!now) {
@@ -485,7 +512,7 @@ __global__ void __launch_bounds__(STREAM_THREADS, 1) k_pcg_stream(PcgStreamArgs 
   __shared__ V rz[CT], bb[CT], alpha_s[CT], beta_s[CT];
   __shared__ double s2[CT];
   __shared__ int done[CT];
-  __shared__ int its;
+  __shared__ int its, itc[CT];
   const int tid = threadIdx.x, G = gridDim.x, bid = blockIdx.x;
   const int nrhs = A.nrhs, ngp = A.ngp;
   const int64_t m = A.m;
@@ -548,6 +575,7 @@ __global__ void __launch_bounds__(STREAM_THREADS, 1) k_pcg_stream(PcgStreamArgs 
     rz[tid] = tid < nrhs ? (V)(A.scal[PS_SC * tid + 0] / s2[tid]) : (V)0;
     bb[tid] = (V)(b2 / s2[tid]);
     done[tid] = tid < nrhs ? (A.scal[PS_SC * tid + 7] != 0.0) : 1;
+    itc[tid] = tid < nrhs ? (int)A.scal[PS_SC * tid + 8] : 0;
   }
   if (tid == 0) its = (int)A.scal[8];
   uint32_t seq = 0, useq = 0;
@@ -594,6 +622,7 @@ __global__ void __launch_bounds__(STREAM_THREADS, 1) k_pcg_stream(PcgStreamArgs 
   X.s2 = s2;
   X.done = done;
   X.its = &its;
+  X.itc = itc;
   X.pW = pW;
   X.pR = pR;
   X.pZ = pZ;
@@ -612,6 +641,7 @@ __global__ void __launch_bounds__(STREAM_THREADS, 1) k_pcg_stream(PcgStreamArgs 
     grid.sync();
     if (producer) {
       // the first S tiles are fetched while the consumers run the vector phase
+      gate_wait();
       npreS = stream_prefetch<T>(A.CS, A.ctaS[bid], A.ctaS[bid + 1], smem, seq, CT);
     } else {
       pcg_phase2<T, CT>(A, X, rc, rn, pc);
@@ -623,6 +653,7 @@ __global__ void __launch_bounds__(STREAM_THREADS, 1) k_pcg_stream(PcgStreamArgs 
     npreS = 0;
     grid.sync();
     if (producer) {
+      gate_wait();
       npreW = stream_prefetch<T>(A.CW, A.ctaW[bid], A.ctaW[bid + 1], smem, seq, CT);
     } else {
       pcg_phase4<T, CT>(A, X, pc, pn);
