@@ -216,6 +216,8 @@ struct Ctx {
   // dependency-driven single-column sweeps (sweep_dep.cu)
   int2* d_dep_tasks[2][2] = {};          // [range][forward, backward]: (subdomain, block) in run order
   int dep_ntask[2][2] = {};
+  int2* d_dep_tasks2[2][2] = {};         // the same for tasks of two blocks (first block of the pair)
+  int dep_ntask2[2][2] = {};
   unsigned long long* d_dep_prog = nullptr;   // per subdomain: epoch << 20 | blocks published
   unsigned long long dep_epoch = 0;
   int* d_dep_err = nullptr;              // set when a sweep wait times out; the poll limit at byte 8

@@ -274,6 +274,244 @@ __global__ void __launch_bounds__(DEP_THREADS, 2)
   }
 }
 
+// Tasks of two blocks (FP32 sweeps). The single-column sweep is bound by its
+// chain of dependent blocks: after block b-1 is published, block b still
+// reads it through L2, reduces, solves its diagonal block and publishes, about
+// 3.5 us per link. A task that solves two consecutive blocks on chip halves the
+// number of links. Both block rows (columns) of the pair walk the merged list
+// of their nonzero tiles, so that the tiles of both are loaded before the
+// waits and each published block is read once for both; the in-pair coupling
+// tile is applied from registers once the first block of the pair is solved,
+// and the pair is published with one counter store (the counter advances by
+// two).
+//
+// Forward pair (b, b+1): y_b as in k_dep_fwd, then
+//   y_{b+1} = Linv_{b+1} (b_{b+1} - sum_{j < b} L_{b+1,j} y_j - L_{b+1,b} y_b).
+template <typename T>
+__global__ void __launch_bounds__(DEP_THREADS, 2)
+    k_dep_fwd2(const SubDev* sd, const SolveDesc* dsc, const int2* tasks, int ntask, const T* L, const T* Linv,
+               const T* B, T* Y, unsigned long long* prog, unsigned long long base, int* err,
+               const int64_t* lptr, const int32_t* lidx, const int* bbase) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  T* Lis0 = reinterpret_cast<T*>(dsm);   // Linv_b, column-major 64 x 64
+  T* Lis1 = Lis0 + NB * NB;              // Linv_{b+1}
+  T* part = Lis1 + NB * NB;              // [4][64]
+  T* rhs = part + 4 * NB;                // [64]
+  T* y0s = rhs + NB;                     // [64] y_b
+  const int tid = threadIdx.x, i = tid % NB, cs = tid / NB;
+  constexpr int VL = 16 / sizeof(T);
+  constexpr int JEND = 1 << 30;
+  for (int t = blockIdx.x; t < ntask; t += gridDim.x) {
+    const int2 tk = tasks[t];
+    const int k = tk.x, b = tk.y;
+    const SubDev s = sd[k];
+    const SolveDesc d = dsc[k];
+    const int64_t n = s.n;
+    const bool two = b + 1 < s.nblk;
+    const T* Lr0 = L + s.A + (int64_t)b * NB + i + n * (cs * 16);   // row b*64+i, columns cs*16.. of block 0
+    const T* Lr1 = Lr0 + NB;                                          // row (b+1)*64+i
+    T* Yk = Y + d.boff - (int64_t)d.b0 * NB;
+    __syncthreads();   // the previous task is done with the shared buffers
+    {
+      const Vec16<T>* src = reinterpret_cast<const Vec16<T>*>(Linv + s.linv + (int64_t)b * NB * NB);
+      Vec16<T>* dst = reinterpret_cast<Vec16<T>*>(Lis0);
+      for (int q = tid; q < (two ? 2 : 1) * NB * NB / VL; q += DEP_THREADS) dst[q] = src[q];
+    }
+    const T bv0 = tid < NB ? B[d.boff + (int64_t)(b - d.b0) * NB + tid] : (T)0;
+    const T bv1 = (two && tid < NB) ? B[d.boff + (int64_t)(b + 1 - d.b0) * NB + tid] : (T)0;
+    // tile lists of both rows from the range start; the in-pair tile L_{b+1,b}
+    // is the last entry of row b+1 if nonzero
+    int64_t e0 = lptr[bbase[k] + b];
+    const int64_t e0e = lptr[bbase[k] + b + 1];
+    int64_t e1 = two ? lptr[bbase[k] + b + 1] : 0;
+    int64_t e1e = two ? lptr[bbase[k] + b + 2] : 0;
+    const bool has_in = two && e1e > e1 && lidx[e1e - 1] == b;
+    if (has_in) --e1e;
+    while (e0 < e0e && lidx[e0] < d.b0) ++e0;
+    while (e1 < e1e && lidx[e1] < d.b0) ++e1;
+    T lin[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) lin[c] = has_in ? Lr1[n * ((int64_t)b * NB + c)] : (T)0;
+    unsigned long long seen = 0;
+    T acc0 = 0, acc1 = 0;
+    while (e0 < e0e || e1 < e1e) {
+      const int j0 = e0 < e0e ? lidx[e0] : JEND, j1 = e1 < e1e ? lidx[e1] : JEND;
+      const int j = min(j0, j1);
+      const bool h0 = j0 == j, h1 = j1 == j;
+      T l0[16], l1[16], y[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        l0[c] = h0 ? Lr0[n * ((int64_t)j * NB + c)] : (T)0;
+        l1[c] = h1 ? Lr1[n * ((int64_t)j * NB + c)] : (T)0;
+      }
+      if (seen < base + j + 1) seen = dep_wait(prog + k, base + j + 1, err);
+      load16_cg(Yk + (int64_t)j * NB + cs * 16, y);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        acc0 += l0[c] * y[c];
+        acc1 += l1[c] * y[c];
+      }
+      e0 += h0 ? 1 : 0;
+      e1 += h1 ? 1 : 0;
+    }
+    // block b
+    part[cs * NB + i] = acc0;
+    __syncthreads();
+    if (tid < NB) rhs[tid] = bv0 - (part[tid] + part[NB + tid] + part[2 * NB + tid] + part[3 * NB + tid]);
+    __syncthreads();
+    T v = 0;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v += Lis0[i + NB * (cs * 16 + c)] * rhs[cs * 16 + c];
+    part[cs * NB + i] = v;
+    __syncthreads();
+    if (tid < NB) {
+      const T yb = part[tid] + part[NB + tid] + part[2 * NB + tid] + part[3 * NB + tid];
+      Yk[(int64_t)b * NB + tid] = yb;
+      y0s[tid] = yb;
+    }
+    if (two) {
+      __syncthreads();   // y_b in shared memory; part is free
+      T a1 = acc1;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) a1 += lin[c] * y0s[cs * 16 + c];
+      part[cs * NB + i] = a1;
+      __syncthreads();
+      if (tid < NB) rhs[tid] = bv1 - (part[tid] + part[NB + tid] + part[2 * NB + tid] + part[3 * NB + tid]);
+      __syncthreads();
+      T v1 = 0;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) v1 += Lis1[i + NB * (cs * 16 + c)] * rhs[cs * 16 + c];
+      part[cs * NB + i] = v1;
+      __syncthreads();
+      if (tid < NB)
+        Yk[(int64_t)(b + 1) * NB + tid] = part[tid] + part[NB + tid] + part[2 * NB + tid] + part[3 * NB + tid];
+    }
+    dep_publish(prog + k, b > d.b0 ? base + (unsigned long long)b : 0ull,
+                base + (unsigned long long)(b + (two ? 2 : 1)), err, seen);
+  }
+}
+
+// Backward pair (b, b-1), b the upper block: x_b as in k_dep_bwd, then
+//   x_{b-1} = Linv_{b-1}^T (y_{b-1} - sum_{j > b} L_{j,b-1}^T x_j - L_{b,b-1}^T x_b).
+template <typename T>
+__global__ void __launch_bounds__(DEP_THREADS, 2)
+    k_dep_bwd2(const SubDev* sd, const SolveDesc* dsc, const int2* tasks, int ntask, const T* L, const T* Linv,
+               const T* Y, T* X, unsigned long long* prog, unsigned long long base, int* err,
+               const int64_t* lptr, const int32_t* lidx, const int* bbase) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  T* Lis0 = reinterpret_cast<T*>(dsm);         // Lis0[l * 65 + i] = Linv_b[l][i]
+  T* Lis1 = Lis0 + NB * (NB + 1);              // Linv_{b-1}, same layout
+  T* red = Lis1 + NB * (NB + 1);               // red[i * 65 + c]: partial column sums of row i
+  T* part = red + NB * (NB + 1);               // [4][64]
+  T* rhs = part + 4 * NB;                      // [64]
+  T* xbs = rhs + NB;                           // [64] x_b
+  const int tid = threadIdx.x, i = tid % NB, cs = tid / NB;
+  for (int t = blockIdx.x; t < ntask; t += gridDim.x) {
+    const int2 tk = tasks[t];
+    const int k = tk.x, b = tk.y;
+    const SubDev s = sd[k];
+    const SolveDesc d = dsc[k];
+    const int64_t n = s.n;
+    const int nb = s.nblk;
+    const bool two = b - 1 >= d.b0;
+    const T* Lc0 = L + s.A + i + n * ((int64_t)b * NB + cs * 16);   // row i of block row 0, columns of block b
+    const T* Lc1 = Lc0 - n * NB;                                      // columns of block b-1
+    const T* Yk = Y + d.boff - (int64_t)d.b0 * NB;
+    T* Xk = X + d.boff - (int64_t)d.b0 * NB;
+    __syncthreads();   // the previous task is done with the shared buffers
+    {
+      const T* Lb = Linv + s.linv + (int64_t)b * NB * NB;   // Lb[l + 64 i] = Linv_b[l][i]
+      for (int q = tid; q < NB * NB; q += DEP_THREADS) Lis0[(q % NB) * (NB + 1) + q / NB] = Lb[q];
+      if (two) {
+        const T* Lm = Lb - NB * NB;
+        for (int q = tid; q < NB * NB; q += DEP_THREADS) Lis1[(q % NB) * (NB + 1) + q / NB] = Lm[q];
+      }
+    }
+    const T yv0 = tid < NB ? Yk[(int64_t)b * NB + tid] : (T)0;
+    const T yv1 = (two && tid < NB) ? Yk[(int64_t)(b - 1) * NB + tid] : (T)0;
+    // column lists (descending j) of both columns; the in-pair tile L_{b,b-1}
+    // is the last entry (smallest j) of column b-1 if nonzero
+    int64_t e0 = lptr[bbase[k] + b];
+    const int64_t e0e = lptr[bbase[k] + b + 1];
+    int64_t e1 = two ? lptr[bbase[k] + b - 1] : 0;
+    int64_t e1e = two ? lptr[bbase[k] + b] : 0;
+    const bool has_in = two && e1e > e1 && lidx[e1e - 1] == b;
+    if (has_in) --e1e;
+    T lin[16];
+    {
+      const T* Li = Lc1 + (int64_t)b * NB;   // row b*64+i, columns (b-1)*64 + cs*16..
+#pragma unroll
+      for (int c = 0; c < 16; ++c) lin[c] = has_in ? Li[n * c] : (T)0;
+    }
+    unsigned long long seen = 0;
+    T acc0[16], acc1[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc0[c] = acc1[c] = 0;
+    while (e0 < e0e || e1 < e1e) {
+      const int j0 = e0 < e0e ? lidx[e0] : -1, j1 = e1 < e1e ? lidx[e1] : -1;
+      const int j = max(j0, j1);   // descending
+      const bool h0 = j0 == j, h1 = j1 == j;
+      T l0[16], l1[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        l0[c] = h0 ? Lc0[(int64_t)j * NB + n * c] : (T)0;
+        l1[c] = h1 ? Lc1[(int64_t)j * NB + n * c] : (T)0;
+      }
+      const unsigned long long need = base + (unsigned long long)(nb - j);
+      if (seen < need) seen = dep_wait(prog + k, need, err);
+      const T x = __ldcg(Xk + (int64_t)j * NB + i);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        acc0[c] += l0[c] * x;
+        acc1[c] += l1[c] * x;
+      }
+      e0 += h0 ? 1 : 0;
+      e1 += h1 ? 1 : 0;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (h == 1 && !two) break;
+      const T* Lis = h == 0 ? Lis0 : Lis1;
+      if (h == 1) {
+        // x_b is in shared memory: add the in-pair products to the sums of block b-1
+        const T xb = xbs[i];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc1[c] += lin[c] * xb;
+      }
+#pragma unroll
+      for (int c = 0; c < 16; ++c) red[i * (NB + 1) + cs * 16 + c] = h == 0 ? acc0[c] : acc1[c];
+      __syncthreads();
+      {
+        const int c = tid % NB, qr = tid / NB;
+        T v = 0;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v += red[(qr * 16 + r) * (NB + 1) + c];
+        part[qr * NB + c] = v;
+      }
+      __syncthreads();
+      if (tid < NB)
+        rhs[tid] = (h == 0 ? yv0 : yv1) - (part[tid] + part[NB + tid] + part[2 * NB + tid] + part[3 * NB + tid]);
+      __syncthreads();
+      T v = 0;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int l = cs * 16 + c;
+        v += Lis[l * (NB + 1) + i] * rhs[l];
+      }
+      part[cs * NB + i] = v;
+      __syncthreads();
+      if (tid < NB) {
+        const T x = part[tid] + part[NB + tid] + part[2 * NB + tid] + part[3 * NB + tid];
+        Xk[(int64_t)(b - h) * NB + tid] = x;
+        if (h == 0) xbs[tid] = x;
+      }
+      __syncthreads();   // x_b visible; red and part free
+    }
+    dep_publish(prog + k, b < nb - 1 ? base + (unsigned long long)(nb - b - 1) : 0ull,
+                base + (unsigned long long)(nb - b + (two ? 1 : 0)), err, seen);
+  }
+}
+
 // Many right-hand sides (the W and Phi solves of the factorisation): a task is
 // one 64-wide block of one subdomain times one tile of up to 64 columns, and
 // every column tile of a subdomain has its own progress counter. Forward,
@@ -391,11 +629,18 @@ template <typename T>
 size_t fwd_smem() { return sizeof(T) * ((size_t)NB * NB + 5 * NB); }
 template <typename T>
 size_t bwd_smem() { return sizeof(T) * (2 * (size_t)NB * (NB + 1) + 5 * NB); }
+template <typename T>
+size_t fwd2_smem() { return sizeof(T) * (2 * (size_t)NB * NB + 6 * NB); }
+template <typename T>
+size_t bwd2_smem() { return sizeof(T) * (3 * (size_t)NB * (NB + 1) + 6 * NB); }
 
 template <typename T>
 ieti_status launch_dep(Ctx* c, bool fwd, int range, const T* B, const T* Yin, T* Yout, cudaStream_t st) {
   const int which = fwd ? 0 : 1;
-  const int ntask = c->dep_ntask[range][which];
+  // FP32: tasks of two blocks (the FP64 pair kernels would need more registers
+  // than two CTAs per SM leave)
+  constexpr bool pairs = sizeof(T) == 4;
+  const int ntask = pairs ? c->dep_ntask2[range][which] : c->dep_ntask[range][which];
   if (ntask == 0) return IETI_OK;
   if (!c->symb_ready) return IETI_ERR_STATE;   // tile lists of the factor
   int dev = 0, coop = 0;
@@ -403,9 +648,11 @@ ieti_status launch_dep(Ctx* c, bool fwd, int range, const T* B, const T* Yin, T*
   IETI_CUDA_TRY(c, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   if (!coop || c->sm_count < 1) return IETI_ERR_STATE;
   const SolveDesc* dd = c->d_desc_rv + (range == RV_IRANGE ? c->nsub : 0);
-  const int2* tasks = c->d_dep_tasks[range][which];
-  const size_t smem = fwd ? fwd_smem<T>() : bwd_smem<T>();
-  void* kern = fwd ? (void*)k_dep_fwd<T> : (void*)k_dep_bwd<T>;
+  const int2* tasks = pairs ? c->d_dep_tasks2[range][which] : c->d_dep_tasks[range][which];
+  const size_t smem = pairs ? (fwd ? fwd2_smem<T>() : bwd2_smem<T>()) : (fwd ? fwd_smem<T>() : bwd_smem<T>());
+  void* kern;
+  if constexpr (pairs) kern = fwd ? (void*)k_dep_fwd2<T> : (void*)k_dep_bwd2<T>;
+  else kern = fwd ? (void*)k_dep_fwd<T> : (void*)k_dep_bwd<T>;
   int per_sm = 0;
   IETI_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, DEP_THREADS, smem));
   if (per_sm < 1) return IETI_ERR_STATE;
@@ -444,6 +691,10 @@ ieti_status dep_sweep_attrs(Ctx* c) {
                                         (int)bwd_smem<float>()));
   IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_dep_bwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)bwd_smem<double>()));
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_dep_fwd2<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)fwd2_smem<float>()));
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_dep_bwd2<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)bwd2_smem<float>()));
   return IETI_OK;
 }
 
@@ -481,6 +732,24 @@ ieti_status dep_sweep_alloc(Ctx* c) {
       c->allocs.push_back({d, bytes});
       if (!tk.empty()) IETI_CUDA_TRY(c, cudaMemcpy(d, tk.data(), sizeof(int2) * tk.size(), cudaMemcpyHostToDevice));
       c->d_dep_tasks[range][which] = d;
+      // pairs of blocks, aligned at the start of the sweep: forward (b0, b0+1),
+      // (b0+2, b0+3), ...; backward (nblk-1, nblk-2), ...; a lone block ends it
+      std::vector<int2> t2;
+      for (int q = 0; 2 * q < c->max_nblk; ++q)
+        for (int k = 0; k < c->nsub; ++k) {
+          const SubDev& sk = c->sd_host[k];
+          if (range == RV_IRANGE && sk.nI == 0) continue;
+          const int b0 = range == RV_IRANGE ? sk.nVp / NB : 0;
+          const int b = which == 0 ? b0 + 2 * q : sk.nblk - 1 - 2 * q;
+          if (b >= b0 && b < sk.nblk) t2.push_back(make_int2(k, b));
+        }
+      c->dep_ntask2[range][which] = (int)t2.size();
+      int2* d2 = nullptr;
+      const size_t bytes2 = sizeof(int2) * std::max<size_t>(t2.size(), 1);
+      IETI_CUDA_TRY(c, cudaMalloc(&d2, bytes2));
+      c->allocs.push_back({d2, bytes2});
+      if (!t2.empty()) IETI_CUDA_TRY(c, cudaMemcpy(d2, t2.data(), sizeof(int2) * t2.size(), cudaMemcpyHostToDevice));
+      c->d_dep_tasks2[range][which] = d2;
     }
   }
   unsigned long long* pg = nullptr;
