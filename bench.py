@@ -23,6 +23,12 @@ import time
 
 import numpy as np
 
+
+# DRAM bytes per PCG iteration of k_pcg_stream<float,1,true> on the 64-patch
+# bench workload, from one ncu capture of the kernel as it stands (4,413,502,464
+# read + 16,712,448 written over a 66-iteration launch)
+PCG_DRAM_BYTES_PER_ITERATION = (4413502464 + 16712448) / 66
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -306,9 +312,18 @@ def ours(args):
     pcg_roof = None
     if prof_pcg[1]:
         achieved = per_it * its_total / (prof_pcg[0] / 1e3) / 1e9
+        its_per_launch = its_total / prof_pcg[1]
+        traffic = PCG_DRAM_BYTES_PER_ITERATION * its_per_launch
         pcg_roof = {"kernel": "k_pcg_stream<float,1,true> (persistent PCG on the streamed products)",
                     "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                    "frac": round(achieved / hbm, 4), "traffic": None, "bytes_per_iteration": per_it,
+                    "frac": round(achieved / hbm, 4), "traffic": round(traffic),
+                    "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one ncu-captured launch of "
+                                    "this kernel on this workload, per iteration x the mean iterations per "
+                                    "launch here: W_k and the Phi_I^T rows "
+                                    "(evict-last) stay in L2 from one iteration to the next, so DRAM carries "
+                                    "about half of the algorithmic bytes",
+                    "dram_gbs": round(traffic / (prof_pcg[0] / prof_pcg[1] / 1e3) / 1e9, 1),
+                    "bytes_per_iteration": per_it,
                     "iterations": its_total, "launches": int(prof_pcg[1]),
                     "avg_launch_ms": round(prof_pcg[0] / prof_pcg[1], 4),
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback"}
