@@ -271,8 +271,9 @@ ieti_status ieti_interface_rhs(ieti_ctx* ctx, double* b_dev, void* stream);
 /* Number of kernel launches this context has issued so far. */
 int64_t ieti_launch_count(const ieti_ctx* ctx);
 
-/* Testing aids for the failure paths (the paper has no counterpart; faults
- * are injected from the host, no device code is made to fault):
+/* Testing aids for the failure paths and the experimental code paths (the
+ * paper has no counterpart; faults are injected from the host, no device code
+ * is made to fault):
  *   IETI_DEBUG_WAIT_POLLS   poll limit of the progress-counter waits of the
  *                           dependency-driven triangular sweeps (value >= 0
  *                           polls of about 0.1 us; < 0 restores the default
@@ -288,8 +289,23 @@ int64_t ieti_launch_count(const ieti_ctx* ctx);
  *                           first correction step as stalled and switches to
  *                           FP64 factors (the path taken when FP32 factors are
  *                           outside their regime).
+ *   IETI_DEBUG_SYRK_TC      value != 0: the FP32 trailing updates run on the
+ *                           tensor cores (tcgen05, split TF32 products); an
+ *                           experimental path, slower than the default CUDA-core
+ *                           update. Only before the first ieti_factor (STATE
+ *                           after it).
+ *   IETI_DEBUG_NO_AUTOTUNE  value != 0: the tile shapes of the streamed
+ *                           products keep their defaults (no timing of
+ *                           candidates at the first factorisation of each
+ *                           precision).
  * Errors: INVALID_ARG (unknown setting, subdomain out of range), STATE. */
-enum { IETI_DEBUG_WAIT_POLLS = 1, IETI_DEBUG_PIVOT_FAULT = 2, IETI_DEBUG_FP64_FALLBACK = 3 };
+enum {
+  IETI_DEBUG_WAIT_POLLS = 1,
+  IETI_DEBUG_PIVOT_FAULT = 2,
+  IETI_DEBUG_FP64_FALLBACK = 3,
+  IETI_DEBUG_SYRK_TC = 4,
+  IETI_DEBUG_NO_AUTOTUNE = 5
+};
 ieti_status ieti_debug_set(ieti_ctx* ctx, int what, int64_t value);
 
 /* Per-kernel-class device timing with CUDA events recorded around each launch

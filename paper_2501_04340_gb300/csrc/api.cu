@@ -328,8 +328,8 @@ ieti_status build(Ctx* c, const ieti_problem_desc* desc, bool device) {
 
   c->host_only = !device;
   if (!device) return IETI_OK;
-  c->syrk_tc = std::getenv("IETI_SYRK_TC") != nullptr;
-  c->autotune = std::getenv("IETI_NO_AUTOTUNE") == nullptr;
+  c->syrk_tc = false;   // the CUDA-core trailing update (tensor cores: IETI_DEBUG_SYRK_TC)
+  c->autotune = true;
   {
     int dev = 0, optin = 48 * 1024;
     IETI_CUDA_TRY(c, cudaGetDevice(&dev));
@@ -789,6 +789,16 @@ ieti_status ieti_debug_set(ieti_ctx* x, int what, int64_t value) {
       return IETI_OK;
     case IETI_DEBUG_FP64_FALLBACK:
       c->force_fallback = value != 0;
+      return IETI_OK;
+    case IETI_DEBUG_SYRK_TC:
+      if (c->symb_ready) {   // the factorisation work lists depend on it
+        c->err = "ieti_debug_set: the trailing-update path is chosen before the first factorisation";
+        return IETI_ERR_STATE;
+      }
+      c->syrk_tc = value != 0;
+      return IETI_OK;
+    case IETI_DEBUG_NO_AUTOTUNE:
+      c->autotune = value == 0;
       return IETI_OK;
     default:
       c->err = "ieti_debug_set: unknown setting";

@@ -79,37 +79,57 @@ __device__ inline int curl_term(int d, int c, int fam[3]) {
   fam[0] = 1; fam[1] = 0; fam[2] = 2; return -1;             // c == 1
 }
 
-__device__ inline void source_eval(const AsmParams& P, int q, const double X[3], double J[][3]) {
+// Fourier modes with integer wave numbers up to FT_KMAX per axis come from
+// per-point tables of e^{2 pi i k x_d} (k = 0..FT_KMAX, one sincospi each), so
+// a mode costs two complex products instead of an FP64 cosine and sine (the
+// FP64 pipe of GB300 is narrow); other modes are evaluated directly.
+constexpr int FT_KMAX = 8;
+
+__device__ inline void fourier_factor(const double2* Et, double kd, double x, double& c, double& s) {
+  const double a = fabs(kd);
+  if (a == rint(a) && a <= FT_KMAX) {
+    const double2 v = Et[(int)a];
+    c = v.x;
+    s = kd < 0 ? -v.y : v.y;
+  } else {
+    sincospi(2.0 * kd * x, &s, &c);
+  }
+}
+
+// the source of load case r at the point X (tab: the point's tables, 3 x
+// (FT_KMAX + 1), used by the Fourier kind)
+__device__ inline void source_eval_r(const AsmParams& P, int q, int r, const double X[3], const double2* tab,
+                                     double J[3]) {
   const double pi = 3.14159265358979323846;
   if (P.source_kind == IETI_SOURCE_SINE) {
-    double sx = sin(pi * X[0]), sy = sin(pi * X[1]), sz = sin(pi * X[2]);
-    double b0 = 2 * pi * pi * sy * sz, b1 = 2 * pi * pi * sx * sz, b2 = 2 * pi * pi * sx * sy;
-    for (int r = 0; r < P.nrhs; ++r) {
-      double s = P.src[r];
-      J[r][0] = s * b0; J[r][1] = s * b1; J[r][2] = s * b2;
-    }
+    const double sx = sin(pi * X[0]), sy = sin(pi * X[1]), sz = sin(pi * X[2]);
+    const double sc = P.src[r];
+    J[0] = sc * 2 * pi * pi * sy * sz;
+    J[1] = sc * 2 * pi * pi * sx * sz;
+    J[2] = sc * 2 * pi * pi * sx * sy;
   } else if (P.source_kind == IETI_SOURCE_FOURIER) {
     int pos = 0;
-    for (int r = 0; r < P.nrhs; ++r) {
-      int nm = (int)P.src[pos++];
-      double a0 = 0, a1 = 0, a2 = 0;
-      for (int m = 0; m < nm; ++m) {
-        const double* M = P.src + pos;
-        pos += 9;
-        double th = 2 * pi * (M[0] * X[0] + M[1] * X[1] + M[2] * X[2]);
-        double cs = cos(th), sn = sin(th);
-        a0 += cs * M[3] - sn * M[6];
-        a1 += cs * M[4] - sn * M[7];
-        a2 += cs * M[5] - sn * M[8];
-      }
-      J[r][0] = a0; J[r][1] = a1; J[r][2] = a2;
+    for (int rr = 0; rr < r; ++rr) pos += 1 + 9 * (int)P.src[pos];
+    const int nm = (int)P.src[pos++];
+    double a0 = 0, a1 = 0, a2 = 0;
+    for (int m = 0; m < nm; ++m) {
+      const double* M = P.src + pos + 9 * m;
+      // e^{i theta}, theta = 2 pi k . X, as the product of the three axis factors
+      double c0, s0, c1, s1, c2, s2;
+      fourier_factor(tab, M[0], X[0], c0, s0);
+      fourier_factor(tab + (FT_KMAX + 1), M[1], X[1], c1, s1);
+      fourier_factor(tab + 2 * (FT_KMAX + 1), M[2], X[2], c2, s2);
+      const double c01 = c0 * c1 - s0 * s1, s01 = s0 * c1 + c0 * s1;
+      const double cs = c01 * c2 - s01 * s2, sn = s01 * c2 + c01 * s2;
+      a0 += cs * M[3] - sn * M[6];
+      a1 += cs * M[4] - sn * M[7];
+      a2 += cs * M[5] - sn * M[8];
     }
+    J[0] = a0; J[1] = a1; J[2] = a2;
   } else {
-    int np = P.P0 * P.P1 * P.P2;
-    for (int r = 0; r < P.nrhs; ++r) {
-      const double* v = P.src + ((size_t)r * np + q) * 3;
-      J[r][0] = v[0]; J[r][1] = v[1]; J[r][2] = v[2];
-    }
+    const int np = P.P0 * P.P1 * P.P2;
+    const double* v = P.src + ((size_t)r * np + q) * 3;
+    J[0] = v[0]; J[1] = v[1]; J[2] = v[2];
   }
 }
 
@@ -321,6 +341,11 @@ __global__ void __launch_bounds__(256) k_elem_j(AsmParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ElemShared<PD>& sh = *reinterpret_cast<ElemShared<PD>*>(smem_raw);
   double* G = reinterpret_cast<double*>(smem_raw + sizeof(ElemShared<PD>));   // NQ3 x nrhs x 3
+  double* As = G + (size_t)NQ3 * P.nrhs * 3;                                   // NQ3 x 9: weighted adj(DF)
+  double* Xs = As + NQ3 * 9;                                                   // NQ3 x 3: the points
+  // NQ3 x 3 x (FT_KMAX + 1) axis exponentials, on a 16-byte boundary (the
+  // shared arrays before it end on an 8-byte one for some degrees)
+  double2* Et = reinterpret_cast<double2*>((reinterpret_cast<uintptr_t>(Xs + NQ3 * 3) + 15) & ~uintptr_t(15));
   const int e = blockIdx.x;
   int q, k;
   // the geometry at the Gauss points does not change between assemblies: it
@@ -350,11 +375,28 @@ __global__ void __launch_bounds__(256) k_elem_j(AsmParams P) {
         for (int r = 0; r < 9; ++r) gk[3 + r] = A[r];
       }
     }
-    double J[MAX_RHS][3];
-    source_eval(P, q, X, J);
-    for (int r = 0; r < P.nrhs; ++r)
-      for (int a = 0; a < 3; ++a)
-        G[(t * P.nrhs + r) * 3 + a] = A[a * 3 + 0] * J[r][0] + A[a * 3 + 1] * J[r][1] + A[a * 3 + 2] * J[r][2];
+    for (int r = 0; r < 9; ++r) As[t * 9 + r] = A[r];
+    for (int r = 0; r < 3; ++r) Xs[t * 3 + r] = X[r];
+  }
+  __syncthreads();
+  if (P.source_kind == IETI_SOURCE_FOURIER) {
+    constexpr int KT = FT_KMAX + 1;
+    for (int u = tid; u < NQ3 * 3 * KT; u += blockDim.x) {
+      const int t = u / (3 * KT), d = (u / KT) % 3, kk = u % KT;
+      double sn, cs;
+      sincospi(2.0 * kk * Xs[t * 3 + d], &sn, &cs);
+      Et[u] = make_double2(cs, sn);
+    }
+    __syncthreads();
+  }
+  // the source at every (point, load case), spread over all threads
+  for (int u = tid; u < NQ3 * P.nrhs; u += blockDim.x) {
+    const int t = u / P.nrhs, r = u % P.nrhs;
+    double J[3];
+    source_eval_r(P, q, r, Xs + t * 3, Et + t * 3 * (FT_KMAX + 1), J);
+    const double* A = As + t * 9;
+    for (int a = 0; a < 3; ++a)
+      G[(t * P.nrhs + r) * 3 + a] = A[a * 3 + 0] * J[0] + A[a * 3 + 1] * J[1] + A[a * 3 + 2] * J[2];
   }
   __syncthreads();
   for (int t = tid; t < NF * P.nrhs; t += blockDim.x) {
@@ -577,7 +619,8 @@ static ieti_status launch_elem(Ctx* c, const AsmParams& P, bool do_K, cudaStream
     prof_end(c, PROF_ASM_K, p0, st);
     IETI_LAUNCH_CHECK(c);
   }
-  size_t smem = sizeof(ElemShared<PD>) + sizeof(double) * (size_t)NQ3 * c->nrhs * 3;
+  size_t smem = sizeof(ElemShared<PD>) + sizeof(double) * (size_t)NQ3 * (c->nrhs * 3 + 9 + 3) + 16 +
+                sizeof(double2) * (size_t)NQ3 * 3 * (FT_KMAX + 1);
   cudaEvent_t p0 = prof_begin(c, st);
   k_elem_j<PD><<<(unsigned)c->nelem, 256, smem, st>>>(P);
   prof_end(c, PROF_ASM_J, p0, st);

@@ -266,6 +266,8 @@ def ieti_launch_count(ctx):
 IETI_DEBUG_WAIT_POLLS = 1
 IETI_DEBUG_PIVOT_FAULT = 2
 IETI_DEBUG_FP64_FALLBACK = 3
+IETI_DEBUG_SYRK_TC = 4
+IETI_DEBUG_NO_AUTOTUNE = 5
 
 
 def ieti_debug_set(ctx, what, value):

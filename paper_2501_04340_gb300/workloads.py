@@ -406,6 +406,19 @@ def cube512_p3_uneven64(seed: int = 3, nrhs: int = 32, span_lo: int = 4, span_hi
                      source_params=sp, nrhs=nrhs)
 
 
+def cube64_uneven8(seed: int = 3, nrhs: int = 32, span_lo: int = 2, span_hi: int = 4) -> Problem:
+    """The reduced uneven case of cube512_p3_uneven64: 4x4x4 patches, spans per
+    patch slab drawn from {2..4}, p=3, 8 uneven simply connected subdomains of
+    4-12 patches, 32 divergence-free random Fourier sources (6 modes each of
+    |k|_inf <= 2), nu = 1; small enough for the oracle."""
+    rng = np.random.default_rng(seed)
+    spans = [list(rng.integers(span_lo, span_hi + 1, size=4)) for _ in range(3)]
+    sub = greedy_partition((4, 4, 4), 4, 12, 8, seed)
+    sp = fourier_source_params(nrhs, 2, seed, nmodes=6)
+    return unit_cube(3, (4, 4, 4), spans, sub_of_patch=sub, nu=np.ones(64),
+                     name="cube64_uneven8", source_kind=SOURCE_FOURIER, source_params=sp, nrhs=nrhs)
+
+
 def annulus(p: int, patches: Tuple[int, int, int], spans, r_in: float, r_out: float, length: float,
             arc: float = 2 * math.pi, sub_of_patch=None, nu=None, name="annulus",
             source_kind=SOURCE_PATCHWISE, source_params=None, nrhs=1) -> Problem:

@@ -264,20 +264,23 @@ def test_many_load_cases_match_the_oracle(ieti, prec):
         ieti.ieti_destroy(ctx)
 
 
-def test_tensor_core_trailing_update_path(ieti, monkeypatch):
-    """The opt-in FP32 trailing update on the tensor cores (split TF32 products)
-    gives a factor good enough for the FP64 refinement: the field matches the
-    monolithic oracle solve to 1e-8, like the CUDA-core update."""
+def test_tensor_core_trailing_update_path(ieti):
+    """The experimental FP32 trailing update on the tensor cores (split TF32
+    products) gives a factor good enough for the FP64 refinement: the field
+    matches the monolithic oracle solve to 1e-8, like the CUDA-core update. The
+    path is chosen before the first factorisation only."""
     prob, mesh, topo, sysd, a_m = oracle_case("cube12_p2_mixed")
-    monkeypatch.setenv("IETI_SYRK_TC", "1")
     ctx = ieti.ieti_create(prob)
     try:
+        ieti.ieti_debug_set(ctx, ieti.IETI_DEBUG_SYRK_TC, 1)
         ieti.ieti_assemble(ctx)
         ieti.ieti_factor(ctx, 1)
         a = torch.zeros((prob.nrhs, mesh.nedge), dtype=torch.float64, device="cuda")
         info = ieti.ieti_solve(ctx, a, tol=1e-10, maxit=400, tol_field=1e-12)
         assert info.converged == 1
         assert np.linalg.norm(a.cpu().numpy().T - a_m) <= 1e-8 * np.linalg.norm(a_m)
+        with pytest.raises(ieti.IetiError, match="STATE"):
+            ieti.ieti_debug_set(ctx, ieti.IETI_DEBUG_SYRK_TC, 0)
     finally:
         ieti.ieti_destroy(ctx)
 
@@ -297,5 +300,69 @@ def test_fp64_fallback_of_the_refinement(ieti):
         info2 = ieti.ieti_solve(ctx, a, tol=1e-11, maxit=400, tol_field=1e-10)
         assert info2.converged == 1 and info2.fp64_fallback == 0 and info2.refinement_steps <= 3
         assert np.linalg.norm(a.cpu().numpy().T - a_m) <= 1e-8 * np.linalg.norm(a_m)
+    finally:
+        ieti.ieti_destroy(ctx)
+
+
+_uneven = {}
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_uneven_subdomains_with_32_load_cases(ieti, prec):
+    """The reduced form of the 512-patch workload: 8 uneven simply connected
+    subdomains of 4-12 patches, spans 2-4 per patch slab, p = 3, 32 Fourier load
+    cases at once (more than eight columns: the per-phase PCG loop and the
+    multi-column sweeps). Every column of the field matches the monolithic
+    oracle solve to 1e-8, for FP64 factors and for FP32 factors with FP64
+    refinement."""
+    if not _uneven:
+        prob = wl.cube64_uneven8()
+        mesh, Kp, jp = dz.assemble_all(prob)
+        topo = tp.build_topology(prob, mesh)
+        a_m, _ = mono.solve(mesh, topo, Kp, jp)
+        _uneven.update(prob=prob, mesh=mesh, a_m=a_m)
+    prob, mesh, a_m = _uneven["prob"], _uneven["mesh"], _uneven["a_m"]
+    ctx = ieti.ieti_create(prob)
+    try:
+        ieti.ieti_assemble(ctx)
+        ieti.ieti_factor(ctx, prec)
+        a = torch.zeros((32, mesh.nedge), dtype=torch.float64, device="cuda")
+        info = ieti.ieti_solve(ctx, a, tol=1e-10, maxit=600, tol_field=1e-10 if prec else 0.0)
+        assert info.converged == 1
+        ag = a.cpu().numpy().T
+        err = np.linalg.norm(ag - a_m, axis=0) / np.linalg.norm(a_m, axis=0)
+        assert err.max() <= 1e-8, err.max()
+    finally:
+        ieti.ieti_destroy(ctx)
+
+
+def test_fourier_loads_match_the_oracle(ieti):
+    """Fourier loads (SOURCE_FOURIER): modes with integer wave numbers up to 8
+    come from per-point tables of the axis exponentials, the others (a
+    non-integer and a large wave number here) are evaluated directly; both give
+    the oracle's load blocks to 1e-12."""
+    base = wl.cube8_p2n4()
+    sp = [3.0,
+          1.0, -2.0, 0.0, 0.3, -0.1, 0.2, 0.05, 0.4, -0.3,
+          0.5, 1.0, -1.5, 1.0, 0.0, 0.25, -0.2, 0.1, 0.0,
+          9.0, 0.0, -11.0, 0.0, 0.7, 0.0, 0.3, 0.0, 0.2,
+          2.0,
+          8.0, -8.0, 8.0, 0.1, 0.2, -0.3, 0.0, 0.1, 0.1,
+          0.0, 0.0, 1.0, -0.4, 0.6, 0.0, 0.2, 0.1, 0.0]
+    prob = wl.unit_cube(2, (2, 2, 2), 4, name="cube8_fourier", source_kind=wl.SOURCE_FOURIER,
+                        source_params=sp, nrhs=2)
+    mesh, Kp, jp = dz.assemble_all(prob)
+    topo = tp.build_topology(prob, mesh)
+    sysd = fd.build_system(prob, (mesh, Kp, jp), topo)
+    ctx = ieti.ieti_create(prob)
+    try:
+        ieti.ieti_assemble(ctx)
+        for k, s in enumerate(sysd.subs):
+            r_lib = np.concatenate([ieti.ieti_get_dofmap(ctx, 4, k), ieti.ieti_get_dofmap(ctx, 5, k)])
+            pos = {int(e): i for i, e in enumerate(s.r_ids)}
+            p = np.array([pos[int(e)] for e in r_lib], dtype=np.int64)
+            assert rel(ieti.ieti_get_block(ctx, 3, k), s.jr[p]) < 1e-12
+            if len(s.Cidx):
+                assert rel(ieti.ieti_get_block(ctx, 4, k), s.jp) < 1e-12
     finally:
         ieti.ieti_destroy(ctx)
