@@ -382,16 +382,62 @@ def ours(args):
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
+    ieti.ieti_destroy(ctx)
+    if rank == 0:
+        out["apply_F_explicit_vs_implicit"] = explicit_vs_implicit()
     if rank == 0 and not args.skip_warmstart:
         out["warm_start"] = warmstart_report()
     if rank == 0 and not args.skip_cpu:
         out["cpu_baseline"] = cpu_sample(info64.iterations)
-    ieti.ieti_destroy(ctx)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def explicit_vs_implicit(nrhs=32, napply=20):
+    """F_DP on 32 load cases of the bench mesh, evaluated two ways with the same
+    factors: the streamed product with the explicit W_k = S_rIrI^-1
+    (ieti_apply_F) and triangular solves with the r_I blocks of the factors
+    (ieti_apply_F_implicit); a 256 MB write flush before every timed apply."""
+    import torch
+    from paper_2501_04340_gb300 import ieti, workloads as wl
+    prob = wl.cube64_p3n8_sub16(nrhs=nrhs)
+    ctx = ieti.ieti_create(prob)
+    q = ieti.ieti_query(ctx)
+    lam = torch.randn((nrhs, q["m_r"]), dtype=torch.float64, device="cuda")
+    y = torch.empty_like(lam)
+    y2 = torch.empty_like(lam)
+    flush = torch.empty(int(256e6) // 4, dtype=torch.float32, device="cuda")
+    res = {"workload": f"{WORKLOAD} with {nrhs} load cases", "nrhs": nrhs}
+    try:
+        ieti.ieti_assemble(ctx)
+        for prec, name in ((ieti.IETI_FP32_IR, "fp32"), (ieti.IETI_FP64, "fp64")):
+            ieti.ieti_factor(ctx, prec)
+            ieti.ieti_apply_F(ctx, lam, y, nrhs)
+            ieti.ieti_apply_F_implicit(ctx, lam, y2, nrhs)
+            diff = float(torch.linalg.norm(y2 - y) / torch.linalg.norm(y))
+            times = {}
+            for kind, fn in (("explicit", lambda: ieti.ieti_apply_F(ctx, lam, y, nrhs)),
+                             ("implicit", lambda: ieti.ieti_apply_F_implicit(ctx, lam, y2, nrhs))):
+                tot = 0.0
+                for _ in range(napply):
+                    flush.fill_(1.0)
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    fn()
+                    e1.record()
+                    torch.cuda.synchronize()
+                    tot += e0.elapsed_time(e1)
+                times[kind] = tot / napply
+            res[name] = {"explicit_ms": round(times["explicit"], 4), "implicit_ms": round(times["implicit"], 4),
+                         "explicit_over_implicit_speedup": round(times["implicit"] / times["explicit"], 2),
+                         "rel_difference": diff}
+    finally:
+        ieti.ieti_destroy(ctx)
+    return res
 
 
 # ----------------------------------------------------------------------------

@@ -173,6 +173,17 @@ ieti_status ieti_factor(ieti_ctx* ctx, ieti_precision prec, void* stream);
 ieti_status ieti_apply_F(ieti_ctx* ctx, const double* lam_dev, double* y_dev, int nrhs,
                          void* stream);
 
+/* Eq. (7), evaluated through the local factors instead of the explicit
+ * W_k = S_rIrI^-1: the local part B_r K_rr^-1 B_r^T lam as triangular solves
+ * with the r_I block of each Cholesky factor (K_rr^-1 restricted to the r_I
+ * rows and columns is (L_II L_II^T)^-1), plus the same coarse part. The same
+ * F_DP lam as ieti_apply_F up to rounding; kept to compare the two
+ * evaluations. nrhs must equal the context's number of load cases (the
+ * solves use its work buffers). Errors: STATE (not factored), INVALID_ARG,
+ * TIMEOUT (a sweep wait gave up), CUDA. */
+ieti_status ieti_apply_F_implicit(ieti_ctx* ctx, const double* lam_dev, double* y_dev, int nrhs,
+                                  void* stream);
+
 /* Eq. (10): z = M_D^-1 r = sum_k D^(k) B_rI^(k) S_rIrI^(k) B_rI^(k)T D^(k) r,
  * with D^(k) the rho-scaling weights nu_l / (nu_k + nu_l). r_dev, z_dev: m_r x
  * nrhs FP64 device arrays, not aliased. */

@@ -566,6 +566,30 @@ ieti_status ieti_apply_F(ieti_ctx* x, const double* lam, double* y, int nrhs, vo
   return apply_F(c, lam, y, nrhs, c->prec == IETI_FP32_IR, (cudaStream_t)stream);
 }
 
+ieti_status ieti_apply_F_implicit(ieti_ctx* x, const double* lam, double* y, int nrhs, void* stream) {
+  if (!x || !lam || !y) return IETI_ERR_INVALID_ARG;
+  Ctx* c = &x->c;
+  if (!c->factored) {
+    c->err = "ieti_apply_F_implicit before ieti_factor";
+    return IETI_ERR_STATE;
+  }
+  if (nrhs != c->nrhs) {
+    c->err = "ieti_apply_F_implicit: nrhs must equal the context's number of load cases";
+    return IETI_ERR_INVALID_ARG;
+  }
+  const cudaStream_t st = (cudaStream_t)stream;
+  IETI_CUDA_TRY(c, cudaMemsetAsync(c->d_dep_err, 0, sizeof(int), st));
+  ieti_status r = apply_F_implicit(c, lam, y, st);
+  if (r != IETI_OK) return r;
+  IETI_CUDA_TRY(c, cudaMemcpyAsync(c->h_err + 1, c->d_dep_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  IETI_CUDA_TRY(c, cudaStreamSynchronize(st));
+  if (c->h_err[1]) {
+    c->err = "a triangular-sweep wait timed out";
+    return IETI_ERR_TIMEOUT;
+  }
+  return IETI_OK;
+}
+
 ieti_status ieti_apply_precond(ieti_ctx* x, const double* r, double* z, int nrhs, void* stream) {
   if (!x || !r || !z) return IETI_ERR_INVALID_ARG;
   Ctx* c = &x->c;
@@ -837,6 +861,9 @@ void ieti_destroy(ieti_ctx* x) {
   for (cudaEvent_t e : x->c.ev_fact)
     if (e) cudaEventDestroy(e);
   if (x->c.aux_stream) cudaStreamDestroy(x->c.aux_stream);
+  for (auto& g : x->c.sgraph)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (x->c.cap_stream) cudaStreamDestroy(x->c.cap_stream);
   delete x;
 }
 

@@ -243,6 +243,17 @@ struct Ctx {
   double* wc[2] = {nullptr, nullptr};    // coarse vectors
   double* wlam[8] = {};                  // PCG vectors (m_r x nrhs)
   float* wvf = nullptr;                  // FP32 PCG vectors of the streamed form (5 x m_r x nrhs)
+  // graphs of the refinement step's launch sequence: [first step, correction]
+  struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    int prec = -1, maxit = 0;
+    double tol_in = 0;
+    const double* a = nullptr;           // the caller's field buffer the graph writes
+    int64_t nkern = 0;                   // kernel launches in the graph (counted at each replay)
+  } sgraph[2];
+  bool graph_ok = true;                  // capture works here (cleared at the first failure)
+  cudaStream_t cap_stream = nullptr;     // the stream the graphs are captured on
+  bool graph_pcg_persistent = false;     // the last directly launched step ran the persistent PCG
   double* wscal = nullptr;               // PCG scalars
   double* wred = nullptr;                // reduction partials
   int* wflag = nullptr;
@@ -390,6 +401,7 @@ ieti_status pcg_stream(Ctx* c, double* lam, double* r, double* z, double* p, dou
 ieti_status pcg_coop(Ctx* c, double* lam, double* r, double* z, double* p, double* q, double tol2, int maxit,
                      bool fp32, cudaStream_t st);
 ieti_status apply_F(Ctx* c, const double* lam, double* y, int nrhs, bool fp32_ops, cudaStream_t s);
+ieti_status apply_F_implicit(Ctx* c, const double* lam, double* y, cudaStream_t s);
 ieti_status apply_precond(Ctx* c, const double* r, double* z, int nrhs, bool fp32_ops, cudaStream_t s);
 ieti_status interface_rhs(Ctx* c, const double* jr, const double* jp, double* b, double* dprime,
                           int nrhs, cudaStream_t s);

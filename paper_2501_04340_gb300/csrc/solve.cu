@@ -655,6 +655,49 @@ static ieti_status apply_F_ex(Ctx* c, const double* lam, double* y, int nrhs, bo
   return IETI_OK;
 }
 
+__global__ void k_negate(double* y, int64_t n) {
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x)
+    y[l] = -y[l];
+}
+
+// F_DP lam through the factors: X_I = K_rr^-1 [0; -B_r^T lam] by forward and
+// backward sweeps over the r_I blocks (the r_V rows of the right-hand side
+// vanish), e = B X_I = -B_r K_rr^-1 B_r^T lam; the gather forms
+// e - (coarse part) = -F_DP lam, which is negated
+template <typename T>
+static ieti_status apply_F_implicit_t(Ctx* c, const double* lam, double* y, cudaStream_t st) {
+  const int nrhs = c->nrhs;
+  ieti_status r;
+  T* B = (T*)c->wr[0];
+  T* Y = (T*)c->wr[1];
+  T* X = (T*)c->wr[2];
+  const dim3 g(256, c->nsub);
+  k_dual_rhs<T><<<g, 256, 0, st>>>(c->d_sd, c->d_I_dual, c->d_I_sign, lam, c->m_r, nrhs, B);
+  IETI_LAUNCH_CHECK(c);
+  if ((r = rv_solve<T>(c, RV_IRANGE, SWEEP_FWD | SWEEP_BWD, B, Y, X, st)) != IETI_OK) return r;
+  const int gb = gather_blocks(c);
+  double* e = c->wlam[7];
+  k_gather_e<T><<<dim3(gb, nrhs), 256, 0, st>>>(c->d_sd, c->d_pair, X, c->m_r, nrhs, e);
+  IETI_LAUNCH_CHECK(c);
+  const bool coarse = c->n_gp > 0;
+  if (coarse) {
+    k_phiT<<<c->nsub, 256, 0, st>>>(c->d_sd, c->Phi, c->d_I_dual, c->d_I_sign, lam, c->m_r, c->wq_part, nrhs);
+    IETI_LAUNCH_CHECK(c);
+    if ((r = coarse_solve(c, c->wq_part, c->wc[0], nrhs, st)) != IETI_OK) return r;
+  }
+  k_gather_F<<<dim3(gb, nrhs), 256, 0, st>>>(c->d_sd, c->d_pair, nullptr, c->Phi, c->d_P_glob,
+                                            coarse ? c->wc[0] : nullptr, (int)c->n_gp, c->m_r, nrhs, y, nullptr,
+                                            nullptr, e, -1.0);
+  IETI_LAUNCH_CHECK(c);
+  k_negate<<<(unsigned)std::min<int64_t>(ceil_div(c->m_r * nrhs, 256), 1216), 256, 0, st>>>(y, c->m_r * nrhs);
+  IETI_LAUNCH_CHECK(c);
+  return IETI_OK;
+}
+
+ieti_status apply_F_implicit(Ctx* c, const double* lam, double* y, cudaStream_t st) {
+  return c->prec == IETI_FP64 ? apply_F_implicit_t<double>(c, lam, y, st) : apply_F_implicit_t<float>(c, lam, y, st);
+}
+
 ieti_status apply_F(Ctx* c, const double* lam, double* y, int nrhs, bool fp32, cudaStream_t st) {
   return apply_F_ex(c, lam, y, nrhs, fp32, nullptr, nullptr, st);
 }
@@ -737,8 +780,11 @@ ieti_status interface_rhs(Ctx* c, const double* jr, const double* jp, double* b,
 }
 
 // PCG on F_DP lam = b (lam holds the initial guess on entry, or zero)
-static ieti_status pcg(Ctx* c, const double* b, double* lam, bool zero_start, double tol, int maxit, bool fp32,
-                       int* iters, double* relres, double* kappa, cudaStream_t st) {
+// The device part of PCG: set-up, then the persistent loop when it applies
+// (*persistent = true: nothing was read back, so the sequence can be captured
+// in a graph), else the per-phase loop with its host checks.
+static ieti_status pcg_run(Ctx* c, const double* b, double* lam, bool zero_start, double tol, int maxit, bool fp32,
+                           bool* persistent_out, cudaStream_t st) {
   const int nrhs = c->nrhs;
   const int64_t m = c->m_r;
   double* r = c->wlam[0];
@@ -806,9 +852,16 @@ static ieti_status pcg(Ctx* c, const double* b, double* lam, bool zero_start, do
     k_update_p<<<vg, 256, 0, st>>>(p, z, scal, m, 0);
     IETI_LAUNCH_CHECK(c);
   }
-  std::vector<double> hs(SC * nrhs);
-  IETI_CUDA_TRY(c, cudaMemcpyAsync(hs.data(), scal, sizeof(double) * SC * nrhs, cudaMemcpyDeviceToHost, st));
-  IETI_CUDA_TRY(c, cudaStreamSynchronize(st));
+  *persistent_out = persistent;
+  return IETI_OK;
+}
+
+// iterations, relative residual and the Lanczos estimate of kappa (when asked
+// for) from the scalars hs of a finished PCG
+static void pcg_stats(Ctx* c, const std::vector<double>& hs, bool want_kappa, int* iters, double* relres,
+                      double* kappa, bool* conv_out) {
+  const int nrhs = c->nrhs;
+  const int hist_cap = 4096;
   int itmax = 0;
   double rel = 0;
   bool conv = true;
@@ -821,12 +874,16 @@ static ieti_status pcg(Ctx* c, const double* b, double* lam, bool zero_start, do
   }
   *iters = itmax;
   *relres = rel;
+  *conv_out = conv;
   // Lanczos estimate of kappa(M^-1 F) from the CG coefficients of column 0
   int n = std::min((int)hs[8], hist_cap);
   *kappa = 0;
-  if (n >= 2) {
+  if (want_kappa && n >= 2) {
     std::vector<double> h(2 * n);
-    IETI_CUDA_TRY(c, cudaMemcpy(h.data(), c->whist, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost));
+    if (cudaMemcpy(h.data(), c->whist, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
     // tridiagonal T: diag 1/a_j + b_{j-1}/a_{j-1}, off sqrt(b_j)/a_j; extreme eigenvalues by bisection
     std::vector<double> dg(n), of(n, 0.0);
     for (int j = 0; j < n; ++j) {
@@ -858,8 +915,8 @@ static ieti_status pcg(Ctx* c, const double* b, double* lam, bool zero_start, do
     double emin = kth(0), emax = kth(n - 1);
     *kappa = emin > 0 ? emax / emin : 0.0;
   }
-  return conv ? IETI_OK : IETI_ERR_NO_CONVERGENCE;
 }
+
 
 // recovery (Eqs. (8), (9)) of the field increment from lam: the primal values
 // p = S_Pi^-1 (d' + Phi_I^T B^T lam) and a_r = K_rr^-1 (j_r - K_rp p - B_r^T lam),
@@ -906,9 +963,10 @@ static ieti_status recover(Ctx* c, const double* lam, const double* ycr, double*
                               : recover_t<float>(c, lam, ycr, a, accumulate, st);
 }
 
-// relative FP64 residual ||j - K a|| / ||j|| (max over columns); local residuals to wres_r/wres_p
-static ieti_status residual(Ctx* c, const double* a, double* rel, double* jn2, cudaStream_t st,
-                           bool zero_field = false) {
+// the device part of the residual: local residuals to wres_r/wres_p, the
+// assembled residual to wglob, its squared column norms to wnorm (no host
+// synchronisation, so that it can be captured in a graph)
+static ieti_status residual_launch(Ctx* c, const double* a, cudaStream_t st, bool zero_field) {
   const int nrhs = c->nrhs;
   const int64_t ne = c->mesh.nedge;
   ieti_status rk;
@@ -930,9 +988,11 @@ static ieti_status residual(Ctx* c, const double* a, double* rel, double* jn2, c
   IETI_LAUNCH_CHECK(c);
   k_colnorm2_sum<<<nrhs, 256, 0, st>>>(c->wred, c->wnorm);
   IETI_LAUNCH_CHECK(c);
-  std::vector<double> h(nrhs);
-  IETI_CUDA_TRY(c, cudaMemcpyAsync(h.data(), c->wnorm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
-  IETI_CUDA_TRY(c, cudaStreamSynchronize(st));
+  return IETI_OK;
+}
+
+// the largest relative residual over the columns from the squared norms h
+static double rel_from_norms(const std::vector<double>& h, const double* jn2, int nrhs) {
   double mx = 0;
   for (int col = 0; col < nrhs; ++col) {
     if (jn2) {
@@ -942,10 +1002,109 @@ static ieti_status residual(Ctx* c, const double* a, double* rel, double* jn2, c
       mx = std::max(mx, h[col]);
     }
   }
-  *rel = mx;
-  if (!jn2) {
-    // caller asked for the raw squared norms (used for ||j||)
+  return mx;
+}
+
+// relative FP64 residual ||j - K a|| / ||j|| (max over columns); local residuals to wres_r/wres_p
+static ieti_status residual(Ctx* c, const double* a, double* rel, double* jn2, cudaStream_t st,
+                           bool zero_field = false) {
+  const int nrhs = c->nrhs;
+  ieti_status rk;
+  if ((rk = residual_launch(c, a, st, zero_field)) != IETI_OK) return rk;
+  std::vector<double> h(nrhs);
+  IETI_CUDA_TRY(c, cudaMemcpyAsync(h.data(), c->wnorm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+  IETI_CUDA_TRY(c, cudaStreamSynchronize(st));
+  *rel = rel_from_norms(h, jn2, nrhs);   // jn2 == nullptr: the raw squared norm (used for ||j||)
+  return IETI_OK;
+}
+
+// The device work of one refinement step (or of the single pass without
+// refinement): interface right-hand side of the current loads, PCG, the
+// multipliers accumulated, the field recovered (added to a after the first
+// step) and, when refining, the new residual and its norms. No host
+// synchronisation when the persistent PCG applies (*pers).
+static ieti_status step_launch(Ctx* c, bool fresh, bool refine, bool zero_start, double* b, double* lam,
+                               double* ycr, double* a, double tol_in, int maxit, bool fp32, bool* pers,
+                               cudaStream_t st) {
+  const int nrhs = c->nrhs;
+  const int64_t m = c->m_r;
+  ieti_status r;
+  const double* jr = fresh ? c->jr : c->wres_r;
+  const double* jp = fresh ? c->jp : c->wres_p;
+  if ((r = interface_rhs(c, jr, jp, b, ycr, nrhs, st)) != IETI_OK) return r;
+  if ((r = pcg_run(c, b, lam, zero_start, tol_in, maxit, fp32, pers, st)) != IETI_OK) return r;
+  k_add<<<1216, 256, 0, st>>>(c->wlam_acc, lam, m * nrhs);
+  IETI_LAUNCH_CHECK(c);
+  if ((r = recover(c, lam, ycr, a, fresh ? 0 : 1, st)) != IETI_OK) return r;
+  if (refine && (r = residual_launch(c, a, st, false)) != IETI_OK) return r;
+  return IETI_OK;
+}
+
+// A step from a CUDA graph of its launch sequence (about 30 launches around
+// the persistent PCG): once a direct step has shown that the persistent PCG
+// applies, the step is captured once per (first step or correction,
+// precision, iteration cap, inner tolerance) and replayed; the kernels'
+// arguments are the context's fixed buffers. *ran = false: nothing was done
+// (no graph applies, or capture is not supported here); the caller launches
+// the step itself.
+static ieti_status step_graph(Ctx* c, bool fresh, bool refine, double* b, double* lam, double* ycr, double* a,
+                              double tol_in, int maxit, bool fp32, bool* ran, cudaStream_t st) {
+  *ran = false;
+  if (!c->graph_ok || !c->graph_pcg_persistent || c->prof.on || !refine) return IETI_OK;
+  Ctx::StepGraph& G = c->sgraph[fresh ? 0 : 1];
+  const bool key_ok = G.exec && G.prec == c->prec && G.maxit == maxit && G.tol_in == tol_in && G.a == a;
+  if (!key_ok) {
+    if (G.exec) {
+      cudaGraphExecDestroy(G.exec);
+      G.exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    // captured on a stream of the context's own (the caller's stream may be the
+    // legacy default stream, which cannot be captured), replayed on the caller's
+    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      c->cap_stream = nullptr;
+      c->graph_ok = false;
+      return IETI_OK;
+    }
+    cudaStream_t cs = c->cap_stream;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      if (std::getenv("IETI_TRACE")) std::fprintf(stderr, "[ieti] step graph not used: capture refused\n");
+      cudaGetLastError();
+      c->graph_ok = false;
+      return IETI_OK;
+    }
+    bool pers = false;
+    const int64_t l0 = c->launches;
+    const ieti_status r = step_launch(c, fresh, refine, true, b, lam, ycr, a, tol_in, maxit, fp32, &pers, cs);
+    const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    const int64_t nk = c->launches - l0;
+    c->launches = l0;   // captured, not launched
+    cudaGraphExec_t exec = nullptr;
+    const bool good = r == IETI_OK && pers && ce == cudaSuccess && graph &&
+                      cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (!good) {
+      // not capturable here: launch the steps directly from now on
+      if (std::getenv("IETI_TRACE"))
+        std::fprintf(stderr, "[ieti] step graph not used: status %d (%s), persistent %d, end capture %s\n", (int)r,
+                     c->err.c_str(), (int)pers, cudaGetErrorString(ce));
+      cudaGetLastError();
+      if (exec) cudaGraphExecDestroy(exec);
+      c->graph_ok = false;
+      c->err.clear();
+      return IETI_OK;
+    }
+    G.exec = exec;
+    G.nkern = nk;
+    G.prec = c->prec;
+    G.maxit = maxit;
+    G.tol_in = tol_in;
+    G.a = a;
   }
+  IETI_CUDA_TRY(c, cudaGraphLaunch(G.exec, st));
+  c->launches += G.nkern;
+  *ran = true;
   return IETI_OK;
 }
 
@@ -999,13 +1158,8 @@ ieti_status solve_all(Ctx* c, const double* lam0, double tol, int maxit, double 
   double* lam = c->wlam[5];
   double* ycr = c->wc[1];
   for (int step = 0; step < max_steps; ++step) {
-    const double* jr = fresh ? c->jr : c->wres_r;
-    const double* jp = fresh ? c->jp : c->wres_p;
-    if ((r = interface_rhs(c, jr, jp, b, ycr, nrhs, st)) != IETI_OK) return r;
     bool warm = (step == 0 && lam0 != nullptr);
     if (warm) IETI_CUDA_TRY(c, cudaMemcpyAsync(lam, lam0, sizeof(double) * m * nrhs, cudaMemcpyDeviceToDevice, st));
-    int its = 0;
-    double rel = 0, kap = 0;
     // with FP32 operators a correction step reduces the field residual by
     // 0.015-0.02 on the 64-patch cube (kappa(K_rr) u_32), whatever the inner
     // tolerance below that level, so the inner PCG only has to beat it. An
@@ -1015,25 +1169,41 @@ ieti_status solve_all(Ctx* c, const double* lam0, double tol, int maxit, double 
     // lower the residual after the first correction); the FP64 residual of
     // the field decides convergence
     const double tol_in = fp32 ? std::max(tol, 2e-3) : tol;
-    ieti_status pr = pcg(c, b, lam, !warm, tol_in, maxit, fp32, &its, &rel, &kap, st);
-    if (pr != IETI_OK && pr != IETI_ERR_NO_CONVERGENCE) return pr;
+    // the step's device work, from a graph when one applies (below), else launched
+    bool pers = false, ran = false;
+    if (!warm && (r = step_graph(c, fresh, refine, b, lam, ycr, a, tol_in, maxit, fp32, &ran, st)) != IETI_OK)
+      return r;
+    if (ran) {
+      pers = true;
+    } else {
+      if ((r = step_launch(c, fresh, refine, !warm, b, lam, ycr, a, tol_in, maxit, fp32, &pers, st)) != IETI_OK)
+        return r;
+      c->graph_pcg_persistent = pers;
+    }
+    // one read-back per step: the PCG scalars, the residual norms and the sweep flag
+    std::vector<double> hs(SC * nrhs), hn(nrhs, 0.0);
+    IETI_CUDA_TRY(c, cudaMemcpyAsync(hs.data(), c->wscal, sizeof(double) * SC * nrhs, cudaMemcpyDeviceToHost, st));
+    if (refine)
+      IETI_CUDA_TRY(c, cudaMemcpyAsync(hn.data(), c->wnorm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+    IETI_CUDA_TRY(c, cudaMemcpyAsync(c->h_err + 1, c->d_dep_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    IETI_CUDA_TRY(c, cudaStreamSynchronize(st));
+    int its = 0;
+    double rel = 0, kap = 0;
+    bool pconv = true;
+    pcg_stats(c, hs, step == 0, &its, &rel, &kap, &pconv);
+    const ieti_status pr = pconv ? IETI_OK : IETI_ERR_NO_CONVERGENCE;
     if (pr == IETI_ERR_NO_CONVERGENCE && !fp32) conv = false;
     total_it += its;
     relres = rel;
     if (step == 0) kappa = kap;
-    k_add<<<1216, 256, 0, st>>>(c->wlam_acc, lam, m * nrhs);
-    IETI_LAUNCH_CHECK(c);
-    if ((r = recover(c, lam, ycr, a, fresh ? 0 : 1, st)) != IETI_OK) return r;
     steps = step + 1;
     fresh = false;
-    if (refine) {
-      if ((r = residual(c, a, &grel, jn2.data(), st)) != IETI_OK) return r;
-    }
+    if (refine) grel = rel_from_norms(hn, jn2.data(), nrhs);
     if (std::getenv("IETI_TRACE"))
-      std::fprintf(stderr, "[ieti] step %d: pcg its %d relres %.3e field residual %.3e\n", step, its, rel, grel);
+      std::fprintf(stderr, "[ieti] step %d: pcg its %d relres %.3e field residual %.3e%s\n", step, its, rel, grel,
+                   ran ? " (graph)" : "");
     if (!refine || grel <= tol_field) break;
     // a timed-out sweep wait leaves garbage: stop and report it (below)
-    IETI_CUDA_TRY(c, cudaMemcpy(c->h_err + 1, c->d_dep_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (c->h_err[1]) break;
     // FP32 factors outside their regime (kappa(K_rr) u_32 not small) show in
     // the first corrections: one of the first two correction steps whose inner

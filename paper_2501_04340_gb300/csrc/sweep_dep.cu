@@ -17,8 +17,9 @@
 // counter says that every block up to it is final); readers poll the counter
 // with acquire loads (bounded, with an error flag on time-out) and read the
 // blocks through L2. Every wait is on a task that comes earlier in the order
-// and all CTAs are resident (cooperative launch), so every wait ends. Progress
-// counters carry an epoch in their upper bits, so they are never reset.
+// and all CTAs are resident (cooperative launch), so every wait ends. The
+// single-column sweeps zero their counters before each launch; the
+// multi-column solves' counters carry an epoch in their upper bits instead.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -657,11 +658,15 @@ ieti_status launch_dep(Ctx* c, bool fwd, int range, const T* B, const T* Yin, T*
   IETI_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, DEP_THREADS, smem));
   if (per_sm < 1) return IETI_ERR_STATE;
   const int grid = std::min(ntask, per_sm * c->sm_count);
-  const unsigned long long base = (++c->dep_epoch) << DEP_EPOCH_SHIFT;
+  // the progress counters start from zero at every sweep (a memset before the
+  // launch), so the launch's arguments are the same every time and a graph of
+  // the step can replay it
+  const unsigned long long base = 1ull << DEP_EPOCH_SHIFT;
+  unsigned long long* prog = c->d_dep_prog;
+  IETI_CUDA_TRY(c, cudaMemsetAsync(prog, 0, sizeof(unsigned long long) * std::max(c->nsub, 1), st));
   const T* L = (const T*)c->L;
   const T* Linv = (const T*)c->Linv;
   const SubDev* sd = c->d_sd;
-  unsigned long long* prog = c->d_dep_prog;
   int* err = c->d_dep_err;
   const int64_t* lptr = fwd ? c->d_lrow_ptr : c->d_lcol_ptr;
   const int32_t* lidx = fwd ? c->d_lrow_col : c->d_lcol_row;

@@ -61,6 +61,7 @@ _sig = {
     "ieti_assemble": (C.c_int, [_vp, _vp]),
     "ieti_factor": (C.c_int, [_vp, C.c_int, _vp]),
     "ieti_apply_F": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp]),
+    "ieti_apply_F_implicit": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp]),
     "ieti_apply_precond": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp]),
     "ieti_solve": (C.c_int, [_vp, _vp, C.c_double, C.c_int, C.c_double, _vp, _vp,
                              C.POINTER(ieti_solve_info), _vp]),
@@ -189,6 +190,10 @@ def ieti_factor(ctx, prec=IETI_FP64, stream=None):
 
 def ieti_apply_F(ctx, lam, y, nrhs=1, stream=None):
     _check(ctx, _lib.ieti_apply_F(ctx, _dptr(lam), _dptr(y), int(nrhs), _stream(stream)))
+
+
+def ieti_apply_F_implicit(ctx, lam, y, nrhs=1, stream=None):
+    _check(ctx, _lib.ieti_apply_F_implicit(ctx, _dptr(lam), _dptr(y), int(nrhs), _stream(stream)))
 
 
 def ieti_apply_precond(ctx, r, z, nrhs=1, stream=None):

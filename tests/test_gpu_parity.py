@@ -366,3 +366,54 @@ def test_fourier_loads_match_the_oracle(ieti):
                 assert rel(ieti.ieti_get_block(ctx, 4, k), s.jp) < 1e-12
     finally:
         ieti.ieti_destroy(ctx)
+
+
+def test_step_graphs_replay_the_direct_steps(ieti):
+    """After a directly launched first step shows that the persistent PCG
+    applies, the refinement steps run from CUDA graphs of their launch
+    sequence (captured once per kind of step). A second solve, every step of it
+    replayed, gives the field of the first to rounding (the residual's
+    assembled sum uses atomic additions), the oracle's to 1e-8, and the same
+    count of kernel launches."""
+    prob, mesh, topo, sysd, a_m = oracle_case("cube32_p3n3_sub8")
+    ctx = ieti.ieti_create(prob)
+    try:
+        ieti.ieti_assemble(ctx)
+        ieti.ieti_factor(ctx, 1)
+        out = []
+        for _ in range(2):
+            a = torch.zeros((prob.nrhs, mesh.nedge), dtype=torch.float64, device="cuda")
+            l0 = ieti.ieti_launch_count(ctx)
+            info = ieti.ieti_solve(ctx, a, tol=1e-10, maxit=400, tol_field=1e-10)
+            out.append((a.cpu().numpy().T, ieti.ieti_launch_count(ctx) - l0, info))
+        (a1, n1, i1), (a2, n2, i2) = out
+        assert i1.converged == 1 and i2.converged == 1
+        assert np.linalg.norm(a2 - a1) <= 1e-12 * np.linalg.norm(a1)
+        assert np.linalg.norm(a2 - a_m) <= 1e-8 * np.linalg.norm(a_m)
+        assert i1.refinement_steps == i2.refinement_steps and n1 == n2
+    finally:
+        ieti.ieti_destroy(ctx)
+
+
+@pytest.mark.parametrize("name", ["ragged_p3", "cube32_p3n3_sub8", "ring24_p3n2"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_apply_F_implicit_matches_the_oracle(ieti, name, prec):
+    """F_DP through the local factors (sweeps over the r_I blocks) equals the
+    oracle's F_DP like the explicit W_k product does (Eq. (7))."""
+    tol = 1e-9 if prec == 0 else fp32_tol(name)
+    if tol is None:
+        pytest.skip("kappa(K_rr) u_32 >= 1: FP32 factors outside their regime")
+    ctx, prob, mesh, topo, sysd, _ = _factored(ieti, name, prec)
+    try:
+        op = fd.InterfaceOperator(sysd)
+        nrhs = prob.nrhs
+        lam = np.random.default_rng(7).standard_normal((sysd.m_r, nrhs))
+        ref = op(lam)
+        lam_d = torch.tensor(lam.T.copy(), dtype=torch.float64, device="cuda")
+        y = torch.empty_like(lam_d)
+        ieti.ieti_apply_F_implicit(ctx, lam_d, y, nrhs)
+        assert rel(y.cpu().numpy().T, ref) < tol
+        with pytest.raises(ieti.IetiError, match="INVALID_ARG"):
+            ieti.ieti_apply_F_implicit(ctx, lam_d, y, nrhs + 1)
+    finally:
+        ieti.ieti_destroy(ctx)
