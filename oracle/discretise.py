@@ -29,7 +29,7 @@ import scipy.sparse as sp
 
 from . import splines
 
-SOURCE_SINE, SOURCE_FOURIER, SOURCE_PATCHWISE = 0, 1, 2
+SOURCE_SINE, SOURCE_FOURIER, SOURCE_PATCHWISE, SOURCE_TRIG = 0, 1, 2, 3
 
 
 @dataclasses.dataclass
@@ -235,6 +235,14 @@ def source_values(prob, X: np.ndarray, q_patch: int) -> np.ndarray:
         P = prob.source_params.reshape(nr, prob.npatch_total, 3)
         for r in range(nr):
             out[..., :, r] = P[r, q_patch]
+    elif prob.source_kind == SOURCE_TRIG:
+        # Sec. 3: curl curl A_ana = 3 A_ana (A_ana is divergence free and each
+        # component is an eigenfunction of -Laplace with eigenvalue 3)
+        base = 3.0 * np.stack([np.cos(y) * np.cos(z) * np.sin(x),
+                               -2.0 * np.cos(x) * np.cos(z) * np.sin(y),
+                               np.cos(x) * np.cos(y) * np.sin(z)], axis=-1)
+        for r in range(nr):
+            out[..., :, r] = prob.source_params[r] * base
     else:
         raise ValueError("unknown source kind")
     return out

@@ -26,6 +26,11 @@ Source kinds (right-hand side j of Eq. (3), one column per load case):
   * SOURCE_FOURIER: J = sum_m Re(c_m exp(2 pi i k_m . x)); params per load case:
     nmodes, then for each mode k (3 values) and Re c (3), Im c (3).
   * SOURCE_PATCHWISE: J constant on each patch; params = nrhs x npatch x 3.
+  * SOURCE_TRIG: J = s * 3 A_ana with A_ana = (cos y cos z sin x,
+    -2 cos x cos z sin y, cos x cos y sin z), params = the amplitudes s. With
+    nu = 1, s A_ana solves the strong problem with the tangential boundary data
+    n x (s A_ana), which is not zero: this kind goes with the non-homogeneous
+    Dirichlet data of the same field.
 """
 from __future__ import annotations
 
@@ -38,6 +43,7 @@ import numpy as np
 SOURCE_SINE = 0
 SOURCE_FOURIER = 1
 SOURCE_PATCHWISE = 2
+SOURCE_TRIG = 3
 
 
 @dataclasses.dataclass
@@ -478,6 +484,57 @@ def machine_annulus(n_ang: int = 36, n_ax: int = 4, spans: int = 6, p: int = 3, 
     return annulus(p, P, spans, r_in, r_out, length, sub_of_patch=sub, nu=nu,
                    name=f"annulus{npt}_p{p}n{spans}_sub{int(sub.max()) + 1}",
                    source_kind=SOURCE_PATCHWISE, source_params=J.ravel(), nrhs=nrhs)
+
+
+def snake_order(npatch) -> List[int]:
+    """Patches of the grid in boustrophedon order: direction 0 fastest, its
+    sense reversed on every other row, the rows' sense reversed on every other
+    layer, so that consecutive patches always share a facet."""
+    P0, P1, P2 = npatch
+    out = []
+    for c in range(P2):
+        rows = range(P1) if c % 2 == 0 else range(P1 - 1, -1, -1)
+        for n, b in enumerate(rows):
+            fwd = (n + c * P1) % 2 == 0
+            cols = range(P0) if fwd else range(P0 - 1, -1, -1)
+            out.extend(a + P0 * (b + P1 * c) for a in cols)
+    return out
+
+
+def snake_partition(npatch, nsub: int) -> np.ndarray:
+    """nsub subdomains of consecutive patches in snake order with sizes that
+    differ by at most one; every subdomain is checked to be simply connected
+    (ValueError otherwise)."""
+    order = snake_order(npatch)
+    total = len(order)
+    if not 1 <= nsub <= total:
+        raise ValueError("nsub out of range")
+    sub = np.empty(total, np.int32)
+    bounds = [round(i * total / nsub) for i in range(nsub + 1)]
+    for k in range(nsub):
+        for q in order[bounds[k]:bounds[k + 1]]:
+            sub[q] = k
+    for k in range(nsub):
+        if not is_simply_connected_union(npatch, np.flatnonzero(sub == k)):
+            raise ValueError(f"snake subdomain {k} of {nsub} is not simply connected")
+    return sub
+
+
+def paper_cube(p: int, spans: int, nsub: int = 3, nrhs: int = 1, amps=None) -> Problem:
+    """The cube (0,3)^3 of 3 x 3 x 3 unit patches of Sec. 3 (Fig. of the
+    decomposition) with the manufactured field A_ana (SOURCE_TRIG, nu = 1):
+    ``spans`` knot spans per patch and direction (mesh size h = 1 / spans), and
+    ``nsub`` subdomains of consecutive patches in snake order (nsub = 3 gives
+    the three slabs of nine patches)."""
+    breaks = [np.linspace(0.0, 3.0, 4)] * 3
+    sp_ = [[spans] * 3 for _ in range(3)]
+    ctrl = box_control_net(p, sp_, breaks)
+    if amps is None:
+        amps = np.ones(nrhs)
+    return Problem(name=f"paper_cube_p{p}n{spans}_sub{nsub}", p=p, npatch=(3, 3, 3), nspan=sp_,
+                   periodic0=False, ctrl=ctrl, nu=np.ones(27),
+                   sub_of_patch=snake_partition((3, 3, 3), nsub), source_kind=SOURCE_TRIG,
+                   source_params=np.asarray(amps, np.float64), nrhs=nrhs, affine=True)
 
 
 def small_cases():
