@@ -61,7 +61,19 @@ typedef enum {
                                 params: one amplitude s per load case */
   IETI_SOURCE_FOURIER = 1,   /* J = sum_m Re(c_m exp(2 pi i k_m.x)); params per load case:
                                 nmodes, then per mode k(3), Re c(3), Im c(3) */
-  IETI_SOURCE_PATCHWISE = 2  /* J constant per patch; params: nrhs x npatch x 3 */
+  IETI_SOURCE_PATCHWISE = 2, /* J constant per patch; params: nrhs x npatch x 3 */
+  IETI_SOURCE_TRIG = 3       /* the manufactured problem of Sec. 3 scaled by s: J = s 3 A_ana with
+                                A_ana = (cos y cos z sin x, -2 cos x cos z sin y, cos x cos y sin z)
+                                (curl curl A_ana = 3 A_ana) and the non-homogeneous tangential
+                                Dirichlet data n x A = n x (s A_ana) on the boundary; params: one
+                                amplitude s per load case. Axis-aligned affine box patches only
+                                (affine = 1) and no periodic direction. The coefficients of the
+                                edges in the boundary faces are s times the boundary L2
+                                projection of the tangential trace of A_ana (computed once in
+                                ieti_create, on the host), the loads are lifted by them
+                                (j - K a_D, in ieti_assemble) and ieti_solve returns them in
+                                the Dirichlet entries of the field. The reference flux of
+                                ieti_eval_B is IETI_BREF_TRIG (exact for nu = 1). */
 } ieti_source_kind;
 
 /* Multipatch problem (Sec. 2): a structured P0 x P1 x P2 block grid of patches,
@@ -73,7 +85,9 @@ typedef enum {
  * direction 0 is periodic). Patch (a,b,c) has index a + P0 (b + P1 c).
  * Subdomains (Sec. 2) are the groups of sub_of_patch; each must be connected
  * and simply connected. The edge space has degree p-1 along an edge and p
- * across it; homogeneous tangential Dirichlet data n x A = 0 on the boundary. */
+ * across it; homogeneous tangential Dirichlet data n x A = 0 on the boundary
+ * except for IETI_SOURCE_TRIG, which brings its own data. The source
+ * parameters are checked against the kind and nrhs (INVALID_ARG if too few). */
 typedef struct {
   int degree;                  /* p >= 1 */
   int npatch[3];               /* P0, P1, P2 */
@@ -204,8 +218,9 @@ ieti_status ieti_apply_precond(ieti_ctx* ctx, const double* r_dev, double* z_dev
  * max(tol, 1e-3) on the first step and max(tol, 3e-3) on the corrections,
  * since a refinement step with FP32 operators cannot reduce the error by much
  * more than that anyway. lam0_dev: m_r x nrhs initial multipliers or
- * NULL for zero (INVALID_ARG if it holds NaN or infinite values). a_dev: nedge x nrhs output field (Dirichlet and tree DOFs are
- * zero). lam_dev: optional m_r x nrhs output of the final multipliers.
+ * NULL for zero (INVALID_ARG if it holds NaN or infinite values). a_dev: nedge x nrhs output field (tree DOFs
+ * are zero; Dirichlet DOFs are zero, or the boundary coefficients of
+ * IETI_SOURCE_TRIG). lam_dev: optional m_r x nrhs output of the final multipliers.
  * info: optional host struct. Synchronises the stream. Errors: STATE,
  * INVALID_ARG, NO_CONVERGENCE (info still filled, a_dev holds the last
  * iterate), TIMEOUT (a bounded wait of the triangular sweeps or of the
@@ -217,10 +232,12 @@ ieti_status ieti_solve(ieti_ctx* ctx, const double* lam0_dev, double tol, int ma
 /* Reference fields of ieti_eval_B. */
 typedef enum {
   IETI_BREF_NONE = 0,   /* no reference: only the norms of B */
-  IETI_BREF_SINE = 1    /* B_ref = s curl(sin pi y sin pi z, sin pi x sin pi z, sin pi x sin pi y)
+  IETI_BREF_SINE = 1,   /* B_ref = s curl(sin pi y sin pi z, sin pi x sin pi z, sin pi x sin pi y)
                            = s pi (sin pi x (cos pi y - cos pi z), sin pi y (cos pi z - cos pi x),
                            sin pi z (cos pi x - cos pi y)), one amplitude s per load case: the
                            exact flux of IETI_SOURCE_SINE with amplitude s when nu = 1 */
+  IETI_BREF_TRIG = 2    /* B_ref = s B_ana = s (-3 cos x sin y sin z, 0, 3 cos z sin x sin y) of
+                           Sec. 3: the exact flux of IETI_SOURCE_TRIG with amplitude s when nu = 1 */
 } ieti_bref_kind;
 
 /* Sec. 3: the magnetic flux density B = curl a and the error
@@ -262,6 +279,13 @@ ieti_status ieti_query(const ieti_ctx* ctx, ieti_sizes* out);
  * Writes min(count, cap) values to out_host and the count to *count. */
 ieti_status ieti_get_dofmap(const ieti_ctx* ctx, int which, int sub, int64_t* out_host,
                             int64_t cap, int64_t* count);
+
+/* IETI_SOURCE_TRIG: the boundary coefficients a_D of the unit-amplitude field
+ * (nedge FP64 values in the global edge numbering, zero off the Dirichlet
+ * faces; host copy, also on a host-only context). Writes min(nedge, cap)
+ * values to out_host and nedge to *count; *count = 0 for the other source
+ * kinds (homogeneous data). */
+ieti_status ieti_get_boundary_data(const ieti_ctx* ctx, double* out_host, int64_t cap, int64_t* count);
 
 /* Copies a dense FP64 block of subdomain `sub` to the host, column-major with
  * leading dimension `rows` as returned in *rows_out, *cols_out. which:

@@ -66,6 +66,31 @@ void compute_scaling(Ctx* c, std::vector<double>& scale) {
 // control point (i, j, k) of each patch at (x0 + L0 g_i, y0 + L1 g_j, z0 + L2 g_k)
 // with g the Greville abscissae of the patch's knot vectors (the only control
 // nets of an open uniform knot vector that give such a map)
+// the source parameters hold everything the kind reads for every load case
+std::string check_source(int kind, const std::vector<double>& src, int nrhs, int np) {
+  switch (kind) {
+    case IETI_SOURCE_SINE:
+    case IETI_SOURCE_TRIG:
+      return (int64_t)src.size() < nrhs ? "the source needs one amplitude per load case" : "";
+    case IETI_SOURCE_PATCHWISE:
+      return (int64_t)src.size() < (int64_t)nrhs * np * 3 ? "the patchwise source needs nrhs x npatch x 3 values"
+                                                           : "";
+    case IETI_SOURCE_FOURIER: {
+      size_t pos = 0;
+      for (int r = 0; r < nrhs; ++r) {
+        if (pos >= src.size()) return "the Fourier source parameters end before the last load case";
+        const double nm = src[pos];
+        if (!(nm >= 0 && nm <= 1e6) || nm != std::floor(nm)) return "bad number of Fourier modes";
+        pos += 1 + 9 * (size_t)nm;
+        if (pos > src.size()) return "the Fourier source parameters end before the last load case";
+      }
+      return "";
+    }
+    default:
+      return "unknown source kind";
+  }
+}
+
 bool nets_are_boxes(const Mesh& m, const std::vector<double>& ctrl, std::string& why) {
   if (m.per0) {
     why = "a periodic direction cannot be an affine box";
@@ -178,7 +203,22 @@ ieti_status build(Ctx* c, const ieti_problem_desc* desc, bool device) {
       return IETI_ERR_INVALID_ARG;
     }
   }
+  if (desc->n_source_params < 0 || (desc->n_source_params > 0 && !desc->source_params_host)) {
+    c->err = "bad source parameters";
+    return IETI_ERR_INVALID_ARG;
+  }
   c->src.assign(desc->source_params_host, desc->source_params_host + desc->n_source_params);
+  {
+    std::string why = check_source(c->source_kind, c->src, desc->nrhs, np);
+    if (!why.empty()) {
+      c->err = why;
+      return IETI_ERR_INVALID_ARG;
+    }
+  }
+  if (c->source_kind == IETI_SOURCE_TRIG && !c->affine) {
+    c->err = "IETI_SOURCE_TRIG needs axis-aligned affine box patches (affine = 1)";
+    return IETI_ERR_INVALID_ARG;
+  }
   if (c->src.empty()) c->src.push_back(0.0);
   for (int q = 0; q < np; ++q)
     if (c->sub_of_patch[q] < 0) {
@@ -299,6 +339,28 @@ ieti_status build(Ctx* c, const ieti_problem_desc* desc, bool device) {
         }
   }
   c->nelem = (int64_t)c->elem_host.size() / 4;
+  // ---- non-homogeneous Dirichlet data: boundary coefficients and the
+  // elements that touch a Dirichlet face (the only ones the lifting changes)
+  c->gD_host.clear();
+  c->belem_host.clear();
+  if (c->source_kind == IETI_SOURCE_TRIG) {
+    std::string why = boundary_projection_trig(m, c->tab, c->ctrl, c->gD_host);
+    if (!why.empty()) {
+      c->err = why;
+      return IETI_ERR_INVALID_ARG;
+    }
+    for (int64_t e = 0; e < c->nelem; ++e) {
+      int a[3];
+      m.patch_abc(c->elem_host[4 * e], a);
+      bool touch = false;
+      for (int d = 0; d < 3; ++d) {
+        const int s = c->elem_host[4 * e + 1 + d];
+        touch = touch || (a[d] == 0 && s == 0) || (a[d] == m.P[d] - 1 && s == m.nspan[d][a[d]] - 1);
+      }
+      if (touch) c->belem_host.push_back((int32_t)e);
+    }
+  }
+  c->nbelem = (int64_t)c->belem_host.size();
   // ---- coarse contributors (CSR by coarse DOF)
   std::vector<int64_t> pcsr_off(c->n_gp + 1, 0);
   for (int k = 0; k < c->nsub; ++k)
@@ -358,6 +420,10 @@ ieti_status build(Ctx* c, const ieti_problem_desc* desc, bool device) {
   TRY(upload(c, &c->d_patch_code_off, pc_off));
   TRY(upload(c, &c->d_sub_of_patch, c->sub_of_patch));
   TRY(upload(c, &c->d_elem, c->elem_host));
+  if (!c->gD_host.empty()) {
+    TRY(upload(c, &c->d_gD, c->gD_host));
+    TRY(upload(c, &c->d_belem, c->belem_host));
+  }
   {
     std::vector<int64_t> eoff(np + 1, 0);
     for (int q = 0; q < np; ++q) eoff[q + 1] = eoff[q] + m.nelem(q);
@@ -403,7 +469,7 @@ ieti_status build(Ctx* c, const ieti_problem_desc* desc, bool device) {
   c->S = Sb;
   c->W = Wb;
   TRY(dalloc(c, &c->jr, c->tot_rv * nr));
-  TRY(dalloc(c, &c->jp, c->tot_pv * nr));
+  TRY(dalloc(c, &c->jp, std::max<int64_t>(c->tot_pv, 1) * nr));
   int64_t wsz = std::max<int64_t>(c->tot_rv * std::max<int64_t>(nr, c->max_nP), wsz_ii);
   for (int i = 0; i < 3; ++i) {
     double* w;
@@ -506,7 +572,13 @@ ieti_status ieti_set_params(ieti_ctx* x, const double* nu, const double* src, in
     IETI_CUDA_TRY(c, cudaMemcpy(c->d_gq, c->gq_host.data(), sizeof(double) * c->gq_host.size(), cudaMemcpyHostToDevice));
   }
   if (src) {
-    if (nsrc > (int)c->allocs.size() * 0 + (int)c->src.size()) {
+    std::vector<double> v(src, src + std::max(nsrc, 0));
+    std::string why = nsrc < 0 ? std::string("bad source parameters") : check_source(c->source_kind, v, c->nrhs, np);
+    if (!why.empty()) {
+      c->err = why;
+      return IETI_ERR_INVALID_ARG;
+    }
+    if (nsrc > (int)c->src.size()) {
       // grow the device copy
       double* d;
       ieti_status r = dalloc(c, &d, nsrc);
@@ -637,7 +709,7 @@ ieti_status ieti_eval_B(ieti_ctx* x, const double* a, int nrhs, int ref_kind, co
     c->err = "context was created without a device";
     return IETI_ERR_STATE;
   }
-  if (!a || !nB2 || nrhs < 1 || nrhs > MAX_RHS || ref_kind < IETI_BREF_NONE || ref_kind > IETI_BREF_SINE ||
+  if (!a || !nB2 || nrhs < 1 || nrhs > MAX_RHS || ref_kind < IETI_BREF_NONE || ref_kind > IETI_BREF_TRIG ||
       (ref_kind != IETI_BREF_NONE && !amp)) {
     c->err = "ieti_eval_B: bad arguments";
     return IETI_ERR_INVALID_ARG;
@@ -707,6 +779,15 @@ ieti_status ieti_get_dofmap(const ieti_ctx* x, int which, int sub, int64_t* out,
   }
   *count = (int64_t)v.size();
   if (out) std::memcpy(out, v.data(), sizeof(int64_t) * std::min<int64_t>(cap, (int64_t)v.size()));
+  return IETI_OK;
+}
+
+ieti_status ieti_get_boundary_data(const ieti_ctx* x, double* out, int64_t cap, int64_t* count) {
+  if (!x || !count || cap < 0 || (cap > 0 && !out)) return IETI_ERR_INVALID_ARG;
+  const Ctx* c = &x->c;
+  const int64_t n = (int64_t)c->gD_host.size();
+  *count = n;
+  std::copy(c->gD_host.begin(), c->gD_host.begin() + std::min(n, cap), out);
   return IETI_OK;
 }
 

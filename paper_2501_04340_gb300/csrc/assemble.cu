@@ -126,6 +126,16 @@ __device__ inline void source_eval_r(const AsmParams& P, int q, int r, const dou
       a2 += cs * M[5] - sn * M[8];
     }
     J[0] = a0; J[1] = a1; J[2] = a2;
+  } else if (P.source_kind == IETI_SOURCE_TRIG) {
+    // 3 A_ana of Sec. 3 (curl curl A_ana = 3 A_ana), scaled by the amplitude
+    double sx, cx, sy, cy, sz, cz;
+    sincos(X[0], &sx, &cx);
+    sincos(X[1], &sy, &cy);
+    sincos(X[2], &sz, &cz);
+    const double sc = 3.0 * P.src[r];
+    J[0] = sc * cy * cz * sx;
+    J[1] = -2.0 * sc * cx * cz * sy;
+    J[2] = sc * cx * cy * sz;
   } else {
     const int np = P.P0 * P.P1 * P.P2;
     const double* v = P.src + ((size_t)r * np + q) * 3;
@@ -421,6 +431,105 @@ __global__ void __launch_bounds__(256) k_elem_j(AsmParams P) {
 }
 
 // ---------------------------------------------------------------------------
+// lifting of the loads by the boundary coefficients of non-homogeneous
+// Dirichlet data: j_i -= s_r sum_f K_if gD_f (Eq. (3) for the coefficients off
+// the Dirichlet faces), over the elements that touch a Dirichlet face
+// ---------------------------------------------------------------------------
+
+// the two nonzero components (into components c0i, c1i) of the reference curl
+// of element function f at the Gauss point (x, y, z)
+template <int PD>
+__device__ inline void ref_curl(const ElemShared<PD>& sh, int f, int x, int y, int z, double& c0, double& c1,
+                                int& c0i, int& c1i) {
+  constexpr int NFD = PD * (PD + 1) * (PD + 1);
+  const int d = f / NFD, r = f % NFD;
+  int ext[3] = {PD + 1, PD + 1, PD + 1};
+  ext[d] = PD;
+  const int la = r % ext[0], lb = (r / ext[0]) % ext[1], lc = r / (ext[0] * ext[1]);
+  c0i = d == 0 ? 1 : 0;
+  c1i = d == 2 ? 1 : 2;
+  if (d == 0) {        // D N N' , -D N' N   (components 1, 2)
+    c0 = sh.D[0][la][x] * sh.N[1][lb][y] * sh.dN[2][lc][z];
+    c1 = -sh.D[0][la][x] * sh.dN[1][lb][y] * sh.N[2][lc][z];
+  } else if (d == 1) { // -N D N' , N' D N   (components 0, 2)
+    c0 = -sh.N[0][la][x] * sh.D[1][lb][y] * sh.dN[2][lc][z];
+    c1 = sh.dN[0][la][x] * sh.D[1][lb][y] * sh.N[2][lc][z];
+  } else {             // N N' D , -N' N D   (components 0, 1)
+    c0 = sh.N[0][la][x] * sh.dN[1][lb][y] * sh.D[2][lc][z];
+    c1 = -sh.dN[0][la][x] * sh.N[1][lb][y] * sh.D[2][lc][z];
+  }
+}
+
+template <int PD>
+__global__ void __launch_bounds__(256) k_elem_lift(AsmParams P, const int32_t* __restrict__ belem,
+                                                   const double* __restrict__ gD) {
+  constexpr int NQ = PD + 1, NQ3 = NQ * NQ * NQ, NF = ElemShared<PD>::NF;
+  constexpr int NFD = PD * (PD + 1) * (PD + 1);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ElemShared<PD>& sh = *reinterpret_cast<ElemShared<PD>*>(smem_raw);
+  double* g = reinterpret_cast<double*>(smem_raw + sizeof(ElemShared<PD>));   // NF: boundary coefficients
+  double* ell = g + NF;                                                        // NF: (K_e gD)_f
+  double* v = ell + NF;                                                        // NQ3 x 3
+  const int e = belem[blockIdx.x];
+  int q, k;
+  elem_setup<PD>(P, e, sh, q, k);
+  const SubDev s = P.sd[k];
+  const int tid = threadIdx.x;
+  int a3[3];
+  patch_abc_d(P, q, a3);
+  const int st[3] = {P.start[0][a3[0]], P.start[1][a3[1]], P.start[2][a3[2]]};
+  const int sp[3] = {P.elem[4 * e + 1], P.elem[4 * e + 2], P.elem[4 * e + 3]};
+  for (int f = tid; f < NF; f += blockDim.x) {
+    const int d = f / NFD, r = f % NFD;
+    int ext[3] = {PD + 1, PD + 1, PD + 1};
+    ext[d] = PD;
+    const int64_t ix[3] = {st[0] + sp[0] + r % ext[0], st[1] + sp[1] + (r / ext[0]) % ext[1],
+                           st[2] + sp[2] + r / (ext[0] * ext[1])};
+    g[f] = gD[P.eoff[d] + ix[0] + P.eext[d][0] * (ix[1] + P.eext[d][1] * ix[2])];
+  }
+  __syncthreads();
+  const double nu = P.nu[q];
+  // v = nu w / |det DF| DF^T DF curl_hat(gD) at every Gauss point
+  for (int t = tid; t < NQ3; t += blockDim.x) {
+    const int x = t % NQ, y = (t / NQ) % NQ, z = t / (NQ * NQ);
+    double ch[3] = {0, 0, 0};
+    for (int f = 0; f < NF; ++f) {
+      if (g[f] == 0.0) continue;
+      double c0, c1;
+      int i0, i1;
+      ref_curl<PD>(sh, f, x, y, z, c0, c1, i0, i1);
+      ch[i0] += g[f] * c0;
+      ch[i1] += g[f] * c1;
+    }
+    const double* F = sh.DF[t];
+    double y3[3];
+    for (int r = 0; r < 3; ++r) y3[r] = F[r * 3 + 0] * ch[0] + F[r * 3 + 1] * ch[1] + F[r * 3 + 2] * ch[2];
+    const double fac = nu * sh.wt[t] / fabs(sh.det[t]);
+    for (int c = 0; c < 3; ++c) v[t * 3 + c] = fac * (F[0 * 3 + c] * y3[0] + F[1 * 3 + c] * y3[1] + F[2 * 3 + c] * y3[2]);
+  }
+  __syncthreads();
+  for (int f = tid; f < NF; f += blockDim.x) {
+    double acc = 0;
+    for (int qq = 0; qq < NQ3; ++qq) {
+      double c0, c1;
+      int i0, i1;
+      ref_curl<PD>(sh, f, qq % NQ, (qq / NQ) % NQ, qq / (NQ * NQ), c0, c1, i0, i1);
+      acc += c0 * v[qq * 3 + i0] + c1 * v[qq * 3 + i1];
+    }
+    ell[f] = acc;
+  }
+  __syncthreads();
+  for (int t = tid; t < NF * P.nrhs; t += blockDim.x) {
+    const int f = t / P.nrhs, r = t % P.nrhs;
+    const int cf = sh.code[f];
+    if (cf < 0) continue;
+    const double val = -P.src[r] * ell[f];
+    if (cf < s.n) atomicAdd(P.jr + RV(s, cf, r, P.nrhs), val);
+    else atomicAdd(P.jp + PV(s, cf - s.n, r, P.nrhs), val);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // K: Kronecker generation of every dense entry (axis-aligned affine patches)
 // ---------------------------------------------------------------------------
 
@@ -623,8 +732,13 @@ static ieti_status launch_elem(Ctx* c, const AsmParams& P, bool do_K, cudaStream
                 sizeof(double2) * (size_t)NQ3 * 3 * (FT_KMAX + 1);
   cudaEvent_t p0 = prof_begin(c, st);
   k_elem_j<PD><<<(unsigned)c->nelem, 256, smem, st>>>(P);
-  prof_end(c, PROF_ASM_J, p0, st);
   IETI_LAUNCH_CHECK(c);
+  if (c->d_gD && c->nbelem > 0) {
+    const size_t lsm = sizeof(ElemShared<PD>) + sizeof(double) * (2 * (size_t)NF + 3 * (size_t)NQ3);
+    k_elem_lift<PD><<<(unsigned)c->nbelem, 256, lsm, st>>>(P, c->d_belem, c->d_gD);
+    IETI_LAUNCH_CHECK(c);
+  }
+  prof_end(c, PROF_ASM_J, p0, st);
   return IETI_OK;
 }
 
@@ -719,6 +833,17 @@ __device__ inline void sine_flux(const double X[3], double amp, double B[3]) {
   B[2] = amp * pi * sz * (cx - cy);
 }
 
+// reference flux density amp B_ana = amp curl A_ana of Sec. 3
+__device__ inline void trig_flux(const double X[3], double amp, double B[3]) {
+  double sx, cx, sy, cy, sz, cz;
+  sincos(X[0], &sx, &cx);
+  sincos(X[1], &sy, &cy);
+  sincos(X[2], &sz, &cz);
+  B[0] = -3.0 * amp * cx * sy * sz;
+  B[1] = 0.0;
+  B[2] = 3.0 * amp * cz * sx * sy;
+}
+
 // one CTA per element: the field's coefficients of the element functions, the
 // reference curls of those functions at the Gauss points (two nonzero
 // components each), B = DF curl_hat / det DF, and the element integrals
@@ -796,9 +921,10 @@ __global__ void __launch_bounds__(256) k_elem_B(AsmParams P, FluxArgs F) {
       const double w = sh.wt[qq] * fabs(det);
       acc[(qq * FLUX_CG + col) * 2 + 0] = w * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
       double e2 = 0;
-      if (F.ref_kind == IETI_BREF_SINE) {
+      if (F.ref_kind != IETI_BREF_NONE) {
         double R[3];
-        sine_flux(sh.X[qq], F.amp[c0 + col], R);
+        if (F.ref_kind == IETI_BREF_SINE) sine_flux(sh.X[qq], F.amp[c0 + col], R);
+        else trig_flux(sh.X[qq], F.amp[c0 + col], R);
         e2 = w * ((R[0] - B[0]) * (R[0] - B[0]) + (R[1] - B[1]) * (R[1] - B[1]) + (R[2] - B[2]) * (R[2] - B[2]));
       }
       acc[(qq * FLUX_CG + col) * 2 + 1] = e2;

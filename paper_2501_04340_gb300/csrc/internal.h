@@ -139,6 +139,8 @@ struct Ctx {
   std::vector<SubDev> sd_host;
   std::vector<double> gq_host;           // per patch: nu * L_c^2 / vol (affine path)
   std::vector<int> elem_host;            // per element: q, s0, s1, s2
+  std::vector<double> gD_host;           // IETI_SOURCE_TRIG: boundary coefficients (nedge)
+  std::vector<int32_t> belem_host;       // elements with a facet in a Dirichlet face
   int64_t nelem = 0;
   double* d_geo = nullptr;               // per element and Gauss point: X, weight |det DF| DF^-1 (assembly)
   bool geo_ready = false, geo_failed = false;
@@ -162,6 +164,9 @@ struct Ctx {
   int64_t* d_patch_code_off = nullptr;
   int32_t* d_sub_of_patch = nullptr;
   int32_t* d_elem = nullptr;
+  double* d_gD = nullptr;                // IETI_SOURCE_TRIG: boundary coefficients of A_ana (nedge), else null
+  int32_t* d_belem = nullptr;            // elements with a facet in a Dirichlet face (lifting of the loads)
+  int64_t nbelem = 0;
   double* d_tabN[3] = {nullptr, nullptr, nullptr};
   double* d_tabdN[3] = {nullptr, nullptr, nullptr};
   double* d_tabD[3] = {nullptr, nullptr, nullptr};

@@ -688,4 +688,167 @@ void update_nu(const Mesh& m, const std::vector<int>& sub_of_patch, const std::v
   (void)sub_of_patch;
 }
 
+// ---------------------------------------------------------------------------
+// non-homogeneous tangential Dirichlet data (Sec. 2 boundary condition with
+// the data of the manufactured field of Sec. 3)
+// ---------------------------------------------------------------------------
+
+static void trig_field(const double X[3], double A[3]) {
+  const double cx = std::cos(X[0]), cy = std::cos(X[1]), cz = std::cos(X[2]);
+  const double sx = std::sin(X[0]), sy = std::sin(X[1]), sz = std::sin(X[2]);
+  A[0] = cy * cz * sx;
+  A[1] = -2.0 * cx * cz * sy;
+  A[2] = cx * cy * sz;
+}
+
+// On a face normal to axis n of an affine box patch (DF = diag(L)), the edge
+// function of direction d != n whose index along n is the boundary index has
+// the single tangential component D_i(xi_d) N_j(xi_e) / L_d (covariant map;
+// the factor along n is 1 there), and every other edge function has a zero
+// tangential trace. The face mass matrix of these traces and the moments of
+// the trace of A_ana use the assembly's Gauss rule (p + 1 points per span);
+// the system over all Dirichlet edges is solved by conjugate gradients with
+// the diagonal as preconditioner (the mass matrix is well conditioned).
+std::string boundary_projection_trig(const Mesh& m, const Tables1D& t, const std::vector<double>& ctrl,
+                                     std::vector<double>& gD) {
+  if (m.per0) return "the boundary data needs a box domain without a periodic direction";
+  const int p = m.p, nq = t.nq;
+  std::vector<int64_t> cidx((size_t)m.nedge, -1);
+  std::vector<int64_t> ids;
+  for (int64_t e = 0; e < m.nedge; ++e)
+    if (m.edge_dirichlet(e)) {
+      cidx[(size_t)e] = (int64_t)ids.size();
+      ids.push_back(e);
+    }
+  const int64_t nb = (int64_t)ids.size();
+  gD.assign((size_t)m.nedge, 0.0);
+  if (nb == 0) return "";
+  std::vector<std::tuple<int64_t, int64_t, double>> trip;
+  std::vector<double> rhs((size_t)nb, 0.0);
+  auto cp = [&](int i, int j, int k, int r) {
+    return ctrl[(((size_t)k * m.N[1] + j) * m.N[0] + i) * 4 + r];
+  };
+  for (int q = 0; q < m.npatch(); ++q) {
+    int a[3], st[3], n[3];
+    m.patch_abc(q, a);
+    for (int d = 0; d < 3; ++d) {
+      st[d] = m.start[d][a[d]];
+      n[d] = m.nspan[d][a[d]];
+    }
+    const double lo[3] = {cp(st[0], st[1], st[2], 0), cp(st[0], st[1], st[2], 1), cp(st[0], st[1], st[2], 2)};
+    const double L[3] = {cp(st[0] + n[0] + p - 1, st[1], st[2], 0) - lo[0],
+                         cp(st[0], st[1] + n[1] + p - 1, st[2], 1) - lo[1],
+                         cp(st[0], st[1], st[2] + n[2] + p - 1, 2) - lo[2]};
+    for (int ax = 0; ax < 3; ++ax)
+      for (int side = 0; side < 2; ++side) {
+        if (a[ax] != (side == 0 ? 0 : m.P[ax] - 1)) continue;
+        const int bidx = side == 0 ? 0 : m.N[ax] - 1;
+        const double xn = lo[ax] + (side == 0 ? 0.0 : L[ax]);
+        for (int d = 0; d < 3; ++d) {
+          if (d == ax) continue;
+          const int e = 3 - ax - d;
+          const int nloc = p * (p + 1);
+          std::vector<int64_t> loc(nloc);
+          std::vector<double> T((size_t)nloc * nq * nq), gq((size_t)nq * nq), wq((size_t)nq * nq);
+          for (int sd = 0; sd < n[d]; ++sd)
+            for (int se = 0; se < n[e]; ++se) {
+              const int gd = m.spanoff[d][a[d]] + sd, ge = m.spanoff[e][a[e]] + se;
+              for (int x = 0; x < nq; ++x)
+                for (int y = 0; y < nq; ++y) {
+                  double X[3];
+                  X[ax] = xn;
+                  X[d] = lo[d] + L[d] * (sd + t.xq[x]) / n[d];
+                  X[e] = lo[e] + L[e] * (se + t.xq[y]) / n[e];
+                  double A[3];
+                  trig_field(X, A);
+                  gq[(size_t)x * nq + y] = A[d];
+                  wq[(size_t)x * nq + y] = t.wq[x] * t.wq[y] * (L[d] / n[d]) * (L[e] / n[e]);
+                }
+              for (int i = 0; i < p; ++i)
+                for (int j = 0; j <= p; ++j) {
+                  const int l = i * (p + 1) + j;
+                  int c[3];
+                  c[ax] = bidx;
+                  c[d] = st[d] + sd + i;
+                  c[e] = st[e] + se + j;
+                  loc[l] = cidx[(size_t)m.edge_id(d, c[0], c[1], c[2])];
+                  for (int x = 0; x < nq; ++x)
+                    for (int y = 0; y < nq; ++y)
+                      T[((size_t)l * nq + x) * nq + y] =
+                          t.D[d][((size_t)gd * p + i) * nq + x] * t.N[e][((size_t)ge * (p + 1) + j) * nq + y] / L[d];
+                }
+              for (int l = 0; l < nloc; ++l) {
+                if (loc[l] < 0) return "a boundary edge is not a Dirichlet edge";
+                double f = 0;
+                for (int u = 0; u < nq * nq; ++u) f += T[(size_t)l * nq * nq + u] * wq[u] * gq[u];
+                rhs[(size_t)loc[l]] += f;
+                for (int l2 = 0; l2 < nloc; ++l2) {
+                  double v = 0;
+                  for (int u = 0; u < nq * nq; ++u)
+                    v += T[(size_t)l * nq * nq + u] * wq[u] * T[(size_t)l2 * nq * nq + u];
+                  trip.emplace_back(loc[l], loc[l2], v);
+                }
+              }
+            }
+        }
+      }
+  }
+  // CSR of the boundary mass matrix (duplicates summed)
+  std::sort(trip.begin(), trip.end());
+  std::vector<int64_t> rp((size_t)nb + 1, 0), ci;
+  std::vector<double> va;
+  for (size_t u = 0; u < trip.size();) {
+    const int64_t r = std::get<0>(trip[u]), c = std::get<1>(trip[u]);
+    double v = 0;
+    while (u < trip.size() && std::get<0>(trip[u]) == r && std::get<1>(trip[u]) == c) v += std::get<2>(trip[u++]);
+    ci.push_back(c);
+    va.push_back(v);
+    rp[(size_t)r + 1] = (int64_t)ci.size();
+  }
+  for (int64_t r = 0; r < nb; ++r) rp[(size_t)r + 1] = std::max(rp[(size_t)r + 1], rp[(size_t)r]);
+  std::vector<double> dg((size_t)nb, 0.0);
+  for (int64_t r = 0; r < nb; ++r)
+    for (int64_t u = rp[(size_t)r]; u < rp[(size_t)r + 1]; ++u)
+      if (ci[(size_t)u] == r) dg[(size_t)r] = va[(size_t)u];
+  for (double v : dg)
+    if (!(v > 0)) return "the boundary mass matrix has a non-positive diagonal";
+  auto mv = [&](const std::vector<double>& x, std::vector<double>& y) {
+    for (int64_t r = 0; r < nb; ++r) {
+      double s = 0;
+      for (int64_t u = rp[(size_t)r]; u < rp[(size_t)r + 1]; ++u) s += va[(size_t)u] * x[(size_t)ci[(size_t)u]];
+      y[(size_t)r] = s;
+    }
+  };
+  std::vector<double> x((size_t)nb, 0.0), r = rhs, z((size_t)nb), pv((size_t)nb), Ap((size_t)nb);
+  auto dot = [&](const std::vector<double>& u, const std::vector<double>& v) {
+    double s = 0;
+    for (int64_t i = 0; i < nb; ++i) s += u[(size_t)i] * v[(size_t)i];
+    return s;
+  };
+  const double r0 = std::sqrt(dot(r, r));
+  for (int64_t i = 0; i < nb; ++i) z[(size_t)i] = r[(size_t)i] / dg[(size_t)i];
+  pv = z;
+  double rz = dot(r, z);
+  bool ok = r0 == 0;
+  for (int it = 0; it < 20000 && !ok; ++it) {
+    mv(pv, Ap);
+    const double al = rz / dot(pv, Ap);
+    for (int64_t i = 0; i < nb; ++i) {
+      x[(size_t)i] += al * pv[(size_t)i];
+      r[(size_t)i] -= al * Ap[(size_t)i];
+    }
+    if (std::sqrt(dot(r, r)) <= 1e-13 * r0) {
+      ok = true;
+      break;
+    }
+    for (int64_t i = 0; i < nb; ++i) z[(size_t)i] = r[(size_t)i] / dg[(size_t)i];
+    const double rz2 = dot(r, z);
+    for (int64_t i = 0; i < nb; ++i) pv[(size_t)i] = z[(size_t)i] + rz2 / rz * pv[(size_t)i];
+    rz = rz2;
+  }
+  if (!ok) return "the boundary projection did not converge";
+  for (int64_t i = 0; i < nb; ++i) gD[(size_t)ids[(size_t)i]] = x[(size_t)i];
+  return "";
+}
+
 }  // namespace ieti

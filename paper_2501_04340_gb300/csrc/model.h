@@ -89,4 +89,12 @@ std::string build_topology(const Mesh& m, const std::vector<int>& sub_of_patch,
 void update_nu(const Mesh& m, const std::vector<int>& sub_of_patch, const std::vector<double>& nu,
                Topology& topo);
 
+// Coefficients (nedge, zero off the Dirichlet faces) of the boundary L2
+// projection of the tangential trace of the manufactured field A_ana of Sec. 3
+// onto the traces of the edge functions, over all Dirichlet faces at once.
+// Axis-aligned affine box patches only (the control net is checked by the
+// caller). Returns an empty string, else an error message.
+std::string boundary_projection_trig(const Mesh& m, const Tables1D& t, const std::vector<double>& ctrl,
+                                     std::vector<double>& gD);
+
 }  // namespace ieti

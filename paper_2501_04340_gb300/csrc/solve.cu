@@ -1108,6 +1108,18 @@ static ieti_status step_graph(Ctx* c, bool fresh, bool refine, double* b, double
   return IETI_OK;
 }
 
+// a[e, col] = s_col gD[e] on the edges with boundary data (column col of the
+// grid's y dimension; s_col the load case's amplitude)
+__global__ void k_set_boundary(const double* __restrict__ gD, const double* __restrict__ amp, int64_t nedge,
+                               double* __restrict__ a) {
+  const int col = blockIdx.y;
+  const double s = amp[col];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nedge; e += (int64_t)gridDim.x * blockDim.x) {
+    const double g = gD[e];
+    if (g != 0.0) a[e + nedge * col] = s * g;
+  }
+}
+
 ieti_status solve_all(Ctx* c, const double* lam0, double tol, int maxit, double tol_field, double* a,
                       double* lam_out, ieti_solve_info* info, cudaStream_t st) {
   const int nrhs = c->nrhs;
@@ -1235,6 +1247,11 @@ ieti_status solve_all(Ctx* c, const double* lam0, double tol, int maxit, double 
     grel_prev = grel;
   }
   if (refine && grel > tol_field) conv = false;
+  if (c->d_gD) {
+    // non-homogeneous Dirichlet data: the boundary coefficients of the field
+    k_set_boundary<<<dim3(256, nrhs), 256, 0, st>>>(c->d_gD, c->d_src, ne, a);
+    IETI_LAUNCH_CHECK(c);
+  }
   if (lam_out)
     IETI_CUDA_TRY(c, cudaMemcpyAsync(lam_out, c->wlam_acc, sizeof(double) * m * nrhs, cudaMemcpyDeviceToDevice, st));
   IETI_CUDA_TRY(c, cudaMemcpyAsync(c->h_err + 1, c->d_dep_err, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -73,6 +73,7 @@ _sig = {
     "ieti_get_block": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(C.c_double), C.c_int64,
                                  C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "ieti_get_coarse": (C.c_int, [_vp, C.POINTER(C.c_double), C.c_int64]),
+    "ieti_get_boundary_data": (C.c_int, [_vp, C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_int64)]),
     "ieti_interface_rhs": (C.c_int, [_vp, _vp, _vp]),
     "ieti_launch_count": (C.c_int64, [_vp]),
     "ieti_debug_set": (C.c_int, [_vp, C.c_int, C.c_int64]),
@@ -216,6 +217,7 @@ def ieti_interface_rhs(ctx, b, stream=None):
 
 IETI_BREF_NONE = 0
 IETI_BREF_SINE = 1
+IETI_BREF_TRIG = 2
 
 
 def ieti_eval_B(ctx, a, npatch, nrhs=None, ref_kind=IETI_BREF_NONE, ref_amp=None, B=None, stream=None):
@@ -256,6 +258,16 @@ def ieti_get_block(ctx, which, sub):
     _check(ctx, _lib.ieti_get_block(ctx, which, sub, out.ctypes.data_as(C.POINTER(C.c_double)), len(out),
                                     C.byref(R), C.byref(Cc)))
     return out.reshape(Cc.value, R.value).T
+
+
+def ieti_get_boundary_data(ctx):
+    """Boundary coefficients of IETI_SOURCE_TRIG (nedge values), or an empty array."""
+    n = C.c_int64()
+    _check(ctx, _lib.ieti_get_boundary_data(ctx, None, 0, C.byref(n)))
+    out = np.zeros(n.value, np.float64)
+    _check(ctx, _lib.ieti_get_boundary_data(ctx, out.ctypes.data_as(C.POINTER(C.c_double)), n.value,
+                                            C.byref(n)))
+    return out
 
 
 def ieti_get_coarse(ctx, n_gp):

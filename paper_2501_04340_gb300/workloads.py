@@ -520,20 +520,39 @@ def snake_partition(npatch, nsub: int) -> np.ndarray:
     return sub
 
 
-def paper_cube(p: int, spans: int, nsub: int = 3, nrhs: int = 1, amps=None) -> Problem:
+def three_columns_partition() -> np.ndarray:
+    """Three subdomains of nine patches on the 3 x 3 x 3 grid: the slab a = 0
+    and two L-shaped columns, {(1,0), (2,0), (2,1)} and {(1,1), (1,2), (2,2)} in
+    (a, b) over all c. The three meet along one interior line of patch edges
+    (x = 1, y = 1), whose edges are the cross-edges of the layout."""
+    sub = np.empty(27, np.int32)
+    col1 = {(1, 0), (2, 0), (2, 1)}
+    for c in range(3):
+        for b in range(3):
+            for a in range(3):
+                sub[a + 3 * (b + 3 * c)] = 0 if a == 0 else (1 if (a, b) in col1 else 2)
+    return sub
+
+
+def paper_cube(p: int, spans: int, nsub: int = 3, nrhs: int = 1, amps=None, layout: str = "columns") -> Problem:
     """The cube (0,3)^3 of 3 x 3 x 3 unit patches of Sec. 3 (Fig. of the
     decomposition) with the manufactured field A_ana (SOURCE_TRIG, nu = 1):
-    ``spans`` knot spans per patch and direction (mesh size h = 1 / spans), and
-    ``nsub`` subdomains of consecutive patches in snake order (nsub = 3 gives
-    the three slabs of nine patches)."""
+    ``spans`` knot spans per patch and direction (mesh size h = 1 / spans).
+    Subdomains: with layout "columns" and nsub = 3 the three columns of
+    three_columns_partition; otherwise (layout "snake") ``nsub`` subdomains of
+    consecutive patches in snake order (nsub = 3 gives three slabs)."""
     breaks = [np.linspace(0.0, 3.0, 4)] * 3
     sp_ = [[spans] * 3 for _ in range(3)]
     ctrl = box_control_net(p, sp_, breaks)
     if amps is None:
         amps = np.ones(nrhs)
-    return Problem(name=f"paper_cube_p{p}n{spans}_sub{nsub}", p=p, npatch=(3, 3, 3), nspan=sp_,
-                   periodic0=False, ctrl=ctrl, nu=np.ones(27),
-                   sub_of_patch=snake_partition((3, 3, 3), nsub), source_kind=SOURCE_TRIG,
+    if layout not in ("columns", "snake"):
+        raise ValueError("layout is 'columns' or 'snake'")
+    cols = layout == "columns" and nsub == 3
+    sub = three_columns_partition() if cols else snake_partition((3, 3, 3), nsub)
+    return Problem(name=f"paper_cube_p{p}n{spans}_{'columns' if cols else 'snake'}{nsub}", p=p, npatch=(3, 3, 3),
+                   nspan=sp_, periodic0=False, ctrl=ctrl, nu=np.ones(27),
+                   sub_of_patch=sub, source_kind=SOURCE_TRIG,
                    source_params=np.asarray(amps, np.float64), nrhs=nrhs, affine=True)
 
 

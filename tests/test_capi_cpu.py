@@ -1,6 +1,7 @@
 """C-ABI library: loads without a GPU, exports every declared entry point, and its
 host-side gauge (Sec. 2.2) and DOF classes equal the oracle's."""
 import ctypes
+import dataclasses
 import os
 
 import numpy as np
@@ -158,3 +159,42 @@ def test_affine_flag_is_checked():
     ring.affine = True
     with pytest.raises(ieti.IetiError, match="INVALID_ARG"):
         ieti.ieti_create_host(ring)
+
+
+@pytest.mark.parametrize("p,spans,nsub", [(1, 2, 3), (2, 1, 5), (3, 1, 2)])
+def test_host_boundary_data_equals_oracle(p, spans, nsub):
+    """The library's boundary L2 projection of the tangential trace of A_ana
+    (IETI_SOURCE_TRIG, computed on the host in ieti_create) equals the oracle's."""
+    from oracle import boundary as bd, discretise as dz
+    prob = wl.paper_cube(p, spans, nsub=nsub)
+    mesh = dz.build_mesh(prob)
+    want = bd.boundary_projection(prob, mesh, bd.manufactured_A)
+    ctx = ieti.ieti_create_host(prob)
+    try:
+        got = ieti.ieti_get_boundary_data(ctx)
+    finally:
+        ieti.ieti_destroy(ctx)
+    assert got.shape == want.shape
+    assert np.array_equal(got != 0, want != 0)
+    assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
+
+
+def test_homogeneous_kinds_have_no_boundary_data():
+    ctx = ieti.ieti_create_host(wl.cube8_p2n4(spans=1))
+    try:
+        assert ieti.ieti_get_boundary_data(ctx).size == 0
+    finally:
+        ieti.ieti_destroy(ctx)
+
+
+def test_rejects_source_parameters_that_do_not_fit_the_kind():
+    base = wl.cube8_p2n4(spans=1)
+    bad = [base.with_params(source_params=[1.0], nrhs=2),                      # sine: 2 amplitudes needed
+           dataclasses.replace(base, source_kind=wl.SOURCE_PATCHWISE, source_params=np.zeros(3 * 8 - 1)),
+           dataclasses.replace(base, source_kind=wl.SOURCE_FOURIER, source_params=np.array([2.0] + [0.0] * 9)),
+           dataclasses.replace(base, source_kind=7),
+           # the manufactured Dirichlet data needs affine boxes
+           dataclasses.replace(wl.paper_cube(1, 1), affine=False)]
+    for prob in bad:
+        with pytest.raises(ieti.IetiError, match="INVALID_ARG"):
+            ieti.ieti_create_host(prob)
