@@ -333,13 +333,18 @@ int64_t ieti_launch_count(const ieti_ctx* ctx);
  *                           products keep their defaults (no timing of
  *                           candidates at the first factorisation of each
  *                           precision).
+ *   IETI_DEBUG_SYRK_RESERVE SMs that the overlapped FP32 trailing update leaves
+ *                           to the panel kernels of the next step (value 0 ..
+ *                           SM count - 1; < 0 restores the default 24). Changes
+ *                           only the time of ieti_factor.
  * Errors: INVALID_ARG (unknown setting, subdomain out of range), STATE. */
 enum {
   IETI_DEBUG_WAIT_POLLS = 1,
   IETI_DEBUG_PIVOT_FAULT = 2,
   IETI_DEBUG_FP64_FALLBACK = 3,
   IETI_DEBUG_SYRK_TC = 4,
-  IETI_DEBUG_NO_AUTOTUNE = 5
+  IETI_DEBUG_NO_AUTOTUNE = 5,
+  IETI_DEBUG_SYRK_RESERVE = 6
 };
 ieti_status ieti_debug_set(ieti_ctx* ctx, int what, int64_t value);
 

@@ -905,6 +905,13 @@ ieti_status ieti_debug_set(ieti_ctx* x, int what, int64_t value) {
     case IETI_DEBUG_NO_AUTOTUNE:
       c->autotune = value == 0;
       return IETI_OK;
+    case IETI_DEBUG_SYRK_RESERVE:
+      if (value >= std::max(c->sm_count, 1)) {
+        c->err = "ieti_debug_set: reserve must be below the SM count";
+        return IETI_ERR_INVALID_ARG;
+      }
+      c->syrk_reserve = value < 0 ? 24 : (int)value;
+      return IETI_OK;
     default:
       c->err = "ieti_debug_set: unknown setting";
       return IETI_ERR_INVALID_ARG;

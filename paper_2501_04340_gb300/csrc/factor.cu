@@ -228,34 +228,17 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool vali
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(src), "r"(bytes) : "memory");
 }
 
-__global__ void __launch_bounds__(256, 2) k_syrk2(const SubDev* sd, float* L, int b, int kb, int col_only,
-                                                 const int4* items) {
-  // items: (subdomain, R, C) of the pair tiles to update, else all of them
-  const int k = items ? items[blockIdx.x].x : (int)blockIdx.y;
-  const SubDev s = sd[k];
+// one pair tile (R, C) of subdomain s (pairs counted from b+kb); returns with
+// the block-uniform early exits before its first barrier
+__device__ __forceinline__ void syrk2_tile(const SubDev& s, float* L, int b, int kb, int col_only, int R, int C,
+                                           float* s2) {
   const int t0 = b + kb;          // first trailing block
   const int Tk = s.nblk - t0;
   if (Tk <= 0) return;
   const int Tt = (Tk + 1) / 2;   // block pairs
-  int R, C;
-  if (items) {
-    R = items[blockIdx.x].y;
-    C = items[blockIdx.x].z;
-  } else if (col_only) {
-    R = blockIdx.x;
-    C = 0;
-  } else {
-    // triangular decode of the pair-tile index: R >= C
-    const int t = blockIdx.x;
-    R = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-    while (R * (R + 1) / 2 > t) --R;
-    while ((R + 1) * (R + 2) / 2 <= t) ++R;
-    C = t - R * (R + 1) / 2;
-  }
   if (R >= Tt) return;
   const int r0 = t0 + 2 * R, c0 = t0 + 2 * C;
   const int nr = min(2, s.nblk - r0), nc = col_only ? 1 : min(2, s.nblk - c0);   // blocks present (1 or 2)
-  extern __shared__ __align__(16) float s2[];
   float(*Pr)[S2_LDS] = reinterpret_cast<float(*)[S2_LDS]>(s2);
   float(*Pc)[S2_LDS] = reinterpret_cast<float(*)[S2_LDS]>(s2 + NB * S2_LDS);
   const int tid = threadIdx.x;
@@ -315,6 +298,35 @@ __global__ void __launch_bounds__(256, 2) k_syrk2(const SubDev* sd, float* L, in
     o[0] = a;
     o[1] = c;
   }
+}
+
+// items: (subdomain, R, C) of the nitems pair tiles to update, each CTA taking
+// every gridDim.x-th (a grid smaller than nitems leaves SMs to other kernels);
+// without items every pair tile, one per CTA (subdomain blockIdx.y)
+__global__ void __launch_bounds__(256, 2) k_syrk2(const SubDev* sd, float* L, int b, int kb, int col_only,
+                                                 const int4* items, int nitems) {
+  extern __shared__ __align__(16) float s2[];
+  if (items) {
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+      if (it != (int)blockIdx.x) __syncthreads();   // the previous tile's shared panels are no longer read
+      const int4 w = items[it];
+      syrk2_tile(sd[w.x], L, b, kb, col_only, w.y, w.z, s2);
+    }
+    return;
+  }
+  int R, C;
+  if (col_only) {
+    R = blockIdx.x;
+    C = 0;
+  } else {
+    // triangular decode of the pair-tile index: R >= C
+    const int t = blockIdx.x;
+    R = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    while (R * (R + 1) / 2 > t) --R;
+    while ((R + 1) * (R + 2) / 2 <= t) ++R;
+    C = t - R * (R + 1) / 2;
+  }
+  syrk2_tile(sd[blockIdx.y], L, b, kb, col_only, R, C, s2);
 }
 
 // S_rIrI snapshot: symmetrised copy of the lower trailing block at the r_I panel
@@ -763,10 +775,11 @@ static ieti_status cholesky(Ctx* c, const SubDev* d_sd, const std::vector<SubDev
         cudaEvent_t p0 = prof_begin(c, st);
         if (plan) {
           if (stp.col_cnt > 0)
-            k_syrk2<<<stp.col_cnt, 256, S2_SMEM, st>>>(d_sd, (float*)L, b, 1, 1, plan->d_items + stp.col_off);
+            k_syrk2<<<stp.col_cnt, 256, S2_SMEM, st>>>(d_sd, (float*)L, b, 1, 1, plan->d_items + stp.col_off,
+                                                         stp.col_cnt);
         } else {
           const int Tp1 = (max_nblk - b - 1 + 1) / 2;
-          k_syrk2<<<dim3(Tp1, nsub), 256, S2_SMEM, st>>>(d_sd, (float*)L, b, 1, 1, nullptr);
+          k_syrk2<<<dim3(Tp1, nsub), 256, S2_SMEM, st>>>(d_sd, (float*)L, b, 1, 1, nullptr, 0);
         }
         prof_end(c, PROF_SYRK, p0, st);
         IETI_LAUNCH_CHECK(c);
@@ -781,7 +794,7 @@ static ieti_status cholesky(Ctx* c, const SubDev* d_sd, const std::vector<SubDev
       const int n0 = stp.trail_cnt0, n1 = stp.trail_cnt - stp.trail_cnt0;
       cudaEvent_t p0 = prof_begin(c, st);
       if (n0 > 0) {
-        if constexpr (sizeof(T) == 4) k_syrk2<<<n0, 256, S2_SMEM, st>>>(d_sd, (float*)L, b, kb, 0, items);
+        if constexpr (sizeof(T) == 4) k_syrk2<<<n0, 256, S2_SMEM, st>>>(d_sd, (float*)L, b, kb, 0, items, n0);
         else k_syrk<T><<<n0, 256, 0, st>>>(d_sd, L, b, items);
         IETI_LAUNCH_CHECK(c);
       }
@@ -790,8 +803,12 @@ static ieti_status cholesky(Ctx* c, const SubDev* d_sd, const std::vector<SubDev
         IETI_CUDA_TRY(c, cudaEventRecord(c->ev_fact[0], st));
         IETI_CUDA_TRY(c, cudaStreamWaitEvent(c->aux_stream, c->ev_fact[0], 0));
         cudaEvent_t p1 = prof_begin(c, c->aux_stream);
+        // the overlapped rest runs on a grid that leaves SMs free for the
+        // next panels' kernels: at two CTAs per SM this kernel holds the whole
+        // register file of an SM, so a full grid keeps them waiting for SMs
         if constexpr (sizeof(T) == 4)
-          k_syrk2<<<n1, 256, S2_SMEM, c->aux_stream>>>(d_sd, (float*)L, b, kb, 0, items + n0);
+          k_syrk2<<<std::min(n1, 2 * std::max(1, c->sm_count - c->syrk_reserve)), 256, S2_SMEM, c->aux_stream>>>(
+              d_sd, (float*)L, b, kb, 0, items + n0, n1);
         else k_syrk<T><<<n1, 256, 0, c->aux_stream>>>(d_sd, L, b, items + n0);
         prof_end(c, PROF_SYRK, p1, c->aux_stream);
         IETI_LAUNCH_CHECK(c);
@@ -809,10 +826,10 @@ static ieti_status cholesky(Ctx* c, const SubDev* d_sd, const std::vector<SubDev
           ieti_status r2 = syrk_tc(c, d_sd, (float*)L, b, max_nblk, nsub, st);
           if (r2 != IETI_OK) return r2;
         } else if (plan) {
-          k_syrk2<<<stp.trail_cnt, 256, S2_SMEM, st>>>(d_sd, (float*)L, b, kb, 0, items);
+          k_syrk2<<<stp.trail_cnt, 256, S2_SMEM, st>>>(d_sd, (float*)L, b, kb, 0, items, stp.trail_cnt);
         } else {
           const int Tp = (Tm + 1) / 2;   // block pairs
-          k_syrk2<<<dim3(Tp * (Tp + 1) / 2, nsub), 256, S2_SMEM, st>>>(d_sd, (float*)L, b, kb, 0, nullptr);
+          k_syrk2<<<dim3(Tp * (Tp + 1) / 2, nsub), 256, S2_SMEM, st>>>(d_sd, (float*)L, b, kb, 0, nullptr, 0);
         }
       } else {
         if (plan) k_syrk<T><<<stp.trail_cnt, 256, 0, st>>>(d_sd, L, b, items);

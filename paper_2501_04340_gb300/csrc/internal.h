@@ -230,7 +230,7 @@ struct Ctx {
   int fp64_fallbacks = 0;                // FP32 factorisations redone in FP64 (non-positive FP32 pivot)
   bool force_fallback = false;           // testing aid: the next FP32 refinement treats its first correction as stalled
   McPlan mcplan[2];                      // [0] W solve, [1] Phi solve
-  bool autotune = true;                  // IETI_NO_AUTOTUNE=1: keep the default tile shapes
+  bool autotune = true;                  // false (IETI_DEBUG_NO_AUTOTUNE): keep the default tile shapes
   bool tuned[2] = {false, false};        // [fp32] tile shapes of the streamed products chosen
   cudaStream_t aux_stream = nullptr;     // low-priority stream of the factorisation's lookahead
   cudaEvent_t ev_fact[3] = {nullptr, nullptr, nullptr};
@@ -296,7 +296,8 @@ struct Ctx {
   int* d_stream_err = nullptr;           // set when a bulk-copy or tensor-core wait times out
   float* tc_img = nullptr;               // TF32 term images of the current panel (syrk_tc.cu)
   int* d_grp_off = nullptr;              // per subdomain: first 128-row group in tc_img
-  bool syrk_tc = false;                  // IETI_SYRK_TC=1: FP32 trailing update with split TF32 tensor-core products
+  bool syrk_tc = false;                  // IETI_DEBUG_SYRK_TC: FP32 trailing update with split TF32 tensor-core products
+  int syrk_reserve = 24;                 // SMs left free by the overlapped FP32 trailing update
 
   bool assembled = false, factored = false, host_only = false;
   ieti_precision prec = IETI_FP64;

@@ -3,19 +3,21 @@ with the manufactured field A_ana (non-homogeneous tangential Dirichlet data,
 nu = 1), one JSON line per run:
 
     python -m paper_2501_04340_gb300.experiments --exp 1 [--degrees 1 2 3]
-        [--spans 1 2 3 4 6 8] [--max-gb 120]
+        [--spans 2 3 4 6 8] [--max-gb 120]
     python -m paper_2501_04340_gb300.experiments --exp 2 [--degrees 1 2 3]
-        [--nsub 2 ... 12] [--spans 12] [--max-gb 120]
+        [--nsub 2 ... 12] [--spans 4] [--max-gb 120]
 
-Experiment 1 varies the mesh size h = 1 / spans and the degree p on the three
-slab subdomains of nine patches; experiment 2 varies the number of subdomains
-(consecutive patches in snake order, each checked to be simply connected) at
-h = 1 / 12. Every run reports the coarse size n_gp, the PCG iterations to the
-relative residual 1e-6 (FP64 factors, one pass), the Lanczos estimate of
-kappa(M_D^-1 F_DP) from the PCG coefficients, and eps_B against B_ana. The
-dense local blocks grow like the square of the subdomain's DOFs: a run whose
-blocks would take more than --max-gb of device memory is reported as skipped
-instead of run.
+The mesh size is the one of the paper's figures, h = 1 / (n * 27^(1/3)) =
+1 / (3 n) for n knot spans per patch and direction (the element width relative
+to the cube's edge). Experiment 1 varies h and the degree p on three subdomains
+(the two L-shaped columns and the slab of workloads.three_columns_partition);
+experiment 2 varies the number of subdomains (consecutive patches in snake
+order, each checked to be simply connected) at h = 1 / 12 (n = 4). Every run
+reports the coarse size n_gp, the PCG iterations to the relative residual 1e-6
+(FP64 factors, one pass), the Lanczos estimate of kappa(M_D^-1 F_DP) from the
+PCG coefficients, and eps_B against B_ana. The dense local blocks grow like the
+square of the subdomain's DOFs: a run whose blocks would take more than
+--max-gb of device memory is reported as skipped instead of run.
 """
 from __future__ import annotations
 
@@ -32,7 +34,7 @@ def _dense_bytes(q) -> int:
 
 def run_one(ieti, wl, torch, p: int, spans: int, nsub: int, tol: float, max_bytes: float, exp: int) -> dict:
     prob = wl.paper_cube(p, spans, nsub=nsub)
-    rec = {"experiment": exp, "p": p, "h": 1.0 / spans, "spans": spans, "nsub": nsub}
+    rec = {"experiment": exp, "p": p, "h": 1.0 / (3 * spans), "spans": spans, "nsub": nsub}
     hctx = ieti.ieti_create_host(prob)
     try:
         q = ieti.ieti_query(hctx)
@@ -80,12 +82,12 @@ def main():
 
     cap = args.max_gb * 1e9
     if args.exp == 1:
-        spans = args.spans or [1, 2, 3, 4, 6, 8]
+        spans = args.spans or [2, 3, 4, 6, 8]
         for p in args.degrees:
             for n in spans:
                 print(json.dumps(run_one(ieti, wl, torch, p, n, 3, args.tol, cap, 1)), flush=True)
     else:
-        spans = (args.spans or [12])[0]
+        spans = (args.spans or [4])[0]
         for p in args.degrees:
             for ns in args.nsub:
                 print(json.dumps(run_one(ieti, wl, torch, p, spans, ns, args.tol, cap, 2)), flush=True)

@@ -285,6 +285,7 @@ IETI_DEBUG_PIVOT_FAULT = 2
 IETI_DEBUG_FP64_FALLBACK = 3
 IETI_DEBUG_SYRK_TC = 4
 IETI_DEBUG_NO_AUTOTUNE = 5
+IETI_DEBUG_SYRK_RESERVE = 6
 
 
 def ieti_debug_set(ctx, what, value):
