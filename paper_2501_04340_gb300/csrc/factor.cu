@@ -26,22 +26,11 @@ ieti_status convert_tiles(Ctx* c, const int4* tiles, int ntiles, const double* s
 // Cholesky kernels
 // ---------------------------------------------------------------------------
 
+// Cholesky of the 64 x 64 block a (lower part) by all threads: one column per
+// step, two barriers a step (the FP64 path: its register form would spill)
 template <typename T>
-__global__ void __launch_bounds__(256) k_potrf_diag(const SubDev* sd, T* L, T* Linv, int b, int* err) {
-  const int k = blockIdx.x;
-  const SubDev s = sd[k];
-  if (b >= s.nblk) return;
-  __shared__ T a[NB][NB + 1];
-  __shared__ T inv[NB][NB + 1];
+__device__ void chol64_cta(T (*a)[NB + 1], int* bad) {
   const int tid = threadIdx.x;
-  T* A = L + s.A + (int64_t)b * NB + (int64_t)s.n * b * NB;
-  for (int t = tid; t < NB * NB; t += blockDim.x) {
-    int i = t % NB, j = t / NB;
-    a[i][j] = A[i + (int64_t)s.n * j];
-  }
-  __shared__ int bad;
-  if (tid == 0) bad = 0;
-  __syncthreads();
   // thread (row i, column group g) updates a[i][16 g .. 16 g + 15]: the lanes of
   // a warp share g, so a[l][c] is a broadcast and a[i][l] is conflict-free
   const int ri = tid % NB, g = tid / NB;
@@ -53,7 +42,7 @@ __global__ void __launch_bounds__(256) k_potrf_diag(const SubDev* sd, T* L, T* L
     if (tid > c && tid < NB) a[tid][c] /= piv;
     __syncthreads();
     if (tid == 0) {
-      if (!(v0 > (T)0)) bad = 1;
+      if (!(v0 > (T)0)) *bad = 1;
       a[c][c] = piv;
     }
     if (ri > c && 16 * g <= ri && 16 * g + 15 > c) {
@@ -67,36 +56,147 @@ __global__ void __launch_bounds__(256) k_potrf_diag(const SubDev* sd, T* L, T* L
     }
     __syncthreads();
   }
-  if (tid == 0 && bad) atomicCAS(err, 0, k + 1);
-  // inverse of the lower triangular diagonal block: column j by the four
-  // threads 4 j .. 4 j + 3 of one warp, each summing every fourth term
-  {
-    __shared__ T rd[NB];   // reciprocals of the pivots
-    if (tid < NB) rd[tid] = (T)1 / a[tid][tid];
-    const int j = tid / 4, part = tid % 4;
-    for (int i = 0; i < j; ++i)
-      if (part == 0) inv[i][j] = (T)0;
-    __syncthreads();
-    if (part == 0) inv[j][j] = rd[j];
-    __syncwarp();
-    // the same trip count in every lane (rows i <= j contribute nothing), so the
-    // shuffles stay warp-uniform; the 16 terms of a lane are independent loads
-    for (int i = 1; i < NB; ++i) {
-      T acc = 0;
-      if (i > j) {
+}
+
+// Cholesky of the 64 x 64 block a (lower part) in the registers of warp 0:
+// lane l holds rows l (columns 0..l) and l + 32 (columns 0..l + 32); column c
+// is scaled by the lanes below the pivot and its entries reach the other
+// lanes by shuffles for the rank-1 update, with no barrier at all
+__device__ void chol64_warp(float (*a)[NB + 1], int* bad) {
+  const int lane = threadIdx.x & 31;
+  float ra[32], rb[64];
 #pragma unroll
-        for (int t = 0; t < 16; ++t) {
-          const int l = j + part + 4 * t;
-          if (l < i) acc += a[i][l] * inv[l][j];
-        }
-      }
-      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-      if (part == 0 && i > j) inv[i][j] = -acc * rd[i];
-      __syncwarp();
+  for (int l = 0; l < 32; ++l) ra[l] = l <= lane ? a[lane][l] : 0.f;
+#pragma unroll
+  for (int l = 0; l < 64; ++l) rb[l] = l <= lane + 32 ? a[lane + 32][l] : 0.f;
+  bool nonpos = false;
+#pragma unroll
+  for (int c = 0; c < 64; ++c) {
+    // (the indices are clamped so that every array index is in range; the
+    // loops are unrolled, so each select is resolved at compile time)
+    const int cc = c < 32 ? c : 0;
+    const float d = __shfl_sync(0xffffffffu, c < 32 ? ra[cc] : rb[c], c & 31);
+    nonpos |= !(d > 0.f);
+    // the pivot and its reciprocal from one reciprocal square root (a
+    // shorter dependent chain than a square root and a division; the FP32
+    // factor is refined in FP64 anyway)
+    const float dd = d > 0.f ? d : 1.f;
+    const float rp = rsqrtf(dd);
+    const float piv = dd * rp;
+    if (c < 32) ra[cc] = lane > c ? ra[cc] * rp : (lane == c ? piv : ra[cc]);
+    rb[c] = lane + 32 > c ? rb[c] * rp : (lane + 32 == c ? piv : rb[c]);
+#pragma unroll
+    for (int l = c + 1; l < 64; ++l) {
+      const float llc = __shfl_sync(0xffffffffu, l < 32 ? ra[cc] : rb[c], l & 31);
+      if (l < 32 && lane >= l) ra[l < 32 ? l : 0] -= ra[cc] * llc;
+      if (lane + 32 >= l) rb[l] -= rb[c] * llc;
+    }
+  }
+#pragma unroll
+  for (int l = 0; l < 32; ++l)
+    if (l <= lane) a[lane][l] = ra[l];
+#pragma unroll
+  for (int l = 0; l < 64; ++l)
+    if (l <= lane + 32) a[lane + 32][l] = rb[l];
+  if (lane == 0 && nonpos) *bad = 1;
+}
+
+// inverse of the lower triangular factor in a into inv (zero above the
+// diagonal) by block doubling, all threads: the four 16 x 16 diagonal blocks
+// by forward substitution (one warp each, one column per lane), then
+// [X11 0; X21 X22] with X21 = -X22 L21 X11 at 32 and at 64. The two products of
+// each level go through the unused upper triangle of a as scratch.
+template <typename T>
+__device__ void inv64_blocks(T (*a)[NB + 1], T (*inv)[NB + 1], T* rd) {
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  for (int t = tid; t < NB * NB; t += blockDim.x) inv[t % NB][t / NB] = (T)0;
+  if (tid < NB) rd[tid] = (T)1 / a[tid][tid];
+  __syncthreads();
+  if (warp < 4 && lane < 16) {
+    const int o = 16 * warp, j = lane;
+    T x[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      T acc = i == j ? (T)1 : (T)0;
+#pragma unroll
+      for (int l = 0; l < i; ++l) acc -= a[o + i][o + l] * x[l];
+      x[i] = i >= j ? acc * rd[o + i] : (T)0;
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) inv[o + i][o + j] = x[i];
+  }
+  __syncthreads();
+  {
+    // 32 x 32 blocks at o = 0 and 32 (128 threads each): scratch
+    // a[o + i][o + 16 + j], above the diagonal
+    const int B = tid / 128, e = tid % 128, o = 32 * B;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = e % 16, j = e / 16 + 8 * h;
+      T acc = 0;
+#pragma unroll
+      for (int l = 0; l < 16; ++l) acc += a[o + 16 + i][o + l] * inv[o + l][o + j];
+      a[o + i][o + 16 + j] = acc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = e % 16, j = e / 16 + 8 * h;
+      T acc = 0;
+#pragma unroll
+      for (int l = 0; l < 16; ++l) acc += inv[o + 16 + i][o + 16 + l] * a[o + l][o + 16 + j];
+      inv[o + 16 + i][o + j] = -acc;
     }
   }
   __syncthreads();
+  // 64 x 64: scratch a[i][32 + j], the upper right block
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    const int i = tid % 32, j = tid / 32 + 8 * h;
+    T acc = 0;
+#pragma unroll 8
+    for (int l = 0; l < 32; ++l) acc += a[32 + i][l] * inv[l][j];
+    a[i][32 + j] = acc;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    const int i = tid % 32, j = tid / 32 + 8 * h;
+    T acc = 0;
+#pragma unroll 8
+    for (int l = 0; l < 32; ++l) acc += inv[32 + i][32 + l] * a[l][32 + j];
+    inv[32 + i][j] = -acc;
+  }
+  __syncthreads();
+}
+
+// diagonal block b of every subdomain: Cholesky factor (lower part written
+// back, zeros above) and the inverse of the factor (to Linv); 256 threads
+template <typename T>
+__global__ void __launch_bounds__(256) k_potrf_diag(const SubDev* sd, T* L, T* Linv, int b, int* err) {
+  const int k = blockIdx.x;
+  const SubDev s = sd[k];
+  if (b >= s.nblk) return;
+  __shared__ T a[NB][NB + 1];
+  __shared__ T inv[NB][NB + 1];
+  __shared__ T rd[NB];
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  T* A = L + s.A + (int64_t)b * NB + (int64_t)s.n * b * NB;
+  for (int t = tid; t < NB * NB; t += blockDim.x) {
+    int i = t % NB, j = t / NB;
+    a[i][j] = A[i + (int64_t)s.n * j];
+  }
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  if constexpr (sizeof(T) == 4) {
+    if (tid < 32) chol64_warp(a, &bad);
+  } else {
+    chol64_cta(a, &bad);
+  }
+  __syncthreads();
+  if (tid == 0 && bad) atomicCAS(err, 0, k + 1);
+  inv64_blocks<T>(a, inv, rd);
   T* Li = Linv + s.linv + (int64_t)b * NB * NB;
   for (int t = tid; t < NB * NB; t += blockDim.x) {
     int i = t % NB, j = t / NB;
