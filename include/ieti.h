@@ -333,6 +333,10 @@ int64_t ieti_launch_count(const ieti_ctx* ctx);
  *                           products keep their defaults (no timing of
  *                           candidates at the first factorisation of each
  *                           precision).
+ *   IETI_DEBUG_ELEMENT_LOADS value != 0: the loads of axis-aligned box patches
+ *                           are integrated element by element like those of
+ *                           curved patches, instead of from separable 1D
+ *                           integrals (the same Gauss rule; kept to compare).
  *   IETI_DEBUG_SYRK_RESERVE SMs that the overlapped FP32 trailing update leaves
  *                           to the panel kernels of the next step (value 0 ..
  *                           SM count - 1; < 0 restores the default 24). Changes
@@ -344,7 +348,8 @@ enum {
   IETI_DEBUG_FP64_FALLBACK = 3,
   IETI_DEBUG_SYRK_TC = 4,
   IETI_DEBUG_NO_AUTOTUNE = 5,
-  IETI_DEBUG_SYRK_RESERVE = 6
+  IETI_DEBUG_SYRK_RESERVE = 6,
+  IETI_DEBUG_ELEMENT_LOADS = 7
 };
 ieti_status ieti_debug_set(ieti_ctx* ctx, int what, int64_t value);
 

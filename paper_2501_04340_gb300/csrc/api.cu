@@ -905,6 +905,9 @@ ieti_status ieti_debug_set(ieti_ctx* x, int what, int64_t value) {
     case IETI_DEBUG_NO_AUTOTUNE:
       c->autotune = value == 0;
       return IETI_OK;
+    case IETI_DEBUG_ELEMENT_LOADS:
+      c->sep_loads = value == 0;
+      return IETI_OK;
     case IETI_DEBUG_SYRK_RESERVE:
       if (value >= std::max(c->sm_count, 1)) {
         c->err = "ieti_debug_set: reserve must be below the SM count";

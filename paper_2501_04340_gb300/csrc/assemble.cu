@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 
 #include "internal.h"
 
@@ -530,6 +531,151 @@ __global__ void __launch_bounds__(256) k_elem_lift(AsmParams P, const int32_t* _
 }
 
 // ---------------------------------------------------------------------------
+// j on axis-aligned box patches from separable 1D integrals
+//
+// With DF = diag(L) the Gauss rule of Eq. (3) is a tensor product, and every
+// source kind is a sum of products of 1D factors,
+//   J_d(x) = Re sum_{fz,fy,fx} C_d[fz][fy][fx] phi_fx(x) phi_fy(y) phi_fz(z),
+// with phi_f(t) = e^{2 pi i (f - KG) t} for Fourier modes with integer wave
+// numbers |k| <= KG, and phi in {1, sin(pi t), sin t, cos t} for the sine,
+// manufactured and patchwise kinds. So the load of the edge function
+// D_a(xi_x) N_b(xi_y) N_c(xi_z) e_x (likewise for the other directions) is
+//   (L_y L_z) Re sum C_x[fz][fy][fx] I^D_x[a][fx] I^N_y[b][fy] I^N_z[c][fz],
+// the 1D sums I[i][f] = sum_spans sum_q (w_q / n) B_i(xi_q) phi_f(x(xi_q)) being
+// the same Gauss rule, one axis at a time. The triple sum is contracted one
+// axis at a time in shared memory (one CTA per patch, direction and load case).
+// ---------------------------------------------------------------------------
+
+struct SepArgs {
+  int NF, KG, kind;        // kind 0: Fourier exponentials, 1: the four real factors
+  int maxfun, Pmax;        // functions per slab at most (n + p), slabs per axis at most
+  int per_patch;           // C per patch (patchwise source, NF = 1)
+  const double* geo;       // per axis and slab: lower coordinate, length
+  const double* xq;        // Gauss points on [0, 1]
+  double2* tab;            // [axis][slab][family N/D][function][factor]
+  const double2* C;        // [load case][(patch)][direction][fz][fy][fx]
+};
+
+__global__ void k_sep_tab(AsmParams P, SepArgs S) {
+  const int64_t tot = (int64_t)3 * S.Pmax * 2 * S.maxfun * S.NF;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int f = (int)(t % S.NF);
+    int64_t r = t / S.NF;
+    const int i = (int)(r % S.maxfun);
+    r /= S.maxfun;
+    const int fam = (int)(r % 2);    // 0: N, 1: D
+    r /= 2;
+    const int sl = (int)(r % S.Pmax), ax = (int)(r / S.Pmax);
+    const int Pa = ax == 0 ? P.P0 : (ax == 1 ? P.P1 : P.P2);
+    double vr = 0, vi = 0;
+    if (sl < Pa) {
+      const int n = P.nspan[ax][sl];
+      if (i < n + P.p - fam) {
+        const double lo = S.geo[(ax * S.Pmax + sl) * 2], L = S.geo[(ax * S.Pmax + sl) * 2 + 1];
+        const int g0 = P.spanoff[ax][sl];
+        const int rmax = P.p - fam;   // local functions of a span: p + 1 (N), p (D)
+        for (int sp = max(0, i - rmax); sp <= min(n - 1, i); ++sp) {
+          const int rr = i - sp;
+          for (int q = 0; q < P.nq; ++q) {
+            const double B = fam ? P.tabD[ax][((int64_t)(g0 + sp) * P.p + rr) * P.nq + q]
+                                 : P.tabN[ax][((int64_t)(g0 + sp) * (P.p + 1) + rr) * P.nq + q];
+            const double w = P.wq[q] / n * B;
+            const double x = lo + L * (sp + S.xq[q]) / n;
+            if (S.kind == 0) {
+              double sn, cs;
+              sincospi(2.0 * (f - S.KG) * x, &sn, &cs);
+              vr += w * cs;
+              vi += w * sn;
+            } else {
+              vr += w * (f == 0 ? 1.0 : f == 1 ? sinpi(x) : f == 2 ? sin(x) : cos(x));
+            }
+          }
+        }
+      }
+    }
+    S.tab[t] = make_double2(vr, vi);
+  }
+}
+
+__device__ inline double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__global__ void __launch_bounds__(256) k_sep_load(AsmParams P, SepArgs S) {
+  const int q = blockIdx.x, d = blockIdx.y, r = blockIdx.z;
+  int a3[3];
+  patch_abc_d(P, q, a3);
+  const SubDev s = P.sd[P.sub_of_patch[q]];
+  const int NF = S.NF, NF2 = NF * NF, NF3 = NF2 * NF;
+  const int tid = threadIdx.x;
+  int ext[3];
+  for (int e = 0; e < 3; ++e) ext[e] = P.nspan[e][a3[e]] + P.p - (e == d ? 1 : 0);
+  int64_t doff = 0;
+  for (int dd = 0; dd < d; ++dd) {
+    int64_t v = 1;
+    for (int e = 0; e < 3; ++e) v *= P.nspan[e][a3[e]] + P.p - (e == dd ? 1 : 0);
+    doff += v;
+  }
+  extern __shared__ __align__(16) double2 sm[];
+  double2* Cs = sm;                            // [fz][fy][fx]
+  double2* Tx = Cs + NF3;                      // [a][fx]
+  double2* Ty = Tx + ext[0] * NF;              // [b][fy]
+  double2* Tz = Ty + ext[1] * NF;              // [c][fz]
+  double2* T1 = Tz + ext[2] * NF;              // [c][fy][fx]
+  double2* T2 = T1 + (size_t)ext[2] * NF2;     // [c][b][fx]
+  const int np = P.P0 * P.P1 * P.P2;
+  const double2* Cg = S.C + (((int64_t)r * (S.per_patch ? np : 1) + (S.per_patch ? q : 0)) * 3 + d) * NF3;
+  for (int t = tid; t < NF3; t += blockDim.x) Cs[t] = Cg[t];
+  double2* T[3] = {Tx, Ty, Tz};
+  for (int e = 0; e < 3; ++e) {
+    const double2* src = S.tab + ((int64_t)((e * S.Pmax + a3[e]) * 2 + (e == d ? 1 : 0)) * S.maxfun) * NF;
+    for (int t = tid; t < ext[e] * NF; t += blockDim.x) T[e][t] = src[t];
+  }
+  __syncthreads();
+  for (int t = tid; t < ext[2] * NF2; t += blockDim.x) {
+    const int c = t / NF2, yx = t % NF2;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int fz = 0; fz < NF; ++fz) {
+      const double2 v = cmul(Cs[fz * NF2 + yx], Tz[c * NF + fz]);
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    T1[t] = acc;
+  }
+  __syncthreads();
+  for (int t = tid; t < ext[2] * ext[1] * NF; t += blockDim.x) {
+    const int fx = t % NF, b = (t / NF) % ext[1], c = t / (NF * ext[1]);
+    double2 acc = make_double2(0.0, 0.0);
+    for (int fy = 0; fy < NF; ++fy) {
+      const double2 v = cmul(T1[(c * NF + fy) * NF + fx], Ty[b * NF + fy]);
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    T2[t] = acc;
+  }
+  __syncthreads();
+  // covariant map and measure: |L_x L_y L_z| / L_d
+  double vol = 1.0;
+  for (int e = 0; e < 3; ++e) vol *= S.geo[(e * S.Pmax + a3[e]) * 2 + 1];
+  const double scale = fabs(vol) / S.geo[(d * S.Pmax + a3[d]) * 2 + 1];
+  const int64_t nloc = (int64_t)ext[0] * ext[1] * ext[2];
+  const int64_t cbase = P.patch_code_off[q] + doff;
+  for (int64_t t = tid; t < nloc; t += blockDim.x) {
+    const int a = (int)(t % ext[0]), bc = (int)(t / ext[0]);   // bc = b + ext1 c
+    const int cf = P.patch_code[cbase + t];
+    if (cf < 0) continue;
+    double v = 0;
+    for (int fx = 0; fx < NF; ++fx) {
+      const double2 u = T2[(int64_t)bc * NF + fx], w = Tx[a * NF + fx];
+      v += u.x * w.x - u.y * w.y;
+    }
+    v *= scale;
+    if (cf < s.n) atomicAdd(P.jr + RV(s, cf, r, P.nrhs), v);
+    else atomicAdd(P.jp + PV(s, cf - s.n, r, P.nrhs), v);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // K: Kronecker generation of every dense entry (axis-aligned affine patches)
 // ---------------------------------------------------------------------------
 
@@ -719,7 +865,7 @@ static AsmParams make_params(Ctx* c) {
 }
 
 template <int PD>
-static ieti_status launch_elem(Ctx* c, const AsmParams& P, bool do_K, cudaStream_t st) {
+static ieti_status launch_elem(Ctx* c, const AsmParams& P, bool do_K, bool do_j, cudaStream_t st) {
   constexpr int NQ3 = (PD + 1) * (PD + 1) * (PD + 1), NF = ElemShared<PD>::NF;
   if (do_K) {
     size_t smem = sizeof(ElemShared<PD>) + sizeof(double) * (NQ3 * 9 + (size_t)NF * NQ3 * 2);
@@ -731,8 +877,10 @@ static ieti_status launch_elem(Ctx* c, const AsmParams& P, bool do_K, cudaStream
   size_t smem = sizeof(ElemShared<PD>) + sizeof(double) * (size_t)NQ3 * (c->nrhs * 3 + 9 + 3) + 16 +
                 sizeof(double2) * (size_t)NQ3 * 3 * (FT_KMAX + 1);
   cudaEvent_t p0 = prof_begin(c, st);
-  k_elem_j<PD><<<(unsigned)c->nelem, 256, smem, st>>>(P);
-  IETI_LAUNCH_CHECK(c);
+  if (do_j) {
+    k_elem_j<PD><<<(unsigned)c->nelem, 256, smem, st>>>(P);
+    IETI_LAUNCH_CHECK(c);
+  }
   if (c->d_gD && c->nbelem > 0) {
     const size_t lsm = sizeof(ElemShared<PD>) + sizeof(double) * (2 * (size_t)NF + 3 * (size_t)NQ3);
     k_elem_lift<PD><<<(unsigned)c->nbelem, 256, lsm, st>>>(P, c->d_belem, c->d_gD);
@@ -750,6 +898,148 @@ ieti_status assemble_kernel_attrs(Ctx* c, int smem_max) {
   IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_elem_j<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
   IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_elem_j<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
   IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_elem_j<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  IETI_CUDA_TRY(c, cudaFuncSetAttribute(k_sep_load, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  return IETI_OK;
+}
+
+// device buffer of at least n elements, grown (and kept) on demand
+template <typename T>
+static ieti_status grow(Ctx* c, T** p, int64_t* cap, int64_t n) {
+  if (n <= *cap) return IETI_OK;
+  void* q = nullptr;
+  const size_t bytes = sizeof(T) * (size_t)std::max<int64_t>(n, 1);
+  if (cudaMalloc(&q, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    c->err = "cudaMalloc of " + std::to_string(bytes) + " bytes failed";
+    return IETI_ERR_OOM;
+  }
+  c->allocs.push_back({q, bytes});
+  *p = (T*)q;
+  *cap = n;
+  return IETI_OK;
+}
+
+// the loads of box patches from separable 1D integrals (above), when the
+// source is a sum of products of the supported 1D factors and the contraction
+// fits in shared memory; *done = false leaves them to the element quadrature
+static ieti_status sep_loads(Ctx* c, const AsmParams& P, bool* done, cudaStream_t st) {
+  *done = false;
+  const Mesh& m = c->mesh;
+  const int nr = c->nrhs, np = m.npatch();
+  int NF = 0, KG = 0, kind = 1, per_patch = 0;
+  std::vector<double2>& C = c->sep_C_host;   // kept: read by the asynchronous copy below
+  const std::vector<double>& src = c->src;
+  auto fill = [&](int NFv) {
+    NF = NFv;
+    C.assign((size_t)nr * (per_patch ? np : 1) * 3 * NF * NF * NF, make_double2(0.0, 0.0));
+  };
+  auto at = [&](int r, int d, int fz, int fy, int fx) -> double2& {
+    return C[((size_t)r * 3 + d) * NF * NF * NF + ((size_t)fz * NF + fy) * NF + fx];
+  };
+  const double pi = 3.14159265358979323846;
+  if (c->source_kind == IETI_SOURCE_FOURIER) {
+    // integer wave numbers up to 4 per axis: the grid of exponentials
+    size_t pos = 0;
+    for (int r = 0; r < nr; ++r) {
+      const int nm = (int)src[pos++];
+      for (int mm = 0; mm < nm; ++mm, pos += 9)
+        for (int a = 0; a < 3; ++a) {
+          const double k = src[pos + a];
+          if (k != std::rint(k) || std::fabs(k) > 4) return IETI_OK;
+          KG = std::max(KG, (int)std::fabs(k));
+        }
+    }
+    kind = 0;
+    fill(2 * KG + 1);
+    pos = 0;
+    for (int r = 0; r < nr; ++r) {
+      const int nm = (int)src[pos++];
+      for (int mm = 0; mm < nm; ++mm, pos += 9) {
+        const int kx = (int)src[pos] + KG, ky = (int)src[pos + 1] + KG, kz = (int)src[pos + 2] + KG;
+        for (int d = 0; d < 3; ++d) {
+          double2& v = at(r, d, kz, ky, kx);
+          v.x += src[pos + 3 + d];
+          v.y += src[pos + 6 + d];
+        }
+      }
+    }
+  } else if (c->source_kind == IETI_SOURCE_SINE) {
+    // factors 0: 1, 1: sin(pi t)
+    fill(4);
+    for (int r = 0; r < nr; ++r) {
+      const double a = src[r] * 2 * pi * pi;
+      at(r, 0, 1, 1, 0).x = a;
+      at(r, 1, 1, 0, 1).x = a;
+      at(r, 2, 0, 1, 1).x = a;
+    }
+  } else if (c->source_kind == IETI_SOURCE_TRIG) {
+    // factors 2: sin t, 3: cos t; 3 A_ana of Sec. 3
+    fill(4);
+    for (int r = 0; r < nr; ++r) {
+      at(r, 0, 3, 3, 2).x = 3.0 * src[r];
+      at(r, 1, 3, 2, 3).x = -6.0 * src[r];
+      at(r, 2, 2, 3, 3).x = 3.0 * src[r];
+    }
+  } else if (c->source_kind == IETI_SOURCE_PATCHWISE) {
+    per_patch = 1;
+    fill(1);
+    for (size_t t = 0; t < C.size(); ++t) C[t].x = src[t];
+  } else {
+    return IETI_OK;
+  }
+  int maxfun = 0, Pmax = 0;
+  for (int a = 0; a < 3; ++a) {
+    Pmax = std::max(Pmax, m.P[a]);
+    for (int sl = 0; sl < m.P[a]; ++sl) maxfun = std::max(maxfun, m.nspan[a][sl] + m.p);
+  }
+  const size_t smem = sizeof(double2) * ((size_t)NF * NF * NF + 3 * (size_t)maxfun * NF +
+                                         (size_t)maxfun * NF * NF + (size_t)maxfun * maxfun * NF);
+  if (smem > (size_t)c->smem_optin) return IETI_OK;
+  // slab geometry of the box net: lower corner and length per axis and slab
+  std::vector<double> geo((size_t)3 * Pmax * 2, 0.0);
+  for (int a = 0; a < 3; ++a)
+    for (int sl = 0; sl < m.P[a]; ++sl) {
+      int i0[3] = {0, 0, 0}, i1[3] = {0, 0, 0};
+      i0[a] = m.start[a][sl];
+      i1[a] = m.start[a][sl] + m.nspan[a][sl] + m.p - 1;
+      auto X = [&](const int* ix) {
+        return c->ctrl[(((size_t)ix[2] * m.N[1] + ix[1]) * m.N[0] + ix[0]) * 4 + a];
+      };
+      geo[(a * Pmax + sl) * 2] = X(i0);
+      geo[(a * Pmax + sl) * 2 + 1] = X(i1) - X(i0);
+    }
+  ieti_status rs;
+  int64_t cap = 0;
+  if (!c->d_sep_geo) {
+    if ((rs = grow(c, &c->d_sep_geo, &cap, (int64_t)geo.size())) != IETI_OK) return rs;
+    cap = 0;
+    if ((rs = grow(c, &c->d_xq, &cap, (int64_t)c->tab.xq.size())) != IETI_OK) return rs;
+    IETI_CUDA_TRY(c, cudaMemcpy(c->d_sep_geo, geo.data(), sizeof(double) * geo.size(), cudaMemcpyHostToDevice));
+    IETI_CUDA_TRY(c, cudaMemcpy(c->d_xq, c->tab.xq.data(), sizeof(double) * c->tab.xq.size(),
+                                cudaMemcpyHostToDevice));
+  }
+  if ((rs = grow(c, &c->d_sep_C, &c->sep_C_cap, (int64_t)C.size())) != IETI_OK) return rs;
+  const int64_t ntab = (int64_t)3 * Pmax * 2 * maxfun * NF;
+  if ((rs = grow(c, &c->d_sep_tab, &c->sep_tab_cap, ntab)) != IETI_OK) return rs;
+  IETI_CUDA_TRY(c, cudaMemcpyAsync(c->d_sep_C, C.data(), sizeof(double2) * C.size(), cudaMemcpyHostToDevice, st));
+  SepArgs S;
+  S.NF = NF;
+  S.KG = KG;
+  S.kind = kind;
+  S.maxfun = maxfun;
+  S.Pmax = Pmax;
+  S.per_patch = per_patch;
+  S.geo = c->d_sep_geo;
+  S.xq = c->d_xq;
+  S.tab = c->d_sep_tab;
+  S.C = c->d_sep_C;
+  cudaEvent_t p0 = prof_begin(c, st);
+  k_sep_tab<<<(unsigned)std::min<int64_t>(ceil_div(ntab, 256), 4096), 256, 0, st>>>(P, S);
+  IETI_LAUNCH_CHECK(c);
+  k_sep_load<<<dim3((unsigned)np, 3, (unsigned)nr), 256, smem, st>>>(P, S);
+  IETI_LAUNCH_CHECK(c);
+  prof_end(c, PROF_ASM_J, p0, st);
+  *done = true;
   return IETI_OK;
 }
 
@@ -783,7 +1073,9 @@ ieti_status assemble_all(Ctx* c, cudaStream_t st) {
     IETI_LAUNCH_CHECK(c);
   }
   ieti_status r;
-  if (!c->d_geo && !c->geo_failed) {
+  bool sep = false;
+  if (kron && c->sep_loads && (r = sep_loads(c, P, &sep, st)) != IETI_OK) return r;
+  if (!sep && !c->d_geo && !c->geo_failed) {
     // geometry kept per element and Gauss point (12 doubles each)
     const int nq3 = (c->mesh.p + 1) * (c->mesh.p + 1) * (c->mesh.p + 1);
     const size_t bytes = sizeof(double) * 12 * (size_t)nq3 * (size_t)std::max<int64_t>(c->nelem, 1);
@@ -798,12 +1090,12 @@ ieti_status assemble_all(Ctx* c, cudaStream_t st) {
     }
   }
   switch (c->mesh.p) {
-    case 1: r = launch_elem<1>(c, P, !kron, st); break;
-    case 2: r = launch_elem<2>(c, P, !kron, st); break;
-    case 3: r = launch_elem<3>(c, P, !kron, st); break;
+    case 1: r = launch_elem<1>(c, P, !kron, !sep, st); break;
+    case 2: r = launch_elem<2>(c, P, !kron, !sep, st); break;
+    case 3: r = launch_elem<3>(c, P, !kron, !sep, st); break;
     default: c->err = "degree p must be 1, 2 or 3"; return IETI_ERR_INVALID_ARG;
   }
-  if (r == IETI_OK && c->d_geo) c->geo_ready = true;
+  if (r == IETI_OK && c->d_geo && !sep) c->geo_ready = true;
   return r;
 }
 

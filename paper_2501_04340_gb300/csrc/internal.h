@@ -143,6 +143,16 @@ struct Ctx {
   std::vector<int32_t> belem_host;       // elements with a facet in a Dirichlet face
   int64_t nelem = 0;
   double* d_geo = nullptr;               // per element and Gauss point: X, weight |det DF| DF^-1 (assembly)
+  // loads of box patches from separable 1D integrals (assemble.cu): coefficient
+  // grid, 1D tables, slab geometry and Gauss points on the device
+  bool sep_loads = true;                 // false (IETI_DEBUG_ELEMENT_LOADS): element quadrature for the loads
+  double2* d_sep_C = nullptr;
+  std::vector<double2> sep_C_host;
+  int64_t sep_C_cap = 0;
+  double2* d_sep_tab = nullptr;
+  int64_t sep_tab_cap = 0;
+  double* d_sep_geo = nullptr;           // per axis and slab: lower coordinate, length
+  double* d_xq = nullptr;                // Gauss points on [0, 1]
   bool geo_ready = false, geo_failed = false;
   int64_t* d_patch_eoff = nullptr;       // per patch: its first element (npatch + 1 entries)
   double* d_flux_part = nullptr;         // flux evaluation: per element and load case, 2 integrals

@@ -286,6 +286,7 @@ IETI_DEBUG_FP64_FALLBACK = 3
 IETI_DEBUG_SYRK_TC = 4
 IETI_DEBUG_NO_AUTOTUNE = 5
 IETI_DEBUG_SYRK_RESERVE = 6
+IETI_DEBUG_ELEMENT_LOADS = 7
 
 
 def ieti_debug_set(ctx, what, value):
