@@ -339,8 +339,6 @@ __device__ __forceinline__ void syrk2_tile(const SubDev& s, float* L, int b, int
   if (R >= Tt) return;
   const int r0 = t0 + 2 * R, c0 = t0 + 2 * C;
   const int nr = min(2, s.nblk - r0), nc = col_only ? 1 : min(2, s.nblk - c0);   // blocks present (1 or 2)
-  float(*Pr)[S2_LDS] = reinterpret_cast<float(*)[S2_LDS]>(s2);
-  float(*Pc)[S2_LDS] = reinterpret_cast<float(*)[S2_LDS]>(s2 + NB * S2_LDS);
   const int tid = threadIdx.x;
   const int64_t n = s.n;
   const int ti = tid % 16, tj = tid / 16;   // rows 8 ti .. 8 ti + 7, columns 8 tj .. 8 tj + 7
@@ -352,23 +350,41 @@ __device__ __forceinline__ void syrk2_tile(const SubDev& s, float* L, int b, int
   for (int u = 0; u < 8; ++u)
 #pragma unroll
     for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
-  for (int ch = 0; ch < kb; ++ch) {
-    const float* P = L + s.A + (int64_t)n * (b + ch) * NB;
-    if (ch > 0) __syncthreads();   // every thread is done with the previous chunk
-    // both panels, 4 consecutive rows per 16-byte asynchronous copy (zero
-    // filled past the blocks present), stored transposed
+  // the panels in pieces of S2_K columns, double buffered: the copies of piece
+  // h + 1 are in flight while piece h is multiplied (two buffers of the row and
+  // column panels, transposed, in the same shared memory as one 64-wide chunk)
+  constexpr int S2_K = NB / 2;
+  auto stage = [&](int h) {
+    float(*Pr)[S2_LDS] = reinterpret_cast<float(*)[S2_LDS]>(s2 + (h & 1) * 2 * S2_K * S2_LDS);
+    float(*Pc)[S2_LDS] = reinterpret_cast<float(*)[S2_LDS]>(s2 + (h & 1) * 2 * S2_K * S2_LDS + S2_K * S2_LDS);
+    const float* P = L + s.A + n * ((int64_t)(b + h / 2) * NB + (h % 2) * S2_K);
+    // 4 consecutive rows per 16-byte asynchronous copy (zero filled past the
+    // blocks present)
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int x = tid + 256 * q;                  // 2048 vectors of 4 rows: i4 = x % 32, l = x / 32
+    for (int q = 0; q < 4; ++q) {
+      const int x = tid + 256 * q;                  // 1024 vectors of 4 rows: i4 = x % 32, l = x / 32
       const int i = 4 * (x % 32), l = x / 32;
       const bool vr = i < nr * NB, vc = i < nc * NB;
       cp_async16(&Pr[l][i], vr ? P + (int64_t)r0 * NB + i + n * l : P, vr);
       cp_async16(&Pc[l][i], vc ? P + (int64_t)c0 * NB + i + n * l : P, vc);
     }
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
-    __syncthreads();
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  const int npieces = 2 * kb;
+  stage(0);
+  for (int h = 0; h < npieces; ++h) {
+    if (h + 1 < npieces) {
+      stage(h + 1);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    __syncthreads();   // piece h is in shared memory for every thread
+    const float(*Pr)[S2_LDS] = reinterpret_cast<const float(*)[S2_LDS]>(s2 + (h & 1) * 2 * S2_K * S2_LDS);
+    const float(*Pc)[S2_LDS] =
+        reinterpret_cast<const float(*)[S2_LDS]>(s2 + (h & 1) * 2 * S2_K * S2_LDS + S2_K * S2_LDS);
 #pragma unroll 4
-    for (int l = 0; l < NB; ++l) {
+    for (int l = 0; l < S2_K; ++l) {
       const float4 x0 = *reinterpret_cast<const float4*>(&Pr[l][8 * ti]);
       const float4 x1 = *reinterpret_cast<const float4*>(&Pr[l][8 * ti + 4]);
       const float4 y0 = *reinterpret_cast<const float4*>(&Pc[l][8 * tj]);
@@ -380,6 +396,7 @@ __device__ __forceinline__ void syrk2_tile(const SubDev& s, float* L, int b, int
 #pragma unroll
         for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(x[u], y[v], acc[u][v]);
     }
+    __syncthreads();   // every thread is done with buffer h & 1 before piece h + 2 is copied into it
   }
   if (!writes) return;   // beyond the trailing matrix or above the block diagonal
   float4 cv[16];         // all loads of the C tile in flight together
