@@ -713,16 +713,104 @@ __global__ void __launch_bounds__(256) k_kron(AsmParams P, T* Lout, int prim_onl
   for (int j = (prim_only ? s.n : 0) + blockIdx.y; j < R; j += gridDim.y) kron_entry<T>(P, Lout, k, s, i, j);
 }
 
-// K_rr entries of the listed nonzero 64 x 64 tiles (k, I, J) only; the other
-// tiles of K_rr are structurally zero and keep the zeros of the first assembly.
-// Thread t: row 64 I + t % 64, columns 64 J + 16 (t / 64) ..
+// slab candidates and slab-local indices of one DOF per direction (the
+// DOF-dependent part of a Kronecker entry, formed once per row and column)
+struct KronInfo {
+  int x[3], d;
+  int n[3], cand[3][2], loc[3][2];
+};
+
+__device__ inline void kron_info(const AsmParams& P, const DofDev& a, KronInfo& I) {
+  I.d = a.d;
+  I.x[0] = a.i;
+  I.x[1] = a.j;
+  I.x[2] = a.k;
+  if (a.d < 0) return;
+  for (int c = 0; c < 3; ++c) {
+    I.n[c] = slab_cands(P, c, I.x[c], a.d == c, I.cand[c]);
+    for (int u = 0; u < I.n[c]; ++u) I.loc[c][u] = local_index(P, c, I.cand[c][u], I.x[c], a.d == c);
+  }
+}
+
+// the K_rr entry of rows with infos A and B in subdomain k: the same terms, in
+// the same order, as kron_entry
+__device__ inline double kron_value(const AsmParams& P, int k, const KronInfo& A, const KronInfo& B, bool diag) {
+  if (A.d < 0 || B.d < 0) return diag ? 1.0 : 0.0;
+  const int p = P.p;
+  for (int c = 0; c < 3; ++c) {
+    int dl = A.x[c] - B.x[c];
+    if (c == 0 && P.per0) {
+      dl = ((dl % P.N0) + P.N0) % P.N0;
+      if (dl > P.N0 / 2) dl -= P.N0;
+    }
+    if (dl > p || dl < -p) return 0.0;
+  }
+  double v = 0.0;
+  for (int u0 = 0; u0 < A.n[0]; ++u0)
+    for (int w0 = 0; w0 < B.n[0]; ++w0) {
+      if (A.cand[0][u0] != B.cand[0][w0]) continue;
+      for (int u1 = 0; u1 < A.n[1]; ++u1)
+        for (int w1 = 0; w1 < B.n[1]; ++w1) {
+          if (A.cand[1][u1] != B.cand[1][w1]) continue;
+          for (int u2 = 0; u2 < A.n[2]; ++u2)
+            for (int w2 = 0; w2 < B.n[2]; ++w2) {
+              if (A.cand[2][u2] != B.cand[2][w2]) continue;
+              const int sl[3] = {A.cand[0][u0], A.cand[1][u1], A.cand[2][u2]};
+              const int q = sl[0] + P.P0 * (sl[1] + P.P1 * sl[2]);
+              if (P.sub_of_patch[q] != k) continue;
+              const int la[3] = {A.loc[0][u0], A.loc[1][u1], A.loc[2][u2]};
+              const int lb[3] = {B.loc[0][w0], B.loc[1][w1], B.loc[2][w2]};
+              if (la[0] < 0 || la[1] < 0 || la[2] < 0 || lb[0] < 0 || lb[1] < 0 || lb[2] < 0) continue;
+              for (int comp = 0; comp < 3; ++comp) {
+                if (comp == A.d || comp == B.d) continue;
+                int fa[3], fb[3];
+                const int sgn = curl_term(A.d, comp, fa) * curl_term(B.d, comp, fb);
+                double prod = P.gq[q * 3 + comp] * sgn;
+                for (int c = 0; c < 3; ++c) {
+                  const int off = lb[c] - la[c] + p;
+                  if (off < 0 || off > 2 * p) {
+                    prod = 0;
+                    break;
+                  }
+                  prod *= P.gram[c][P.gram_per[c] * sl[c] +
+                                    ((int64_t)(fa[c] * 3 + fb[c]) * P.gram_nfun[c] + la[c]) * (2 * p + 1) + off];
+                }
+                v += prod;
+              }
+            }
+        }
+    }
+  return v;
+}
+
+// K_rr entries of the listed nonzero 64 x 64 tiles (k, I, J), I >= J, only;
+// the other tiles of K_rr are structurally zero and keep the zeros of the first
+// assembly. The column infos are formed once per tile in shared memory, the
+// row's once per thread (row 64 I + t % 64, columns 64 J + 16 (t / 64) ..);
+// the tile is staged in shared memory and written with its mirror (J, I),
+// both with coalesced stores.
 __global__ void __launch_bounds__(256) k_kron_tiles(AsmParams P, const int4* tiles) {
   const int4 tl = tiles[blockIdx.x];
   const int k = tl.x;
   const SubDev s = P.sd[k];
-  const int i = tl.y * NB + (int)threadIdx.x % NB;
-  const int j0 = tl.z * NB + 16 * ((int)threadIdx.x / NB);
-  for (int j = j0; j < j0 + 16; ++j) kron_entry<double>(P, (double*)nullptr, k, s, i, j);
+  __shared__ KronInfo cinfo[NB];
+  __shared__ double T[NB][NB + 1];
+  const int tid = threadIdx.x;
+  if (tid < NB) kron_info(P, P.dof[s.dof + tl.z * NB + tid], cinfo[tid]);
+  KronInfo A;
+  const int ii = tid % NB, j0 = 16 * (tid / NB);
+  kron_info(P, P.dof[s.dof + tl.y * NB + ii], A);
+  __syncthreads();
+  const bool dtile = tl.y == tl.z;
+  for (int jj = j0; jj < j0 + 16; ++jj) T[ii][jj] = kron_value(P, k, A, cinfo[jj], dtile && ii == jj);
+  __syncthreads();
+  double* K = P.K64 + s.A;
+  for (int t = tid; t < NB * NB; t += blockDim.x) {
+    const int r = t % NB, c = t / NB;
+    // (a diagonal tile takes its lower half for both halves: K_rr exactly symmetric)
+    K[(int64_t)tl.y * NB + r + (int64_t)s.n * (tl.z * NB + c)] = (dtile && r < c) ? T[c][r] : T[r][c];
+    if (!dtile) K[(int64_t)tl.z * NB + r + (int64_t)s.n * (tl.y * NB + c)] = T[c][r];
+  }
 }
 
 template <typename T>

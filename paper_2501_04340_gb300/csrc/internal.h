@@ -220,7 +220,7 @@ struct Ctx {
   unsigned char* d_lflags = nullptr;
   int64_t* d_tile_off = nullptr;
   bool ktile_ready = false;
-  int4* d_ktile_list = nullptr;          // nonzero tiles (k, I, J) of K_rr, both triangles
+  int4* d_ktile_list = nullptr;          // nonzero lower tiles (k, I, J), I >= J, of K_rr
   int n_ktiles = 0;
   int4* d_ltile_list = nullptr;          // lower tiles (k, I, J) of the factor's pattern
   int n_ltiles = 0;

@@ -89,7 +89,8 @@ ieti_status build_ktiles(Ctx* c, cudaStream_t st) {
     const int m = c->sd_host[k].nblk;
     for (int J = 0; J < m; ++J)
       for (int I = 0; I < m; ++I)
-        if (c->kflags[c->tile_off[k] + I + (int64_t)m * J]) kt.push_back(make_int4(k, I, J, 0));
+        // the lower tiles: the Kronecker assembly writes each with its mirror
+        if (I >= J && c->kflags[c->tile_off[k] + I + (int64_t)m * J]) kt.push_back(make_int4(k, I, J, 0));
   }
   c->n_ktiles = (int)kt.size();
   if (kt.empty()) kt.push_back(make_int4(0, 0, 0, 0));

@@ -77,3 +77,24 @@ def test_non_integer_wave_numbers_keep_the_element_quadrature(ieti):
     _, _, n_s = _loads(ieti, prob, False)
     _, _, n_e = _loads(ieti, prob, True)
     assert n_s == n_e
+
+
+@pytest.mark.parametrize("name", ["sine_ragged_p3", "fourier_box_p3", "trig_paper_cube"])
+def test_tile_reassembly_equals_first_assembly(ieti, name):
+    """After the first factorisation found the nonzero tiles of K_rr, later
+    assemblies generate only those (the lower ones, written with their
+    mirrors); the blocks equal the full first assembly's to rounding."""
+    prob = CASES[name]()
+    ctx = ieti.ieti_create(prob)
+    try:
+        ieti.ieti_assemble(ctx)
+        nsub = ieti.ieti_query(ctx)["nsub"]
+        K1 = [ieti.ieti_get_block(ctx, 0, k) for k in range(nsub)]
+        ieti.ieti_factor(ctx, ieti.IETI_FP64)
+        ieti.ieti_assemble(ctx)
+        for k in range(nsub):
+            K2 = ieti.ieti_get_block(ctx, 0, k)
+            assert np.abs(K2 - K1[k]).max() <= 1e-14 * np.abs(K1[k]).max()
+            assert np.array_equal(K2, K2.T)
+    finally:
+        ieti.ieti_destroy(ctx)
