@@ -418,6 +418,43 @@ ieti_status build(Ctx* c, const ieti_problem_desc* desc, bool device) {
   TRY(upload(c, &c->d_pair, t.dual_pair));
   TRY(upload(c, &c->d_patch_code, pcode));
   TRY(upload(c, &c->d_patch_code_off, pc_off));
+  if (c->affine) {
+    // the separable loads of box patches sum the patch contributions of every
+    // local DOF in a fixed order (ascending patch-local edge): no atomics, so
+    // repeated assemblies give bit-identical loads
+    const int64_t nslot = c->tot_rv + c->tot_pv;
+    std::vector<int64_t> gofs(nslot + 1, 0), gbase(std::max<int64_t>(nslot, 1), 0);
+    std::vector<int32_t> gstride(std::max<int64_t>(nslot, 1), 0);
+    auto slot_of = [&](int q, int32_t code) -> int64_t {
+      const SubDev& d = c->sd_host[c->sub_of_patch[q]];
+      return code < d.n ? d.rv + code : c->tot_rv + d.pv + (code - d.n);
+    };
+    for (int q = 0; q < np; ++q)
+      for (int64_t g = pc_off[q]; g < pc_off[q + 1]; ++g)
+        if (pcode[g] >= 0) gofs[slot_of(q, pcode[g]) + 1]++;
+    for (int64_t t = 0; t < nslot; ++t) gofs[t + 1] += gofs[t];
+    std::vector<int64_t> glist(std::max<int64_t>(gofs[nslot], 1)), fillp(gofs.begin(), gofs.end() - 1);
+    for (int q = 0; q < np; ++q)
+      for (int64_t g = pc_off[q]; g < pc_off[q + 1]; ++g)
+        if (pcode[g] >= 0) glist[fillp[slot_of(q, pcode[g])]++] = g;
+    for (int k = 0; k < c->nsub; ++k) {
+      const SubDev& d = c->sd_host[k];
+      for (int i = 0; i < d.n; ++i) {
+        gbase[d.rv + i] = RV(d, i, 0, c->nrhs);
+        gstride[d.rv + i] = d.n;
+      }
+      for (int i = 0; i < d.nP; ++i) {
+        gbase[c->tot_rv + d.pv + i] = PV(d, i, 0, c->nrhs);
+        gstride[c->tot_rv + d.pv + i] = d.nP;
+      }
+    }
+    TRY(upload(c, &c->d_sep_gofs, gofs));
+    TRY(upload(c, &c->d_sep_glist, glist));
+    TRY(upload(c, &c->d_sep_gbase, gbase));
+    TRY(upload(c, &c->d_sep_gstride, gstride));
+    c->sep_nslot = nslot;
+    c->sep_npl = pc_off[np];
+  }
   TRY(upload(c, &c->d_sub_of_patch, c->sub_of_patch));
   TRY(upload(c, &c->d_elem, c->elem_host));
   if (!c->gD_host.empty()) {

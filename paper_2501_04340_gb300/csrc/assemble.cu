@@ -554,6 +554,8 @@ struct SepArgs {
   const double* xq;        // Gauss points on [0, 1]
   double2* tab;            // [axis][slab][family N/D][function][factor]
   const double2* C;        // [load case][(patch)][direction][fz][fy][fx]
+  double* ploc;            // per patch-local edge and load case: the patch's part of its load
+  int64_t npl;             // patch-local edges (column stride of ploc)
 };
 
 __global__ void k_sep_tab(AsmParams P, SepArgs S) {
@@ -662,16 +664,28 @@ __global__ void __launch_bounds__(256) k_sep_load(AsmParams P, SepArgs S) {
   const int64_t cbase = P.patch_code_off[q] + doff;
   for (int64_t t = tid; t < nloc; t += blockDim.x) {
     const int a = (int)(t % ext[0]), bc = (int)(t / ext[0]);   // bc = b + ext1 c
-    const int cf = P.patch_code[cbase + t];
-    if (cf < 0) continue;
+    if (P.patch_code[cbase + t] < 0) continue;
     double v = 0;
     for (int fx = 0; fx < NF; ++fx) {
       const double2 u = T2[(int64_t)bc * NF + fx], w = Tx[a * NF + fx];
       v += u.x * w.x - u.y * w.y;
     }
-    v *= scale;
-    if (cf < s.n) atomicAdd(P.jr + RV(s, cf, r, P.nrhs), v);
-    else atomicAdd(P.jp + PV(s, cf - s.n, r, P.nrhs), v);
+    // this patch's part of the DOF's load; k_sep_gather sums the parts
+    S.ploc[cbase + t + S.npl * r] = v * scale;
+  }
+}
+
+// loads of the local DOFs: the parts of their patch-local edges summed in a
+// fixed order (deterministic, no atomics)
+__global__ void k_sep_gather(AsmParams P, SepArgs S, const int64_t* __restrict__ gofs,
+                             const int64_t* __restrict__ glist, const int64_t* __restrict__ gbase,
+                             const int32_t* __restrict__ gstride, int64_t nslot, int64_t nslot_r) {
+  const int r = blockIdx.y;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nslot; t += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0;
+    for (int64_t e = gofs[t]; e < gofs[t + 1]; ++e) v += S.ploc[glist[e] + S.npl * r];
+    double* dst = t < nslot_r ? P.jr : P.jp;
+    dst[gbase[t] + (int64_t)gstride[t] * r] = v;
   }
 }
 
@@ -1012,6 +1026,7 @@ static ieti_status grow(Ctx* c, T** p, int64_t* cap, int64_t n) {
 // fits in shared memory; *done = false leaves them to the element quadrature
 static ieti_status sep_loads(Ctx* c, const AsmParams& P, bool* done, cudaStream_t st) {
   *done = false;
+  if (!c->d_sep_gofs) return IETI_OK;
   const Mesh& m = c->mesh;
   const int nr = c->nrhs, np = m.npatch();
   int NF = 0, KG = 0, kind = 1, per_patch = 0;
@@ -1107,6 +1122,7 @@ static ieti_status sep_loads(Ctx* c, const AsmParams& P, bool* done, cudaStream_
                                 cudaMemcpyHostToDevice));
   }
   if ((rs = grow(c, &c->d_sep_C, &c->sep_C_cap, (int64_t)C.size())) != IETI_OK) return rs;
+  if ((rs = grow(c, &c->d_sep_ploc, &c->sep_ploc_cap, c->sep_npl * nr)) != IETI_OK) return rs;
   const int64_t ntab = (int64_t)3 * Pmax * 2 * maxfun * NF;
   if ((rs = grow(c, &c->d_sep_tab, &c->sep_tab_cap, ntab)) != IETI_OK) return rs;
   IETI_CUDA_TRY(c, cudaMemcpyAsync(c->d_sep_C, C.data(), sizeof(double2) * C.size(), cudaMemcpyHostToDevice, st));
@@ -1121,10 +1137,16 @@ static ieti_status sep_loads(Ctx* c, const AsmParams& P, bool* done, cudaStream_
   S.xq = c->d_xq;
   S.tab = c->d_sep_tab;
   S.C = c->d_sep_C;
+  S.ploc = c->d_sep_ploc;
+  S.npl = c->sep_npl;
   cudaEvent_t p0 = prof_begin(c, st);
   k_sep_tab<<<(unsigned)std::min<int64_t>(ceil_div(ntab, 256), 4096), 256, 0, st>>>(P, S);
   IETI_LAUNCH_CHECK(c);
   k_sep_load<<<dim3((unsigned)np, 3, (unsigned)nr), 256, smem, st>>>(P, S);
+  IETI_LAUNCH_CHECK(c);
+  k_sep_gather<<<dim3((unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(c->sep_nslot, 1), 256), 1184),
+                      (unsigned)nr), 256, 0, st>>>(P, S, c->d_sep_gofs, c->d_sep_glist, c->d_sep_gbase,
+                                                   c->d_sep_gstride, c->sep_nslot, c->tot_rv);
   IETI_LAUNCH_CHECK(c);
   prof_end(c, PROF_ASM_J, p0, st);
   *done = true;

@@ -153,6 +153,15 @@ struct Ctx {
   int64_t sep_tab_cap = 0;
   double* d_sep_geo = nullptr;           // per axis and slab: lower coordinate, length
   double* d_xq = nullptr;                // Gauss points on [0, 1]
+  double* d_sep_ploc = nullptr;          // per patch-local edge and load case: its patch's load
+  int64_t sep_ploc_cap = 0;
+  // deterministic sums of the patch loads: per local DOF slot (r DOFs of all
+  // subdomains, then p DOFs) the patch-local edges that carry it, in order
+  int64_t* d_sep_gofs = nullptr;         // slots + 1 offsets into d_sep_glist
+  int64_t* d_sep_glist = nullptr;
+  int64_t* d_sep_gbase = nullptr;        // per slot: destination of load case 0 in jr (r slots) or jp
+  int32_t* d_sep_gstride = nullptr;      // per slot: column stride of the destination
+  int64_t sep_nslot = 0, sep_npl = 0;    // slots, patch-local edges
   bool geo_ready = false, geo_failed = false;
   int64_t* d_patch_eoff = nullptr;       // per patch: its first element (npatch + 1 entries)
   double* d_flux_part = nullptr;         // flux evaluation: per element and load case, 2 integrals
