@@ -319,6 +319,7 @@ __global__ void __launch_bounds__(256) k_syrk(const SubDev* sd, T* L, int b, con
 // update covers block column b+kb alone (one tile column, blockIdx.x = R).
 constexpr int S2_LDS = 128 + 4;
 constexpr int S2_SMEM = 2 * NB * S2_LDS * 4;
+constexpr int S2_THREADS = 128;   // 8 x 16 outputs per thread
 
 // 16-byte global -> shared copy that bypasses registers; valid == false
 // writes zeros (no bytes are read from src)
@@ -341,15 +342,17 @@ __device__ __forceinline__ void syrk2_tile(const SubDev& s, float* L, int b, int
   const int nr = min(2, s.nblk - r0), nc = col_only ? 1 : min(2, s.nblk - c0);   // blocks present (1 or 2)
   const int tid = threadIdx.x;
   const int64_t n = s.n;
-  const int ti = tid % 16, tj = tid / 16;   // rows 8 ti .. 8 ti + 7, columns 8 tj .. 8 tj + 7
-  const int rb = r0 + (8 * ti) / NB, cb = c0 + (8 * tj) / NB;
-  const bool writes = (8 * ti) / NB < nr && (8 * tj) / NB < nc && rb >= cb;
-  float* Out = L + s.A + (int64_t)r0 * NB + 8 * ti + n * ((int64_t)c0 * NB + 8 * tj);
-  float acc[8][8];
+  // rows 8 ti .. 8 ti + 7, columns 16 tj .. 16 tj + 15: 8 x 16 outputs per
+  // thread, so that each operand loaded from shared memory feeds more products
+  const int ti = tid % 16, tj = tid / 16;
+  const int rb = r0 + (8 * ti) / NB, cb = c0 + (16 * tj) / NB;
+  const bool writes = (8 * ti) / NB < nr && (16 * tj) / NB < nc && rb >= cb;
+  float* Out = L + s.A + (int64_t)r0 * NB + 8 * ti + n * ((int64_t)c0 * NB + 16 * tj);
+  float acc[8][16];
 #pragma unroll
   for (int u = 0; u < 8; ++u)
 #pragma unroll
-    for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
+    for (int v = 0; v < 16; ++v) acc[u][v] = 0.f;
   // the panels in pieces of S2_K columns, double buffered: the copies of piece
   // h + 1 are in flight while piece h is multiplied (two buffers of the row and
   // column panels, transposed, in the same shared memory as one 64-wide chunk)
@@ -361,8 +364,8 @@ __device__ __forceinline__ void syrk2_tile(const SubDev& s, float* L, int b, int
     // 4 consecutive rows per 16-byte asynchronous copy (zero filled past the
     // blocks present)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int x = tid + 256 * q;                  // 1024 vectors of 4 rows: i4 = x % 32, l = x / 32
+    for (int q = 0; q < 1024 / S2_THREADS; ++q) {
+      const int x = tid + S2_THREADS * q;           // 1024 vectors of 4 rows: i4 = x % 32, l = x / 32
       const int i = 4 * (x % 32), l = x / 32;
       const bool vr = i < nr * NB, vc = i < nc * NB;
       cp_async16(&Pr[l][i], vr ? P + (int64_t)r0 * NB + i + n * l : P, vr);
@@ -387,40 +390,48 @@ __device__ __forceinline__ void syrk2_tile(const SubDev& s, float* L, int b, int
     for (int l = 0; l < S2_K; ++l) {
       const float4 x0 = *reinterpret_cast<const float4*>(&Pr[l][8 * ti]);
       const float4 x1 = *reinterpret_cast<const float4*>(&Pr[l][8 * ti + 4]);
-      const float4 y0 = *reinterpret_cast<const float4*>(&Pc[l][8 * tj]);
-      const float4 y1 = *reinterpret_cast<const float4*>(&Pc[l][8 * tj + 4]);
+      const float4 y0 = *reinterpret_cast<const float4*>(&Pc[l][16 * tj]);
+      const float4 y1 = *reinterpret_cast<const float4*>(&Pc[l][16 * tj + 4]);
+      const float4 y2 = *reinterpret_cast<const float4*>(&Pc[l][16 * tj + 8]);
+      const float4 y3 = *reinterpret_cast<const float4*>(&Pc[l][16 * tj + 12]);
       const float x[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-      const float y[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+      const float y[16] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w,
+                           y2.x, y2.y, y2.z, y2.w, y3.x, y3.y, y3.z, y3.w};
 #pragma unroll
       for (int u = 0; u < 8; ++u)
 #pragma unroll
-        for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(x[u], y[v], acc[u][v]);
+        for (int v = 0; v < 16; ++v) acc[u][v] = fmaf(x[u], y[v], acc[u][v]);
     }
     __syncthreads();   // every thread is done with buffer h & 1 before piece h + 2 is copied into it
   }
   if (!writes) return;   // beyond the trailing matrix or above the block diagonal
-  float4 cv[16];         // all loads of the C tile in flight together
+  // the C tile in two halves of 8 columns, each half's loads in flight together
 #pragma unroll
-  for (int v = 0; v < 8; ++v) {
-    const float4* o = reinterpret_cast<const float4*>(Out + n * v);
-    cv[2 * v] = o[0];
-    cv[2 * v + 1] = o[1];
-  }
+  for (int hh = 0; hh < 2; ++hh) {
+    float4 cv[16];
 #pragma unroll
-  for (int v = 0; v < 8; ++v) {
-    float4* o = reinterpret_cast<float4*>(Out + n * v);
-    float4 a = cv[2 * v], c = cv[2 * v + 1];
-    a.x -= acc[0][v]; a.y -= acc[1][v]; a.z -= acc[2][v]; a.w -= acc[3][v];
-    c.x -= acc[4][v]; c.y -= acc[5][v]; c.z -= acc[6][v]; c.w -= acc[7][v];
-    o[0] = a;
-    o[1] = c;
+    for (int v = 0; v < 8; ++v) {
+      const float4* o = reinterpret_cast<const float4*>(Out + n * (8 * hh + v));
+      cv[2 * v] = o[0];
+      cv[2 * v + 1] = o[1];
+    }
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      float4* o = reinterpret_cast<float4*>(Out + n * (8 * hh + v));
+      float4 a = cv[2 * v], c = cv[2 * v + 1];
+      const int w = 8 * hh + v;
+      a.x -= acc[0][w]; a.y -= acc[1][w]; a.z -= acc[2][w]; a.w -= acc[3][w];
+      c.x -= acc[4][w]; c.y -= acc[5][w]; c.z -= acc[6][w]; c.w -= acc[7][w];
+      o[0] = a;
+      o[1] = c;
+    }
   }
 }
 
 // items: (subdomain, R, C) of the nitems pair tiles to update, each CTA taking
 // every gridDim.x-th (a grid smaller than nitems leaves SMs to other kernels);
 // without items every pair tile, one per CTA (subdomain blockIdx.y)
-__global__ void __launch_bounds__(256, 2) k_syrk2(const SubDev* sd, float* L, int b, int kb, int col_only,
+__global__ void __launch_bounds__(S2_THREADS, 2) k_syrk2(const SubDev* sd, float* L, int b, int kb, int col_only,
                                                  const int4* items, int nitems) {
   extern __shared__ __align__(16) float s2[];
   if (items) {
@@ -892,11 +903,11 @@ static ieti_status cholesky(Ctx* c, const SubDev* d_sd, const std::vector<SubDev
         cudaEvent_t p0 = prof_begin(c, st);
         if (plan) {
           if (stp.col_cnt > 0)
-            k_syrk2<<<stp.col_cnt, 256, S2_SMEM, st>>>(d_sd, (float*)L, b, 1, 1, plan->d_items + stp.col_off,
+            k_syrk2<<<stp.col_cnt, S2_THREADS, S2_SMEM, st>>>(d_sd, (float*)L, b, 1, 1, plan->d_items + stp.col_off,
                                                          stp.col_cnt);
         } else {
           const int Tp1 = (max_nblk - b - 1 + 1) / 2;
-          k_syrk2<<<dim3(Tp1, nsub), 256, S2_SMEM, st>>>(d_sd, (float*)L, b, 1, 1, nullptr, 0);
+          k_syrk2<<<dim3(Tp1, nsub), S2_THREADS, S2_SMEM, st>>>(d_sd, (float*)L, b, 1, 1, nullptr, 0);
         }
         prof_end(c, PROF_SYRK, p0, st);
         IETI_LAUNCH_CHECK(c);
@@ -911,7 +922,7 @@ static ieti_status cholesky(Ctx* c, const SubDev* d_sd, const std::vector<SubDev
       const int n0 = stp.trail_cnt0, n1 = stp.trail_cnt - stp.trail_cnt0;
       cudaEvent_t p0 = prof_begin(c, st);
       if (n0 > 0) {
-        if constexpr (sizeof(T) == 4) k_syrk2<<<n0, 256, S2_SMEM, st>>>(d_sd, (float*)L, b, kb, 0, items, n0);
+        if constexpr (sizeof(T) == 4) k_syrk2<<<n0, S2_THREADS, S2_SMEM, st>>>(d_sd, (float*)L, b, kb, 0, items, n0);
         else k_syrk<T><<<n0, 256, 0, st>>>(d_sd, L, b, items);
         IETI_LAUNCH_CHECK(c);
       }
@@ -924,7 +935,7 @@ static ieti_status cholesky(Ctx* c, const SubDev* d_sd, const std::vector<SubDev
         // next panels' kernels: at two CTAs per SM this kernel holds the whole
         // register file of an SM, so a full grid keeps them waiting for SMs
         if constexpr (sizeof(T) == 4)
-          k_syrk2<<<std::min(n1, 2 * std::max(1, c->sm_count - c->syrk_reserve)), 256, S2_SMEM, c->aux_stream>>>(
+          k_syrk2<<<std::min(n1, 2 * std::max(1, c->sm_count - c->syrk_reserve)), S2_THREADS, S2_SMEM, c->aux_stream>>>(
               d_sd, (float*)L, b, kb, 0, items + n0, n1);
         else k_syrk<T><<<n1, 256, 0, c->aux_stream>>>(d_sd, L, b, items + n0);
         prof_end(c, PROF_SYRK, p1, c->aux_stream);
@@ -943,10 +954,10 @@ static ieti_status cholesky(Ctx* c, const SubDev* d_sd, const std::vector<SubDev
           ieti_status r2 = syrk_tc(c, d_sd, (float*)L, b, max_nblk, nsub, st);
           if (r2 != IETI_OK) return r2;
         } else if (plan) {
-          k_syrk2<<<stp.trail_cnt, 256, S2_SMEM, st>>>(d_sd, (float*)L, b, kb, 0, items, stp.trail_cnt);
+          k_syrk2<<<stp.trail_cnt, S2_THREADS, S2_SMEM, st>>>(d_sd, (float*)L, b, kb, 0, items, stp.trail_cnt);
         } else {
           const int Tp = (Tm + 1) / 2;   // block pairs
-          k_syrk2<<<dim3(Tp * (Tp + 1) / 2, nsub), 256, S2_SMEM, st>>>(d_sd, (float*)L, b, kb, 0, nullptr, 0);
+          k_syrk2<<<dim3(Tp * (Tp + 1) / 2, nsub), S2_THREADS, S2_SMEM, st>>>(d_sd, (float*)L, b, kb, 0, nullptr, 0);
         }
       } else {
         if (plan) k_syrk<T><<<stp.trail_cnt, 256, 0, st>>>(d_sd, L, b, items);
