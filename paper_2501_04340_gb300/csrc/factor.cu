@@ -205,6 +205,16 @@ __global__ void __launch_bounds__(256) k_potrf_diag(const SubDev* sd, T* L, T* L
   }
 }
 
+// four consecutive entries of a shared-memory row (16-byte aligned)
+__device__ __forceinline__ void lds4(const float* p, float v[4]) {
+  const float4 w = *reinterpret_cast<const float4*>(p);
+  v[0] = w.x; v[1] = w.y; v[2] = w.z; v[3] = w.w;
+}
+__device__ __forceinline__ void lds4(const double* p, double v[4]) {
+  const double2 w0 = *reinterpret_cast<const double2*>(p), w1 = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = w0.x; v[1] = w0.y; v[2] = w1.x; v[3] = w1.y;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_trsm_panel(const SubDev* sd, T* L, const T* Linv, int b,
                                                     const int2* items) {
@@ -213,29 +223,42 @@ __global__ void __launch_bounds__(256) k_trsm_panel(const SubDev* sd, T* L, cons
   const int r = items ? items[blockIdx.x].y : b + 1 + (int)blockIdx.x;
   const SubDev s = sd[k];
   if (r >= s.nblk) return;
-  __shared__ T A[NB][NB + 1];
-  __shared__ T Li[NB][NB + 1];
+  // the tile and the inverse of the diagonal block, both transposed in shared
+  // memory (rows of 64 + 4 entries, 16-byte aligned), so that a thread reads
+  // its four rows and its four columns with one vector load each
+  constexpr int LD = NB + 4;
+  __shared__ __align__(16) T At[NB][LD];    // At[l][i] = A[i][l]
+  __shared__ __align__(16) T LiT[NB][LD];   // LiT[l][j] = Linv[j][l]
   const int tid = threadIdx.x;
   T* Ab = L + s.A + (int64_t)r * NB + (int64_t)s.n * b * NB;
   const T* Lb = Linv + s.linv + (int64_t)b * NB * NB;
   for (int t = tid; t < NB * NB; t += blockDim.x) {
-    int i = t % NB, j = t / NB;
-    A[i][j] = Ab[i + (int64_t)s.n * j];
-    Li[i][j] = Lb[i + NB * j];
+    const int i = t % NB, l = t / NB;
+    At[l][i] = Ab[i + (int64_t)s.n * l];
+    LiT[l][i] = Lb[i + NB * l];
   }
   __syncthreads();
-  // X = A Linv^T: X[i][j] = sum_{l <= j} A[i][l] Linv[j][l]
-  const int i = tid % NB, jg = tid / NB;   // 4 groups of 16 columns
-  T acc[16];
+  // X = A Linv^T: X[i][j] = sum_l A[i][l] Linv[j][l]; rows 4 ti .., columns 4 tj ..
+  const int ti = tid % 16, tj = tid / 16;
+  T acc[4][4];
 #pragma unroll
-  for (int u = 0; u < 16; ++u) acc[u] = 0;
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0;
+#pragma unroll 8
   for (int l = 0; l < NB; ++l) {
-    T av = A[i][l];
+    T a[4], y[4];
+    lds4(&At[l][4 * ti], a);
+    lds4(&LiT[l][4 * tj], y);
 #pragma unroll
-    for (int u = 0; u < 16; ++u) acc[u] += av * Li[jg * 16 + u][l];
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * y[v];
   }
 #pragma unroll
-  for (int u = 0; u < 16; ++u) Ab[i + (int64_t)s.n * (jg * 16 + u)] = acc[u];
+  for (int v = 0; v < 4; ++v)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) Ab[4 * ti + u + (int64_t)s.n * (4 * tj + v)] = acc[u][v];
 }
 
 template <typename T>
