@@ -114,7 +114,9 @@ def allmax(world, x):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    # NCCL reduces device tensors, gloo host tensors
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -517,10 +519,9 @@ def reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
-        return
-    vals = []
-    for _ in range(args.warmup):
-        pass   # the oracle has no warm-up state; keep the run bounded
+        return   # the oracle runs on rank 0 alone; the other ranks exit without work
+    # (the oracle keeps no state between calls: the warm-up steps are not run,
+    # which keeps the run bounded)
     t0 = time.perf_counter()
     samples = []
     for _ in range(args.steps):
