@@ -198,3 +198,33 @@ def test_rejects_source_parameters_that_do_not_fit_the_kind():
     for prob in bad:
         with pytest.raises(ieti.IetiError, match="INVALID_ARG"):
             ieti.ieti_create_host(prob)
+
+
+@pytest.mark.parametrize("make", [lambda: wl.paper_cube(2, 2), lambda: wl.paper_cube(1, 2, nsub=5, layout="snake"),
+                                  lambda: wl.paper_cube(3, 1, nsub=12, layout="snake")])
+def test_host_gauge_equals_oracle_on_the_paper_cube(make):
+    """The 27-patch cube of Sec. 3 with the layouts of the experiments: the same
+    tree, primal and dual sets on the host as in the oracle."""
+    prob = make()
+    topo = tp.build_topology(prob)
+    ctx = ieti.ieti_create_host(prob)
+    try:
+        assert np.array_equal(ieti.ieti_get_dofmap(ctx, 0).astype(bool), topo.tree)
+        assert np.array_equal(ieti.ieti_get_dofmap(ctx, 2), topo.primal_edges)
+        assert np.array_equal(ieti.ieti_get_dofmap(ctx, 3), topo.dual_edges)
+    finally:
+        ieti.ieti_destroy(ctx)
+
+
+def test_coarse_size_of_the_three_columns_does_not_depend_on_h_and_p():
+    """Sec. 3, Experiment 1: one interior line of patch edges is shared by the
+    three subdomains; all of its edges but one join the tree, so n_gp = 1 for
+    every mesh size and degree (and 0 for three slabs, which share no line)."""
+    for p in (1, 2, 3):
+        for n in (1, 2, 3):
+            for layout, want in (("columns", 1), ("snake", 0)):
+                ctx = ieti.ieti_create_host(wl.paper_cube(p, n, layout=layout))
+                try:
+                    assert ieti.ieti_query(ctx)["n_gp"] == want, (p, n, layout)
+                finally:
+                    ieti.ieti_destroy(ctx)
